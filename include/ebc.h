@@ -1,0 +1,178 @@
+/*
+ * ebc.h -- C ABI of the GB300 exemplar-based clustering (EBC) library.
+ *
+ * What is computed (paper: "Providing Meaningful Data Summarizations Using
+ * Exemplar-based Clustering in Industry 4.0"):
+ *
+ *   d(x, y) = ||x - y||^2                         squared Euclidean (Sec. 5)
+ *   L(S)    = (1/|V|) sum_{v in V} min_{s in S} d(v, s)   k-medoids loss (Sec. 4)
+ *   f(S)    = L({e0}) - L(S u {e0}),  e0 = 0      EBC function (Sec. 4)
+ *           = (1/n) sum_v max(0, ||v||^2 - min_{s in S} d(v, s))
+ *   Delta_f(c | S) = f(S u {c}) - f(S)            discrete derivative (Sec. 3, Def. 1)
+ *                  = (1/n) sum_v max(0, m_v - d(v, c)),  m_v = min_{s in S u {e0}} d(v, s)
+ *
+ * A handle owns one ground set V (n points of dimension d) resident on the
+ * GPU, its norms, quantised copies and the Greedy state (S, m_v, f).  Every
+ * call is enqueued on the handle's CUDA stream.  Nothing here falls back to
+ * the CPU: a handle can only be created on an sm_103 device.
+ *
+ * Conventions for every function below:
+ *   - Indices are 0-based int32 in [0, n).
+ *   - "device pointer" arguments must point to device memory that stays
+ *     valid until the stream reaches the call; the caller owns them.
+ *     "_host" variants take ordinary host pointers and return after the
+ *     results are in host memory (they synchronise the stream).
+ *   - Calls on one handle must not run concurrently from several host
+ *     threads.  Different handles are independent.
+ *   - On failure a negative ebc_status is returned and ebc_last_error(h)
+ *     holds a one-line description.  Errors that only the device can detect
+ *     (an out-of-range index inside a device CSR list) are recorded in the
+ *     handle and returned by the next ebc_sync().
+ */
+#ifndef EBC_H
+#define EBC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ebc_ctx *ebc_t;
+
+typedef enum {
+    EBC_OK = 0,
+    EBC_EINVAL = -1,   /* bad argument: sizes, NULL pointers, non-monotone CSR offsets,
+                          k larger than the unselected points, non-finite V */
+    EBC_EINDEX = -2,   /* an index outside [0, n) */
+    EBC_ENOMEM = -3,   /* a device or host allocation failed */
+    EBC_ECUDA = -4,    /* a CUDA runtime call failed (text in ebc_last_error) */
+    EBC_ETIMEOUT = -5, /* a bounded device-side wait ran out */
+    EBC_EBUSY = -6,    /* resource temporarily unavailable */
+    EBC_ENODEV = -7    /* no sm_103 device is current */
+} ebc_status;
+
+/* Arithmetic used for the bulk distance work (Sec. 5 compares FP32 with
+ * half precision; here the low-precision paths run on tcgen05 tensor cores
+ * with FP32 accumulation and exact FP64 re-evaluation of the leaders). */
+typedef enum {
+    EBC_FP32 = 0,    /* direct (v - c)^2 in FP32 on the CUDA cores */
+    EBC_BF16 = 1,    /* V.C^T in BF16 on tensor cores, FP32 accumulate */
+    EBC_FP16 = 2,    /* V.C^T in FP16 on tensor cores, FP32 accumulate */
+    EBC_FP8E4M3 = 3  /* V.C^T in FP8 e4m3 with a per-row FP32 scale */
+} ebc_prec;
+
+/* Counters of the certified Greedy pick (see ebc_greedy). */
+typedef struct {
+    int64_t rounds;               /* Greedy rounds run since create / reset */
+    int64_t certified_rounds;     /* rounds decided by the top-K exact re-evaluation alone */
+    int64_t escalated_rounds;     /* rounds that exactly re-evaluated further candidates */
+    int64_t escalated_candidates; /* total such extra candidates */
+    double max_raw_rel_err;       /* max |bulk - exact| / exact over re-evaluated leaders,
+                                     bulk = the upper-bound gain of the bulk kernel */
+    int32_t prec;                 /* current ebc_prec */
+    int32_t refine_k;             /* current K */
+} ebc_stats;
+
+/* Library version, (major << 16) | minor. */
+int32_t ebc_version(void);
+
+/*
+ * Create a handle for the ground set V (Sec. 4.2 "Memory Layout": V is copied
+ * to the GPU once at initialisation and stays resident).
+ *   V            n x d FP32, row-major (point i is V[i*d .. i*d+d-1]).
+ *   v_on_device  0: V is a host pointer; 1: V is a device pointer.
+ *   stream       cudaStream_t to enqueue on (NULL = the legacy default stream).
+ *   out          receives the handle.
+ * The library copies V; the caller may free it when this returns.  The
+ * prologue computes ||v||^2 (= d(v, e0)), L({e0}) (computed once and shared,
+ * Sec. 4.2 "Algorithm"), the quantised copies and m_v = ||v||^2 (S = {}).
+ * Synchronises the stream once.  EINVAL for n <= 0, d <= 0, d > 4096 or a
+ * non-finite entry of V; ENODEV when the current device is not sm_103.
+ */
+ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device, void *stream, ebc_t *out);
+
+/* Release every resource of the handle (NULL is accepted). */
+ebc_status ebc_destroy(ebc_t h);
+
+/* Change the stream later calls are enqueued on. */
+ebc_status ebc_set_stream(ebc_t h, void *stream);
+
+/*
+ * Select the bulk arithmetic and K, the number of leading candidates that
+ * Greedy re-evaluates exactly each round (1 <= K <= 32; default FP32, K = 8).
+ * EINVAL for an unsupported precision or K outside [1, 32].
+ */
+ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k);
+
+/*
+ * f(S_j) for a list of l sets (the multi-set S_multi = {S_1..S_l} of
+ * Sec. 4.1, evaluated as the work matrix W and its row sums W.1 of
+ * Sec. 4.2, Eq. "work matrix"; W is never materialised).
+ *   csr_idx  device int32[csr_off[l]]: members of set j are
+ *            csr_idx[csr_off[j] .. csr_off[j+1]-1]; duplicates allowed.
+ *   csr_off  device int64[l+1], csr_off[0] = 0, non-decreasing.
+ *   out_f    device double[l]; an empty set gives 0.
+ * Independent of the Greedy state.  With EBC_FP32 the distances are direct
+ * FP32; with a tensor-core precision the minimum per set is formed from
+ * V.S^T products.  Out-of-range members are detected on the device: the set
+ * is evaluated without them and ebc_sync() returns EINDEX.  l = 0 is OK.
+ */
+ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off, int64_t l, double *out_f);
+
+/* Host-pointer form of ebc_eval_sets; validates offsets and indices on the host. */
+ebc_status ebc_eval_sets_host(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off, int64_t l, double *out_f);
+
+/*
+ * Marginal gains Delta_f(c | S) (Sec. 3, Def. 1) for m candidates, relative
+ * to the handle's current Greedy state S (S = {} after create / reset).
+ *   cand_idx  device int32[m], or NULL for all n points (then m must be n).
+ *   out_gain  device double[m].  Candidates already in S get 0.
+ * EBC_FP32 gives direct-FP32 distances with FP64 sums over V; tensor-core
+ * precisions give the raw low-precision gain (no re-evaluation).
+ */
+ebc_status ebc_gains(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_gain);
+
+/* Host-pointer form of ebc_gains. */
+ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_gain);
+
+/*
+ * k rounds of Greedy (Sec. 3; the step is described in Sec. 4.1): each round
+ * adds the not-yet-selected point of largest marginal gain, ties to the
+ * smallest index, continuing from the handle's current state.
+ *   out_idx  device int32[k]: the picks in order.
+ *   out_f    device double[k]: out_f[t] = f(S) after pick t (cumulative).
+ * Each round evaluates the gain of every unselected point with the bulk
+ * precision as a rigorous upper bound, re-evaluates the K largest exactly
+ * (direct FP64 distances, FP64 sums) and certifies the pick: if the best
+ * exact gain is below the (K+1)-th upper bound, every candidate whose bound
+ * reaches it is re-evaluated exactly as well.  The pick is therefore the
+ * exact argmax up to FP64 rounding, at every precision.
+ * EINVAL when k < 0 or k exceeds the number of unselected points.
+ */
+ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);
+
+/* Host-pointer form of ebc_greedy. */
+ebc_status ebc_greedy_host(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);
+
+/* Return the Greedy state to S = {} (m_v = ||v||^2, f = 0, counters zeroed). */
+ebc_status ebc_reset(ebc_t h);
+
+/* Wait for the handle's stream; returns the first device-detected error. */
+ebc_status ebc_sync(ebc_t h);
+
+/* Certification counters (synchronises the stream). */
+ebc_status ebc_get_stats(ebc_t h, ebc_stats *out);
+
+/* f(S) of the current Greedy state, computed on the device (synchronises). */
+ebc_status ebc_current_f(ebc_t h, double *out_f);
+
+/* Text of the last error on this handle ("" if none); h may be NULL for
+ * errors from ebc_create.  The pointer stays valid until the next call. */
+const char *ebc_last_error(ebc_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EBC_H */

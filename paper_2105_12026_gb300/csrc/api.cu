@@ -1,0 +1,446 @@
+// C ABI of the library (include/ebc.h): handle life cycle, argument checks,
+// and the per-round orchestration of Greedy.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "ebc_internal.cuh"
+
+struct ebc_ctx {
+    ebc::Ctx c;
+    int64_t nsel = 0;       // points picked since create / reset (host mirror)
+    int64_t ch = 0;         // bulk-gains V chunk (points)
+    int nch = 0;            // number of bulk-gains chunks
+    int64_t ref_ch = 0;     // refine V chunk
+    int nref = 0;           // number of refine chunks
+    int nblk = 0;           // select blocks
+    double *esc_part = nullptr;
+    double *d_scalar = nullptr;  // one device double for ebc_current_f
+    int *d_bad = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int32_t kMaxD = 4096;
+
+ebc_status fail(ebc_t h, ebc_status s, const std::string &msg) {
+    if (h)
+        h->c.last_error = msg;
+    else
+        g_create_error = msg;
+    return s;
+}
+
+ebc_status cuda_fail(ebc_t h, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? EBC_ENOMEM : EBC_ECUDA, m);
+}
+
+#define CK(h, expr)                                   \
+    do {                                              \
+        cudaError_t _e = (expr);                      \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, #expr); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+void free_all(ebc::Ctx &c, ebc_ctx *h) {
+    void *ptrs[] = {c.V32, c.nv64, c.nv32, c.m64, c.sel, c.st, c.Vq, c.qscale, c.qnorm2, c.qerr, c.qnorm,
+                    c.a32, c.b32, c.partial, c.gain_up, c.blk_idx, c.blk_val, c.top_idx, c.top_val,
+                    c.top_exact, c.esc_idx, c.esc_exact, c.ref_part, c.cand_buf, c.set_part,
+                    h ? h->esc_part : nullptr, h ? h->d_scalar : nullptr, h ? h->d_bad : nullptr};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c.h_err) cudaFreeHost(c.h_err);
+}
+
+double bulk_eta(const ebc::Ctx &c) {
+    (void)c;
+    // each bulk partial is a sum of at most 128 non-negative FP32 terms,
+    // each term one rounding from its bound: relative error <= 130 * 2^-24
+    return 131.0 * ldexp(1.0, -24) + 1e-12;
+}
+
+__global__ void k_sanitize(const int32_t *__restrict__ in, int64_t m, int64_t n, int32_t *__restrict__ out,
+                           ebc::DevState *st) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    int x = in ? in[j] : (int)j;
+    if (x < 0 || (int64_t)x >= n) {
+        atomicCAS(&st->err, 0, (int)EBC_EINDEX);
+        x = -1;
+    }
+    out[j] = x;
+}
+
+__global__ void k_zero_masked(const int32_t *__restrict__ cand, int64_t m, double *__restrict__ out) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < m && cand[j] < 0) out[j] = 0.0;
+}
+
+__global__ void k_check_csr(const int64_t *__restrict__ off, int64_t l, ebc::DevState *st, int *bad) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j == 0 && off[0] != 0) {
+        atomicCAS(&st->err, 0, (int)EBC_EINVAL);
+        atomicExch(bad, 1);
+    }
+    if (j < l && off[j + 1] < off[j]) {
+        atomicCAS(&st->err, 0, (int)EBC_EINVAL);
+        atomicExch(bad, 1);
+    }
+}
+
+__global__ void k_fill_zero(double *p, int64_t n) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < n) p[j] = 0.0;
+}
+
+ebc_status check_handle(ebc_t h) {
+    if (!h) return EBC_EINVAL;
+    return EBC_OK;
+}
+
+ebc_status ensure_set_part(ebc_t h, int64_t want) {
+    ebc::Ctx &c = h->c;
+    if (c.set_part_cap >= want) return EBC_OK;
+    if (c.set_part) cudaFree(c.set_part);
+    c.set_part = nullptr;
+    c.set_part_cap = 0;
+    CK(h, dalloc(&c.set_part, (size_t)want));
+    c.set_part_cap = want;
+    return EBC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t ebc_version(void) { return (0 << 16) | 1; }
+
+const char *ebc_last_error(ebc_t h) { return h ? h->c.last_error.c_str() : g_create_error.c_str(); }
+
+ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device, void *stream, ebc_t *out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, EBC_EINVAL, "ebc_create: out is NULL");
+    *out = nullptr;
+    if (!V) return fail(nullptr, EBC_EINVAL, "ebc_create: V is NULL");
+    if (n <= 0) return fail(nullptr, EBC_EINVAL, "ebc_create: n must be > 0");
+    if (n > (int64_t)INT32_MAX - 1) return fail(nullptr, EBC_EINVAL, "ebc_create: n exceeds int32 indexing");
+    if (d <= 0 || d > kMaxD) return fail(nullptr, EBC_EINVAL, "ebc_create: d must be in [1, 4096]");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, EBC_ENODEV, std::string("ebc_create: ") + cudaGetErrorString(e));
+    int maj = 0, min = 0;
+    cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, dev);
+    if (!(maj == 10 && min == 3)) {
+        char b[128];
+        snprintf(b, sizeof b, "ebc_create: device %d is sm_%d%d; this library is built for sm_103a only", dev, maj,
+                 min);
+        return fail(nullptr, EBC_ENODEV, b);
+    }
+    ebc_ctx *h = new (std::nothrow) ebc_ctx();
+    if (!h) return fail(nullptr, EBC_ENOMEM, "ebc_create: host allocation failed");
+    ebc::Ctx &c = h->c;
+    c.n = n;
+    c.d = d;
+    c.dpad = (d + 63) / 64 * 64;
+    c.device = dev;
+    c.stream = (cudaStream_t)stream;
+
+    // chunking of the V axis
+    h->ch = std::max<int64_t>(4096, ((n + 63) / 64 + 127) / 128 * 128);
+    h->nch = (int)((n + h->ch - 1) / h->ch);
+    h->ref_ch = std::max<int64_t>(8192, ((n + 31) / 32 + 255) / 256 * 256);
+    h->nref = (int)((n + h->ref_ch - 1) / h->ref_ch);
+    h->nblk = (int)std::min<int64_t>(512, std::max<int64_t>(1, (n + 2047) / 2048));
+
+    auto bail = [&](ebc_status s, const std::string &m) {
+        free_all(c, h);
+        delete h;
+        return fail(nullptr, s, m);
+    };
+#define CKC(expr)                                                                                  \
+    do {                                                                                           \
+        cudaError_t _e = (expr);                                                                   \
+        if (_e != cudaSuccess)                                                                     \
+            return bail(_e == cudaErrorMemoryAllocation ? EBC_ENOMEM : EBC_ECUDA,                  \
+                        std::string("ebc_create: ") + #expr + ": " + cudaGetErrorString(_e));     \
+    } while (0)
+    CKC(dalloc(&c.V32, (size_t)n * d));
+    CKC(dalloc(&c.nv64, n));
+    CKC(dalloc(&c.nv32, n));
+    CKC(dalloc(&c.m64, n));
+    CKC(dalloc(&c.sel, n));
+    CKC(dalloc(&c.st, 1));
+    c.partial_cap = (int64_t)h->nch * n;
+    CKC(dalloc(&c.partial, (size_t)c.partial_cap));
+    CKC(dalloc(&c.gain_up, n));
+    c.blk_cap = h->nblk * (ebc::kMaxRefineK + 1);
+    CKC(dalloc(&c.blk_idx, c.blk_cap));
+    CKC(dalloc(&c.blk_val, c.blk_cap));
+    CKC(dalloc(&c.top_idx, ebc::kMaxRefineK + 1));
+    CKC(dalloc(&c.top_val, ebc::kMaxRefineK + 1));
+    CKC(dalloc(&c.top_exact, ebc::kMaxRefineK));
+    CKC(dalloc(&c.esc_idx, n));
+    CKC(dalloc(&c.esc_exact, n));
+    c.ref_cap = (int64_t)ebc::kMaxRefineK * h->nref;
+    CKC(dalloc(&c.ref_part, (size_t)c.ref_cap));
+    CKC(dalloc(&h->esc_part, n));
+    CKC(dalloc(&c.cand_buf, n));
+    CKC(dalloc(&h->d_scalar, 1));
+    CKC(dalloc(&h->d_bad, 1));
+    CKC(cudaMallocHost((void **)&c.h_err, sizeof(int32_t) * 4));
+
+    CKC(cudaMemcpyAsync(c.V32, V, sizeof(float) * (size_t)n * d,
+                        v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream));
+    CKC(cudaMemsetAsync(h->d_bad, 0, sizeof(int), c.stream));
+    CKC(ebc::launch_reset_state(c));
+    CKC(ebc::launch_prologue(c, h->d_bad));
+    CKC(cudaMemcpyAsync(c.h_err, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    CKC(cudaStreamSynchronize(c.stream));
+    if (c.h_err[0]) return bail(EBC_EINVAL, "ebc_create: V has a non-finite entry");
+#undef CKC
+    *out = h;
+    return EBC_OK;
+}
+
+ebc_status ebc_destroy(ebc_t h) {
+    if (!h) return EBC_OK;
+    cudaStreamSynchronize(h->c.stream);
+    free_all(h->c, h);
+    delete h;
+    return EBC_OK;
+}
+
+ebc_status ebc_set_stream(ebc_t h, void *stream) {
+    if (check_handle(h)) return EBC_EINVAL;
+    h->c.stream = (cudaStream_t)stream;
+    return EBC_OK;
+}
+
+ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k) {
+    if (check_handle(h)) return EBC_EINVAL;
+    if (refine_k < 1 || refine_k > ebc::kMaxRefineK) return fail(h, EBC_EINVAL, "ebc_set_precision: K must be in [1, 32]");
+    if (prec != EBC_FP32) return fail(h, EBC_EINVAL, "ebc_set_precision: precision not available in this build");
+    h->c.prec = prec;
+    h->c.refine_k = refine_k;
+    return EBC_OK;
+}
+
+ebc_status ebc_reset(ebc_t h) {
+    if (check_handle(h)) return EBC_EINVAL;
+    CK(h, ebc::launch_reset_state(h->c));
+    h->nsel = 0;
+    return EBC_OK;
+}
+
+ebc_status ebc_sync(ebc_t h) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    CK(h, cudaMemcpyAsync(c.h_err, &c.st->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaStreamSynchronize(c.stream));
+    int err = c.h_err[0];
+    if (err) {
+        CK(h, cudaMemsetAsync(&c.st->err, 0, sizeof(int), c.stream));
+        CK(h, cudaStreamSynchronize(c.stream));
+        return fail(h, (ebc_status)err, err == EBC_EINDEX ? "device: index outside [0, n)" : "device: invalid argument");
+    }
+    return EBC_OK;
+}
+
+ebc_status ebc_get_stats(ebc_t h, ebc_stats *out) {
+    if (check_handle(h) || !out) return fail(h, EBC_EINVAL, "ebc_get_stats: NULL argument");
+    ebc::Ctx &c = h->c;
+    ebc::DevState s;
+    CK(h, cudaMemcpyAsync(&s, c.st, sizeof(s), cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaStreamSynchronize(c.stream));
+    out->rounds = s.rounds;
+    out->certified_rounds = s.certified;
+    out->escalated_rounds = s.escalated_rounds;
+    out->escalated_candidates = s.escalated_cands;
+    out->max_raw_rel_err = s.max_raw_rel_err;
+    out->prec = (int32_t)c.prec;
+    out->refine_k = c.refine_k;
+    return EBC_OK;
+}
+
+ebc_status ebc_current_f(ebc_t h, double *out_f) {
+    if (check_handle(h) || !out_f) return fail(h, EBC_EINVAL, "ebc_current_f: NULL argument");
+    ebc::Ctx &c = h->c;
+    CK(h, ebc::launch_current_f(c, h->d_scalar));
+    double v = 0;
+    CK(h, cudaMemcpyAsync(&v, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaStreamSynchronize(c.stream));
+    *out_f = v;
+    return EBC_OK;
+}
+
+ebc_status ebc_gains(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_gain) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (m < 0) return fail(h, EBC_EINVAL, "ebc_gains: m < 0");
+    if (!cand_idx && m != c.n) return fail(h, EBC_EINVAL, "ebc_gains: cand_idx NULL requires m == n");
+    if (m == 0) return EBC_OK;
+    if (!out_gain) return fail(h, EBC_EINVAL, "ebc_gains: out_gain is NULL");
+    // process in batches of at most n candidates (the partial buffer holds nch x n)
+    for (int64_t j0 = 0; j0 < m; j0 += c.n) {
+        int64_t mb = std::min<int64_t>(c.n, m - j0);
+        k_sanitize<<<(unsigned)((mb + 255) / 256), 256, 0, c.stream>>>(cand_idx ? cand_idx + j0 : nullptr, mb, c.n,
+                                                                       c.cand_buf, c.st);
+        CK(h, cudaGetLastError());
+        CK(h, ebc::launch_gains_fp32(c, c.cand_buf, mb, false, h->ch, h->nch));
+        CK(h, ebc::launch_reduce_select(c, mb, h->nch, c.cand_buf, false, out_gain + j0, h->nblk));
+        k_zero_masked<<<(unsigned)((mb + 255) / 256), 256, 0, c.stream>>>(c.cand_buf, mb, out_gain + j0);
+        CK(h, cudaGetLastError());
+    }
+    return EBC_OK;
+}
+
+ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_gain) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (m < 0 || (!cand_idx && m != c.n) || (m > 0 && !out_gain)) return fail(h, EBC_EINVAL, "ebc_gains_host: bad arguments");
+    if (m == 0) return EBC_OK;
+    if (cand_idx)
+        for (int64_t j = 0; j < m; ++j)
+            if (cand_idx[j] < 0 || (int64_t)cand_idx[j] >= c.n) return fail(h, EBC_EINDEX, "ebc_gains_host: index outside [0, n)");
+    int32_t *d_c = nullptr;
+    double *d_g = nullptr;
+    if (cand_idx) CK(h, dalloc(&d_c, m));
+    cudaError_t e = dalloc(&d_g, m);
+    if (e != cudaSuccess) {
+        if (d_c) cudaFree(d_c);
+        return cuda_fail(h, e, "ebc_gains_host: cudaMalloc");
+    }
+    ebc_status s = EBC_OK;
+    if (cand_idx) e = cudaMemcpyAsync(d_c, cand_idx, sizeof(int32_t) * m, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) s = ebc_gains(h, d_c, m, d_g);
+    if (e == cudaSuccess && s == EBC_OK)
+        e = cudaMemcpyAsync(out_gain, d_g, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess && s == EBC_OK) e = cudaStreamSynchronize(c.stream);
+    cudaFree(d_g);
+    if (d_c) cudaFree(d_c);
+    if (e != cudaSuccess) return cuda_fail(h, e, "ebc_gains_host");
+    if (s != EBC_OK) return s;
+    return ebc_sync(h);
+}
+
+ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off, int64_t l, double *out_f) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (l < 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: l < 0");
+    if (l == 0) return EBC_OK;
+    if (!csr_off || !out_f) return fail(h, EBC_EINVAL, "ebc_eval_sets: NULL argument");
+    CK(h, cudaMemsetAsync(h->d_bad, 0, sizeof(int), c.stream));
+    k_check_csr<<<(unsigned)((l + 255) / 256), 256, 0, c.stream>>>(csr_off, l, c.st, h->d_bad);
+    CK(h, cudaGetLastError());
+    int64_t ntiles = (c.n + 127) / 128;
+    int64_t want = std::min<int64_t>(ntiles * l, std::max<int64_t>(ntiles * 64, (int64_t)1 << 24));
+    ebc_status s = ensure_set_part(h, want);
+    if (s) return s;
+    CK(h, ebc::launch_eval_sets_fp32(c, csr_idx, csr_off, l, out_f, h->d_bad));
+    return EBC_OK;
+}
+
+ebc_status ebc_eval_sets_host(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off, int64_t l, double *out_f) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (l < 0 || (l > 0 && (!csr_off || !out_f))) return fail(h, EBC_EINVAL, "ebc_eval_sets_host: bad arguments");
+    if (l == 0) return EBC_OK;
+    if (csr_off[0] != 0) return fail(h, EBC_EINVAL, "ebc_eval_sets_host: csr_off[0] != 0");
+    for (int64_t j = 0; j < l; ++j)
+        if (csr_off[j + 1] < csr_off[j]) return fail(h, EBC_EINVAL, "ebc_eval_sets_host: offsets decrease");
+    int64_t nnz = csr_off[l];
+    if (nnz > 0 && !csr_idx) return fail(h, EBC_EINVAL, "ebc_eval_sets_host: csr_idx is NULL");
+    for (int64_t p = 0; p < nnz; ++p)
+        if (csr_idx[p] < 0 || (int64_t)csr_idx[p] >= c.n) return fail(h, EBC_EINDEX, "ebc_eval_sets_host: index outside [0, n)");
+    int32_t *d_i = nullptr;
+    int64_t *d_o = nullptr;
+    double *d_f = nullptr;
+    cudaError_t e = dalloc(&d_i, nnz);
+    if (e == cudaSuccess) e = dalloc(&d_o, l + 1);
+    if (e == cudaSuccess) e = dalloc(&d_f, l);
+    ebc_status s = EBC_OK;
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(d_i, csr_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_o, csr_off, sizeof(int64_t) * (l + 1), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) s = ebc_eval_sets(h, d_i, d_o, l, d_f);
+    if (e == cudaSuccess && s == EBC_OK) e = cudaMemcpyAsync(out_f, d_f, sizeof(double) * l, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess && s == EBC_OK) e = cudaStreamSynchronize(c.stream);
+    if (d_i) cudaFree(d_i);
+    if (d_o) cudaFree(d_o);
+    if (d_f) cudaFree(d_f);
+    if (e != cudaSuccess) return cuda_fail(h, e, "ebc_eval_sets_host");
+    if (s != EBC_OK) return s;
+    return ebc_sync(h);
+}
+
+static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_base) {
+    ebc::Ctx &c = h->c;
+    const int K = c.refine_k;
+    const double eta = bulk_eta(c);
+    CK(h, ebc::launch_gains_fp32(c, nullptr, c.n, true, h->ch, h->nch));
+    CK(h, ebc::launch_reduce_select(c, c.n, h->nch, nullptr, true, nullptr, h->nblk));
+    CK(h, ebc::launch_merge_top(c, h->nblk, K, eta));
+    CK(h, ebc::launch_refine(c, c.top_idx, &c.st->top_count, K, c.ref_part, h->ref_ch, h->nref));
+    CK(h, ebc::launch_decide_n(c, h->nref, eta));
+    CK(h, ebc::launch_collect_escalation(c, eta));
+    CK(h, ebc::launch_refine(c, c.esc_idx, &c.st->esc_count, (int)c.n, h->esc_part, c.n, 1));
+    CK(h, ebc::launch_commit_n(c, h->esc_part, 1, out_idx_base, out_f_base));
+    CK(h, ebc::launch_update(c));
+    return EBC_OK;
+}
+
+ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (k < 0) return fail(h, EBC_EINVAL, "ebc_greedy: k < 0");
+    if ((int64_t)k > c.n - h->nsel) return fail(h, EBC_EINVAL, "ebc_greedy: k exceeds the unselected points");
+    if (k == 0) return EBC_OK;
+    if (!out_idx || !out_f) return fail(h, EBC_EINVAL, "ebc_greedy: NULL output");
+    // k_commit writes out[round] with round counted since reset: shift the base
+    int32_t *ib = out_idx - h->nsel;
+    double *fb = out_f - h->nsel;
+    for (int32_t t = 0; t < k; ++t) {
+        ebc_status s = greedy_round(h, ib, fb);
+        if (s) return s;
+        h->nsel += 1;
+    }
+    return EBC_OK;
+}
+
+ebc_status ebc_greedy_host(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (k < 0 || (int64_t)k > c.n - h->nsel) return fail(h, EBC_EINVAL, "ebc_greedy_host: bad k");
+    if (k == 0) return EBC_OK;
+    if (!out_idx || !out_f) return fail(h, EBC_EINVAL, "ebc_greedy_host: NULL output");
+    int32_t *d_i = nullptr;
+    double *d_f = nullptr;
+    cudaError_t e = dalloc(&d_i, k);
+    if (e == cudaSuccess) e = dalloc(&d_f, k);
+    ebc_status s = EBC_OK;
+    if (e == cudaSuccess) s = ebc_greedy(h, k, d_i, d_f);
+    if (e == cudaSuccess && s == EBC_OK) e = cudaMemcpyAsync(out_idx, d_i, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess && s == EBC_OK) e = cudaMemcpyAsync(out_f, d_f, sizeof(double) * k, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess && s == EBC_OK) e = cudaStreamSynchronize(c.stream);
+    if (d_i) cudaFree(d_i);
+    if (d_f) cudaFree(d_f);
+    if (e != cudaSuccess) return cuda_fail(h, e, "ebc_greedy_host");
+    if (s != EBC_OK) return s;
+    return ebc_sync(h);
+}
+
+}  // extern "C"

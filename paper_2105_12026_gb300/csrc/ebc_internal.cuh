@@ -1,0 +1,118 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the public ABI (include/ebc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ebc.h"
+
+namespace ebc {
+
+constexpr int kMaxRefineK = 32;
+
+__host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t lmax(int64_t a, int64_t b) { return a > b ? a : b; }
+constexpr int kNumSMsHint = 152;
+
+// Device-resident scalar state of one handle (Greedy state + certification).
+struct DevState {
+    double f;               // f(S) of the current Greedy state
+    double pick_gain;       // exact gain of the last pick
+    double top_thr;         // (K+1)-th largest upper bound, -1 if none
+    double esc_thr;         // escalation threshold on upper bounds
+    double max_raw_rel_err; // max (bound - exact)/exact over re-evaluated leaders
+    long long certified;    // rounds certified by the top-K alone
+    long long escalated_rounds;
+    long long escalated_cands;
+    long long rounds;
+    int round;              // picks made so far (index into out arrays)
+    int pick;               // last pick
+    int top_count;          // entries in the top-K list this round
+    int esc_count;          // entries in the escalation list this round
+    int need_esc;           // 1 when this round needs escalation
+    int err;                // first device-detected error (ebc_status), 0 if none
+    unsigned int mmax_bits; // max_v m_v as FP32 bits (rounded up), for the TC slack
+    int zero_scan;          // 1 when every remaining gain is exactly 0
+};
+
+// Scratch / resident buffers of one handle.
+struct Ctx {
+    int64_t n = 0;
+    int32_t d = 0;
+    int32_t dpad = 0;  // d rounded up to the tensor-core K tile (64)
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    ebc_prec prec = EBC_FP32;
+    int32_t refine_k = 8;
+    bool owns_stream = false;
+
+    // resident ground set
+    float *V32 = nullptr;    // [n, d] FP32 row-major, exact copy of the input
+    double *nv64 = nullptr;  // [n] ||v||^2 in FP64
+    float *nv32 = nullptr;   // [n] ||v||^2 rounded to nearest FP32
+    // Greedy state
+    double *m64 = nullptr;   // [n] m_v = min over S u {e0} of d(v, s)
+    uint8_t *sel = nullptr;  // [n] 1 if v is in S
+    DevState *st = nullptr;  // device scalars
+
+    // quantised ground set (tensor-core precisions)
+    void *Vq = nullptr;        // [n, dpad] bf16 / fp16 / e4m3, zero padded
+    int qprec = -1;            // precision Vq currently holds, -1 = none
+    float *qscale = nullptr;   // [n] FP8 per-row scale (1 for bf16/fp16)
+    float *qnorm2 = nullptr;   // [n] ||v_hat||^2 of the dequantised row (FP32, from FP64)
+    float *qerr = nullptr;     // [n] ||v_hat - v|| rounded up
+    float *qnorm = nullptr;    // [n] ||v_hat|| rounded up
+    float *a32 = nullptr;      // [n] per-round a_v for the tensor-core epilogue
+    float *b32 = nullptr;      // [n] per-round b_c for the tensor-core epilogue
+    float qerr_max = 0.f;      // max_v qerr (host copy)
+    float qnorm_max = 0.f;     // max_v qnorm (host copy)
+
+    // scratch
+    double *partial = nullptr;  // [nchunk_cap, n] per-V-chunk partial sums of the bulk gains
+    int64_t partial_cap = 0;    // doubles
+    double *gain_up = nullptr;  // [n] bulk gains (upper bounds in Greedy)
+    int *blk_idx = nullptr;     // per-block top lists
+    double *blk_val = nullptr;
+    int blk_cap = 0;
+    int *top_idx = nullptr;     // [kMaxRefineK + 1]
+    double *top_val = nullptr;  // [kMaxRefineK + 1] upper bounds of the top list
+    double *top_exact = nullptr;// [kMaxRefineK] exact gains
+    int *esc_idx = nullptr;     // [n] escalation list
+    double *esc_exact = nullptr;// [n]
+    double *ref_part = nullptr; // [ref_cap] refine partials
+    int64_t ref_cap = 0;
+    int *cand_buf = nullptr;    // [n] gathered candidate list for ebc_gains
+    double *set_part = nullptr; // eval_sets partials
+    int64_t set_part_cap = 0;
+    int32_t *h_err = nullptr;   // pinned host word for error read-back
+
+    std::string last_error;
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+cudaError_t launch_prologue(Ctx &c, int *d_bad);
+cudaError_t launch_reset_state(Ctx &c);
+cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, int64_t chunk, int nchunks);
+cudaError_t launch_reduce_select(Ctx &c, int64_t m, int nchunks, const int *cand, bool greedy,
+                                 double *out_gain, int nblk);
+cudaError_t launch_merge_top(Ctx &c, int nblk, int K, double eta);
+cudaError_t launch_refine(Ctx &c, const int *list, const int *count, int list_cap, double *out_exact,
+                          int64_t chunk, int nchunks);
+cudaError_t launch_decide_n(Ctx &c, int nchunks, double eta);
+cudaError_t launch_collect_escalation(Ctx &c, double eta);
+cudaError_t launch_commit_n(Ctx &c, const double *esc_part, int nchunks, int32_t *out_idx, double *out_f);
+cudaError_t launch_update(Ctx &c);
+cudaError_t launch_current_f(Ctx &c, double *d_out);
+cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,
+                                  const int *bad);
+
+// tensor-core path
+cudaError_t launch_quantize(Ctx &c, ebc_prec p, float *d_maxes);
+cudaError_t launch_prep_tc(Ctx &c, bool upper, const int *cand, int64_t m);
+cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, int nchunks, int64_t chunk);
+bool tc_supported(const Ctx &c);
+
+}  // namespace ebc

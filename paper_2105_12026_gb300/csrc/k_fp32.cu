@@ -1,0 +1,288 @@
+// FP32 "plain" kernels on the CUDA cores: the direct (v - c)^2 form of the
+// distance, as in the paper's GPU kernel (Algorithm 2), register-tiled.
+//
+//  * k_gains_fp32: partial[q][j] = sum over the V chunk q of
+//        max(0, mu_v - k1 * dhat(v, c_j))
+//    where dhat is the FP32 direct distance.  In upper-bound mode (Greedy)
+//    mu_v = m_v rounded up to FP32 and k1 = 1 - rho rounded down, with
+//    rho = (d + 4) 2^-24 >= the relative error of dhat, so every term bounds
+//    max(0, m_v - d(v, c_j)) from above up to one rounding of the FMA.  In
+//    plain mode mu_v = m_v rounded to nearest and k1 = 1.
+//  * k_eval_sets_fp32: the work-matrix rows W[j, .] of Sec. 4.2 reduced on
+//    the fly: for each set j and point v, min over members of dhat, then
+//    max(0, ||v||^2 - min), summed over V in FP64.
+#include <float.h>
+#include <math.h>
+
+#include "ebc_internal.cuh"
+
+namespace ebc {
+
+namespace {
+constexpr int TC = 64;   // candidates per block tile
+constexpr int TV = 128;  // points per block tile
+constexpr int KC = 16;   // dimensions per smem stage
+}  // namespace
+
+// 256 threads: tx = tid % 16 covers 8 points (two runs of 4), ty = tid / 16
+// covers 4 candidates.
+__global__ void __launch_bounds__(256) k_gains_fp32(const float *__restrict__ V, int64_t n, int d,
+                                                    const double *__restrict__ m64, const int *__restrict__ cand,
+                                                    int64_t m, int upper, float k1, int64_t chunk,
+                                                    double *__restrict__ partial) {
+    __shared__ __align__(16) float Cs[KC][TC];
+    __shared__ __align__(16) float Vs[KC][TV];
+    __shared__ float Ms[TV];
+    __shared__ int Ci[TC];
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t c0 = (int64_t)blockIdx.x * TC;
+    const int q = blockIdx.y;
+    const int64_t vb = (int64_t)q * chunk;
+    const int64_t ve = lmin(vb + chunk, n);
+
+    if (tid < TC) {
+        int64_t j = c0 + tid;
+        Ci[tid] = j < m ? (cand ? cand[j] : (int)j) : -1;
+    }
+    double accd[4] = {0.0, 0.0, 0.0, 0.0};
+
+    for (int64_t v0 = vb; v0 < ve; v0 += TV) {
+        __syncthreads();
+        if (tid < TV) {
+            int64_t v = v0 + tid;
+            float mv = -INFINITY;
+            if (v < ve) {
+                double md = m64[v];
+                mv = upper ? __double2float_ru(md) : __double2float_rn(md);
+            }
+            Ms[tid] = mv;
+        }
+        float acc[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+        for (int k0 = 0; k0 < d; k0 += KC) {
+            __syncthreads();
+            // candidates: TC x KC values, 4 per thread
+#pragma unroll
+            for (int s = 0; s < (TC * KC) / 256; ++s) {
+                int e = tid + 256 * s;
+                int r = e / KC, kk = e % KC;
+                int ci = Ci[r];
+                float x = 0.f;
+                if (ci >= 0 && k0 + kk < d) x = V[(int64_t)ci * d + k0 + kk];
+                Cs[kk][r] = x;
+            }
+            // points: TV x KC values, 8 per thread
+#pragma unroll
+            for (int s = 0; s < (TV * KC) / 256; ++s) {
+                int e = tid + 256 * s;
+                int r = e / KC, kk = e % KC;
+                int64_t v = v0 + r;
+                float x = 0.f;
+                if (v < ve && k0 + kk < d) x = V[v * d + k0 + kk];
+                Vs[kk][r] = x;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                float4 c4 = *reinterpret_cast<const float4 *>(&Cs[kk][ty * 4]);
+                float4 va = *reinterpret_cast<const float4 *>(&Vs[kk][tx * 4]);
+                float4 vb4 = *reinterpret_cast<const float4 *>(&Vs[kk][64 + tx * 4]);
+                float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                float vv[8] = {va.x, va.y, va.z, va.w, vb4.x, vb4.y, vb4.z, vb4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float df = vv[j] - cv[i];
+                        acc[i][j] = fmaf(df, df, acc[i][j]);
+                    }
+            }
+        }
+        // epilogue for this V tile
+        float mv[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            mv[j] = Ms[tx * 4 + j];
+            mv[4 + j] = Ms[64 + tx * 4 + j];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s += fmaxf(0.f, fmaf(-k1, acc[i][j], mv[j]));
+            // the 16 lanes with the same ty hold the other points of this tile
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            s += __shfl_xor_sync(0xffffffffu, s, 4);
+            s += __shfl_xor_sync(0xffffffffu, s, 8);
+            accd[i] += (double)s;
+        }
+    }
+    if (tx == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int64_t j = c0 + ty * 4 + i;
+            if (j < m) partial[(int64_t)q * m + j] = accd[i];
+        }
+    }
+}
+
+cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, int64_t chunk, int nchunks) {
+    float k1 = 1.0f;
+    if (upper) {
+        double rho = (double)(c.d + 4) * ldexp(1.0, -24);
+        double want = 1.0 - rho;
+        k1 = (float)want;
+        if ((double)k1 > want) k1 = nextafterf(k1, 0.f);  // round down
+    }
+    dim3 grid((unsigned)((m + TC - 1) / TC), (unsigned)nchunks);
+    k_gains_fp32<<<grid, 256, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, cand, m, upper ? 1 : 0, k1, chunk, c.partial);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Multi-set evaluation, FP32 direct distances.
+// Block: 128 threads, one point each; the block's 128 points are staged in
+// shared memory dimension-major (Vt[i][t]) when d <= 128, otherwise each
+// thread reads its own row.  Members are processed four at a time from a
+// shared [dim][4] stage so one 16-byte load feeds four distances.
+// Grid: (point tiles of 128, groups of SG sets).  Output: set_part[tile][j]
+// = sum over the tile's points of max(0, ||v||^2 - min_{s in S_j} dhat(v, s)),
+// summed in FP64.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int ES_T = 128;
+constexpr int ES_SG = 8;
+constexpr int ES_DMAX_RES = 128;
+constexpr int ES_DC = 256;  // member stage depth (dims) for the non-resident path
+}  // namespace
+
+template <bool RESIDENT>
+__global__ void __launch_bounds__(ES_T) k_eval_sets_fp32(const float *__restrict__ V, int64_t n, int d,
+                                                         const float *__restrict__ nv32, const int32_t *__restrict__ idx,
+                                                         const int64_t *__restrict__ off, int64_t l,
+                                                         double *__restrict__ set_part, DevState *st,
+                                                         const int *__restrict__ bad) {
+    if (*bad) return;  // offsets failed validation: read nothing
+    extern __shared__ __align__(16) float esm[];
+    float *Vt = esm;                                        // [d][ES_T] when RESIDENT
+    float4 *S4 = reinterpret_cast<float4 *>(esm + (RESIDENT ? d * ES_T : 0));  // [dstage][4]
+    const int dstage = RESIDENT ? d : min(d, ES_DC);
+    const int t = threadIdx.x;
+    const int64_t tile = blockIdx.x;
+    const int64_t v = tile * ES_T + t;
+    const bool vok = v < n;
+    if (RESIDENT) {
+        for (int e = t; e < d * ES_T; e += ES_T) {
+            int r = e / d, i = e % d;
+            int64_t vv = tile * ES_T + r;
+            Vt[i * ES_T + r] = vv < n ? V[vv * d + i] : 0.f;
+        }
+    }
+    const float nv = vok ? nv32[v] : 0.f;
+    const int64_t j0 = (int64_t)blockIdx.y * ES_SG;
+    for (int64_t j = j0; j < lmin(j0 + ES_SG, l); ++j) {
+        const int64_t mb = off[j], me = off[j + 1];
+        float dmin = INFINITY;
+        for (int64_t s0 = mb; s0 < me; s0 += 4) {
+            int mi[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int64_t p = s0 + u;
+                int x = p < me ? idx[p] : -1;
+                if (p < me && (x < 0 || (int64_t)x >= n)) {
+                    if (t == 0) atomicCAS(&st->err, 0, (int)EBC_EINDEX);
+                    x = -1;
+                }
+                mi[u] = x;
+            }
+            float dist[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k0 = 0; k0 < d; k0 += dstage) {
+                int kn = min(dstage, d - k0);
+                __syncthreads();
+                for (int e = t; e < kn * 4; e += ES_T) {
+                    int i = e >> 2, u = e & 3;
+                    float x = mi[u] >= 0 ? V[(int64_t)mi[u] * d + k0 + i] : 0.f;
+                    reinterpret_cast<float *>(S4)[i * 4 + u] = x;
+                }
+                __syncthreads();
+                if (vok) {
+                    for (int i = 0; i < kn; ++i) {
+                        float x = RESIDENT ? Vt[(k0 + i) * ES_T + t] : V[v * d + k0 + i];
+                        float4 s4 = S4[i];
+                        float d0 = x - s4.x, d1 = x - s4.y, d2 = x - s4.z, d3 = x - s4.w;
+                        dist[0] = fmaf(d0, d0, dist[0]);
+                        dist[1] = fmaf(d1, d1, dist[1]);
+                        dist[2] = fmaf(d2, d2, dist[2]);
+                        dist[3] = fmaf(d3, d3, dist[3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (mi[u] >= 0) dmin = fminf(dmin, dist[u]);
+        }
+        double val = vok ? (double)fmaxf(0.f, nv - dmin) : 0.0;
+        // block sum in FP64, fixed order
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+        __shared__ double red[ES_T / 32];
+        __syncthreads();
+        if ((t & 31) == 0) red[t >> 5] = val;
+        __syncthreads();
+        if (t == 0) {
+            double s = 0.0;
+            for (int w = 0; w < ES_T / 32; ++w) s += red[w];
+            set_part[tile * l + j] = s;
+        }
+    }
+}
+
+__global__ void k_sets_finalize(const double *__restrict__ set_part, int64_t ntiles, int64_t l, int64_t j0,
+                                int64_t lall, double inv_n, double *__restrict__ out_f) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= l) return;
+    double s = 0.0;
+    for (int64_t q = 0; q < ntiles; ++q) s += set_part[q * l + j];
+    out_f[j0 + j] = s * inv_n;
+    (void)lall;
+}
+
+cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,
+                                  const int *bad) {
+    int64_t ntiles = (c.n + ES_T - 1) / ES_T;
+    // process the sets in batches so the partials fit the scratch buffer
+    int64_t batch = c.set_part_cap / ntiles;
+    if (batch < 1) return cudaErrorMemoryAllocation;
+    bool resident = c.d <= ES_DMAX_RES;
+    size_t smem = resident ? (size_t)c.d * ES_T * 4 + (size_t)c.d * 16 : (size_t)min(c.d, ES_DC) * 16;
+    if (resident && smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_eval_sets_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    for (int64_t j0 = 0; j0 < l; j0 += batch) {
+        int64_t lb = min(batch, l - j0);
+        dim3 grid((unsigned)ntiles, (unsigned)((lb + ES_SG - 1) / ES_SG));
+        if (resident)
+            k_eval_sets_fp32<true><<<grid, ES_T, smem, c.stream>>>(c.V32, c.n, c.d, c.nv32, idx, off + j0, lb,
+                                                                   c.set_part, c.st, bad);
+        else
+            k_eval_sets_fp32<false><<<grid, ES_T, smem, c.stream>>>(c.V32, c.n, c.d, c.nv32, idx, off + j0, lb,
+                                                                    c.set_part, c.st, bad);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_sets_finalize<<<(unsigned)((lb + 255) / 256), 256, 0, c.stream>>>(c.set_part, ntiles, lb, j0, l,
+                                                                              1.0 / (double)c.n, out_f);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace ebc

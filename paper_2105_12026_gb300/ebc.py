@@ -1,0 +1,290 @@
+"""Thin Python binding of the C ABI in include/ebc.h (argument marshalling only).
+
+Function names match the C entry points.  Device pointers are taken from
+torch CUDA tensors (``tensor.data_ptr()``); streams from
+``torch.cuda.current_stream().cuda_stream``.  Every step of the computation
+runs in the CUDA library: if ``_build/libebc.so`` is missing this module
+raises instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+EBC_OK, EBC_EINVAL, EBC_EINDEX, EBC_ENOMEM, EBC_ECUDA, EBC_ETIMEOUT, EBC_EBUSY, EBC_ENODEV = 0, -1, -2, -3, -4, -5, -6, -7
+EBC_FP32, EBC_BF16, EBC_FP16, EBC_FP8E4M3 = 0, 1, 2, 3
+PRECISIONS = {"fp32": EBC_FP32, "bf16": EBC_BF16, "fp16": EBC_FP16, "fp8": EBC_FP8E4M3}
+_NAMES = {EBC_EINVAL: "EINVAL", EBC_EINDEX: "EINDEX", EBC_ENOMEM: "ENOMEM", EBC_ECUDA: "ECUDA",
+          EBC_ETIMEOUT: "ETIMEOUT", EBC_EBUSY: "EBUSY", EBC_ENODEV: "ENODEV"}
+
+
+class EbcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ebc_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("certified_rounds", ctypes.c_int64),
+                ("escalated_rounds", ctypes.c_int64), ("escalated_candidates", ctypes.c_int64),
+                ("max_raw_rel_err", ctypes.c_double), ("prec", ctypes.c_int32), ("refine_k", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+# name -> argtypes (restype is ebc_status = int unless noted)
+_SIGS = {
+    "ebc_version": [],
+    "ebc_create": [_P, _I64, _I32, _I32, _P, ctypes.POINTER(_P)],
+    "ebc_destroy": [_P],
+    "ebc_set_stream": [_P, _P],
+    "ebc_set_precision": [_P, ctypes.c_int, _I32],
+    "ebc_eval_sets": [_P, _P, _P, _I64, _P],
+    "ebc_eval_sets_host": [_P, _P, _P, _I64, _P],
+    "ebc_gains": [_P, _P, _I64, _P],
+    "ebc_gains_host": [_P, _P, _I64, _P],
+    "ebc_greedy": [_P, _I32, _P, _P],
+    "ebc_greedy_host": [_P, _I32, _P, _P],
+    "ebc_reset": [_P],
+    "ebc_sync": [_P],
+    "ebc_get_stats": [_P, ctypes.POINTER(ebc_stats)],
+    "ebc_current_f": [_P, ctypes.POINTER(ctypes.c_double)],
+    "ebc_last_error": [_P],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load the library (build it first with ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or library_path()
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
+            lib = ctypes.CDLL(p)
+            for name, args in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            lib.ebc_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _raise(h, rc):
+    if rc != EBC_OK:
+        msg = load().ebc_last_error(h)
+        raise EbcError(rc, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---------------------------------------------------------------------------
+# one wrapper per C entry point
+# ---------------------------------------------------------------------------
+
+def ebc_version() -> int:
+    return int(load().ebc_version())
+
+
+def ebc_create(V_ptr: int, n: int, d: int, v_on_device: bool, stream=None) -> int:
+    h = _P()
+    rc = load().ebc_create(_P(V_ptr), n, d, int(bool(v_on_device)), _P(_stream_ptr(stream)), ctypes.byref(h))
+    _raise(None, rc)
+    return h.value
+
+
+def ebc_destroy(h: int) -> None:
+    load().ebc_destroy(_P(h))
+
+
+def ebc_set_stream(h: int, stream) -> None:
+    _raise(h, load().ebc_set_stream(_P(h), _P(_stream_ptr(stream))))
+
+
+def ebc_set_precision(h: int, prec: int, refine_k: int = 8) -> None:
+    _raise(h, load().ebc_set_precision(_P(h), int(prec), int(refine_k)))
+
+
+def ebc_eval_sets(h: int, idx_ptr: int, off_ptr: int, l: int, out_ptr: int) -> None:
+    _raise(h, load().ebc_eval_sets(_P(h), _P(idx_ptr), _P(off_ptr), int(l), _P(out_ptr)))
+
+
+def ebc_eval_sets_host(h: int, idx: np.ndarray, off: np.ndarray) -> np.ndarray:
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    l = off.size - 1
+    out = np.zeros(max(l, 0), dtype=np.float64)
+    _raise(h, load().ebc_eval_sets_host(_P(h), idx.ctypes.data_as(_P), off.ctypes.data_as(_P), l,
+                                        out.ctypes.data_as(_P)))
+    return out
+
+
+def ebc_gains(h: int, cand_ptr, m: int, out_ptr: int) -> None:
+    _raise(h, load().ebc_gains(_P(h), _P(cand_ptr), int(m), _P(out_ptr)))
+
+
+def ebc_gains_host(h: int, cand: np.ndarray | None, m: int | None = None) -> np.ndarray:
+    if cand is None:
+        out = np.zeros(int(m), dtype=np.float64)
+        _raise(h, load().ebc_gains_host(_P(h), None, int(m), out.ctypes.data_as(_P)))
+        return out
+    cand = np.ascontiguousarray(cand, dtype=np.int32)
+    out = np.zeros(cand.size, dtype=np.float64)
+    _raise(h, load().ebc_gains_host(_P(h), cand.ctypes.data_as(_P), cand.size, out.ctypes.data_as(_P)))
+    return out
+
+
+def ebc_greedy(h: int, k: int, out_idx_ptr: int, out_f_ptr: int) -> None:
+    _raise(h, load().ebc_greedy(_P(h), int(k), _P(out_idx_ptr), _P(out_f_ptr)))
+
+
+def ebc_greedy_host(h: int, k: int):
+    idx = np.zeros(k, dtype=np.int32)
+    f = np.zeros(k, dtype=np.float64)
+    _raise(h, load().ebc_greedy_host(_P(h), int(k), idx.ctypes.data_as(_P), f.ctypes.data_as(_P)))
+    return idx, f
+
+
+def ebc_reset(h: int) -> None:
+    _raise(h, load().ebc_reset(_P(h)))
+
+
+def ebc_sync(h: int) -> None:
+    _raise(h, load().ebc_sync(_P(h)))
+
+
+def ebc_get_stats(h: int) -> dict:
+    s = ebc_stats()
+    _raise(h, load().ebc_get_stats(_P(h), ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in ebc_stats._fields_}
+
+
+def ebc_current_f(h: int) -> float:
+    v = ctypes.c_double()
+    _raise(h, load().ebc_current_f(_P(h), ctypes.byref(v)))
+    return v.value
+
+
+def ebc_last_error(h: int | None) -> str:
+    m = load().ebc_last_error(_P(h) if h else None)
+    return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------
+# convenience object over torch tensors (marshalling only)
+# ---------------------------------------------------------------------------
+
+class Instance:
+    """One resident ground set.  ``V`` is an (n, d) float32 torch tensor or numpy array."""
+
+    def __init__(self, V, precision: str = "fp32", refine_k: int = 8, stream=None):
+        import torch
+        self._keep = None
+        if isinstance(V, np.ndarray):
+            V = np.ascontiguousarray(V, dtype=np.float32)
+            self.n, self.d = V.shape
+            self.h = ebc_create(V.ctypes.data, self.n, self.d, False, stream)
+        else:
+            if V.dtype != torch.float32 or V.dim() != 2:
+                raise ValueError("V must be a 2-D float32 tensor")
+            V = V.contiguous()
+            self.n, self.d = V.shape
+            self.h = ebc_create(V.data_ptr(), self.n, self.d, V.is_cuda, stream)
+        self.precision = precision
+        if precision != "fp32" or refine_k != 8:
+            ebc_set_precision(self.h, PRECISIONS[precision], refine_k)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ebc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_precision(self, precision: str, refine_k: int = 8):
+        ebc_set_precision(self.h, PRECISIONS[precision], refine_k)
+        self.precision = precision
+
+    def greedy(self, k: int):
+        """Device outputs: (idx int32[k], f float64[k]) CUDA tensors."""
+        import torch
+        idx = torch.empty(k, dtype=torch.int32, device="cuda")
+        f = torch.empty(k, dtype=torch.float64, device="cuda")
+        ebc_greedy(self.h, k, idx.data_ptr(), f.data_ptr())
+        return idx, f
+
+    def greedy_host(self, k: int):
+        return ebc_greedy_host(self.h, k)
+
+    def gains(self, cand=None):
+        import torch
+        if cand is None:
+            out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+            ebc_gains(self.h, None, self.n, out.data_ptr())
+            return out
+        cand = cand.to(device="cuda", dtype=torch.int32).contiguous()
+        out = torch.empty(cand.numel(), dtype=torch.float64, device="cuda")
+        ebc_gains(self.h, cand.data_ptr(), cand.numel(), out.data_ptr())
+        self._keep = cand
+        return out
+
+    def eval_sets(self, idx, off):
+        import torch
+        idx = idx.to(device="cuda", dtype=torch.int32).contiguous()
+        off = off.to(device="cuda", dtype=torch.int64).contiguous()
+        l = off.numel() - 1
+        out = torch.empty(max(l, 0), dtype=torch.float64, device="cuda")
+        ebc_eval_sets(self.h, idx.data_ptr(), off.data_ptr(), l, out.data_ptr())
+        self._keep = (idx, off)
+        return out
+
+    def eval_sets_host(self, idx, off):
+        return ebc_eval_sets_host(self.h, idx, off)
+
+    def gains_host(self, cand=None):
+        return ebc_gains_host(self.h, cand, self.n if cand is None else None)
+
+    def reset(self):
+        ebc_reset(self.h)
+
+    def sync(self):
+        ebc_sync(self.h)
+
+    def stats(self):
+        return ebc_get_stats(self.h)
+
+    def current_f(self):
+        return ebc_current_f(self.h)

@@ -1,0 +1,78 @@
+"""The C-ABI library loads on a machine without a GPU, exports every entry
+point include/ebc.h declares, and rejects bad arguments on the host before
+touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2105_12026_gb300 import build as _build
+from paper_2105_12026_gb300 import ebc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ebc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return ebc.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ebc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_calls():
+    names = declared_functions()
+    for required in ("ebc_create", "ebc_eval_sets", "ebc_gains", "ebc_greedy", "ebc_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_binding_covers_every_symbol():
+    assert set(declared_functions()) <= set(ebc._SIGS)
+
+
+def test_version(lib):
+    assert ebc.ebc_version() >= 1
+
+
+@pytest.mark.parametrize("n,d", [(0, 4), (-5, 4), (10, 0), (10, 4097)])
+def test_create_rejects_bad_sizes_on_host(lib, n, d):
+    V = np.zeros((max(n, 1), max(d, 1)), np.float32)
+    with pytest.raises(ebc.EbcError) as ei:
+        ebc.ebc_create(V.ctypes.data, n, d, False, stream=0)
+    assert ei.value.status == ebc.EBC_EINVAL
+
+
+def test_create_rejects_null(lib):
+    with pytest.raises(ebc.EbcError) as ei:
+        ebc.ebc_create(0, 10, 4, False, stream=0)
+    assert ei.value.status == ebc.EBC_EINVAL
+    assert "NULL" in ebc.ebc_last_error(None)
+
+
+def test_null_handle_calls_are_rejected(lib):
+    assert lib.ebc_reset(None) == ebc.EBC_EINVAL
+    assert lib.ebc_sync(None) == ebc.EBC_EINVAL
+    assert lib.ebc_destroy(None) == ebc.EBC_OK
+
+
+def test_no_gpu_gives_enodev_not_a_crash(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    V = np.zeros((4, 2), np.float32)
+    with pytest.raises(ebc.EbcError) as ei:
+        ebc.ebc_create(V.ctypes.data, 4, 2, False, stream=0)
+    assert ei.value.status == ebc.EBC_ENODEV
