@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the EBC Greedy hot path on one GB300 (or N replicas).
+
+Workload (default): drifting-regime sensor features, n = 200,000, d = 128,
+Greedy k = 100, all points candidates.  One step = the instance prologue
+(V device-to-device into the resident slot, norms, quantised copy, m_v) plus
+k certified Greedy rounds.  Metric: distance evaluations per second, one
+evaluation being one (candidate, point) pair of a round's bulk gains,
+summed over rounds as sum_t (n - t) * n.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp16|fp8|fp32]
+    python bench.py --impl reference      # the CPU oracle on the same metric
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EBC distance-evals/s, BF16-TC vs FP32 plain at matched picks; serve p99 ms"
+UNIT = "distance-evals/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            j = json.load(fh)
+        return {"hbm_gbs": j["hbm_gbs"], "bf16": j["bf16_tflops"], "bf16_sustained": j["bf16_tflops_sustained"],
+                "sm_max_mhz": j.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi sampler run during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def greedy_evals(n: int, k: int) -> int:
+    return sum((n - t) * n for t in range(k))
+
+
+def make_workload(args, rank: int):
+    from paper_2105_12026_gb300 import synth
+    if args.workload == "regime":
+        w = synth.regime_greedy(seed=args.seed + rank, n=args.n, d=args.d, k=args.k)
+        name = f"greedy drifting-regime features n={args.n} d={args.d} k={args.k}"
+    else:
+        w = synth.plain_greedy_small(seed=args.seed + rank, n=args.n, d=args.d)
+        w["k"] = args.k
+        name = f"greedy 8-cluster GMM n={args.n} d={args.d} k={args.k}"
+    return w["V"], w["k"], name
+
+
+def cpu_baseline(V, budget_s: float, seed: int = 0):
+    """Oracle (FP64, all host threads) gains at S = {} on a sample of candidates."""
+    import oracle
+    n = V.shape[0]
+    m = oracle.norms(V)
+    rng = np.random.default_rng(seed)
+    count, elapsed, done = 4, 0.0, 0
+    t_all = time.perf_counter()
+    while True:
+        cand = rng.choice(n, size=count, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.gains(V, m, cand)
+        dt = time.perf_counter() - t0
+        elapsed += dt
+        done += count
+        if time.perf_counter() - t_all + 2.2 * dt > budget_s:
+            break
+        count = min(count * 2, n)
+    return {"value": done * n / elapsed, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"oracle gains at S={{}} for {done} sampled candidates x all {n} points, FP64, "
+                      f"{oracle.num_threads()} threads, {elapsed:.1f}s"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the same metric, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    V, k, name = make_workload(args, 0)
+    n = V.shape[0]
+    m = oracle.norms(V)
+    rng = np.random.default_rng(1)
+    per_step = max(1, int(args.ref_cands))
+    times = []
+    for s in range(args.warmup + args.steps):
+        cand = rng.choice(n, size=per_step, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.gains(V, m, cand)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = args.steps * per_step * n / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": name, "sample": f"{per_step} candidates x {n} points per step (S = {{}})"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{per_step} sampled candidates x all {n} points per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["bf16", "fp16", "fp8", "fp32"])
+    ap.add_argument("--refine-k", type=int, default=8)
+    ap.add_argument("--workload", default="regime", choices=["regime", "small"])
+    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--d", type=int, default=128)
+    ap.add_argument("--k", type=int, default=100)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp32-rounds", type=int, default=3, help="rounds of the FP32 plain comparison")
+    ap.add_argument("--ref-cands", type=int, default=64, help="reference arm: candidates per step")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2105_12026_gb300 import build as _b
+    from paper_2105_12026_gb300 import ebc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if not os.path.exists(_b.LIB):
+        raise SystemExit("CUDA library not built; run __graft_entry__.build() first")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    V, k, wname = make_workload(args, rank)
+    n, d = V.shape
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    Vd = torch.from_numpy(V).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    inst = ebc.Instance(Vd, precision=args.prec, refine_k=args.refine_k, stream=stream)
+    out_idx = torch.empty(k, dtype=torch.int32, device=dev)
+    out_f = torch.empty(k, dtype=torch.float64, device=dev)
+
+    def step():
+        inst.reload(Vd)
+        ebc.ebc_greedy(inst.h, k, out_idx.data_ptr(), out_f.data_ptr())
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    inst.sync()
+
+    # timed region -------------------------------------------------------
+    inst.profiling(True)
+    inst.reset_profile()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()  # L2 flush, outside the step's events
+        ev[s][0].record(stream)
+        step()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    prof = inst.profile()
+    inst.profiling(False)
+    inst.sync()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    idx_bf = out_idx.cpu().numpy().copy()
+    f_bf = out_f.cpu().numpy().copy()
+    stats = inst.stats()
+
+    t_max = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    t_max_ms = float(t_max.item())
+    evals_step = greedy_evals(n, k)
+    value = world * args.steps * evals_step / (t_max_ms / 1e3)
+
+    # roofline of the dominant kernel (the bulk gains kernel) -------------
+    pk = peaks()
+    bulk_avg_s = prof["bulk_ms"] / 1e3 / max(1, prof["bulk_launches"])
+    evals_per_launch = prof["bulk_evals"] / max(1, prof["bulk_launches"])
+    if args.prec == "fp32":
+        # direct (v - c)^2: sub + fma per (pair, dim) = 3 flops, 2 lane-ops;
+        # 152 SMs x 128 FP32 lanes at the maximum SM clock
+        flops = 3.0 * d * evals_per_launch
+        peak = 152 * 128 * 1.5 * pk["sm_max_mhz"] * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 128 FP32 lanes x 1.5 flop/lane-op "
+                                                                   "x max SM clock"}
+    else:
+        flops = 2.0 * d * evals_per_launch
+        peak = pk["bf16_sustained"] if args.prec in ("bf16", "fp16") else 2 * pk["bf16_sustained"]
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_source": f"{pk['source']} bf16 sustained" + (" x2 (fp8 nominal ratio)" if args.prec == "fp8" else "")}
+    achieved = flops / bulk_avg_s / 1e12 if bulk_avg_s > 0 else None
+    roof.update({"achieved": achieved, "peak": peak, "frac": (achieved / peak) if achieved else None,
+                 "traffic": None, "kernel": "bulk gains", "launches": prof["bulk_launches"],
+                 "avg_ms": bulk_avg_s * 1e3, "algorithmic_flops_per_launch": flops})
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16",
+                                                              "fp8": "fp8e4m3"}[args.prec],
+            "data": "synthetic (seeded generator, drifting-regime injection-moulding-like features)",
+            "config": {"workload": wname, "n": n, "d": d, "k": k, "precision": args.prec, "refine_k": args.refine_k,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed between steps (256 MB write, outside the step events)",
+                       "evals_per_step": evals_step, "wall_s_timed_region": t_wall},
+            "roofline": roof, "gpu_launches": prof["launches"], "clocks": clk,
+            "certification": {k2: stats[k2] for k2 in ("rounds", "certified_rounds", "escalated_rounds",
+                                                         "escalated_candidates", "max_raw_rel_err")},
+            "f_final": float(f_bf[-1]), "picks_head": idx_bf[:10].tolist()}
+
+    # FP32 plain comparison at matched picks ------------------------------
+    if args.prec != "fp32" and args.fp32_rounds > 0 and rank == 0:
+        R = min(args.fp32_rounds, k)
+        p32 = ebc.Instance(Vd, precision="fp32", stream=stream)
+        p32.greedy(R)  # warm
+        p32.reload(Vd)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        i32, f32 = p32.greedy(R)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms32 = a.elapsed_time(b)
+        ev32 = greedy_evals(n, R)
+        i32 = i32.cpu().numpy()
+        p32.close()
+        v32 = ev32 / (ms32 / 1e3)
+        line["fp32_plain"] = {"value": v32, "unit": UNIT, "rounds": R,
+                              "picks_match": bool((i32 == idx_bf[:R]).all()),
+                              "tc_over_fp32": value / world / v32}
+
+    # end-to-end through the C ABI with host buffers ----------------------
+    if not args.no_e2e:
+        Vh = torch.from_numpy(V).pin_memory()
+        for _ in range(1):
+            inst.reload(Vh)
+            inst.greedy_host(k)
+        e2e_t = []
+        barrier()
+        for s in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            inst.reload(Vh)  # host -> device copy of V inside the step
+            hidx, hf = inst.greedy_host(k)  # device -> host read of the picks and f
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_s = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": world * args.steps * evals_step / float(e2e_s.item()), "unit": UNIT,
+                       "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(k * (4 + 8))}
+
+    inst.close()
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(V, args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

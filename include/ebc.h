@@ -92,6 +92,15 @@ int32_t ebc_version(void);
  */
 ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device, void *stream, ebc_t *out);
 
+/*
+ * Replace the ground set of an existing handle by a new V of the same n and
+ * d (same layout and pointer kinds as ebc_create), rerun the prologue and
+ * return the Greedy state to S = {}.  Allocates nothing, so a resident slot
+ * can be reused for the next instance.  Asynchronous; a non-finite entry of
+ * V is reported by the next ebc_sync() as EINVAL.
+ */
+ebc_status ebc_reload(ebc_t h, const float *V, int32_t v_on_device);
+
 /* Release every resource of the handle (NULL is accepted). */
 ebc_status ebc_destroy(ebc_t h);
 
@@ -163,6 +172,29 @@ ebc_status ebc_sync(ebc_t h);
 
 /* Certification counters (synchronises the stream). */
 ebc_status ebc_get_stats(ebc_t h, ebc_stats *out);
+
+/* Launch and device-time counters of one handle.  Device times are
+ * measured with CUDA events on the handle's stream around each launch while
+ * profiling is on (ebc_set_profiling); launch counts are always kept. */
+typedef struct {
+    int64_t launches;      /* kernels launched by this handle */
+    int64_t bulk_launches; /* launches of the bulk gains kernel (any precision) */
+    double bulk_ms;        /* summed device time of those launches (profiling on) */
+    int64_t bulk_evals;    /* (candidate, point) pairs those launches evaluated */
+    int64_t refine_launches;
+    double refine_ms;      /* exact FP64 re-evaluation of the leaders */
+    int64_t eval_launches; /* launches of the multi-set kernel */
+    double eval_ms;
+} ebc_profile;
+
+/* Turn per-launch event timing on (1) or off (0); counters keep running. */
+ebc_status ebc_set_profiling(ebc_t h, int32_t on);
+
+/* Read the counters (synchronises the stream). */
+ebc_status ebc_get_profile(ebc_t h, ebc_profile *out);
+
+/* Zero the counters. */
+ebc_status ebc_reset_profile(ebc_t h);
 
 /* f(S) of the current Greedy state, computed on the device (synchronises). */
 ebc_status ebc_current_f(ebc_t h, double *out_f);

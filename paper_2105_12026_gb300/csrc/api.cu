@@ -10,8 +10,23 @@
 
 #include "ebc_internal.cuh"
 
+struct Prof {
+    bool on = false;
+    ebc_profile p{};
+    std::vector<cudaEvent_t> pool;
+    // (start, end, kind) of launches not yet folded into p
+    struct Rec {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<Rec> pending;
+};
+
+enum { PK_BULK = 0, PK_REFINE = 1, PK_EVAL = 2 };
+
 struct ebc_ctx {
     ebc::Ctx c;
+    Prof prof;
     int64_t nsel = 0;       // points picked since create / reset (host mirror)
     int64_t ch = 0;         // bulk-gains V chunk (points)
     int nch = 0;            // number of bulk-gains chunks
@@ -111,6 +126,59 @@ ebc_status check_handle(ebc_t h) {
     return EBC_OK;
 }
 
+cudaEvent_t take_event(Prof &p) {
+    if (!p.pool.empty()) {
+        cudaEvent_t e = p.pool.back();
+        p.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Run one launcher; count it and, with profiling on, bracket it with events.
+template <class F>
+cudaError_t launch(ebc_t h, int kind, int64_t nlaunch, F &&fn) {
+    Prof &p = h->prof;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (p.on && kind >= 0) {
+        a = take_event(p);
+        b = take_event(p);
+        if (a && b) cudaEventRecord(a, h->c.stream);
+    }
+    cudaError_t e = fn();
+    p.p.launches += nlaunch;
+    if (kind == PK_BULK) p.p.bulk_launches += nlaunch;
+    if (kind == PK_REFINE) p.p.refine_launches += nlaunch;
+    if (kind == PK_EVAL) p.p.eval_launches += nlaunch;
+    if (a && b) {
+        cudaEventRecord(b, h->c.stream);
+        p.pending.push_back({a, b, kind});
+    } else {
+        if (a) p.pool.push_back(a);
+        if (b) p.pool.push_back(b);
+    }
+    return e;
+}
+
+cudaError_t fold_profile(ebc_t h) {
+    Prof &p = h->prof;
+    cudaError_t e = cudaStreamSynchronize(h->c.stream);
+    if (e != cudaSuccess) return e;
+    for (auto &r : p.pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        if (r.kind == PK_BULK) p.p.bulk_ms += ms;
+        if (r.kind == PK_REFINE) p.p.refine_ms += ms;
+        if (r.kind == PK_EVAL) p.p.eval_ms += ms;
+        p.pool.push_back(r.a);
+        p.pool.push_back(r.b);
+    }
+    p.pending.clear();
+    return cudaSuccess;
+}
+
 ebc_status ensure_set_part(ebc_t h, int64_t want) {
     ebc::Ctx &c = h->c;
     if (c.set_part_cap >= want) return EBC_OK;
@@ -205,10 +273,9 @@ ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device,
 
     CKC(cudaMemcpyAsync(c.V32, V, sizeof(float) * (size_t)n * d,
                         v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream));
-    CKC(cudaMemsetAsync(h->d_bad, 0, sizeof(int), c.stream));
     CKC(ebc::launch_reset_state(c));
-    CKC(ebc::launch_prologue(c, h->d_bad));
-    CKC(cudaMemcpyAsync(c.h_err, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    CKC(ebc::launch_prologue(c));
+    CKC(cudaMemcpyAsync(c.h_err, &c.st->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     CKC(cudaStreamSynchronize(c.stream));
     if (c.h_err[0]) return bail(EBC_EINVAL, "ebc_create: V has a non-finite entry");
 #undef CKC
@@ -219,8 +286,45 @@ ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device,
 ebc_status ebc_destroy(ebc_t h) {
     if (!h) return EBC_OK;
     cudaStreamSynchronize(h->c.stream);
+    for (auto &r : h->prof.pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->prof.pool) cudaEventDestroy(e);
     free_all(h->c, h);
     delete h;
+    return EBC_OK;
+}
+
+ebc_status ebc_reload(ebc_t h, const float *V, int32_t v_on_device) {
+    if (check_handle(h)) return EBC_EINVAL;
+    if (!V) return fail(h, EBC_EINVAL, "ebc_reload: V is NULL");
+    ebc::Ctx &c = h->c;
+    CK(h, cudaMemcpyAsync(c.V32, V, sizeof(float) * (size_t)c.n * c.d,
+                          v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream));
+    CK(h, launch(h, -1, 1, [&] { return ebc::launch_reset_state(c); }));
+    CK(h, launch(h, -1, 1, [&] { return ebc::launch_prologue(c); }));
+    h->nsel = 0;
+    return EBC_OK;
+}
+
+ebc_status ebc_set_profiling(ebc_t h, int32_t on) {
+    if (check_handle(h)) return EBC_EINVAL;
+    h->prof.on = on != 0;
+    return EBC_OK;
+}
+
+ebc_status ebc_get_profile(ebc_t h, ebc_profile *out) {
+    if (check_handle(h) || !out) return fail(h, EBC_EINVAL, "ebc_get_profile: NULL argument");
+    CK(h, fold_profile(h));
+    *out = h->prof.p;
+    return EBC_OK;
+}
+
+ebc_status ebc_reset_profile(ebc_t h) {
+    if (check_handle(h)) return EBC_EINVAL;
+    CK(h, fold_profile(h));
+    h->prof.p = ebc_profile{};
     return EBC_OK;
 }
 
@@ -300,8 +404,12 @@ ebc_status ebc_gains(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_ga
         k_sanitize<<<(unsigned)((mb + 255) / 256), 256, 0, c.stream>>>(cand_idx ? cand_idx + j0 : nullptr, mb, c.n,
                                                                        c.cand_buf, c.st);
         CK(h, cudaGetLastError());
-        CK(h, ebc::launch_gains_fp32(c, c.cand_buf, mb, false, h->ch, h->nch));
-        CK(h, ebc::launch_reduce_select(c, mb, h->nch, c.cand_buf, false, out_gain + j0, h->nblk));
+        h->prof.p.launches += 1;
+        CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, c.cand_buf, mb, false, h->ch, h->nch); }));
+        h->prof.p.bulk_evals += mb * c.n;
+        CK(h, launch(h, -1, 2, [&] {
+               return ebc::launch_reduce_select(c, mb, h->nch, c.cand_buf, false, out_gain + j0, h->nblk);
+           }));
         k_zero_masked<<<(unsigned)((mb + 255) / 256), 256, 0, c.stream>>>(c.cand_buf, mb, out_gain + j0);
         CK(h, cudaGetLastError());
     }
@@ -350,7 +458,8 @@ ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off
     int64_t want = std::min<int64_t>(ntiles * l, std::max<int64_t>(ntiles * 64, (int64_t)1 << 24));
     ebc_status s = ensure_set_part(h, want);
     if (s) return s;
-    CK(h, ebc::launch_eval_sets_fp32(c, csr_idx, csr_off, l, out_f, h->d_bad));
+    h->prof.p.launches += 1;
+    CK(h, launch(h, PK_EVAL, 2, [&] { return ebc::launch_eval_sets_fp32(c, csr_idx, csr_off, l, out_f, h->d_bad); }));
     return EBC_OK;
 }
 
@@ -391,15 +500,24 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
     ebc::Ctx &c = h->c;
     const int K = c.refine_k;
     const double eta = bulk_eta(c);
-    CK(h, ebc::launch_gains_fp32(c, nullptr, c.n, true, h->ch, h->nch));
-    CK(h, ebc::launch_reduce_select(c, c.n, h->nch, nullptr, true, nullptr, h->nblk));
-    CK(h, ebc::launch_merge_top(c, h->nblk, K, eta));
-    CK(h, ebc::launch_refine(c, c.top_idx, &c.st->top_count, K, c.ref_part, h->ref_ch, h->nref));
-    CK(h, ebc::launch_decide_n(c, h->nref, eta));
-    CK(h, ebc::launch_collect_escalation(c, eta));
-    CK(h, ebc::launch_refine(c, c.esc_idx, &c.st->esc_count, (int)c.n, h->esc_part, c.n, 1));
-    CK(h, ebc::launch_commit_n(c, h->esc_part, 1, out_idx_base, out_f_base));
-    CK(h, ebc::launch_update(c));
+    CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, nullptr, c.n, true, h->ch, h->nch); }));
+    h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
+    CK(h, launch(h, -1, 1, [&] { return ebc::launch_reduce_select(c, c.n, h->nch, nullptr, true, nullptr, h->nblk); }));
+    CK(h, launch(h, -1, 1, [&] { return ebc::launch_merge_top(c, h->nblk, K, eta); }));
+    CK(h, launch(h, PK_REFINE, 1, [&] {
+           return ebc::launch_refine(c, c.top_idx, &c.st->top_count, K, c.ref_part, h->ref_ch, h->nref);
+       }));
+    CK(h, launch(h, -1, 2, [&] {
+           cudaError_t e = ebc::launch_decide_n(c, h->nref, eta);
+           return e != cudaSuccess ? e : ebc::launch_collect_escalation(c, eta);
+       }));
+    CK(h, launch(h, PK_REFINE, 1, [&] {
+           return ebc::launch_refine(c, c.esc_idx, &c.st->esc_count, (int)c.n, h->esc_part, c.n, 1);
+       }));
+    CK(h, launch(h, -1, 2, [&] {
+           cudaError_t e = ebc::launch_commit_n(c, h->esc_part, 1, out_idx_base, out_f_base);
+           return e != cudaSuccess ? e : ebc::launch_update(c);
+       }));
     return EBC_OK;
 }
 

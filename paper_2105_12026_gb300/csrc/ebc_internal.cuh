@@ -93,7 +93,7 @@ struct Ctx {
 };
 
 // ---- launchers (defined in the .cu files) --------------------------------
-cudaError_t launch_prologue(Ctx &c, int *d_bad);
+cudaError_t launch_prologue(Ctx &c);
 cudaError_t launch_reset_state(Ctx &c);
 cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, int64_t chunk, int nchunks);
 cudaError_t launch_reduce_select(Ctx &c, int64_t m, int nchunks, const int *cand, bool greedy,

@@ -43,7 +43,7 @@ __device__ __forceinline__ float screen_sqdist(const float *__restrict__ v, cons
 // ---------------------------------------------------------------------------
 __global__ void k_prologue(const float *__restrict__ V, int64_t n, int d, double *__restrict__ nv64,
                            float *__restrict__ nv32, double *__restrict__ m64, uint8_t *__restrict__ sel,
-                           int *__restrict__ bad) {
+                           DevState *st) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     const float *v = V + r * d;
@@ -59,13 +59,13 @@ __global__ void k_prologue(const float *__restrict__ V, int64_t n, int d, double
     nv32[r] = (float)acc;
     m64[r] = acc;
     sel[r] = 0;
-    if (!finite) atomicExch(bad, 1);
+    if (!finite) atomicCAS(&st->err, 0, (int)EBC_EINVAL);
 }
 
-cudaError_t launch_prologue(Ctx &c, int *d_bad) {
+cudaError_t launch_prologue(Ctx &c) {
     int th = 256;
     int64_t bl = (c.n + th - 1) / th;
-    k_prologue<<<(unsigned)bl, th, 0, c.stream>>>(c.V32, c.n, c.d, c.nv64, c.nv32, c.m64, c.sel, d_bad);
+    k_prologue<<<(unsigned)bl, th, 0, c.stream>>>(c.V32, c.n, c.d, c.nv64, c.nv32, c.m64, c.sel, c.st);
     return cudaGetLastError();
 }
 

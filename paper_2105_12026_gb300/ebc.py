@@ -38,6 +38,12 @@ class ebc_stats(ctypes.Structure):
                 ("max_raw_rel_err", ctypes.c_double), ("prec", ctypes.c_int32), ("refine_k", ctypes.c_int32)]
 
 
+class ebc_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("bulk_launches", ctypes.c_int64), ("bulk_ms", ctypes.c_double),
+                ("bulk_evals", ctypes.c_int64), ("refine_launches", ctypes.c_int64), ("refine_ms", ctypes.c_double),
+                ("eval_launches", ctypes.c_int64), ("eval_ms", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -46,7 +52,11 @@ _I32 = ctypes.c_int32
 _SIGS = {
     "ebc_version": [],
     "ebc_create": [_P, _I64, _I32, _I32, _P, ctypes.POINTER(_P)],
+    "ebc_reload": [_P, _P, _I32],
     "ebc_destroy": [_P],
+    "ebc_set_profiling": [_P, _I32],
+    "ebc_get_profile": [_P, ctypes.POINTER(ebc_profile)],
+    "ebc_reset_profile": [_P],
     "ebc_set_stream": [_P, _P],
     "ebc_set_precision": [_P, ctypes.c_int, _I32],
     "ebc_eval_sets": [_P, _P, _P, _I64, _P],
@@ -114,6 +124,24 @@ def ebc_create(V_ptr: int, n: int, d: int, v_on_device: bool, stream=None) -> in
     rc = load().ebc_create(_P(V_ptr), n, d, int(bool(v_on_device)), _P(_stream_ptr(stream)), ctypes.byref(h))
     _raise(None, rc)
     return h.value
+
+
+def ebc_reload(h: int, V_ptr: int, v_on_device: bool) -> None:
+    _raise(h, load().ebc_reload(_P(h), _P(V_ptr), int(bool(v_on_device))))
+
+
+def ebc_set_profiling(h: int, on: bool) -> None:
+    _raise(h, load().ebc_set_profiling(_P(h), int(bool(on))))
+
+
+def ebc_get_profile(h: int) -> dict:
+    p = ebc_profile()
+    _raise(h, load().ebc_get_profile(_P(h), ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in ebc_profile._fields_}
+
+
+def ebc_reset_profile(h: int) -> None:
+    _raise(h, load().ebc_reset_profile(_P(h)))
 
 
 def ebc_destroy(h: int) -> None:
@@ -279,6 +307,27 @@ class Instance:
 
     def reset(self):
         ebc_reset(self.h)
+
+    def reload(self, V):
+        """Replace V (same n, d): torch tensor (host or CUDA) or numpy array."""
+        if isinstance(V, np.ndarray):
+            V = np.ascontiguousarray(V, dtype=np.float32)
+            assert V.shape == (self.n, self.d)
+            ebc_reload(self.h, V.ctypes.data, False)
+            self._keep = V
+        else:
+            assert tuple(V.shape) == (self.n, self.d) and V.is_contiguous()
+            ebc_reload(self.h, V.data_ptr(), V.is_cuda)
+            self._keep = V
+
+    def profiling(self, on: bool = True):
+        ebc_set_profiling(self.h, on)
+
+    def profile(self):
+        return ebc_get_profile(self.h)
+
+    def reset_profile(self):
+        ebc_reset_profile(self.h)
 
     def sync(self):
         ebc_sync(self.h)

@@ -218,3 +218,36 @@ def test_rejects_non_finite(torch):
     with pytest.raises(ebc.EbcError) as ei:
         ebc.Instance(V)
     assert ei.value.status == ebc.EBC_EINVAL
+
+
+def test_reload_and_profile_counters(torch):
+    V1 = rand_V(2000, 24, 31, clusters=5)
+    V2 = rand_V(2000, 24, 32, clusters=7)
+    r1 = oracle.greedy(V1, 4)
+    r2 = oracle.greedy(V2, 4)
+    with ebc.Instance(torch.from_numpy(V1).cuda()) as inst:
+        inst.profiling(True)
+        i1, f1 = inst.greedy_host(4)
+        inst.reload(torch.from_numpy(V2).cuda())
+        i2, f2 = inst.greedy_host(4)
+        inst.reload(V1)  # host pointer form
+        i3, f3 = inst.greedy_host(4)
+        p = inst.profile()
+    check_greedy(i1, f1, *r1)
+    check_greedy(i2, f2, *r2)
+    np.testing.assert_array_equal(i1, i3)
+    np.testing.assert_array_equal(f1, f3)
+    assert p["bulk_launches"] == 12 and p["bulk_ms"] > 0
+    assert p["bulk_evals"] == 3 * sum((2000 - t) * 2000 for t in range(4))
+    assert p["launches"] >= 12 * 9
+
+
+def test_reload_rejects_non_finite(torch):
+    V = rand_V(50, 3, 2)
+    with ebc.Instance(V) as inst:
+        W = V.copy()
+        W[7, 0] = np.inf
+        inst.reload(W)
+        with pytest.raises(ebc.EbcError) as ei:
+            inst.sync()
+        assert ei.value.status == ebc.EBC_EINVAL
