@@ -71,8 +71,8 @@ cudaError_t dalloc(T **p, size_t count) {
 }
 
 void free_all(ebc::Ctx &c, ebc_ctx *h) {
-    void *ptrs[] = {c.V32, c.nv64, c.nv32, c.m64, c.sel, c.st, c.Vq, c.qscale, c.qnorm2, c.qerr, c.qnorm,
-                    c.a32, c.b32, c.partial, c.gain_up, c.blk_idx, c.blk_val, c.top_idx, c.top_val,
+    ebc::tc_free(c);
+    void *ptrs[] = {c.V32, c.nv64, c.nv32, c.m64, c.sel, c.st, c.partial, c.gain_up, c.blk_idx, c.blk_val, c.top_idx, c.top_val,
                     c.top_exact, c.esc_idx, c.esc_exact, c.ref_part, c.cand_buf, c.set_part,
                     h ? h->esc_part : nullptr, h ? h->d_scalar : nullptr, h ? h->d_bad : nullptr};
     for (void *p : ptrs)
@@ -252,7 +252,8 @@ ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device,
     CKC(dalloc(&c.m64, n));
     CKC(dalloc(&c.sel, n));
     CKC(dalloc(&c.st, 1));
-    c.partial_cap = (int64_t)h->nch * n;
+    cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    c.partial_cap = (int64_t)std::max(h->nch, 16) * n;
     CKC(dalloc(&c.partial, (size_t)c.partial_cap));
     CKC(dalloc(&c.gain_up, n));
     c.blk_cap = h->nblk * (ebc::kMaxRefineK + 1);
@@ -304,6 +305,7 @@ ebc_status ebc_reload(ebc_t h, const float *V, int32_t v_on_device) {
                           v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream));
     CK(h, launch(h, -1, 1, [&] { return ebc::launch_reset_state(c); }));
     CK(h, launch(h, -1, 1, [&] { return ebc::launch_prologue(c); }));
+    if (c.tc.prec >= 0) CK(h, launch(h, -1, 1, [&] { return ebc::tc_quantize(c); }));
     h->nsel = 0;
     return EBC_OK;
 }
@@ -337,9 +339,28 @@ ebc_status ebc_set_stream(ebc_t h, void *stream) {
 ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k) {
     if (check_handle(h)) return EBC_EINVAL;
     if (refine_k < 1 || refine_k > ebc::kMaxRefineK) return fail(h, EBC_EINVAL, "ebc_set_precision: K must be in [1, 32]");
-    if (prec != EBC_FP32) return fail(h, EBC_EINVAL, "ebc_set_precision: precision not available in this build");
-    h->c.prec = prec;
-    h->c.refine_k = refine_k;
+    ebc::Ctx &c = h->c;
+    if (prec == EBC_BF16 || prec == EBC_FP16) {
+        if (!ebc::tc_supported(c))
+            return fail(h, EBC_EINVAL, "ebc_set_precision: the tensor-core path supports d <= 128");
+        if (c.tc.prec != (int)prec) {
+            // flush earlier device errors so a quantisation failure is seen on its own
+            ebc_status s0 = ebc_sync(h);
+            if (s0 != EBC_OK) return s0;
+            CK(h, ebc::tc_setup(c, (int)prec));
+            CK(h, cudaMemcpyAsync(c.h_err, &c.st->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+            CK(h, cudaStreamSynchronize(c.stream));
+            if (c.h_err[0]) {
+                CK(h, cudaMemsetAsync(&c.st->err, 0, sizeof(int), c.stream));
+                c.tc.prec = -1;
+                return fail(h, EBC_EINVAL, "ebc_set_precision: V overflows the requested 16-bit format");
+            }
+        }
+    } else if (prec != EBC_FP32) {
+        return fail(h, EBC_EINVAL, "ebc_set_precision: precision not available in this build");
+    }
+    c.prec = prec;
+    c.refine_k = refine_k;
     return EBC_OK;
 }
 
@@ -405,10 +426,16 @@ ebc_status ebc_gains(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_ga
                                                                        c.cand_buf, c.st);
         CK(h, cudaGetLastError());
         h->prof.p.launches += 1;
-        CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, c.cand_buf, mb, false, h->ch, h->nch); }));
+        int nch = h->nch;
+        if (c.prec == EBC_FP32) {
+            CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, c.cand_buf, mb, false, h->ch, h->nch); }));
+        } else {
+            CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, false); }));
+            CK(h, launch(h, PK_BULK, 2, [&] { return ebc::launch_gains_tc(c, c.cand_buf, mb, false, &nch); }));
+        }
         h->prof.p.bulk_evals += mb * c.n;
         CK(h, launch(h, -1, 2, [&] {
-               return ebc::launch_reduce_select(c, mb, h->nch, c.cand_buf, false, out_gain + j0, h->nblk);
+               return ebc::launch_reduce_select(c, mb, nch, c.cand_buf, false, out_gain + j0, h->nblk);
            }));
         k_zero_masked<<<(unsigned)((mb + 255) / 256), 256, 0, c.stream>>>(c.cand_buf, mb, out_gain + j0);
         CK(h, cudaGetLastError());
@@ -500,9 +527,15 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
     ebc::Ctx &c = h->c;
     const int K = c.refine_k;
     const double eta = bulk_eta(c);
-    CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, nullptr, c.n, true, h->ch, h->nch); }));
+    int nch = h->nch;
+    if (c.prec == EBC_FP32) {
+        CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, nullptr, c.n, true, h->ch, h->nch); }));
+    } else {
+        CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, true); }));
+        CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_tc(c, nullptr, c.n, true, &nch); }));
+    }
     h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
-    CK(h, launch(h, -1, 1, [&] { return ebc::launch_reduce_select(c, c.n, h->nch, nullptr, true, nullptr, h->nblk); }));
+    CK(h, launch(h, -1, 1, [&] { return ebc::launch_reduce_select(c, c.n, nch, nullptr, true, nullptr, h->nblk); }));
     CK(h, launch(h, -1, 1, [&] { return ebc::launch_merge_top(c, h->nblk, K, eta); }));
     CK(h, launch(h, PK_REFINE, 1, [&] {
            return ebc::launch_refine(c, c.top_idx, &c.st->top_count, K, c.ref_part, h->ref_ch, h->nref);

@@ -2,6 +2,7 @@
 // Nothing here is part of the public ABI (include/ebc.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -59,16 +60,22 @@ struct Ctx {
     DevState *st = nullptr;  // device scalars
 
     // quantised ground set (tensor-core precisions)
-    void *Vq = nullptr;        // [n, dpad] bf16 / fp16 / e4m3, zero padded
-    int qprec = -1;            // precision Vq currently holds, -1 = none
-    float *qscale = nullptr;   // [n] FP8 per-row scale (1 for bf16/fp16)
-    float *qnorm2 = nullptr;   // [n] ||v_hat||^2 of the dequantised row (FP32, from FP64)
-    float *qerr = nullptr;     // [n] ||v_hat - v|| rounded up
-    float *qnorm = nullptr;    // [n] ||v_hat|| rounded up
-    float *a32 = nullptr;      // [n] per-round a_v for the tensor-core epilogue
-    float *b32 = nullptr;      // [n] per-round b_c for the tensor-core epilogue
-    float qerr_max = 0.f;      // max_v qerr (host copy)
-    float qnorm_max = 0.f;     // max_v qnorm (host copy)
+    struct Tc {
+        int prec = -1;            // precision Vq holds (EBC_BF16 / EBC_FP16), -1 = none
+        int64_t n_pad = 0;        // n rounded up to the point tile (256)
+        int DP = 0;               // d rounded up to the 64-element swizzle atom
+        uint16_t *Vq = nullptr;   // [n_pad, DP] quantised rows, zero padded
+        uint16_t *Cq = nullptr;   // [n_pad, DP] gathered candidate rows (ebc_gains with a list)
+        double *qn64 = nullptr;   // [n_pad] ||v_hat||^2 (FP64)
+        float *qerr = nullptr;    // [n_pad] ||v_hat - v|| rounded up
+        float *qnorm = nullptr;   // [n_pad] ||v_hat|| rounded up
+        float *qmax = nullptr;    // [2] max qerr, max qnorm (as floats, via bit-pattern atomics)
+        float *a32 = nullptr;     // [n_pad] per-round a_v = m_v - ||v_hat||^2, -inf past n
+        CUtensorMap tmA_V;  // candidate tiles over Vq (box 64 x 128)
+        CUtensorMap tmB_V;  // point tiles over Vq (box 64 x 256)
+        CUtensorMap tmA_C;  // candidate tiles over Cq
+    } tc;
+    int num_sms = 152;
 
     // scratch
     double *partial = nullptr;  // [nchunk_cap, n] per-V-chunk partial sums of the bulk gains
@@ -110,9 +117,12 @@ cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off
                                   const int *bad);
 
 // tensor-core path
-cudaError_t launch_quantize(Ctx &c, ebc_prec p, float *d_maxes);
-cudaError_t launch_prep_tc(Ctx &c, bool upper, const int *cand, int64_t m);
-cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, int nchunks, int64_t chunk);
 bool tc_supported(const Ctx &c);
+cudaError_t tc_setup(Ctx &c, int prec);          // allocate, quantise, build tensor maps
+cudaError_t tc_quantize(Ctx &c);                 // (re)quantise V into Vq
+cudaError_t launch_prep_tc(Ctx &c, bool upper);  // a_v for every point (+ max m_v)
+// bulk gains on tensor cores; returns the number of V chunks used in *nchunks
+cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int *nchunks);
+void tc_free(Ctx &c);
 
 }  // namespace ebc

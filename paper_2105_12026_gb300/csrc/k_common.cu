@@ -405,10 +405,11 @@ __global__ void k_commit(const double *__restrict__ esc_part, int nchunks, doubl
 
 // m_v <- min(m_v, d(v, c*)) with the exact distance; points whose screen
 // distance is clearly above m_v keep m_v unchanged.
-__global__ void k_update(const float *__restrict__ V, int64_t n, int d, double *__restrict__ m64, const DevState *st,
+__global__ void k_update(const float *__restrict__ V, int64_t n, int d, double *__restrict__ m64, DevState *st,
                          double rho) {
     extern __shared__ float cs[];
     int c = st->pick;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->mmax_bits = 0u;  // the next round recomputes max_v m_v
     if (c < 0 || (int64_t)c >= n) return;  // no valid pick this round (error already recorded)
     for (int i = threadIdx.x; i < d; i += blockDim.x) cs[i] = V[(int64_t)c * d + i];
     __syncthreads();
