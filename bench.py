@@ -174,7 +174,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["bf16", "fp16", "fp8", "fp32"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
     ap.add_argument("--refine-k", type=int, default=8)
     ap.add_argument("--workload", default="regime", choices=["regime", "small"])
     ap.add_argument("--n", type=int, default=200_000)
