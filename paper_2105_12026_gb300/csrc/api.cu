@@ -33,6 +33,7 @@ struct ebc_ctx {
     int64_t ref_ch = 0;     // refine V chunk
     int nref = 0;           // number of refine chunks
     int nblk = 0;           // select blocks
+    int esc_cap = 0;        // escalated candidates with chunked partials
     double *esc_part = nullptr;
     double *d_scalar = nullptr;  // one device double for ebc_current_f
     int *d_bad = nullptr;
@@ -230,8 +231,9 @@ ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device,
     // chunking of the V axis
     h->ch = std::max<int64_t>(4096, ((n + 63) / 64 + 127) / 128 * 128);
     h->nch = (int)((n + h->ch - 1) / h->ch);
-    h->ref_ch = std::max<int64_t>(8192, ((n + 31) / 32 + 255) / 256 * 256);
+    h->ref_ch = std::max<int64_t>(1024, ((n + 303) / 304 + 255) / 256 * 256);  // ~2 chunks per SM
     h->nref = (int)((n + h->ref_ch - 1) / h->ref_ch);
+    h->esc_cap = (int)std::min<int64_t>(n, 4096);
     h->nblk = (int)std::min<int64_t>(512, std::max<int64_t>(1, (n + 2047) / 2048));
 
     auto bail = [&](ebc_status s, const std::string &m) {
@@ -266,7 +268,7 @@ ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device,
     CKC(dalloc(&c.esc_exact, n));
     c.ref_cap = (int64_t)ebc::kMaxRefineK * h->nref;
     CKC(dalloc(&c.ref_part, (size_t)c.ref_cap));
-    CKC(dalloc(&h->esc_part, n));
+    CKC(dalloc(&h->esc_part, (size_t)h->esc_cap * h->nref));
     CKC(dalloc(&c.cand_buf, n));
     CKC(dalloc(&h->d_scalar, 1));
     CKC(dalloc(&h->d_bad, 1));
@@ -544,11 +546,13 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
            cudaError_t e = ebc::launch_decide_n(c, h->nref, eta);
            return e != cudaSuccess ? e : ebc::launch_collect_escalation(c, eta);
        }));
-    CK(h, launch(h, PK_REFINE, 1, [&] {
-           return ebc::launch_refine(c, c.esc_idx, &c.st->esc_count, (int)c.n, h->esc_part, c.n, 1);
+    CK(h, launch(h, PK_REFINE, 2, [&] {
+           cudaError_t e = ebc::launch_refine(c, c.esc_idx, &c.st->esc_count, h->esc_cap, h->esc_part, h->ref_ch,
+                                              h->nref);
+           return e != cudaSuccess ? e : ebc::launch_refine_overflow(c, c.esc_idx, &c.st->esc_count, h->esc_cap, c.esc_exact);
        }));
     CK(h, launch(h, -1, 2, [&] {
-           cudaError_t e = ebc::launch_commit_n(c, h->esc_part, 1, out_idx_base, out_f_base);
+           cudaError_t e = ebc::launch_commit_n(c, h->esc_part, h->nref, h->esc_cap, out_idx_base, out_f_base);
            return e != cudaSuccess ? e : ebc::launch_update(c);
        }));
     return EBC_OK;

@@ -70,7 +70,8 @@ struct Ctx {
         float *qerr = nullptr;    // [n_pad] ||v_hat - v|| rounded up
         float *qnorm = nullptr;   // [n_pad] ||v_hat|| rounded up
         float *qmax = nullptr;    // [2] max qerr, max qnorm (as floats, via bit-pattern atomics)
-        float *a32 = nullptr;     // [n_pad] per-round a_v = m_v - ||v_hat||^2, -inf past n
+        float *a32 = nullptr;     // [n_pad] per-round a_v = m_v - ||v_hat||^2 (+ point slack), -inf past n
+        float *w32 = nullptr;     // [n_pad] per-round w_v = 2 sqrt(m_v) + 2 ||v_hat - v|| (0 in plain mode)
         CUtensorMap tmA_V;  // candidate tiles over Vq (box 64 x 128)
         CUtensorMap tmB_V;  // point tiles over Vq (box 64 x 256)
         CUtensorMap tmA_C;  // candidate tiles over Cq
@@ -110,7 +111,8 @@ cudaError_t launch_refine(Ctx &c, const int *list, const int *count, int list_ca
                           int64_t chunk, int nchunks);
 cudaError_t launch_decide_n(Ctx &c, int nchunks, double eta);
 cudaError_t launch_collect_escalation(Ctx &c, double eta);
-cudaError_t launch_commit_n(Ctx &c, const double *esc_part, int nchunks, int32_t *out_idx, double *out_f);
+cudaError_t launch_commit_n(Ctx &c, const double *esc_part, int nchunks, int cap, int32_t *out_idx, double *out_f);
+cudaError_t launch_refine_overflow(Ctx &c, const int *list, const int *count, int cap, double *out_exact);
 cudaError_t launch_update(Ctx &c);
 cudaError_t launch_current_f(Ctx &c, double *d_out);
 cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,

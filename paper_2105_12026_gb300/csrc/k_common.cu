@@ -232,34 +232,132 @@ cudaError_t launch_merge_top(Ctx &c, int nblk, int K, double) {
 // ---------------------------------------------------------------------------
 // Exact gains of a candidate list (count read from device memory):
 //   out[e * nchunks + q] = sum_{v in chunk q} max(0, m_v - d(v, c_e))
-// with d exact in FP64.  Points whose FP32 screen distance already exceeds
-// m_v by more than its error bound contribute exactly 0 and skip the FP64
-// work.  Grid-stride over (entry, chunk) items.
+// with d exact in FP64.  A block takes a group of RB candidates (rows staged
+// in shared memory) and one V chunk; each point's row is read once for the
+// RB FP32 screen distances.  A pair whose screen distance exceeds m_v by
+// more than the screen's error bound contributes exactly 0 and skips the
+// FP64 work.  Grid-stride over (group, chunk) items.
 // ---------------------------------------------------------------------------
+constexpr int RB = 8;
+
+template <bool VEC4>
 __global__ void __launch_bounds__(256) k_refine(const float *__restrict__ V, int64_t n, int d,
                                                 const double *__restrict__ m64, const int *__restrict__ list,
                                                 const int *__restrict__ count, int cap, int64_t chunk, int nchunks,
                                                 double rho, double *__restrict__ out) {
-    extern __shared__ float cs[];
-    __shared__ double red[8];
-    int cnt = min(*count, cap);
-    int64_t items = (int64_t)cnt * nchunks;
+    extern __shared__ __align__(16) float cs[];  // [RB][d]
+    __shared__ double red[RB][8];
+    const int cnt = min(*count, cap);
+    const int groups = (cnt + RB - 1) / RB;
+    const int64_t items = (int64_t)groups * nchunks;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-        int e = (int)(it / nchunks);
-        int q = (int)(it % nchunks);
-        int cidx = list[e];
+        const int grp = (int)(it / nchunks);
+        const int q = (int)(it % nchunks);
+        const int e0 = grp * RB;
+        const int ng = min(RB, cnt - e0);
         __syncthreads();
-        for (int i = threadIdx.x; i < d; i += blockDim.x) cs[i] = V[(int64_t)cidx * d + i];
+        for (int x = threadIdx.x; x < RB * d; x += blockDim.x) {
+            int k = x / d, i = x % d;
+            cs[x] = k < ng ? V[(int64_t)list[e0 + k] * d + i] : 0.f;
+        }
         __syncthreads();
-        int64_t b = (int64_t)q * chunk, en = lmin(b + chunk, n);
-        double acc = 0.0;
+        const int64_t b = (int64_t)q * chunk, en = lmin(b + chunk, n);
+        double acc[RB];
+#pragma unroll
+        for (int k = 0; k < RB; ++k) acc[k] = 0.0;
         for (int64_t v = b + threadIdx.x; v < en; v += blockDim.x) {
             const float *vr = V + v * d;
-            double mv = m64[v];
-            float ds = screen_sqdist(vr, cs, d);
-            if ((double)ds * (1.0 - rho) >= mv) continue;  // exact distance >= m_v: term is 0
-            double de = exact_sqdist(vr, cs, d);
-            double t = mv - de;
+            float sd[RB];
+#pragma unroll
+            for (int k = 0; k < RB; ++k) sd[k] = 0.f;
+            if (VEC4) {
+                for (int i = 0; i < d; i += 4) {
+                    const float4 x = *reinterpret_cast<const float4 *>(vr + i);
+#pragma unroll
+                    for (int k = 0; k < RB; ++k) {
+                        const float4 c4 = *reinterpret_cast<const float4 *>(cs + k * d + i);
+                        float d0 = x.x - c4.x, d1 = x.y - c4.y, d2 = x.z - c4.z, d3 = x.w - c4.w;
+                        sd[k] = fmaf(d0, d0, sd[k]);
+                        sd[k] = fmaf(d1, d1, sd[k]);
+                        sd[k] = fmaf(d2, d2, sd[k]);
+                        sd[k] = fmaf(d3, d3, sd[k]);
+                    }
+                }
+            } else {
+                for (int i = 0; i < d; ++i) {
+                    const float x = vr[i];
+#pragma unroll
+                    for (int k = 0; k < RB; ++k) {
+                        float df = x - cs[k * d + i];
+                        sd[k] = fmaf(df, df, sd[k]);
+                    }
+                }
+            }
+            const double mv = m64[v];
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                if (k >= ng || (double)sd[k] * (1.0 - rho) >= mv) continue;  // exact distance >= m_v: term 0
+                const double de = exact_sqdist(vr, cs + k * d, d);
+                const double t = mv - de;
+                if (t > 0.0) acc[k] += t;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            double a = acc[k];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) red[k][w] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x < ng) {
+            double s = 0.0;
+            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += red[threadIdx.x][ww];
+            out[(int64_t)(e0 + threadIdx.x) * nchunks + q] = s;
+        }
+    }
+}
+
+cudaError_t launch_refine(Ctx &c, const int *list, const int *count, int list_cap, double *out, int64_t chunk,
+                          int nchunks) {
+    const double rho = (double)(c.d + 4) * ldexp(1.0, -24);
+    const int grid = c.num_sms * 4;
+    const size_t sm = sizeof(float) * (size_t)c.d * RB;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    if (c.d % 4 == 0)
+        k_refine<true><<<grid, 256, sm, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, list_cap, chunk, nchunks, rho,
+                                                    out);
+    else
+        k_refine<false><<<grid, 256, sm, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, list_cap, chunk, nchunks,
+                                                     rho, out);
+    return cudaGetLastError();
+}
+
+// Escalated candidates beyond the chunked buffer's capacity: one block per
+// candidate over all of V, result written directly.  No work in the usual
+// case (count <= cap).
+__global__ void __launch_bounds__(256) k_refine_overflow(const float *__restrict__ V, int64_t n, int d,
+                                                         const double *__restrict__ m64, const int *__restrict__ list,
+                                                         const int *__restrict__ count, int cap, double rho,
+                                                         double *__restrict__ out_exact, double inv_n) {
+    extern __shared__ float cs1[];
+    __shared__ double red[8];
+    const int cnt = *count;
+    for (int e = cap + blockIdx.x; e < cnt; e += gridDim.x) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < d; i += blockDim.x) cs1[i] = V[(int64_t)list[e] * d + i];
+        __syncthreads();
+        double acc = 0.0;
+        for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
+            const float *vr = V + v * d;
+            const double mv = m64[v];
+            if ((double)screen_sqdist(vr, cs1, d) * (1.0 - rho) >= mv) continue;
+            const double t = mv - exact_sqdist(vr, cs1, d);
             if (t > 0.0) acc += t;
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -267,18 +365,16 @@ __global__ void __launch_bounds__(256) k_refine(const float *__restrict__ V, int
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-            out[(int64_t)e * nchunks + q] = s;
+            for (int w = 0; w < 8; ++w) s += red[w];
+            out_exact[e] = s * inv_n;
         }
     }
 }
 
-cudaError_t launch_refine(Ctx &c, const int *list, const int *count, int list_cap, double *out, int64_t chunk,
-                          int nchunks) {
-    double rho = (double)(c.d + 4) * ldexp(1.0, -24);
-    int grid = kNumSMsHint * 4;
-    size_t sm = sizeof(float) * (size_t)c.d;
-    k_refine<<<grid, 256, sm, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, list_cap, chunk, nchunks, rho, out);
+cudaError_t launch_refine_overflow(Ctx &c, const int *list, const int *count, int cap, double *out_exact) {
+    const double rho = (double)(c.d + 4) * ldexp(1.0, -24);
+    k_refine_overflow<<<c.num_sms * 2, 256, sizeof(float) * (size_t)c.d, c.stream>>>(
+        c.V32, c.n, c.d, c.m64, list, count, cap, rho, out_exact, 1.0 / (double)c.n);
     return cudaGetLastError();
 }
 
@@ -351,18 +447,23 @@ cudaError_t launch_collect_escalation(Ctx &c, double eta) {
 }
 
 // Final pick: best of the top list and the escalated list, then commit.
-__global__ void k_commit(const double *__restrict__ esc_part, int nchunks, double inv_n, const int *__restrict__ esc_idx,
-                         double *__restrict__ esc_exact, uint8_t *__restrict__ sel, int64_t n, int32_t *__restrict__ out_idx,
-                         double *__restrict__ out_f, DevState *st) {
+__global__ void k_commit(const double *__restrict__ esc_part, int nchunks, int cap, double inv_n,
+                         const int *__restrict__ esc_idx, double *__restrict__ esc_exact, uint8_t *__restrict__ sel,
+                         int64_t n, int32_t *__restrict__ out_idx, double *__restrict__ out_f, DevState *st) {
     double bv = st->pick_gain;
     int bi = st->pick;
     if (st->need_esc) {
         int cnt = st->esc_count;
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-            double s = 0.0;
-            for (int q = 0; q < nchunks; ++q) s += esc_part[(int64_t)e * nchunks + q];
-            s *= inv_n;
-            esc_exact[e] = s;
+            double s;
+            if (e < cap) {
+                s = 0.0;
+                for (int q = 0; q < nchunks; ++q) s += esc_part[(int64_t)e * nchunks + q];
+                s *= inv_n;
+                esc_exact[e] = s;
+            } else {
+                s = esc_exact[e];  // written by the overflow kernel
+            }
             if (better(s, esc_idx[e], bv, bi)) {
                 bv = s;
                 bi = esc_idx[e];
@@ -459,8 +560,8 @@ cudaError_t launch_decide_n(Ctx &c, int nchunks, double eta) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_commit_n(Ctx &c, const double *esc_part, int nchunks, int32_t *out_idx, double *out_f) {
-    k_commit<<<1, 256, 0, c.stream>>>(esc_part, nchunks, 1.0 / (double)c.n, c.esc_idx, c.esc_exact, c.sel, c.n,
+cudaError_t launch_commit_n(Ctx &c, const double *esc_part, int nchunks, int cap, int32_t *out_idx, double *out_f) {
+    k_commit<<<1, 256, 0, c.stream>>>(esc_part, nchunks, cap, 1.0 / (double)c.n, c.esc_idx, c.esc_exact, c.sel, c.n,
                                       out_idx, out_f, c.st);
     return cudaGetLastError();
 }

@@ -5,24 +5,30 @@
 // rows, and the epilogue turns every entry into one term of
 //     gain(c) = (1/n) sum_v max(0, m_v - d(v, c))
 // through the norm expansion d_hat = ||v_hat||^2 + ||c_hat||^2 - 2 D:
-//     t = 2 D + a_v + b_c,   a_v = m_v - ||v_hat||^2,   b_c = -||c_hat||^2 (+ slack)
+//     t = 2 D + a_v + dc * w_v + b_c,
+//     a_v = m_v - ||v_hat||^2 (+ slack),   b_c = -||c_hat||^2 (+ slack)
 // then max(0, t) is summed over the 128 columns a thread owns in FP32 and
 // over tiles in FP64.  Candidates sit on the lane axis so each thread's
 // sum over V stays in its own registers (no shuffles).
 //
-// Greedy runs this kernel in upper-bound mode: b_c carries a per-candidate
-// slack E_c that bounds, for every pair that can contribute (d(v,c) < m_v <=
-// M = max_v m_v), the difference between the exact distance and the
-// computed one:
-//   quantisation  | ||v_hat-c_hat||^2 - ||v-c||^2 | <= D(2 sqrt(M) + D),
-//                 D = max_v ||v_hat - v|| + ||c_hat - c||;
-//   accumulation  2 |D_tc - v_hat.c_hat| <= 2 gamma ||v_hat|| ||c_hat||,
-//                 gamma = K 2^-20 (FP32 accumulation, generous);
-//   epilogue      two FP32 roundings of values bounded by Z, 2^-22 Z.
-// a_v is rounded up, so every term is >= the exact term and the sum is a
-// rigorous upper bound on the exact gain, up to the relative error of the
-// FP32 partial sums (accounted for by the caller's eta).
-//
+// Greedy runs this kernel in upper-bound mode.  For a pair (v, c) that can
+// contribute to the exact gain, d(v, c) < m_v, so ||v - c|| < sqrt(m_v), and
+// with e = (v_hat - v) - (c_hat - c), |e| <= dv + dc (dv = ||v_hat - v||):
+//   | ||v_hat - c_hat||^2 - ||v - c||^2 | = |2 (v - c).e + |e|^2|
+//                                        <= (dv + dc)(2 sqrt(m_v) + dv + dc)
+//   = [dv (2 sqrt(m_v) + dv)] + dc [2 sqrt(m_v) + 2 dv] + dc^2.
+// The first bracket depends on v only and is added to a_v; the last term on
+// c only and goes to b_c; the cross term is dc * w_v, one FMA per entry.
+// Further slack in b_c: the FP32 accumulation of the tensor core,
+// 2 gamma ||v_hat|| ||c_hat|| with gamma = (K/4 + 4) 2^-22 (one unit in the
+// last place per four products plus four, far above the behaviour reported
+// for NVIDIA tensor cores), bounded with max ||v_hat||; and the three FP32
+// roundings of the epilogue, 2^-22 Z_c with Z_c a bound on every
+// intermediate magnitude.  a_v and b_c are rounded up, so every term is >=
+// the exact term max(0, m_v - d(v, c)): the sum is a rigorous upper bound on
+// the exact gain, up to the relative error of the FP32 partial sums, which
+// the caller accounts for.
+
 // Warp roles (320 threads, one CTA per SM, persistent over work units):
 //   warp 0      TMA producer: candidate tile (A, resident per unit, two
 //               buffers) and a ring of point tiles (B stages)
@@ -68,6 +74,7 @@ struct TcArgs {
     uint32_t idesc;      // instruction descriptor
     int upper;           // 1: upper-bound mode (Greedy), 0: plain gains
     const float *a32;    // [n_vtiles * BN] a_v, -inf past n
+    const float *w32;    // [n_vtiles * BN] w_v
     const int *cand;     // candidate slot -> point index (nullptr: identity)
     const double *qn64;  // ||v_hat||^2
     const float *qerr;   // ||v_hat - v||
@@ -89,7 +96,7 @@ __host__ __device__ inline SmemLayout smem_layout(int DP, int nstages) {
     L.b_bytes = (uint32_t)BN * DP * 2;
     L.off_b = 2 * L.a_bytes;
     L.off_as = L.off_b + nstages * L.b_bytes;
-    L.off_comb = L.off_as + 2 * BN * 4;
+    L.off_comb = L.off_as + 4 * BN * 4;  // a_s[2][BN], w_s[2][BN]
     L.off_bar = L.off_comb + BM * 8;
     L.off_misc = L.off_bar + (2 * nstages + 8) * 8;
     L.total = L.off_misc + 64 + 1024;  // + alignment slack for the 1024-byte base
@@ -112,6 +119,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint8_t *sA = base;
     uint8_t *sB = base + L.off_b;
     float *a_s = reinterpret_cast<float *>(base + L.off_as);
+    float *w_s = a_s + 2 * BN;
     double *comb = reinterpret_cast<double *>(base + L.off_comb);
     uint64_t *full = reinterpret_cast<uint64_t *>(base + L.off_bar);
     uint64_t *empty = full + ns;
@@ -251,19 +259,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int64_t j = (int64_t)ct * BM + row;
             int cidx = -1;
             if (j < args.m) cidx = args.cand ? args.cand[j] : (int)j;
-            float bc = 0.f;
+            float bc = 0.f, dc = 0.f;
             if (cidx >= 0) {
                 const double qn = args.qn64[cidx];
                 if (args.upper) {
                     const double M = (double)__uint_as_float(*args.mmax_bits);
+                    const double sM = sqrt(M);
                     const double qe = (double)args.qerr[cidx];
                     const double qm = (double)args.qnorm[cidx];
-                    const double Dl = (double)args.qmax[0] + qe;
-                    const double Eq = Dl * (2.0 * sqrt(M) + Dl);
-                    const double Eacc = args.gamma * (double)args.qmax[1] * qm;
-                    const double Z = 2.0 * (double)args.qmax[1] * qm + (double)args.qmax[1] * (double)args.qmax[1] + M +
-                                     qn + Eq + 2.0 * Eacc;
-                    bc = __double2float_ru(-qn + Eq + 2.0 * Eacc + Z * inv_big);
+                    const double dmax = (double)args.qmax[0], qmax = (double)args.qmax[1];
+                    const double Eacc = 2.0 * args.gamma * qmax * qm;
+                    const double Z = 2.0 * qmax * qm + qmax * qmax + M + dmax * (2.0 * sM + dmax) +
+                                     qe * (2.0 * sM + 2.0 * dmax) + qn + qe * qe + Eacc;
+                    bc = __double2float_ru(-qn + qe * qe + Eacc + Z * inv_big);
+                    dc = __double2float_ru(qe);
                 } else {
                     bc = __double2float_rn(-qn);
                 }
@@ -272,6 +281,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int vt = vt0; vt < vt1; ++vt, ++t) {
                 const int b = t & 1;
                 a_s[b * BN + etid] = args.a32[(int64_t)vt * BN + etid];
+                w_s[b * BN + etid] = args.w32[(int64_t)vt * BN + etid];
                 tc::named_bar_sync(1, NEPI);
                 if (alive) {
                     // the TMEM loads below are warp-collective: decide per warp
@@ -285,6 +295,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc::tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * 128);
                 const float *ap = a_s + b * BN + half * 128;
+                const float *wp = w_s + b * BN + half * 128;
                 float s = 0.f;
 #pragma unroll
                 for (int rr = 0; rr < 2; ++rr) {
@@ -299,21 +310,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         if (lane == 0) tc::mbar_arrive(&t_empty[b]);
                     }
                     const float4 *ap4 = reinterpret_cast<const float4 *>(ap + rr * 64);
+                    const float4 *wp4 = reinterpret_cast<const float4 *>(wp + rr * 64);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
+                    for (int i = 0; i < 16; ++i) {
                         const float4 a4 = ap4[i];
-                        s += fmaxf(fmaf(2.f, __uint_as_float(r0[4 * i + 0]), a4.x) + bc, 0.f);
-                        s += fmaxf(fmaf(2.f, __uint_as_float(r0[4 * i + 1]), a4.y) + bc, 0.f);
-                        s += fmaxf(fmaf(2.f, __uint_as_float(r0[4 * i + 2]), a4.z) + bc, 0.f);
-                        s += fmaxf(fmaf(2.f, __uint_as_float(r0[4 * i + 3]), a4.w) + bc, 0.f);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 a4 = ap4[8 + i];
-                        s += fmaxf(fmaf(2.f, __uint_as_float(r1[4 * i + 0]), a4.x) + bc, 0.f);
-                        s += fmaxf(fmaf(2.f, __uint_as_float(r1[4 * i + 1]), a4.y) + bc, 0.f);
-                        s += fmaxf(fmaf(2.f, __uint_as_float(r1[4 * i + 2]), a4.z) + bc, 0.f);
-                        s += fmaxf(fmaf(2.f, __uint_as_float(r1[4 * i + 3]), a4.w) + bc, 0.f);
+                        const float4 w4 = wp4[i];
+                        const uint32_t *r = i < 8 ? &r0[4 * i] : &r1[4 * (i - 8)];
+                        s += fmaxf(fmaf(dc, w4.x, fmaf(2.f, __uint_as_float(r[0]), a4.x)) + bc, 0.f);
+                        s += fmaxf(fmaf(dc, w4.y, fmaf(2.f, __uint_as_float(r[1]), a4.y)) + bc, 0.f);
+                        s += fmaxf(fmaf(dc, w4.z, fmaf(2.f, __uint_as_float(r[2]), a4.z)) + bc, 0.f);
+                        s += fmaxf(fmaf(dc, w4.w, fmaf(2.f, __uint_as_float(r[3]), a4.w)) + bc, 0.f);
                     }
                 }
                 acc += (double)s;
@@ -362,8 +368,8 @@ __device__ __forceinline__ float from_q(uint16_t h, int prec) {
 
 __global__ void k_quantize(const float *__restrict__ V, int64_t n, int d, int64_t n_pad, int DP, int prec,
                            uint16_t *__restrict__ Vq, double *__restrict__ qn64, float *__restrict__ qerr,
-                           float *__restrict__ qnorm, float *__restrict__ a32, unsigned int *__restrict__ qmax_bits,
-                           int *__restrict__ err) {
+                           float *__restrict__ qnorm, float *__restrict__ a32, float *__restrict__ w32,
+                           unsigned int *__restrict__ qmax_bits, int *__restrict__ err) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
     uint16_t *dst = Vq + r * DP;
@@ -373,6 +379,7 @@ __global__ void k_quantize(const float *__restrict__ V, int64_t n, int d, int64_
         qerr[r] = 0.f;
         qnorm[r] = 0.f;
         a32[r] = -INFINITY;
+        w32[r] = 0.f;
         return;
     }
     const float *v = V + r * d;
@@ -401,19 +408,27 @@ __global__ void k_quantize(const float *__restrict__ V, int64_t n, int d, int64_
     atomicMax(&qmax_bits[1], __float_as_uint(qm));
 }
 
-// a_v = m_v - ||v_hat||^2 for every point (rounded up in upper-bound mode,
-// to nearest otherwise) and M = max_v m_v rounded up.
-__global__ void k_prep_tc(const double *__restrict__ m64, const double *__restrict__ qn64, int64_t n,
-                          float *__restrict__ a32, int upper, unsigned int *__restrict__ mmax_bits) {
+// Per-round point terms.  Upper-bound mode: a_v = m_v - ||v_hat||^2 +
+// dv (2 sqrt(m_v) + dv) and w_v = 2 sqrt(m_v) + 2 dv, both rounded up, and
+// M = max_v m_v rounded up.  Plain mode: a_v = m_v - ||v_hat||^2 rounded to
+// nearest and w_v = 0.
+__global__ void k_prep_tc(const double *__restrict__ m64, const double *__restrict__ qn64,
+                          const float *__restrict__ qerr, int64_t n, float *__restrict__ a32, float *__restrict__ w32,
+                          int upper, unsigned int *__restrict__ mmax_bits) {
     int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     float mx = 0.f;
     if (v < n) {
         double mv = m64[v];
         if (upper) {
-            a32[v] = __double2float_ru(__dsub_ru(mv, qn64[v]));
+            const double dv = (double)qerr[v];
+            const double sq = __dsqrt_ru(mv);
+            const double sv = __dmul_ru(dv, __dadd_ru(__dmul_ru(2.0, sq), dv));
+            a32[v] = __double2float_ru(__dadd_ru(__dsub_ru(mv, qn64[v]), sv));
+            w32[v] = __double2float_ru(__dadd_ru(__dmul_ru(2.0, sq), __dmul_ru(2.0, dv)));
             mx = __double2float_ru(mv);
         } else {
             a32[v] = __double2float_rn(mv - qn64[v]);
+            w32[v] = 0.f;
         }
     }
     if (!upper) return;
@@ -478,7 +493,7 @@ int pick_stages(int DP) {
 bool tc_supported(const Ctx &c) { return c.d <= 128; }
 
 void tc_free(Ctx &c) {
-    void *ptrs[] = {c.tc.Vq, c.tc.Cq, c.tc.qn64, c.tc.qerr, c.tc.qnorm, c.tc.qmax, c.tc.a32};
+    void *ptrs[] = {c.tc.Vq, c.tc.Cq, c.tc.qn64, c.tc.qerr, c.tc.qnorm, c.tc.qmax, c.tc.a32, c.tc.w32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c.tc = Ctx::Tc();
@@ -490,7 +505,7 @@ cudaError_t tc_quantize(Ctx &c) {
     if (e != cudaSuccess) return e;
     int th = 128;
     k_quantize<<<(unsigned)((T.n_pad + th - 1) / th), th, 0, c.stream>>>(
-        c.V32, c.n, c.d, T.n_pad, T.DP, T.prec, T.Vq, T.qn64, T.qerr, T.qnorm, T.a32,
+        c.V32, c.n, c.d, T.n_pad, T.DP, T.prec, T.Vq, T.qn64, T.qerr, T.qnorm, T.a32, T.w32,
         reinterpret_cast<unsigned int *>(T.qmax), &c.st->err);
     return cudaGetLastError();
 }
@@ -509,6 +524,7 @@ cudaError_t tc_setup(Ctx &c, int prec) {
         if ((e = cudaMalloc(&T.qnorm, rows * 4)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&T.qmax, 2 * 4)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&T.a32, rows * 4)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&T.w32, rows * 4)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Cq, 0, rows * T.DP * 2, c.stream)) != cudaSuccess) return e;
     }
     T.prec = prec;
@@ -521,8 +537,8 @@ cudaError_t tc_setup(Ctx &c, int prec) {
 
 cudaError_t launch_prep_tc(Ctx &c, bool upper) {
     int th = 256;
-    k_prep_tc<<<(unsigned)((c.n + th - 1) / th), th, 0, c.stream>>>(c.m64, c.tc.qn64, c.n, c.tc.a32, upper ? 1 : 0,
-                                                                     &c.st->mmax_bits);
+    k_prep_tc<<<(unsigned)((c.n + th - 1) / th), th, 0, c.stream>>>(c.m64, c.tc.qn64, c.tc.qerr, c.n, c.tc.a32,
+                                                                     c.tc.w32, upper ? 1 : 0, &c.st->mmax_bits);
     return cudaGetLastError();
 }
 
@@ -571,13 +587,14 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BM, BN);
     a.upper = upper ? 1 : 0;
     a.a32 = T.a32;
+    a.w32 = T.w32;
     a.cand = cand;
     a.qn64 = T.qn64;
     a.qerr = T.qerr;
     a.qnorm = T.qnorm;
     a.qmax = T.qmax;
     a.mmax_bits = &c.st->mmax_bits;
-    a.gamma = (double)DP * ldexp(1.0, -20);
+    a.gamma = ((double)DP / 4.0 + 4.0) * ldexp(1.0, -22);
     a.partial = c.partial;
     a.err = &c.st->err;
     const int units = a.n_ctiles * a.nchunks;
