@@ -64,17 +64,22 @@ struct Ctx {
         int prec = -1;            // precision Vq holds (EBC_BF16 / EBC_FP16), -1 = none
         int64_t n_pad = 0;        // n rounded up to the point tile (256)
         int DP = 0;               // d rounded up to the 64-element swizzle atom
-        uint16_t *Vq = nullptr;   // [n_pad, DP] quantised rows, zero padded
+        uint16_t *Vq = nullptr;   // [n_pad, DP] quantised rows v_hat (candidate operand), zero padded
+        uint16_t *Vq2 = nullptr;  // [n_pad, DP] 2 v_hat (point operand; exact scaling)
+        uint16_t *Aext = nullptr; // [n_pad, 16] bf16 candidate-side extension columns (static)
+        uint16_t *Bext = nullptr; // [n_pad, 16] bf16 point-side extension columns (per round)
         uint16_t *Cq = nullptr;   // [n_pad, DP] gathered candidate rows (ebc_gains with a list)
+        uint16_t *Cqx = nullptr;  // [n_pad, 16] gathered candidate extension rows
         double *qn64 = nullptr;   // [n_pad] ||v_hat||^2 (FP64)
         float *qerr = nullptr;    // [n_pad] ||v_hat - v|| rounded up
         float *qnorm = nullptr;   // [n_pad] ||v_hat|| rounded up
         float *qmax = nullptr;    // [2] max qerr, max qnorm (as floats, via bit-pattern atomics)
-        float *a32 = nullptr;     // [n_pad] per-round a_v = m_v - ||v_hat||^2 (+ point slack), -inf past n
-        float *w32 = nullptr;     // [n_pad] per-round w_v = 2 sqrt(m_v) + 2 ||v_hat - v|| (0 in plain mode)
-        CUtensorMap tmA_V;  // candidate tiles over Vq (box 64 x 128)
-        CUtensorMap tmB_V;  // point tiles over Vq (box 64 x 256)
-        CUtensorMap tmA_C;  // candidate tiles over Cq
+        CUtensorMap tmA_V;        // candidate tiles over Vq (box 64 x 128)
+        CUtensorMap tmB_V;        // point tiles over Vq2 (box 64 x 256)
+        CUtensorMap tmA_C;        // candidate tiles over Cq
+        CUtensorMap tmAx_V;       // candidate extension over Aext (box 16 x 128)
+        CUtensorMap tmAx_C;       // candidate extension over Cqx
+        CUtensorMap tmBx;         // point extension over Bext (box 16 x 256)
     } tc;
     int num_sms = 152;
 

@@ -1,37 +1,39 @@
 // Bulk marginal gains on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // For a tile of 128 candidates c (TMEM lanes) and 256 points v (TMEM
-// columns) the tensor core forms D = C_hat . V_hat^T in FP32 from BF16/FP16
-// rows, and the epilogue turns every entry into one term of
-//     gain(c) = (1/n) sum_v max(0, m_v - d(v, c))
-// through the norm expansion d_hat = ||v_hat||^2 + ||c_hat||^2 - 2 D:
-//     t = 2 D + a_v + dc * w_v + b_c,
-//     a_v = m_v - ||v_hat||^2 (+ slack),   b_c = -||c_hat||^2 (+ slack)
-// then max(0, t) is summed over the 128 columns a thread owns in FP32 and
-// over tiles in FP64.  Candidates sit on the lane axis so each thread's
-// sum over V stays in its own registers (no shuffles).
+// columns) one accumulator receives, entirely from the tensor core,
+//     t(c, v) = c_hat . (2 v_hat) + X_c . Y_v
+// where the 16 "extension" columns X (per candidate, static) and Y (per
+// point, rewritten every round) carry the remaining terms of
+//     m_v - d(v, c) ~= 2 c_hat.v_hat - ||c_hat||^2 + (m_v - ||v_hat||^2)
+// plus, in upper-bound mode, a rigorous slack (below), each term split into
+// two or three bf16 pieces whose sum is never below the term:
+//     X = [q q q | s s | al al al' al' | 1 1 1 | 0..]   q = -||c_hat||^2, s = slack_c,
+//     Y = [1 1 1 | sg sg | w w' w w'  | a a a | 0..]    al = ||c_hat - c||, a = a_v,
+// giving q + sg*s + (al + al')(w + w') + a.  The epilogue only forms
+// sum_v max(0, t) over the 128 columns a thread owns (FP32), then over tiles
+// (FP64).  Candidates sit on the lane axis, so a thread's sum over V stays in
+// its registers.  Scaling v_hat by 2 is exact.
 //
-// Greedy runs this kernel in upper-bound mode.  For a pair (v, c) that can
-// contribute to the exact gain, d(v, c) < m_v, so ||v - c|| < sqrt(m_v), and
-// with e = (v_hat - v) - (c_hat - c), |e| <= dv + dc (dv = ||v_hat - v||):
+// Upper-bound mode (Greedy, sg = 1).  For a pair that can contribute to the
+// exact gain, d(v, c) < m_v, so ||v - c|| < sqrt(m_v); with dv = ||v_hat - v||,
+// dc = ||c_hat - c|| and e = (v_hat - v) - (c_hat - c), |e| <= dv + dc and
 //   | ||v_hat - c_hat||^2 - ||v - c||^2 | = |2 (v - c).e + |e|^2|
-//                                        <= (dv + dc)(2 sqrt(m_v) + dv + dc)
-//   = [dv (2 sqrt(m_v) + dv)] + dc [2 sqrt(m_v) + 2 dv] + dc^2.
-// The first bracket depends on v only and is added to a_v; the last term on
-// c only and goes to b_c; the cross term is dc * w_v, one FMA per entry.
-// Further slack in b_c: the FP32 accumulation of the tensor core,
-// 2 gamma ||v_hat|| ||c_hat|| with gamma = (K/4 + 4) 2^-22 (one unit in the
-// last place per four products plus four, far above the behaviour reported
-// for NVIDIA tensor cores), bounded with max ||v_hat||; and the three FP32
-// roundings of the epilogue, 2^-22 Z_c with Z_c a bound on every
-// intermediate magnitude.  a_v and b_c are rounded up, so every term is >=
-// the exact term max(0, m_v - d(v, c)): the sum is a rigorous upper bound on
-// the exact gain, up to the relative error of the FP32 partial sums, which
-// the caller accounts for.
-
+//       <= dv (2 sqrt(m_v) + dv) + dc (2 sqrt(m_v) + 2 dv) + dc^2.
+// The first part goes to a_v, the cross part is al * w with
+// w = 2 sqrt(m_v) + 2 dv, and dc^2 goes to s_c.  The FP32 accumulation of the
+// tensor core is bounded by gamma * sum |terms| with gamma = (K/4 + 4) 2^-22
+// (one unit in the last place per four products plus four, far above the
+// behaviour reported for NVIDIA tensor cores); its candidate part is in s_c,
+// its point part in a_v.  Every piece is rounded so the sums are upper bounds,
+// hence each max(0, t) >= max(0, m_v - d(v, c)) and the gain is a rigorous
+// upper bound up to the relative error of the FP32 partial sums, which the
+// caller accounts for.  Plain mode (sg = 0, w = 0, a rounded to nearest)
+// gives the raw low-precision gain.
+//
 // Warp roles (320 threads, one CTA per SM, persistent over work units):
-//   warp 0      TMA producer: candidate tile (A, resident per unit, two
-//               buffers) and a ring of point tiles (B stages)
+//   warp 0      TMA producer: candidate tile (A, two buffers) and a ring of
+//               point tiles (B stages), each with its extension tile
 //   warp 1      TMEM allocator and single-thread MMA issuer
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, warps
 //               2-5 the first 128 columns of an accumulator, 6-9 the rest
@@ -58,10 +60,12 @@ namespace {
 constexpr int BM = 128;          // candidates per tile
 constexpr int BN = 256;          // points per tile
 constexpr int KATOM = 64;        // 16-bit elements per 128-byte swizzle atom
+constexpr int KEXT = 16;         // extension columns (one MMA K step)
 constexpr int NTHREADS = 320;
 constexpr int NEPI = 256;        // epilogue threads
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_LIMIT = 227 * 1024;
+constexpr float PAD_A = -1.0e30f;  // a_v of padding points: every term is 0
 
 struct TcArgs {
     int64_t m;           // candidates
@@ -69,34 +73,26 @@ struct TcArgs {
     int n_ctiles;        // candidate tiles covering m
     int nchunks;         // V chunks
     int vt_per_chunk;    // point tiles per chunk
-    int DP;              // padded K
+    int DP;              // padded K of the main part
     int nstages;         // B ring depth
-    uint32_t idesc;      // instruction descriptor
-    int upper;           // 1: upper-bound mode (Greedy), 0: plain gains
-    const float *a32;    // [n_vtiles * BN] a_v, -inf past n
-    const float *w32;    // [n_vtiles * BN] w_v
-    const int *cand;     // candidate slot -> point index (nullptr: identity)
-    const double *qn64;  // ||v_hat||^2
-    const float *qerr;   // ||v_hat - v||
-    const float *qnorm;  // ||v_hat||
-    const float *qmax;   // [2] max qerr, max qnorm
-    const unsigned int *mmax_bits;  // max_v m_v, FP32 bits
-    double gamma;        // accumulation error factor
+    uint32_t idesc;      // instruction descriptor, main part
+    uint32_t idesc_ext;  // instruction descriptor, extension (bf16)
     double *partial;     // [nchunks][m]
     int *err;            // device error word
 };
 
 struct SmemLayout {
-    uint32_t a_bytes, b_bytes, off_b, off_as, off_comb, off_bar, off_misc, total;
+    uint32_t a_main, a_bytes, b_main, b_bytes, off_b, off_comb, off_bar, off_misc, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int DP, int nstages) {
     SmemLayout L;
-    L.a_bytes = (uint32_t)BM * DP * 2;
-    L.b_bytes = (uint32_t)BN * DP * 2;
+    L.a_main = (uint32_t)BM * DP * 2;
+    L.a_bytes = L.a_main + BM * KEXT * 2;
+    L.b_main = (uint32_t)BN * DP * 2;
+    L.b_bytes = L.b_main + BN * KEXT * 2;
     L.off_b = 2 * L.a_bytes;
-    L.off_as = L.off_b + nstages * L.b_bytes;
-    L.off_comb = L.off_as + 4 * BN * 4;  // a_s[2][BN], w_s[2][BN]
+    L.off_comb = L.off_b + nstages * L.b_bytes;
     L.off_bar = L.off_comb + BM * 8;
     L.off_misc = L.off_bar + (2 * nstages + 8) * 8;
     L.total = L.off_misc + 64 + 1024;  // + alignment slack for the 1024-byte base
@@ -108,18 +104,29 @@ __device__ __forceinline__ void record_timeout(int *err, volatile int *abort) {
     atomicCAS(err, 0, (int)EBC_ETIMEOUT);
 }
 
+__device__ __forceinline__ float relu_sum32(const uint32_t (&r)[32]) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; i += 4) {
+        s0 += fmaxf(__uint_as_float(r[i + 0]), 0.f);
+        s1 += fmaxf(__uint_as_float(r[i + 1]), 0.f);
+        s2 += fmaxf(__uint_as_float(r[i + 2]), 0.f);
+        s3 += fmaxf(__uint_as_float(r[i + 3]), 0.f);
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_gains_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
+    k_gains_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+               const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ns = args.nstages;
     const SmemLayout L = smem_layout(args.DP, ns);
     uint8_t *sA = base;
     uint8_t *sB = base + L.off_b;
-    float *a_s = reinterpret_cast<float *>(base + L.off_as);
-    float *w_s = a_s + 2 * BN;
     double *comb = reinterpret_cast<double *>(base + L.off_comb);
     uint64_t *full = reinterpret_cast<uint64_t *>(base + L.off_bar);
     uint64_t *empty = full + ns;
@@ -130,9 +137,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + L.off_misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(base + L.off_misc + 4);
     // drain bookkeeping: parity of the last issued phase, -1 if none
-    int *last_full = reinterpret_cast<int *>(base + L.off_misc + 8);      // [ns] (ns <= 8)
-    int *last_afull = last_full + 8;                                        // [2]
-    int *last_tfull = last_afull + 2;                                       // [2]
+    int *last_full = reinterpret_cast<int *>(base + L.off_misc + 8);  // [ns] (ns <= 8)
+    int *last_afull = last_full + 8;                                    // [2]
+    int *last_tfull = last_afull + 2;                                   // [2]
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -169,7 +176,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             tc::tma_prefetch_desc(&tmA);
+            tc::tma_prefetch_desc(&tmAx);
             tc::tma_prefetch_desc(&tmB);
+            tc::tma_prefetch_desc(&tmBx);
             int g = 0, ua = 0;
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
                 const int ct = u / args.nchunks, ch = u % args.nchunks;
@@ -180,9 +189,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     record_timeout(args.err, abort_flag);
                     break;
                 }
+                uint8_t *abuf = sA + ab * L.a_bytes;
                 tc::mbar_arrive_expect_tx(&a_full[ab], L.a_bytes);
                 for (int j = 0; j < katoms; ++j)
-                    tc::tma_load_2d(sA + ab * L.a_bytes + j * (BM * 128), &tmA, &a_full[ab], j * KATOM, ct * BM);
+                    tc::tma_load_2d(abuf + j * (BM * 128), &tmA, &a_full[ab], j * KATOM, ct * BM);
+                tc::tma_load_2d(abuf + L.a_main, &tmAx, &a_full[ab], 0, ct * BM);
                 last_afull[ab] = (ua >> 1) & 1;
                 bool ok = true;
                 for (int vt = vt0; vt < vt1; ++vt, ++g) {
@@ -193,9 +204,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         ok = false;
                         break;
                     }
+                    uint8_t *bbuf = sB + s * L.b_bytes;
                     tc::mbar_arrive_expect_tx(&full[s], L.b_bytes);
                     for (int j = 0; j < katoms; ++j)
-                        tc::tma_load_2d(sB + s * L.b_bytes + j * (BN * 128), &tmB, &full[s], j * KATOM, vt * BN);
+                        tc::tma_load_2d(bbuf + j * (BN * 128), &tmB, &full[s], j * KATOM, vt * BN);
+                    tc::tma_load_2d(bbuf + L.b_main, &tmBx, &full[s], 0, vt * BN);
                     last_full[s] = ph;
                 }
                 if (!ok) break;
@@ -234,6 +247,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const uint64_t bd = tc::sdesc_sw128(b0 + j * (BN * 128) + w * 32);
                         tc::mma_f16(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
                     }
+                    tc::mma_f16(d_tmem, tc::sdesc_sw32(a0 + L.a_main), tc::sdesc_sw32(b0 + L.b_main), args.idesc_ext,
+                                1u);
                     tc::mma_commit(&empty[s]);
                     tc::mma_commit(&t_full[b]);
                     last_tfull[b] = (t >> 1) & 1;
@@ -244,12 +259,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int ew = warp - 2;           // 0..7
-        const int q = warp & 3;            // TMEM lane quarter this warp may access
-        const int half = ew >> 2;          // column half of the accumulator
-        const int row = q * 32 + lane;     // candidate row within the tile
-        const int etid = threadIdx.x - 64; // 0..255
-        const double inv_big = ldexp(1.0, -22);
+        const int ew = warp - 2;        // 0..7
+        const int q = warp & 3;         // TMEM lane quarter this warp may access
+        const int half = ew >> 2;       // column half of the accumulator
+        const int row = q * 32 + lane;  // candidate row within the tile
         int t = 0;
         bool alive = true;
         for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
@@ -257,32 +270,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int vt0 = ch * args.vt_per_chunk;
             const int vt1 = min(vt0 + args.vt_per_chunk, args.n_vtiles);
             const int64_t j = (int64_t)ct * BM + row;
-            int cidx = -1;
-            if (j < args.m) cidx = args.cand ? args.cand[j] : (int)j;
-            float bc = 0.f, dc = 0.f;
-            if (cidx >= 0) {
-                const double qn = args.qn64[cidx];
-                if (args.upper) {
-                    const double M = (double)__uint_as_float(*args.mmax_bits);
-                    const double sM = sqrt(M);
-                    const double qe = (double)args.qerr[cidx];
-                    const double qm = (double)args.qnorm[cidx];
-                    const double dmax = (double)args.qmax[0], qmax = (double)args.qmax[1];
-                    const double Eacc = 2.0 * args.gamma * qmax * qm;
-                    const double Z = 2.0 * qmax * qm + qmax * qmax + M + dmax * (2.0 * sM + dmax) +
-                                     qe * (2.0 * sM + 2.0 * dmax) + qn + qe * qe + Eacc;
-                    bc = __double2float_ru(-qn + qe * qe + Eacc + Z * inv_big);
-                    dc = __double2float_ru(qe);
-                } else {
-                    bc = __double2float_rn(-qn);
-                }
-            }
             double acc = 0.0;
             for (int vt = vt0; vt < vt1; ++vt, ++t) {
                 const int b = t & 1;
-                a_s[b * BN + etid] = args.a32[(int64_t)vt * BN + etid];
-                w_s[b * BN + etid] = args.w32[(int64_t)vt * BN + etid];
-                tc::named_bar_sync(1, NEPI);
                 if (alive) {
                     // the TMEM loads below are warp-collective: decide per warp
                     const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[b], (t >> 1) & 1, abort_flag));
@@ -294,40 +284,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!alive) continue;
                 tc::tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * 128);
-                const float *ap = a_s + b * BN + half * 128;
-                const float *wp = w_s + b * BN + half * 128;
-                float s = 0.f;
-#pragma unroll
-                for (int rr = 0; rr < 2; ++rr) {
-                    uint32_t r0[32], r1[32];
-                    tc::tmem_ld32(taddr + rr * 64, r0);
-                    tc::tmem_ld32(taddr + rr * 64 + 32, r1);
-                    tc::tmem_ld_wait();
-                    if (rr == 1) {
-                        // this warp is done with accumulator b
-                        tc::tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&t_empty[b]);
-                    }
-                    const float4 *ap4 = reinterpret_cast<const float4 *>(ap + rr * 64);
-                    const float4 *wp4 = reinterpret_cast<const float4 *>(wp + rr * 64);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float4 a4 = ap4[i];
-                        const float4 w4 = wp4[i];
-                        const uint32_t *r = i < 8 ? &r0[4 * i] : &r1[4 * (i - 8)];
-                        s += fmaxf(fmaf(dc, w4.x, fmaf(2.f, __uint_as_float(r[0]), a4.x)) + bc, 0.f);
-                        s += fmaxf(fmaf(dc, w4.y, fmaf(2.f, __uint_as_float(r[1]), a4.y)) + bc, 0.f);
-                        s += fmaxf(fmaf(dc, w4.z, fmaf(2.f, __uint_as_float(r[2]), a4.z)) + bc, 0.f);
-                        s += fmaxf(fmaf(dc, w4.w, fmaf(2.f, __uint_as_float(r[3]), a4.w)) + bc, 0.f);
-                    }
-                }
+                uint32_t r0[32], r1[32], r2[32], r3[32];
+                tc::tmem_ld32(taddr, r0);
+                tc::tmem_ld32(taddr + 32, r1);
+                tc::tmem_ld_wait();
+                tc::tmem_ld32(taddr + 64, r2);
+                tc::tmem_ld32(taddr + 96, r3);
+                float s = relu_sum32(r0) + relu_sum32(r1);
+                tc::tmem_ld_wait();
+                // this warp is done with accumulator b
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&t_empty[b]);
+                s += relu_sum32(r2) + relu_sum32(r3);
                 acc += (double)s;
             }
             // combine the two column halves in a fixed order
             if (half == 1) comb[row] = acc;
             tc::named_bar_sync(2, NEPI);
-            if (half == 0 && cidx >= 0 && alive) args.partial[(int64_t)ch * args.m + j] = acc + comb[row];
+            if (half == 0 && j < args.m && alive) args.partial[(int64_t)ch * args.m + j] = acc + comb[row];
             tc::named_bar_sync(2, NEPI);
         }
     }
@@ -353,10 +328,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Quantisation: v_hat = RN(v) in bf16 or fp16, zero padded to DP; FP64
-// ||v_hat||^2, the quantisation error norm ||v_hat - v|| and ||v_hat||
-// (both rounded up) and their maxima.  One thread per row.
+// bf16 pieces.  hi is the nearest bf16; each residual is exact in FP64
+// (Sterbenz); the last piece is rounded up (or to nearest) so that the sum of
+// the pieces is >= x with an error of about 2^-24 |x|.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 h) { return __bfloat16_as_ushort(h); }
+
+__device__ __forceinline__ void split3(double x, bool up, uint16_t *out) {
+    __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+    double r1 = x - (double)__bfloat162float(hi);
+    __nv_bfloat16 mid = __float2bfloat16_rn((float)r1);
+    double r2 = r1 - (double)__bfloat162float(mid);
+    __nv_bfloat16 lo = up ? __float2bfloat16_ru(__double2float_ru(r2)) : __float2bfloat16_rn((float)r2);
+    out[0] = bf16_bits(hi);
+    out[1] = bf16_bits(mid);
+    out[2] = bf16_bits(lo);
+}
+
+__device__ __forceinline__ void split2_up(double x, uint16_t *out) {
+    __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+    double r1 = x - (double)__bfloat162float(hi);
+    __nv_bfloat16 lo = __float2bfloat16_ru(__double2float_ru(r1));
+    out[0] = bf16_bits(hi);
+    out[1] = bf16_bits(lo);
+}
+
 __device__ __forceinline__ uint16_t to_q(float x, int prec) {
     if (prec == EBC_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
     return __half_as_ushort(__float2half_rn(x));
@@ -366,20 +362,22 @@ __device__ __forceinline__ float from_q(uint16_t h, int prec) {
     return __half2float(__ushort_as_half(h));
 }
 
+// Quantisation: v_hat = RN(v) in bf16 or fp16 (zero padded to DP) and 2 v_hat;
+// FP64 ||v_hat||^2, ||v_hat - v|| and ||v_hat|| (rounded up) and their maxima.
+// One thread per row, sums in index order.
 __global__ void k_quantize(const float *__restrict__ V, int64_t n, int d, int64_t n_pad, int DP, int prec,
-                           uint16_t *__restrict__ Vq, double *__restrict__ qn64, float *__restrict__ qerr,
-                           float *__restrict__ qnorm, float *__restrict__ a32, float *__restrict__ w32,
-                           unsigned int *__restrict__ qmax_bits, int *__restrict__ err) {
+                           uint16_t *__restrict__ Vq, uint16_t *__restrict__ Vq2, double *__restrict__ qn64,
+                           float *__restrict__ qerr, float *__restrict__ qnorm, unsigned int *__restrict__ qmax_bits,
+                           int *__restrict__ err) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
     uint16_t *dst = Vq + r * DP;
+    uint16_t *dst2 = Vq2 + r * DP;
     if (r >= n) {
-        for (int i = 0; i < DP; ++i) dst[i] = 0;
+        for (int i = 0; i < DP; ++i) dst[i] = dst2[i] = 0;
         qn64[r] = 0.0;
         qerr[r] = 0.f;
         qnorm[r] = 0.f;
-        a32[r] = -INFINITY;
-        w32[r] = 0.f;
         return;
     }
     const float *v = V + r * d;
@@ -388,9 +386,10 @@ __global__ void k_quantize(const float *__restrict__ V, int64_t n, int d, int64_
     for (int i = 0; i < DP; ++i) {
         float x = i < d ? v[i] : 0.f;
         uint16_t h = to_q(x, prec);
-        dst[i] = h;
         float xq = from_q(h, prec);
-        finite = finite && isfinite(xq);
+        dst[i] = h;
+        dst2[i] = to_q(2.f * xq, prec);  // exact: a power-of-two scaling
+        finite = finite && isfinite(2.f * xq);
         double xd = (double)xq;
         qn = __dadd_rn(qn, __dmul_rn(xd, xd));
         double e = xd - (double)x;
@@ -398,8 +397,8 @@ __global__ void k_quantize(const float *__restrict__ V, int64_t n, int d, int64_
     }
     if (!finite) atomicCAS(err, 0, (int)EBC_EINVAL);
     qn64[r] = qn;
-    // the sums above carry at most (DP + 1) relative rounding errors of
-    // 2^-53; pad the square roots by 2^-40 relative before rounding up
+    // the sums above carry at most (DP + 1) relative roundings of 2^-53;
+    // pad the square roots by 2^-40 relative before rounding up
     float qe = __double2float_ru(__dsqrt_ru(e2) * (1.0 + ldexp(1.0, -40)));
     float qm = __double2float_ru(__dsqrt_ru(qn) * (1.0 + ldexp(1.0, -40)));
     qerr[r] = qe;
@@ -408,47 +407,105 @@ __global__ void k_quantize(const float *__restrict__ V, int64_t n, int d, int64_
     atomicMax(&qmax_bits[1], __float_as_uint(qm));
 }
 
-// Per-round point terms.  Upper-bound mode: a_v = m_v - ||v_hat||^2 +
-// dv (2 sqrt(m_v) + dv) and w_v = 2 sqrt(m_v) + 2 dv, both rounded up, and
-// M = max_v m_v rounded up.  Plain mode: a_v = m_v - ||v_hat||^2 rounded to
-// nearest and w_v = 0.
-__global__ void k_prep_tc(const double *__restrict__ m64, const double *__restrict__ qn64,
-                          const float *__restrict__ qerr, int64_t n, float *__restrict__ a32, float *__restrict__ w32,
-                          int upper, unsigned int *__restrict__ mmax_bits) {
-    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    float mx = 0.f;
-    if (v < n) {
-        double mv = m64[v];
-        if (upper) {
-            const double dv = (double)qerr[v];
-            const double sq = __dsqrt_ru(mv);
-            const double sv = __dmul_ru(dv, __dadd_ru(__dmul_ru(2.0, sq), dv));
-            a32[v] = __double2float_ru(__dadd_ru(__dsub_ru(mv, qn64[v]), sv));
-            w32[v] = __double2float_ru(__dadd_ru(__dmul_ru(2.0, sq), __dmul_ru(2.0, dv)));
-            mx = __double2float_ru(mv);
-        } else {
-            a32[v] = __double2float_rn(mv - qn64[v]);
-            w32[v] = 0.f;
-        }
+// Static candidate extension X and the padding rows of the point extension.
+__global__ void k_make_aext(int64_t n, int64_t n_pad, const double *__restrict__ qn64, const float *__restrict__ qerr,
+                            const float *__restrict__ qnorm, const float *__restrict__ qmax, double gamma,
+                            uint16_t *__restrict__ Aext, uint16_t *__restrict__ Bext) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    __align__(16) uint16_t row[KEXT];
+    for (int i = 0; i < KEXT; ++i) row[i] = 0;
+    const uint16_t one = bf16_bits(__float2bfloat16_rn(1.f));
+    if (r < n) {
+        const double qn = qn64[r], dc = (double)qerr[r], qm = (double)qnorm[r], qmx = (double)qmax[1];
+        // s_c = dc^2 + gamma (2 max||v_hat|| ||c_hat|| + ||c_hat||^2 + 1)
+        const double sc = __dadd_ru(__dmul_ru(dc, dc),
+                                    __dmul_ru(gamma, __dadd_ru(__dadd_ru(__dmul_ru(2.0 * qmx, qm), qn), 1.0)));
+        split3(-qn, true, row + 0);
+        split2_up(sc, row + 3);
+        uint16_t al[2];
+        split2_up(dc, al);
+        row[5] = al[0];
+        row[6] = al[0];
+        row[7] = al[1];
+        row[8] = al[1];
+        row[9] = row[10] = row[11] = one;
     }
-    if (!upper) return;
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(mmax_bits, __float_as_uint(mx));
+    uint4 *dst = reinterpret_cast<uint4 *>(Aext + r * KEXT);
+    const uint4 *src = reinterpret_cast<const uint4 *>(row);
+    dst[0] = src[0];
+    dst[1] = src[1];
+    if (r >= n) {
+        // padding points: a_v = -1e30 makes every term of the column 0
+        __align__(16) uint16_t prow[KEXT];
+        for (int i = 0; i < KEXT; ++i) prow[i] = 0;
+        prow[9] = bf16_bits(__float2bfloat16_rn(PAD_A));
+        uint4 *bd = reinterpret_cast<uint4 *>(Bext + r * KEXT);
+        const uint4 *ps = reinterpret_cast<const uint4 *>(prow);
+        bd[0] = ps[0];
+        bd[1] = ps[1];
+    }
 }
 
-// Gather candidate rows of Vq into Cq (16 bytes per thread); invalid
-// (sanitised, -1) candidates get a zero row.
-__global__ void k_gather_rows(const uint16_t *__restrict__ Vq, const int *__restrict__ cand, int64_t m, int DP,
-                              uint16_t *__restrict__ Cq) {
-    const int per_row = DP / 8;  // uint4 per row
+// Per-round point extension Y.  Upper-bound mode: sg = 1,
+// w = 2 sqrt(m_v) + 2 dv and a_v = m_v - ||v_hat||^2 + dv (2 sqrt(m_v) + dv)
+// + gamma (|m_v - ||v_hat||^2| + dv (2 sqrt(m_v) + dv) + max(dc) w), all
+// rounded up.  Plain mode: sg = 0, w = 0, a_v = m_v - ||v_hat||^2 to nearest.
+__global__ void k_prep_tc(const double *__restrict__ m64, const double *__restrict__ qn64,
+                          const float *__restrict__ qerr, const float *__restrict__ qmax, int64_t n, int upper,
+                          double gamma, uint16_t *__restrict__ Bext) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    __align__(16) uint16_t row[KEXT];
+    for (int i = 0; i < KEXT; ++i) row[i] = 0;
+    const uint16_t one = bf16_bits(__float2bfloat16_rn(1.f));
+    row[0] = row[1] = row[2] = one;
+    const double mv = m64[v];
+    if (upper) {
+        const double dv = (double)qerr[v];
+        const double sq = __dsqrt_ru(mv);
+        const double beta = __dmul_ru(dv, __dadd_ru(__dmul_ru(2.0, sq), dv));
+        const double w = __dadd_ru(__dmul_ru(2.0, sq), __dmul_ru(2.0, dv));
+        const double base = __dsub_ru(mv, qn64[v]);
+        const double acc = __dmul_ru(gamma, __dadd_ru(__dadd_ru(fabs(base), beta), __dmul_ru((double)qmax[0], w)));
+        const double a = __dadd_ru(__dadd_ru(base, beta), acc);
+        row[3] = row[4] = one;
+        uint16_t wp[2];
+        split2_up(w, wp);
+        row[5] = wp[0];
+        row[6] = wp[1];
+        row[7] = wp[0];
+        row[8] = wp[1];
+        split3(a, true, row + 9);
+    } else {
+        split3(mv - qn64[v], false, row + 9);
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(Bext + v * KEXT);
+    const uint4 *src = reinterpret_cast<const uint4 *>(row);
+    dst[0] = src[0];
+    dst[1] = src[1];
+}
+
+// Gather candidate rows of Vq and Aext into Cq / Cqx (16 bytes per thread);
+// invalid (sanitised, -1) candidates get zero rows.
+__global__ void k_gather_rows(const uint16_t *__restrict__ Vq, const uint16_t *__restrict__ Aext,
+                              const int *__restrict__ cand, int64_t m, int DP, uint16_t *__restrict__ Cq,
+                              uint16_t *__restrict__ Cqx) {
+    const int per_row = DP / 8 + 2;  // uint4 per row: main part, then 2 for the extension
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= m * per_row) return;
     int64_t j = e / per_row;
     int w = (int)(e % per_row);
     int c = cand[j];
     uint4 val = make_uint4(0, 0, 0, 0);
-    if (c >= 0) val = reinterpret_cast<const uint4 *>(Vq + (int64_t)c * DP)[w];
-    reinterpret_cast<uint4 *>(Cq + j * DP)[w] = val;
+    if (w < DP / 8) {
+        if (c >= 0) val = reinterpret_cast<const uint4 *>(Vq + (int64_t)c * DP)[w];
+        reinterpret_cast<uint4 *>(Cq + j * DP)[w] = val;
+    } else {
+        int x = w - DP / 8;
+        if (c >= 0) val = reinterpret_cast<const uint4 *>(Aext + (int64_t)c * KEXT)[x];
+        reinterpret_cast<uint4 *>(Cqx + j * KEXT)[x] = val;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -469,16 +526,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-cudaError_t make_map(CUtensorMap *map, void *gptr, int64_t rows, int DP, int prec, int box_rows) {
+// 2-D map over a row-major [rows, cols] array of 16-bit elements; box of
+// box_cols x box_rows with the given swizzle.
+cudaError_t make_map(CUtensorMap *map, void *gptr, int64_t rows, int cols, bool bf16, int box_cols, int box_rows,
+                     CUtensorMapSwizzle swz) {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
-    cuuint64_t dims[2] = {(cuuint64_t)DP, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)DP * 2};
-    cuuint32_t box[2] = {(cuuint32_t)KATOM, (cuuint32_t)box_rows};
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, prec == EBC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, gptr,
-                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, gptr, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -488,12 +548,15 @@ int pick_stages(int DP) {
     return 0;
 }
 
+double gamma_for(int DP) { return ((double)(DP + KEXT) / 4.0 + 4.0) * ldexp(1.0, -22); }
+
 }  // namespace
 
 bool tc_supported(const Ctx &c) { return c.d <= 128; }
 
 void tc_free(Ctx &c) {
-    void *ptrs[] = {c.tc.Vq, c.tc.Cq, c.tc.qn64, c.tc.qerr, c.tc.qnorm, c.tc.qmax, c.tc.a32, c.tc.w32};
+    void *ptrs[] = {c.tc.Vq, c.tc.Vq2, c.tc.Aext, c.tc.Bext, c.tc.Cq, c.tc.Cqx, c.tc.qn64, c.tc.qerr, c.tc.qnorm,
+                    c.tc.qmax};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c.tc = Ctx::Tc();
@@ -504,9 +567,11 @@ cudaError_t tc_quantize(Ctx &c) {
     cudaError_t e = cudaMemsetAsync(T.qmax, 0, 2 * sizeof(float), c.stream);
     if (e != cudaSuccess) return e;
     int th = 128;
-    k_quantize<<<(unsigned)((T.n_pad + th - 1) / th), th, 0, c.stream>>>(
-        c.V32, c.n, c.d, T.n_pad, T.DP, T.prec, T.Vq, T.qn64, T.qerr, T.qnorm, T.a32, T.w32,
-        reinterpret_cast<unsigned int *>(T.qmax), &c.st->err);
+    unsigned g = (unsigned)((T.n_pad + th - 1) / th);
+    k_quantize<<<g, th, 0, c.stream>>>(c.V32, c.n, c.d, T.n_pad, T.DP, T.prec, T.Vq, T.Vq2, T.qn64, T.qerr, T.qnorm,
+                                       reinterpret_cast<unsigned int *>(T.qmax), &c.st->err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_make_aext<<<g, th, 0, c.stream>>>(c.n, T.n_pad, T.qn64, T.qerr, T.qnorm, T.qmax, gamma_for(T.DP), T.Aext, T.Bext);
     return cudaGetLastError();
 }
 
@@ -518,31 +583,40 @@ cudaError_t tc_setup(Ctx &c, int prec) {
         size_t rows = (size_t)T.n_pad;
         cudaError_t e;
         if ((e = cudaMalloc(&T.Vq, rows * T.DP * 2)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&T.Vq2, rows * T.DP * 2)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&T.Aext, rows * KEXT * 2)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&T.Bext, rows * KEXT * 2)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&T.Cq, rows * T.DP * 2)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&T.Cqx, rows * KEXT * 2)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&T.qn64, rows * 8)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&T.qerr, rows * 4)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&T.qnorm, rows * 4)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&T.qmax, 2 * 4)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.a32, rows * 4)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.w32, rows * 4)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Cq, 0, rows * T.DP * 2, c.stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(T.Cqx, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(T.Bext, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
     }
     T.prec = prec;
-    cudaError_t e = make_map(&T.tmA_V, T.Vq, T.n_pad, T.DP, prec, BM);
-    if (e == cudaSuccess) e = make_map(&T.tmB_V, T.Vq, T.n_pad, T.DP, prec, BN);
-    if (e == cudaSuccess) e = make_map(&T.tmA_C, T.Cq, T.n_pad, T.DP, prec, BM);
+    const bool bf = prec == EBC_BF16;
+    cudaError_t e = make_map(&T.tmA_V, T.Vq, T.n_pad, T.DP, bf, KATOM, BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e == cudaSuccess) e = make_map(&T.tmB_V, T.Vq2, T.n_pad, T.DP, bf, KATOM, BN, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e == cudaSuccess) e = make_map(&T.tmA_C, T.Cq, T.n_pad, T.DP, bf, KATOM, BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e == cudaSuccess) e = make_map(&T.tmAx_V, T.Aext, T.n_pad, KEXT, true, KEXT, BM, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (e == cudaSuccess) e = make_map(&T.tmAx_C, T.Cqx, T.n_pad, KEXT, true, KEXT, BM, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (e == cudaSuccess) e = make_map(&T.tmBx, T.Bext, T.n_pad, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B);
     if (e != cudaSuccess) return e;
     return tc_quantize(c);
 }
 
 cudaError_t launch_prep_tc(Ctx &c, bool upper) {
     int th = 256;
-    k_prep_tc<<<(unsigned)((c.n + th - 1) / th), th, 0, c.stream>>>(c.m64, c.tc.qn64, c.tc.qerr, c.n, c.tc.a32,
-                                                                     c.tc.w32, upper ? 1 : 0, &c.st->mmax_bits);
+    k_prep_tc<<<(unsigned)((c.n + th - 1) / th), th, 0, c.stream>>>(c.m64, c.tc.qn64, c.tc.qerr, c.tc.qmax, c.n,
+                                                                     upper ? 1 : 0, gamma_for(c.tc.DP), c.tc.Bext);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int *nchunks_out) {
+    (void)upper;  // the mode is carried by the point extension written by launch_prep_tc
     Ctx::Tc &T = c.tc;
     const int DP = T.DP;
     const int ns = pick_stages(DP);
@@ -555,8 +629,8 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
         configured_smem = (int)L.total;
     }
     if (cand) {
-        int64_t tot = m * (DP / 8);
-        k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Vq, cand, m, DP, T.Cq);
+        int64_t tot = m * (DP / 8 + 2);
+        k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Vq, T.Aext, cand, m, DP, T.Cq, T.Cqx);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -579,27 +653,18 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
             best = nch;
         }
     }
-    a.nchunks = best;
     a.vt_per_chunk = (a.n_vtiles + best - 1) / best;
     a.nchunks = (a.n_vtiles + a.vt_per_chunk - 1) / a.vt_per_chunk;
     a.DP = DP;
     a.nstages = ns;
     a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BM, BN);
-    a.upper = upper ? 1 : 0;
-    a.a32 = T.a32;
-    a.w32 = T.w32;
-    a.cand = cand;
-    a.qn64 = T.qn64;
-    a.qerr = T.qerr;
-    a.qnorm = T.qnorm;
-    a.qmax = T.qmax;
-    a.mmax_bits = &c.st->mmax_bits;
-    a.gamma = ((double)DP / 4.0 + 4.0) * ldexp(1.0, -22);
+    a.idesc_ext = tc::idesc_f16(1u, BM, BN);
     a.partial = c.partial;
     a.err = &c.st->err;
     const int units = a.n_ctiles * a.nchunks;
     const int grid = std::min(units, G);
-    k_gains_tc<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, T.tmB_V, a);
+    k_gains_tc<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V, T.tmB_V,
+                                                      T.tmBx, a);
     *nchunks_out = a.nchunks;
     return cudaGetLastError();
 }
