@@ -1,7 +1,10 @@
 // Bulk marginal gains on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// For a tile of 128 candidates c (TMEM lanes) and 256 points v (TMEM
-// columns) one accumulator receives, entirely from the tensor core,
+// A work unit holds 256 candidates as two sub-tiles of 128 (TMEM lanes),
+// each with its own 256-column TMEM region; every streamed tile of 256
+// points feeds the MMAs of both sub-tiles, so each point byte brought into
+// shared memory serves 256 candidates.  For a candidate c and point v the
+// accumulator receives, entirely from the tensor core,
 //     t(c, v) = c_hat . (2 v_hat) + X_c . Y_v
 // where the 16 "extension" columns X (per candidate, static) and Y (per
 // point, rewritten every round) carry the remaining terms of
@@ -32,13 +35,15 @@
 // gives the raw low-precision gain.
 //
 // Warp roles (320 threads, one CTA per SM, persistent over work units):
-//   warp 0      TMA producer: candidate tile (A, two buffers) and a ring of
-//               point tiles (B stages), each with its extension tile
-//   warp 1      TMEM allocator and single-thread MMA issuer
+//   warp 0      TMA producer: the 256-candidate tile (A, one or two buffers)
+//               and a ring of point tiles (B stages), each with its extension
+//   warp 1      TMEM allocator and single-thread MMA issuer: for every point
+//               tile, sub-tile 0 into region 0, then sub-tile 1 into region 1
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, warps
-//               2-5 the first 128 columns of an accumulator, 6-9 the rest
-// Two 256-column FP32 accumulators (all 512 TMEM columns) let the epilogue
-// of tile i overlap the MMAs of tile i+1.
+//               2-5 the first 128 columns of a region, 6-9 the rest; they
+//               drain region 0 while region 1 fills and vice versa
+// The two regions use all 512 TMEM columns; the tensor pipe never waits for
+// the epilogue as long as draining a region is faster than filling the other.
 //
 // Every wait is bounded (tc_ptx.cuh); on a timeout the CTA records
 // EBC_ETIMEOUT, stops issuing, waits (bounded) for its own TMA copies and
@@ -57,8 +62,10 @@
 namespace ebc {
 
 namespace {
-constexpr int BM = 128;          // candidates per tile
-constexpr int BN = 256;          // points per tile
+constexpr int BMS = 128;         // candidates per MMA sub-tile (TMEM lanes)
+constexpr int BM = 2 * BMS;      // candidates per work unit (two sub-tiles share every point tile)
+constexpr int BN = 256;          // points per tile (TMEM columns per region)
+constexpr int NPAD = 256;        // row padding of the quantised arrays
 constexpr int KATOM = 64;        // 16-bit elements per 128-byte swizzle atom
 constexpr int KEXT = 16;         // extension columns (one MMA K step)
 constexpr int NTHREADS = 320;
@@ -75,6 +82,7 @@ struct TcArgs {
     int vt_per_chunk;    // point tiles per chunk
     int DP;              // padded K of the main part
     int nstages;         // B ring depth
+    int na;              // candidate-tile buffers (1 or 2)
     uint32_t idesc;      // instruction descriptor, main part
     uint32_t idesc_ext;  // instruction descriptor, extension (bf16)
     double *partial;     // [nchunks][m]
@@ -82,18 +90,21 @@ struct TcArgs {
 };
 
 struct SmemLayout {
-    uint32_t a_main, a_bytes, b_main, b_bytes, off_b, off_comb, off_bar, off_misc, total;
+    uint32_t a_main, a_sub, a_bytes, b_main, b_bytes, off_b, off_comb, off_bar, off_misc, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int DP, int nstages) {
+// A buffer: sub-tile 0 (main K atoms, then its extension), sub-tile 1 (same).
+// B stage: main K atoms, then the extension.
+__host__ __device__ inline SmemLayout smem_layout(int DP, int nstages, int na) {
     SmemLayout L;
-    L.a_main = (uint32_t)BM * DP * 2;
-    L.a_bytes = L.a_main + BM * KEXT * 2;
+    L.a_main = (uint32_t)BMS * DP * 2;
+    L.a_sub = L.a_main + BMS * KEXT * 2;
+    L.a_bytes = 2 * L.a_sub;
     L.b_main = (uint32_t)BN * DP * 2;
     L.b_bytes = L.b_main + BN * KEXT * 2;
-    L.off_b = 2 * L.a_bytes;
+    L.off_b = na * L.a_bytes;
     L.off_comb = L.off_b + nstages * L.b_bytes;
-    L.off_bar = L.off_comb + BM * 8;
+    L.off_bar = L.off_comb + 2 * BMS * 8;
     L.off_misc = L.off_bar + (2 * nstages + 8) * 8;
     L.total = L.off_misc + 64 + 1024;  // + alignment slack for the 1024-byte base
     return L;
@@ -124,15 +135,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ns = args.nstages;
-    const SmemLayout L = smem_layout(args.DP, ns);
+    const int na = args.na;
+    const SmemLayout L = smem_layout(args.DP, ns, na);
     uint8_t *sA = base;
     uint8_t *sB = base + L.off_b;
-    double *comb = reinterpret_cast<double *>(base + L.off_comb);
+    double *comb = reinterpret_cast<double *>(base + L.off_comb);  // [2][BMS]
     uint64_t *full = reinterpret_cast<uint64_t *>(base + L.off_bar);
     uint64_t *empty = full + ns;
     uint64_t *a_full = empty + ns;
     uint64_t *a_empty = a_full + 2;
-    uint64_t *t_full = a_empty + 2;
+    uint64_t *t_full = a_empty + 2;   // per TMEM region (candidate sub-tile)
     uint64_t *t_empty = t_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + L.off_misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(base + L.off_misc + 4);
@@ -184,17 +196,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int ct = u / args.nchunks, ch = u % args.nchunks;
                 const int vt0 = ch * args.vt_per_chunk;
                 const int vt1 = min(vt0 + args.vt_per_chunk, args.n_vtiles);
-                const int ab = ua & 1;
-                if (!tc::mbar_wait(&a_empty[ab], ((ua >> 1) & 1) ^ 1, abort_flag)) {
+                const int ab = ua % na;
+                const int aph = (ua / na) & 1;
+                if (!tc::mbar_wait(&a_empty[ab], aph ^ 1, abort_flag)) {
                     record_timeout(args.err, abort_flag);
                     break;
                 }
                 uint8_t *abuf = sA + ab * L.a_bytes;
                 tc::mbar_arrive_expect_tx(&a_full[ab], L.a_bytes);
-                for (int j = 0; j < katoms; ++j)
-                    tc::tma_load_2d(abuf + j * (BM * 128), &tmA, &a_full[ab], j * KATOM, ct * BM);
-                tc::tma_load_2d(abuf + L.a_main, &tmAx, &a_full[ab], 0, ct * BM);
-                last_afull[ab] = (ua >> 1) & 1;
+                for (int h = 0; h < 2; ++h) {
+                    uint8_t *sub = abuf + h * L.a_sub;
+                    const int row0 = ct * BM + h * BMS;
+                    for (int j = 0; j < katoms; ++j)
+                        tc::tma_load_2d(sub + j * (BMS * 128), &tmA, &a_full[ab], j * KATOM, row0);
+                    tc::tma_load_2d(sub + L.a_main, &tmAx, &a_full[ab], 0, row0);
+                }
+                last_afull[ab] = aph;
                 bool ok = true;
                 for (int vt = vt0; vt < vt1; ++vt, ++g) {
                     const int s = g % ns;
@@ -216,42 +233,51 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
+        // For every point tile: sub-tile 0 into TMEM region 0, then sub-tile 1
+        // into region 1.  The epilogue drains one region while the other fills.
         if (lane == 0) {
             int g = 0, t = 0, ua = 0;
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
                 const int ch = u % args.nchunks;
                 const int vt0 = ch * args.vt_per_chunk;
                 const int vt1 = min(vt0 + args.vt_per_chunk, args.n_vtiles);
-                const int ab = ua & 1;
-                if (!tc::mbar_wait(&a_full[ab], (ua >> 1) & 1, abort_flag)) {
+                const int ab = ua % na;
+                if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag)) {
                     record_timeout(args.err, abort_flag);
                     break;
                 }
+                const uint32_t a0 = tc::smem_u32(sA + ab * L.a_bytes);
                 bool ok = true;
-                for (int vt = vt0; vt < vt1; ++vt, ++g, ++t) {
+                for (int vt = vt0; vt < vt1 && ok; ++vt, ++g, ++t) {
                     const int s = g % ns;
-                    const int b = t & 1;
-                    if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag) ||
-                        !tc::mbar_wait(&t_empty[b], ((t >> 1) & 1) ^ 1, abort_flag)) {
+                    if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag)) {
                         record_timeout(args.err, abort_flag);
                         ok = false;
                         break;
                     }
-                    tc::tc_fence_after();
-                    const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-                    const uint32_t a0 = tc::smem_u32(sA + ab * L.a_bytes);
                     const uint32_t b0 = tc::smem_u32(sB + s * L.b_bytes);
-                    for (int kk = 0; kk < args.DP / 16; ++kk) {
-                        const uint32_t j = kk >> 2, w = kk & 3;
-                        const uint64_t ad = tc::sdesc_sw128(a0 + j * (BM * 128) + w * 32);
-                        const uint64_t bd = tc::sdesc_sw128(b0 + j * (BN * 128) + w * 32);
-                        tc::mma_f16(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
+                    for (int h = 0; h < 2; ++h) {
+                        if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag)) {
+                            record_timeout(args.err, abort_flag);
+                            ok = false;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
+                        const uint32_t ah = a0 + h * L.a_sub;
+                        for (int kk = 0; kk < args.DP / 16; ++kk) {
+                            const uint32_t j = kk >> 2, w = kk & 3;
+                            const uint64_t ad = tc::sdesc_sw128(ah + j * (BMS * 128) + w * 32);
+                            const uint64_t bd = tc::sdesc_sw128(b0 + j * (BN * 128) + w * 32);
+                            tc::mma_f16(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
+                        }
+                        tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main),
+                                    args.idesc_ext, 1u);
+                        tc::mma_commit(&t_full[h]);
+                        last_tfull[h] = t & 1;
                     }
-                    tc::mma_f16(d_tmem, tc::sdesc_sw32(a0 + L.a_main), tc::sdesc_sw32(b0 + L.b_main), args.idesc_ext,
-                                1u);
+                    if (!ok) break;
                     tc::mma_commit(&empty[s]);
-                    tc::mma_commit(&t_full[b]);
-                    last_tfull[b] = (t >> 1) & 1;
                 }
                 if (!ok) break;
                 tc::mma_commit(&a_empty[ab]);
@@ -261,48 +287,57 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------ epilogue
         const int ew = warp - 2;        // 0..7
         const int q = warp & 3;         // TMEM lane quarter this warp may access
-        const int half = ew >> 2;       // column half of the accumulator
-        const int row = q * 32 + lane;  // candidate row within the tile
+        const int half = ew >> 2;       // column half of a region
+        const int row = q * 32 + lane;  // candidate row within a sub-tile
         int t = 0;
         bool alive = true;
         for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
             const int ct = u / args.nchunks, ch = u % args.nchunks;
             const int vt0 = ch * args.vt_per_chunk;
             const int vt1 = min(vt0 + args.vt_per_chunk, args.n_vtiles);
-            const int64_t j = (int64_t)ct * BM + row;
-            double acc = 0.0;
+            double acc[2] = {0.0, 0.0};
             for (int vt = vt0; vt < vt1; ++vt, ++t) {
-                const int b = t & 1;
-                if (alive) {
-                    // the TMEM loads below are warp-collective: decide per warp
-                    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[b], (t >> 1) & 1, abort_flag));
-                    if (!ok) {
-                        if (lane == 0) record_timeout(args.err, abort_flag);
-                        alive = false;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (alive) {
+                        // the TMEM loads below are warp-collective: decide per warp
+                        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag));
+                        if (!ok) {
+                            if (lane == 0) record_timeout(args.err, abort_flag);
+                            alive = false;
+                        }
                     }
+                    if (!alive) continue;
+                    tc::tc_fence_after();
+                    const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN + half * 128);
+                    // all 128 columns into registers, then hand the region back
+                    // to the MMA issuer before doing any arithmetic
+                    uint32_t r0[32], r1[32], r2[32], r3[32];
+                    tc::tmem_ld32(taddr, r0);
+                    tc::tmem_ld32(taddr + 32, r1);
+                    tc::tmem_ld32(taddr + 64, r2);
+                    tc::tmem_ld32(taddr + 96, r3);
+                    tc::tmem_ld_wait();
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&t_empty[h]);
+                    const float s = (relu_sum32(r0) + relu_sum32(r1)) + (relu_sum32(r2) + relu_sum32(r3));
+                    acc[h] += (double)s;
                 }
-                if (!alive) continue;
-                tc::tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * 128);
-                uint32_t r0[32], r1[32], r2[32], r3[32];
-                tc::tmem_ld32(taddr, r0);
-                tc::tmem_ld32(taddr + 32, r1);
-                tc::tmem_ld_wait();
-                tc::tmem_ld32(taddr + 64, r2);
-                tc::tmem_ld32(taddr + 96, r3);
-                float s = relu_sum32(r0) + relu_sum32(r1);
-                tc::tmem_ld_wait();
-                // this warp is done with accumulator b
-                tc::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&t_empty[b]);
-                s += relu_sum32(r2) + relu_sum32(r3);
-                acc += (double)s;
             }
             // combine the two column halves in a fixed order
-            if (half == 1) comb[row] = acc;
+            if (half == 1) {
+                comb[row] = acc[0];
+                comb[BMS + row] = acc[1];
+            }
             tc::named_bar_sync(2, NEPI);
-            if (half == 0 && j < args.m && alive) args.partial[(int64_t)ch * args.m + j] = acc + comb[row];
+            if (half == 0 && alive) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t j = (int64_t)ct * BM + h * BMS + row;
+                    if (j < args.m) args.partial[(int64_t)ch * args.m + j] = acc[h] + comb[h * BMS + row];
+                }
+            }
             tc::named_bar_sync(2, NEPI);
         }
     }
@@ -542,10 +577,20 @@ cudaError_t make_map(CUtensorMap *map, void *gptr, int64_t rows, int cols, bool 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-int pick_stages(int DP) {
-    for (int ns = 6; ns >= 2; --ns)
-        if ((int)smem_layout(DP, ns).total <= SMEM_LIMIT) return ns;
-    return 0;
+// Pipeline shape: candidate-tile buffers (na) and point-tile stages (ns).
+// Two point stages are enough (each tile feeds two sub-tiles' MMAs, twice
+// the time of its load); a second candidate buffer removes the reload
+// bubble at unit changes when it fits; deeper point rings use what is left.
+void pick_pipeline(int DP, int *na, int *ns) {
+    *na = 0;
+    *ns = 0;
+    for (int a = 2; a >= 1; --a)
+        for (int s = 6; s >= 2; --s)
+            if ((int)smem_layout(DP, s, a).total <= SMEM_LIMIT) {
+                *na = a;
+                *ns = s;
+                return;
+            }
 }
 
 double gamma_for(int DP) { return ((double)(DP + KEXT) / 4.0 + 4.0) * ldexp(1.0, -22); }
@@ -578,7 +623,7 @@ cudaError_t tc_quantize(Ctx &c) {
 cudaError_t tc_setup(Ctx &c, int prec) {
     Ctx::Tc &T = c.tc;
     if (T.Vq == nullptr) {
-        T.n_pad = (c.n + BN - 1) / BN * BN;
+        T.n_pad = (c.n + NPAD - 1) / NPAD * NPAD;
         T.DP = (c.d + KATOM - 1) / KATOM * KATOM;
         size_t rows = (size_t)T.n_pad;
         cudaError_t e;
@@ -598,11 +643,11 @@ cudaError_t tc_setup(Ctx &c, int prec) {
     }
     T.prec = prec;
     const bool bf = prec == EBC_BF16;
-    cudaError_t e = make_map(&T.tmA_V, T.Vq, T.n_pad, T.DP, bf, KATOM, BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    cudaError_t e = make_map(&T.tmA_V, T.Vq, T.n_pad, T.DP, bf, KATOM, BMS, CU_TENSOR_MAP_SWIZZLE_128B);
     if (e == cudaSuccess) e = make_map(&T.tmB_V, T.Vq2, T.n_pad, T.DP, bf, KATOM, BN, CU_TENSOR_MAP_SWIZZLE_128B);
-    if (e == cudaSuccess) e = make_map(&T.tmA_C, T.Cq, T.n_pad, T.DP, bf, KATOM, BM, CU_TENSOR_MAP_SWIZZLE_128B);
-    if (e == cudaSuccess) e = make_map(&T.tmAx_V, T.Aext, T.n_pad, KEXT, true, KEXT, BM, CU_TENSOR_MAP_SWIZZLE_32B);
-    if (e == cudaSuccess) e = make_map(&T.tmAx_C, T.Cqx, T.n_pad, KEXT, true, KEXT, BM, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (e == cudaSuccess) e = make_map(&T.tmA_C, T.Cq, T.n_pad, T.DP, bf, KATOM, BMS, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e == cudaSuccess) e = make_map(&T.tmAx_V, T.Aext, T.n_pad, KEXT, true, KEXT, BMS, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (e == cudaSuccess) e = make_map(&T.tmAx_C, T.Cqx, T.n_pad, KEXT, true, KEXT, BMS, CU_TENSOR_MAP_SWIZZLE_32B);
     if (e == cudaSuccess) e = make_map(&T.tmBx, T.Bext, T.n_pad, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B);
     if (e != cudaSuccess) return e;
     return tc_quantize(c);
@@ -619,9 +664,10 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     (void)upper;  // the mode is carried by the point extension written by launch_prep_tc
     Ctx::Tc &T = c.tc;
     const int DP = T.DP;
-    const int ns = pick_stages(DP);
+    int na = 0, ns = 0;
+    pick_pipeline(DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = smem_layout(DP, ns);
+    const SmemLayout L = smem_layout(DP, ns, na);
     static int configured_smem = 0;
     if (configured_smem < (int)L.total) {
         cudaError_t e = cudaFuncSetAttribute(k_gains_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
@@ -657,8 +703,9 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     a.nchunks = (a.n_vtiles + a.vt_per_chunk - 1) / a.vt_per_chunk;
     a.DP = DP;
     a.nstages = ns;
-    a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BM, BN);
-    a.idesc_ext = tc::idesc_f16(1u, BM, BN);
+    a.na = na;
+    a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, BN);
+    a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
     a.partial = c.partial;
     a.err = &c.st->err;
     const int units = a.n_ctiles * a.nchunks;
