@@ -199,6 +199,32 @@ ebc_status ebc_reset_profile(ebc_t h);
 /* f(S) of the current Greedy state, computed on the device (synchronises). */
 ebc_status ebc_current_f(ebc_t h, double *out_f);
 
+/*
+ * Multi-set evaluation that allocates nothing (the paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory at
+ * run time, such as a control loop with a fixed latency budget, where
+ * cudaMalloc can synchronise the device, or a program whose device memory is
+ * owned by another allocator).  Same result as ebc_eval_sets at EBC_FP32,
+ * without a handle:
+ *   V        device float[n * d], row-major;  n >= 1, 1 <= d <= 4096
+ *   csr_idx  device int32[csr_off[l]];  csr_off device int64[l + 1]
+ *   out_f    device double[l]
+ *   stream   cudaStream_t (NULL = legacy default stream)
+ * Scratch is a static 8 MiB device array held by every GPU that loads the
+ * library until exit; n may be at most 134,217,728 (1,048,576 tiles of 128
+ * points), larger n is rejected with EINVAL.  All calls share the array:
+ * calls whose work overlaps on the GPU race and must not be issued.  The
+ * first call on a device looks up the array's address with that device
+ * current; make that first call before any stream capture.  Synchronises
+ * the stream and returns EINDEX / EINVAL for bad members / offsets found on
+ * the device.  Text of the last failure: ebc_noalloc_last_error().
+ */
+ebc_status ebc_eval_sets_noalloc(const float *V, int64_t n, int32_t d, const int32_t *csr_idx,
+                                 const int64_t *csr_off, int64_t l, double *out_f, void *stream);
+
+/* Text of the last ebc_eval_sets_noalloc failure on this host thread. */
+const char *ebc_noalloc_last_error(void);
+
 /* Text of the last error on this handle ("" if none); h may be NULL for
  * errors from ebc_create.  The pointer stays valid until the next call. */
 const char *ebc_last_error(ebc_t h);

@@ -70,6 +70,8 @@ _SIGS = {
     "ebc_get_stats": [_P, ctypes.POINTER(ebc_stats)],
     "ebc_current_f": [_P, ctypes.POINTER(ctypes.c_double)],
     "ebc_last_error": [_P],
+    "ebc_eval_sets_noalloc": [_P, _I64, _I32, _P, _P, _I64, _P, _P],
+    "ebc_noalloc_last_error": [],
 }
 
 
@@ -91,6 +93,7 @@ def load(path: str | None = None):
                 fn.argtypes = args
                 fn.restype = ctypes.c_int
             lib.ebc_last_error.restype = ctypes.c_char_p
+            lib.ebc_noalloc_last_error.restype = ctypes.c_char_p
             _lib = lib
     return _lib
 
@@ -214,6 +217,16 @@ def ebc_current_f(h: int) -> float:
     v = ctypes.c_double()
     _raise(h, load().ebc_current_f(_P(h), ctypes.byref(v)))
     return v.value
+
+
+def ebc_eval_sets_noalloc(V_ptr: int, n: int, d: int, idx_ptr: int, off_ptr: int, l: int, out_ptr: int,
+                          stream=None) -> None:
+    """Allocation-free multi-set evaluation over device pointers (see include/ebc.h)."""
+    rc = load().ebc_eval_sets_noalloc(_P(V_ptr), int(n), int(d), _P(idx_ptr), _P(off_ptr), int(l), _P(out_ptr),
+                                      _P(_stream_ptr(stream)))
+    if rc != EBC_OK:
+        msg = load().ebc_noalloc_last_error()
+        raise EbcError(rc, msg.decode() if msg else "")
 
 
 def ebc_last_error(h: int | None) -> str:
