@@ -297,6 +297,9 @@ def main():
             "roofline": roof, "gpu_launches": prof["launches"], "clocks": clk,
             "certification": {k2: stats[k2] for k2 in ("rounds", "certified_rounds", "escalated_rounds",
                                                          "escalated_candidates", "max_raw_rel_err")},
+            "breakdown_ms_per_step": {"bulk_gains": prof["bulk_ms"] / args.steps,
+                                      "exact_refine": prof["refine_ms"] / args.steps,
+                                      "rest": t_max_ms / args.steps - (prof["bulk_ms"] + prof["refine_ms"]) / args.steps},
             "f_final": float(f_bf[-1]), "picks_head": idx_bf[:10].tolist()}
 
     # FP32 plain comparison at matched picks ------------------------------
