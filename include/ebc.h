@@ -68,8 +68,9 @@ typedef struct {
     int64_t certified_rounds;     /* rounds decided by the top-K exact re-evaluation alone */
     int64_t escalated_rounds;     /* rounds that exactly re-evaluated further candidates */
     int64_t escalated_candidates; /* total such extra candidates */
-    double max_raw_rel_err;       /* max |bulk - exact| / exact over re-evaluated leaders,
-                                     bulk = the upper-bound gain of the bulk kernel */
+    double max_raw_rel_err;       /* max (bulk bound - lower bound) / lower bound over the top
+                                     list: how loose the bulk upper bounds were */
+    int64_t exact_evaluations;    /* candidates whose exact FP64 gain was computed */
     int32_t prec;                 /* current ebc_prec */
     int32_t refine_k;             /* current K */
 } ebc_stats;
@@ -152,11 +153,12 @@ ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *o
  *   out_idx  device int32[k]: the picks in order.
  *   out_f    device double[k]: out_f[t] = f(S) after pick t (cumulative).
  * Each round evaluates the gain of every unselected point with the bulk
- * precision as a rigorous upper bound, re-evaluates the K largest exactly
- * (direct FP64 distances, FP64 sums) and certifies the pick: if the best
- * exact gain is below the (K+1)-th upper bound, every candidate whose bound
- * reaches it is re-evaluated exactly as well.  The pick is therefore the
- * exact argmax up to FP64 rounding, at every precision.
+ * precision as a rigorous upper bound; the K largest get rigorous FP32
+ * direct-distance bounds [lo, hi]; if the (K+1)-th bulk bound can reach the
+ * best lo, every candidate whose bulk bound reaches it gets [lo, hi] too;
+ * the candidates whose hi reaches the best lo get the exact gain (FP64
+ * direct distances and sums), and the pick is the best of those.  The pick
+ * is therefore the exact argmax up to FP64 rounding, at every precision.
  * EINVAL when k < 0 or k exceeds the number of unselected points.
  */
 ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);

@@ -34,7 +34,6 @@ struct ebc_ctx {
     int nref = 0;           // number of refine chunks
     int nblk = 0;           // select blocks
     int esc_cap = 0;        // escalated candidates with chunked partials
-    double *esc_part = nullptr;
     double *d_scalar = nullptr;  // one device double for ebc_current_f
     int *d_bad = nullptr;
 };
@@ -74,8 +73,10 @@ cudaError_t dalloc(T **p, size_t count) {
 void free_all(ebc::Ctx &c, ebc_ctx *h) {
     ebc::tc_free(c);
     void *ptrs[] = {c.V32, c.nv64, c.nv32, c.m64, c.sel, c.st, c.partial, c.gain_up, c.blk_idx, c.blk_val, c.top_idx, c.top_val,
-                    c.top_exact, c.esc_idx, c.esc_exact, c.ref_part, c.cand_buf, c.set_part,
-                    h ? h->esc_part : nullptr, h ? h->d_scalar : nullptr, h ? h->d_bad : nullptr};
+                    c.esc_idx, c.esc_exact, c.cand_buf, c.set_part,
+                    c.cert.top_lo, c.cert.top_hi, c.cert.esc_lo, c.cert.esc_hi, c.cert.part_lo, c.cert.part_hi,
+                    c.cert.ctd_idx, c.cert.ctd_part, c.cert.ctd_exact,
+                    h ? h->d_scalar : nullptr, h ? h->d_bad : nullptr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c.h_err) cudaFreeHost(c.h_err);
@@ -115,11 +116,6 @@ __global__ void k_check_csr(const int64_t *__restrict__ off, int64_t l, ebc::Dev
         atomicCAS(&st->err, 0, (int)EBC_EINVAL);
         atomicExch(bad, 1);
     }
-}
-
-__global__ void k_fill_zero(double *p, int64_t n) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j < n) p[j] = 0.0;
 }
 
 ebc_status check_handle(ebc_t h) {
@@ -263,12 +259,24 @@ ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device,
     CKC(dalloc(&c.blk_val, c.blk_cap));
     CKC(dalloc(&c.top_idx, ebc::kMaxRefineK + 1));
     CKC(dalloc(&c.top_val, ebc::kMaxRefineK + 1));
-    CKC(dalloc(&c.top_exact, ebc::kMaxRefineK));
     CKC(dalloc(&c.esc_idx, n));
     CKC(dalloc(&c.esc_exact, n));
-    c.ref_cap = (int64_t)ebc::kMaxRefineK * h->nref;
-    CKC(dalloc(&c.ref_part, (size_t)c.ref_cap));
-    CKC(dalloc(&h->esc_part, (size_t)h->esc_cap * h->nref));
+    {
+        ebc::Ctx::Sel &S = c.cert;
+        S.cap = h->esc_cap;
+        S.nchunks = h->nref;
+        S.chunk = h->ref_ch;
+        const size_t pool = (size_t)ebc::kMaxRefineK + S.cap;
+        CKC(dalloc(&S.top_lo, ebc::kMaxRefineK));
+        CKC(dalloc(&S.top_hi, ebc::kMaxRefineK));
+        CKC(dalloc(&S.esc_lo, S.cap));
+        CKC(dalloc(&S.esc_hi, S.cap));
+        CKC(dalloc(&S.part_lo, pool * S.nchunks));
+        CKC(dalloc(&S.part_hi, pool * S.nchunks));
+        CKC(dalloc(&S.ctd_idx, pool));
+        CKC(dalloc(&S.ctd_part, pool * S.nchunks));
+        CKC(dalloc(&S.ctd_exact, pool));
+    }
     CKC(dalloc(&c.cand_buf, n));
     CKC(dalloc(&h->d_scalar, 1));
     CKC(dalloc(&h->d_bad, 1));
@@ -398,6 +406,7 @@ ebc_status ebc_get_stats(ebc_t h, ebc_stats *out) {
     out->escalated_rounds = s.escalated_rounds;
     out->escalated_candidates = s.escalated_cands;
     out->max_raw_rel_err = s.max_raw_rel_err;
+    out->exact_evaluations = s.exact_evals;
     out->prec = (int32_t)c.prec;
     out->refine_k = c.refine_k;
     return EBC_OK;
@@ -539,20 +548,34 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
     h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
     CK(h, launch(h, -1, 1, [&] { return ebc::launch_reduce_select(c, c.n, nch, nullptr, true, nullptr, h->nblk); }));
     CK(h, launch(h, -1, 1, [&] { return ebc::launch_merge_top(c, h->nblk, K, eta); }));
+    // level 1: bounds for the top list, then for the escalated candidates
+    ebc::Ctx::Sel &S = c.cert;
+    const int64_t esc_off = (int64_t)ebc::kMaxRefineK * S.nchunks;
     CK(h, launch(h, PK_REFINE, 1, [&] {
-           return ebc::launch_refine(c, c.top_idx, &c.st->top_count, K, c.ref_part, h->ref_ch, h->nref);
+           return ebc::launch_refine(c, c.top_idx, &c.st->top_count, K, S.part_lo, S.part_hi, S.chunk, S.nchunks);
        }));
-    CK(h, launch(h, -1, 2, [&] {
-           cudaError_t e = ebc::launch_decide_n(c, h->nref, eta);
+    CK(h, launch(h, -1, 3, [&] {
+           cudaError_t e = ebc::launch_fold_bounds(c, S.part_lo, S.part_hi, &c.st->top_count, K, S.top_lo, S.top_hi);
+           if (e == cudaSuccess) e = ebc::launch_decide_top(c, eta);
            return e != cudaSuccess ? e : ebc::launch_collect_escalation(c, eta);
        }));
     CK(h, launch(h, PK_REFINE, 2, [&] {
-           cudaError_t e = ebc::launch_refine(c, c.esc_idx, &c.st->esc_count, h->esc_cap, h->esc_part, h->ref_ch,
-                                              h->nref);
-           return e != cudaSuccess ? e : ebc::launch_refine_overflow(c, c.esc_idx, &c.st->esc_count, h->esc_cap, c.esc_exact);
+           cudaError_t e = ebc::launch_refine(c, c.esc_idx, &c.st->esc_count, S.cap, S.part_lo + esc_off,
+                                              S.part_hi + esc_off, S.chunk, S.nchunks);
+           return e != cudaSuccess ? e : ebc::launch_refine_overflow(c, c.esc_idx, &c.st->esc_count, S.cap, c.esc_exact);
        }));
     CK(h, launch(h, -1, 2, [&] {
-           cudaError_t e = ebc::launch_commit_n(c, h->esc_part, h->nref, h->esc_cap, out_idx_base, out_f_base);
+           cudaError_t e = ebc::launch_fold_bounds(c, S.part_lo + esc_off, S.part_hi + esc_off, &c.st->esc_count,
+                                                   S.cap, S.esc_lo, S.esc_hi);
+           return e != cudaSuccess ? e : ebc::launch_decide_contenders(c);
+       }));
+    // level 2: exact gains of the contenders only
+    CK(h, launch(h, PK_REFINE, 1, [&] {
+           return ebc::launch_refine(c, S.ctd_idx, &c.st->ctd_count, ebc::kMaxRefineK + S.cap, S.ctd_part, nullptr,
+                                     S.chunk, S.nchunks);
+       }));
+    CK(h, launch(h, -1, 2, [&] {
+           cudaError_t e = ebc::launch_commit_pick(c, out_idx_base, out_f_base);
            return e != cudaSuccess ? e : ebc::launch_update(c);
        }));
     return EBC_OK;

@@ -29,6 +29,7 @@ struct DevState {
     long long escalated_rounds;
     long long escalated_cands;
     long long rounds;
+    long long exact_evals;  // contenders whose exact FP64 gain was computed
     int round;              // picks made so far (index into out arrays)
     int pick;               // last pick
     int top_count;          // entries in the top-K list this round
@@ -37,6 +38,8 @@ struct DevState {
     int err;                // first device-detected error (ebc_status), 0 if none
     unsigned int mmax_bits; // max_v m_v as FP32 bits (rounded up), for the TC slack
     int zero_scan;          // 1 when every remaining gain is exactly 0
+    int ctd_count;          // contenders needing the exact FP64 gain this round
+    double best_lo;         // largest certified lower bound of the round
 };
 
 // Scratch / resident buffers of one handle.
@@ -92,15 +95,25 @@ struct Ctx {
     int blk_cap = 0;
     int *top_idx = nullptr;     // [kMaxRefineK + 1]
     double *top_val = nullptr;  // [kMaxRefineK + 1] upper bounds of the top list
-    double *top_exact = nullptr;// [kMaxRefineK] exact gains
     int *esc_idx = nullptr;     // [n] escalation list
     double *esc_exact = nullptr;// [n]
-    double *ref_part = nullptr; // [ref_cap] refine partials
-    int64_t ref_cap = 0;
     int *cand_buf = nullptr;    // [n] gathered candidate list for ebc_gains
     double *set_part = nullptr; // eval_sets partials
     int64_t set_part_cap = 0;
     int32_t *h_err = nullptr;   // pinned host word for error read-back
+
+    // two-level certification of the Greedy pick (k_select.cu)
+    struct Sel {
+        int cap = 0;               // escalated entries with chunked bounds
+        int nchunks = 0;           // V chunks of the refine kernels
+        int64_t chunk = 0;         // points per chunk
+        double *top_lo = nullptr, *top_hi = nullptr;    // [kMaxRefineK] bounds of the top list
+        double *esc_lo = nullptr, *esc_hi = nullptr;    // [cap] bounds of the escalated entries
+        double *part_lo = nullptr, *part_hi = nullptr;  // [(kMaxRefineK + cap) * nchunks] chunk partials
+        int *ctd_idx = nullptr;                         // [kMaxRefineK + cap] contenders
+        double *ctd_part = nullptr;                     // [(kMaxRefineK + cap) * nchunks]
+        double *ctd_exact = nullptr;                    // [kMaxRefineK + cap]
+    } cert;
 
     std::string last_error;
 };
@@ -112,12 +125,20 @@ cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, in
 cudaError_t launch_reduce_select(Ctx &c, int64_t m, int nchunks, const int *cand, bool greedy,
                                  double *out_gain, int nblk);
 cudaError_t launch_merge_top(Ctx &c, int nblk, int K, double eta);
-cudaError_t launch_refine(Ctx &c, const int *list, const int *count, int list_cap, double *out_exact,
+// Exact FP64 gains (out_hi == nullptr) or rigorous FP32 [lo, hi] bounds of
+// the gains (out holds lo, out_hi hi) of a device list, as chunk partials.
+cudaError_t launch_refine(Ctx &c, const int *list, const int *count, int list_cap, double *out, double *out_hi,
                           int64_t chunk, int nchunks);
-cudaError_t launch_decide_n(Ctx &c, int nchunks, double eta);
 cudaError_t launch_collect_escalation(Ctx &c, double eta);
-cudaError_t launch_commit_n(Ctx &c, const double *esc_part, int nchunks, int cap, int32_t *out_idx, double *out_f);
 cudaError_t launch_refine_overflow(Ctx &c, const int *list, const int *count, int cap, double *out_exact);
+cudaError_t launch_refine_rows(Ctx &c, const int *list, const int *count, int list_cap, double *out,
+                               double *out_hi, int64_t chunk, int nchunks);
+// two-level certified pick (k_select.cu)
+cudaError_t launch_fold_bounds(Ctx &c, const double *part_lo, const double *part_hi, const int *count, int cap,
+                               double *lo, double *hi);
+cudaError_t launch_decide_top(Ctx &c, double eta_bulk);
+cudaError_t launch_decide_contenders(Ctx &c);
+cudaError_t launch_commit_pick(Ctx &c, int32_t *out_idx, double *out_f);
 cudaError_t launch_update(Ctx &c);
 cudaError_t launch_current_f(Ctx &c, double *d_out);
 cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,

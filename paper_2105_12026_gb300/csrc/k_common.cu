@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "ebc_internal.cuh"
+#include "sel_util.cuh"
 
 namespace ebc {
 
@@ -89,54 +90,6 @@ cudaError_t launch_reset_state(Ctx &c) {
     int64_t bl = (c.n + th - 1) / th;
     k_reset<<<(unsigned)bl, th, 0, c.stream>>>(c.nv64, c.m64, c.sel, c.n, c.st);
     return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Block-wide argmax in the order (value descending, index ascending).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool better(double va, int ia, double vb, int ib) {
-    return va > vb || (va == vb && ia < ib);
-}
-
-__device__ void block_best(double &v, int &i) {
-    __shared__ double sv[32];
-    __shared__ int si[32];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        int oi = __shfl_xor_sync(0xffffffffu, i, o);
-        if (better(ov, oi, v, i)) {
-            v = ov;
-            i = oi;
-        }
-    }
-    __syncthreads();
-    if (lane == 0) {
-        sv[w] = v;
-        si[w] = i;
-    }
-    __syncthreads();
-    int nw = (blockDim.x + 31) >> 5;
-    if (w == 0) {
-        v = lane < nw ? sv[lane] : -DBL_MAX;
-        i = lane < nw ? si[lane] : INT_MAX;
-        for (int o = 16; o > 0; o >>= 1) {
-            double ov = __shfl_xor_sync(0xffffffffu, v, o);
-            int oi = __shfl_xor_sync(0xffffffffu, i, o);
-            if (better(ov, oi, v, i)) {
-                v = ov;
-                i = oi;
-            }
-        }
-        if (lane == 0) {
-            sv[0] = v;
-            si[0] = i;
-        }
-    }
-    __syncthreads();
-    v = sv[0];
-    i = si[0];
-    __syncthreads();
 }
 
 // Extract the `cnt` best entries of the thread-strided range [beg, end) of
@@ -240,11 +193,21 @@ cudaError_t launch_merge_top(Ctx &c, int nblk, int K, double) {
 // ---------------------------------------------------------------------------
 constexpr int RB = 8;
 
-template <bool VEC4>
+// Rigorous bounds on max(0, m_v - d) from the FP32 screen distance s, for
+// which d lies in [s / (1 + rho), s / (1 - rho)] within [s (1 - rho), s (1 + 2 rho)].
+__device__ __forceinline__ void bound_terms(double mv, float s, double rho, double &lo, double &hi) {
+    const double sd = (double)s;
+    const double th = __dsub_ru(mv, __dmul_rd(sd, 1.0 - rho));
+    const double tl = __dsub_rd(mv, __dmul_ru(sd, 1.0 + 2.0 * rho));
+    if (th > 0.0) hi += th;
+    if (tl > 0.0) lo += tl;
+}
+
+template <bool VEC4, bool BOUNDS>
 __global__ void __launch_bounds__(256) k_refine(const float *__restrict__ V, int64_t n, int d,
                                                 const double *__restrict__ m64, const int *__restrict__ list,
                                                 const int *__restrict__ count, int cap, int64_t chunk, int nchunks,
-                                                double rho, double *__restrict__ out) {
+                                                double rho, double *__restrict__ out, double *__restrict__ out_hi) {
     extern __shared__ __align__(16) float cs[];  // [RB][d]
     __shared__ double red[RB][8];
     const int cnt = min(*count, cap);
@@ -263,9 +226,9 @@ __global__ void __launch_bounds__(256) k_refine(const float *__restrict__ V, int
         }
         __syncthreads();
         const int64_t b = (int64_t)q * chunk, en = lmin(b + chunk, n);
-        double acc[RB];
+        double acc[RB], acch[RB];
 #pragma unroll
-        for (int k = 0; k < RB; ++k) acc[k] = 0.0;
+        for (int k = 0; k < RB; ++k) acc[k] = acch[k] = 0.0;
         for (int64_t v = b + threadIdx.x; v < en; v += blockDim.x) {
             const float *vr = V + v * d;
             float sd[RB];
@@ -297,45 +260,182 @@ __global__ void __launch_bounds__(256) k_refine(const float *__restrict__ V, int
             const double mv = m64[v];
 #pragma unroll
             for (int k = 0; k < RB; ++k) {
-                if (k >= ng || (double)sd[k] * (1.0 - rho) >= mv) continue;  // exact distance >= m_v: term 0
+                if (k >= ng) continue;
+                if (BOUNDS) {
+                    bound_terms(mv, sd[k], rho, acc[k], acch[k]);
+                    continue;
+                }
+                if ((double)sd[k] * (1.0 - rho) >= mv) continue;  // exact distance >= m_v: term 0
                 const double de = exact_sqdist(vr, cs + k * d, d);
                 const double t = mv - de;
                 if (t > 0.0) acc[k] += t;
             }
         }
+        for (int pass = 0; pass < (BOUNDS ? 2 : 1); ++pass) {
+            __syncthreads();
 #pragma unroll
-        for (int k = 0; k < RB; ++k) {
-            double a = acc[k];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) red[k][w] = a;
-        }
-        __syncthreads();
-        if (threadIdx.x < ng) {
-            double s = 0.0;
-            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += red[threadIdx.x][ww];
-            out[(int64_t)(e0 + threadIdx.x) * nchunks + q] = s;
+            for (int k = 0; k < RB; ++k) {
+                double a = pass == 0 ? acc[k] : acch[k];
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) red[k][w] = a;
+            }
+            __syncthreads();
+            if (threadIdx.x < ng) {
+                double s = 0.0;
+                for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += red[threadIdx.x][ww];
+                (pass == 0 ? out : out_hi)[(int64_t)(e0 + threadIdx.x) * nchunks + q] = s;
+            }
         }
     }
 }
 
-cudaError_t launch_refine(Ctx &c, const int *list, const int *count, int list_cap, double *out, int64_t chunk,
-                          int nchunks) {
+// Same contract as k_refine, for d <= 256: a tile of 64 points is staged in
+// shared memory with coalesced loads (rows padded to d + 1 floats so that the
+// 32 points a warp handles fall in distinct banks); each thread owns one
+// point of the tile and two of the group's 8 candidates, and both the FP32
+// screen and the FP64 exact distance read from shared memory.
+constexpr int RT = 64;  // points per staged tile
+
+template <bool BOUNDS>
+__global__ void __launch_bounds__(256) k_refine_tiled(const float *__restrict__ V, int64_t n, int d,
+                                                      const double *__restrict__ m64, const int *__restrict__ list,
+                                                      const int *__restrict__ count, int cap, int64_t chunk,
+                                                      int nchunks, double rho, double *__restrict__ out,
+                                                      double *__restrict__ out_hi) {
+    extern __shared__ __align__(16) float sm[];
+    const int dp = d + 1;
+    float *cs = sm;                 // [RB][d]
+    float *ps = sm + RB * d;        // [RT][d + 1]
+    __shared__ double ms[RT];
+    __shared__ double red[RB][8];
+    __shared__ double redh[RB][2];
+    const int cnt = min(*count, cap);
+    const int groups = (cnt + RB - 1) / RB;
+    const int64_t items = (int64_t)groups * nchunks;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int p = tid & (RT - 1);   // point of the tile
+    const int k0 = (tid >> 6) * 2;  // first of this thread's two candidates
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int grp = (int)(it / nchunks);
+        const int q = (int)(it % nchunks);
+        const int e0 = grp * RB;
+        const int ng = min(RB, cnt - e0);
+        __syncthreads();
+        for (int x = tid; x < RB * d; x += blockDim.x) {
+            int k = x / d, i = x % d;
+            cs[x] = k < ng ? V[(int64_t)list[e0 + k] * d + i] : 0.f;
+        }
+        const int64_t b = (int64_t)q * chunk, en = lmin(b + chunk, n);
+        double acc0 = 0.0, acc1 = 0.0, hi0 = 0.0, hi1 = 0.0;
+        for (int64_t v0 = b; v0 < en; v0 += RT) {
+            const int np = (int)lmin(RT, en - v0);
+            __syncthreads();
+            for (int x = tid; x < RT * d; x += blockDim.x) {
+                int r = x / d, i = x % d;
+                ps[r * dp + i] = r < np ? V[(v0 + r) * d + i] : 0.f;
+            }
+            if (tid < RT) ms[tid] = tid < np ? m64[v0 + tid] : -1.0;
+            __syncthreads();
+            const float *pr = ps + p * dp;
+            const float *c0 = cs + k0 * d;
+            const float *c1 = c0 + d;
+            float s0 = 0.f, s1 = 0.f;
+            for (int i = 0; i < d; ++i) {
+                const float x = pr[i];
+                const float a = x - c0[i], bb = x - c1[i];
+                s0 = fmaf(a, a, s0);
+                s1 = fmaf(bb, bb, s1);
+            }
+            const double mv = ms[p];
+            if (BOUNDS) {
+                if (p < np) {
+                    if (k0 < ng) bound_terms(mv, s0, rho, acc0, hi0);
+                    if (k0 + 1 < ng) bound_terms(mv, s1, rho, acc1, hi1);
+                }
+            } else if (p < np) {
+                if (k0 < ng && (double)s0 * (1.0 - rho) < mv) {
+                    const double t = mv - exact_sqdist(pr, c0, d);
+                    if (t > 0.0) acc0 += t;
+                }
+                if (k0 + 1 < ng && (double)s1 * (1.0 - rho) < mv) {
+                    const double t = mv - exact_sqdist(pr, c1, d);
+                    if (t > 0.0) acc1 += t;
+                }
+            }
+        }
+        // threads 64 j .. 64 j + 63 hold candidates 2 j, 2 j + 1: two warps each
+        for (int o = 16; o > 0; o >>= 1) {
+            acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+            acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+            if (BOUNDS) {
+                hi0 += __shfl_xor_sync(0xffffffffu, hi0, o);
+                hi1 += __shfl_xor_sync(0xffffffffu, hi1, o);
+            }
+        }
+        if (lane == 0) {
+            red[k0][w & 1] = acc0;
+            red[k0 + 1][w & 1] = acc1;
+            if (BOUNDS) {
+                redh[k0][w & 1] = hi0;
+                redh[k0 + 1][w & 1] = hi1;
+            }
+        }
+        __syncthreads();
+        if (tid < ng) {
+            out[(int64_t)(e0 + tid) * nchunks + q] = red[tid][0] + red[tid][1];
+            if (BOUNDS) out_hi[(int64_t)(e0 + tid) * nchunks + q] = redh[tid][0] + redh[tid][1];
+        }
+    }
+}
+
+cudaError_t launch_refine(Ctx &c, const int *list, const int *count, int list_cap, double *out, double *out_hi,
+                          int64_t chunk, int nchunks) {
+    if (c.d <= 256) {
+        const double rho = (double)(c.d + 4) * ldexp(1.0, -24);
+        const size_t sm = sizeof(float) * ((size_t)RB * c.d + (size_t)RT * (c.d + 1));
+        static size_t configured = 0;
+        if (sm > 48 * 1024 && sm > configured) {
+            cudaError_t e = cudaFuncSetAttribute(k_refine_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sm);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_refine_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            configured = sm;
+        }
+        if (out_hi)
+            k_refine_tiled<true><<<c.num_sms * 4, 256, sm, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, list_cap,
+                                                                        chunk, nchunks, rho, out, out_hi);
+        else
+            k_refine_tiled<false><<<c.num_sms * 4, 256, sm, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, list_cap,
+                                                                         chunk, nchunks, rho, out, nullptr);
+        return cudaGetLastError();
+    }
+    return launch_refine_rows(c, list, count, list_cap, out, out_hi, chunk, nchunks);
+}
+
+template <bool VEC4, bool BOUNDS>
+static cudaError_t refine_rows_one(Ctx &c, const int *list, const int *count, int list_cap, double *out,
+                                   double *out_hi, int64_t chunk, int nchunks) {
     const double rho = (double)(c.d + 4) * ldexp(1.0, -24);
     const int grid = c.num_sms * 4;
     const size_t sm = sizeof(float) * (size_t)c.d * RB;
     if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = cudaFuncSetAttribute(k_refine<VEC4, BOUNDS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (c.d % 4 == 0)
-        k_refine<true><<<grid, 256, sm, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, list_cap, chunk, nchunks, rho,
-                                                    out);
-    else
-        k_refine<false><<<grid, 256, sm, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, list_cap, chunk, nchunks,
-                                                     rho, out);
+    k_refine<VEC4, BOUNDS><<<grid, 256, sm, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, list_cap, chunk, nchunks,
+                                                        rho, out, out_hi);
     return cudaGetLastError();
+}
+
+cudaError_t launch_refine_rows(Ctx &c, const int *list, const int *count, int list_cap, double *out,
+                               double *out_hi, int64_t chunk, int nchunks) {
+    const bool v4 = c.d % 4 == 0;
+    if (out_hi)
+        return v4 ? refine_rows_one<true, true>(c, list, count, list_cap, out, out_hi, chunk, nchunks)
+                  : refine_rows_one<false, true>(c, list, count, list_cap, out, out_hi, chunk, nchunks);
+    return v4 ? refine_rows_one<true, false>(c, list, count, list_cap, out, nullptr, chunk, nchunks)
+              : refine_rows_one<false, false>(c, list, count, list_cap, out, nullptr, chunk, nchunks);
 }
 
 // Escalated candidates beyond the chunked buffer's capacity: one block per
@@ -378,50 +478,6 @@ cudaError_t launch_refine_overflow(Ctx &c, const int *list, const int *count, in
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Decide the round from the top-K exact gains.  The pick is certified when
-// the best exact gain is at least (1 + eta) times the (K+1)-th upper bound,
-// because every other candidate's exact gain is at most (1 + eta) times its
-// bound and every such bound is at most the (K+1)-th.
-// ---------------------------------------------------------------------------
-__global__ void k_decide(const double *__restrict__ ref_part, int nchunks, double inv_n, const int *__restrict__ top_idx,
-                         const double *__restrict__ top_val, double *__restrict__ top_exact, double eta, DevState *st) {
-    if (threadIdx.x != 0) return;
-    int cnt = st->top_count;
-    double best = -1.0;
-    int bi = INT_MAX;
-    double maxerr = st->max_raw_rel_err;
-    for (int e = 0; e < cnt; ++e) {
-        double s = 0.0;
-        for (int q = 0; q < nchunks; ++q) s += ref_part[(int64_t)e * nchunks + q];
-        s *= inv_n;
-        top_exact[e] = s;
-        if (better(s, top_idx[e], best, bi)) {
-            best = s;
-            bi = top_idx[e];
-        }
-        if (s > 0.0) maxerr = fmax(maxerr, (top_val[e] - s) / s);
-    }
-    st->max_raw_rel_err = maxerr;
-    double thr = st->top_thr;
-    int need = 0, zero_scan = 0;
-    if (thr < 0.0) {
-        need = 0;  // no candidate outside the top list
-    } else if (best > 0.0) {
-        need = !(best >= thr * (1.0 + eta));
-    } else if (thr > 0.0) {
-        need = 1;  // best is 0 but some bound is not: evaluate every remaining candidate
-    } else {
-        zero_scan = 1;  // every gain is 0: the pick is the smallest unselected index
-    }
-    st->need_esc = need;
-    st->zero_scan = zero_scan;
-    st->esc_thr = best;
-    st->esc_count = 0;
-    st->pick_gain = best;
-    st->pick = bi;
-}
-
 // Collect every unselected candidate outside the top list whose bound could
 // reach the best exact gain.
 __global__ void k_collect(const double *__restrict__ gain_up, int64_t m, const int *__restrict__ top_idx, double eta,
@@ -444,64 +500,6 @@ __global__ void k_collect(const double *__restrict__ gain_up, int64_t m, const i
 cudaError_t launch_collect_escalation(Ctx &c, double eta) {
     k_collect<<<kNumSMsHint * 2, 256, 0, c.stream>>>(c.gain_up, c.n, c.top_idx, eta, c.st, c.esc_idx, (int)c.n);
     return cudaGetLastError();
-}
-
-// Final pick: best of the top list and the escalated list, then commit.
-__global__ void k_commit(const double *__restrict__ esc_part, int nchunks, int cap, double inv_n,
-                         const int *__restrict__ esc_idx, double *__restrict__ esc_exact, uint8_t *__restrict__ sel,
-                         int64_t n, int32_t *__restrict__ out_idx, double *__restrict__ out_f, DevState *st) {
-    double bv = st->pick_gain;
-    int bi = st->pick;
-    if (st->need_esc) {
-        int cnt = st->esc_count;
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-            double s;
-            if (e < cap) {
-                s = 0.0;
-                for (int q = 0; q < nchunks; ++q) s += esc_part[(int64_t)e * nchunks + q];
-                s *= inv_n;
-                esc_exact[e] = s;
-            } else {
-                s = esc_exact[e];  // written by the overflow kernel
-            }
-            if (better(s, esc_idx[e], bv, bi)) {
-                bv = s;
-                bi = esc_idx[e];
-            }
-        }
-    }
-    if (st->zero_scan) {
-        // all remaining gains are exactly 0: smallest unselected index wins
-        bv = 0.0;
-        bi = INT_MAX;
-        for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
-            if (!sel[j]) {
-                bi = (int)j;
-                break;
-            }
-    }
-    block_best(bv, bi);
-    if (threadIdx.x == 0) {
-        if (bi == INT_MAX || bi < 0) {
-            if (st->err == 0) st->err = (int)EBC_EINVAL;  // no candidate left (host checks prevent this)
-            return;
-        }
-        int r = st->round;
-        sel[bi] = 1;
-        st->f += bv;
-        st->pick = bi;
-        st->pick_gain = bv;
-        if (out_idx) out_idx[r] = bi;
-        if (out_f) out_f[r] = st->f;
-        st->round = r + 1;
-        st->rounds += 1;
-        if (st->need_esc) {
-            st->escalated_rounds += 1;
-            st->escalated_cands += st->esc_count;
-        } else {
-            st->certified += 1;
-        }
-    }
 }
 
 // m_v <- min(m_v, d(v, c*)) with the exact distance; points whose screen
@@ -550,19 +548,6 @@ __global__ void k_current_f(const double *__restrict__ nv64, const double *__res
 
 cudaError_t launch_current_f(Ctx &c, double *d_out) {
     k_current_f<<<1, 1024, 0, c.stream>>>(c.nv64, c.m64, c.n, 1.0 / (double)c.n, d_out);
-    return cudaGetLastError();
-}
-
-// exported helpers for api.cu ---------------------------------------------------
-cudaError_t launch_decide_n(Ctx &c, int nchunks, double eta) {
-    k_decide<<<1, 32, 0, c.stream>>>(c.ref_part, nchunks, 1.0 / (double)c.n, c.top_idx, c.top_val, c.top_exact, eta,
-                                     c.st);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_commit_n(Ctx &c, const double *esc_part, int nchunks, int cap, int32_t *out_idx, double *out_f) {
-    k_commit<<<1, 256, 0, c.stream>>>(esc_part, nchunks, cap, 1.0 / (double)c.n, c.esc_idx, c.esc_exact, c.sel, c.n,
-                                      out_idx, out_f, c.st);
     return cudaGetLastError();
 }
 

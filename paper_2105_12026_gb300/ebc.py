@@ -35,7 +35,8 @@ class EbcError(RuntimeError):
 class ebc_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int64), ("certified_rounds", ctypes.c_int64),
                 ("escalated_rounds", ctypes.c_int64), ("escalated_candidates", ctypes.c_int64),
-                ("max_raw_rel_err", ctypes.c_double), ("prec", ctypes.c_int32), ("refine_k", ctypes.c_int32)]
+                ("max_raw_rel_err", ctypes.c_double), ("exact_evaluations", ctypes.c_int64),
+                ("prec", ctypes.c_int32), ("refine_k", ctypes.c_int32)]
 
 
 class ebc_profile(ctypes.Structure):

@@ -135,7 +135,21 @@ def test_tc_greedy_duplicates_to_exhaustion(torch):
         st = inst.stats()
     assert sorted(idx.tolist()) == list(range(n))
     check_greedy(idx, f, *ref)
-    assert st["escalated_rounds"] > 0  # zero-gain tail and ties need escalation
+    assert st["exact_evaluations"] >= n  # at least one contender per round
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp32"])
+def test_refine_k1_forces_escalation(torch, prec):
+    # with a single leader the (K+1)-th bulk bound nearly always reaches the
+    # leader's lower bound, so the escalation path decides most rounds
+    V = gmm(3000, 24, 77, clusters=5)
+    ref = oracle.greedy(V, 12)
+    with ebc.Instance(V, precision=prec, refine_k=1) as inst:
+        idx, f = inst.greedy_host(12)
+        st = inst.stats()
+    check_greedy(idx, f, *ref)
+    assert st["escalated_rounds"] > 0
+    assert st["certified_rounds"] + st["escalated_rounds"] == 12
 
 
 def test_tc_switch_precision_and_reload(torch):
