@@ -552,7 +552,7 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
     ebc::Ctx::Sel &S = c.cert;
     const int64_t esc_off = (int64_t)ebc::kMaxRefineK * S.nchunks;
     CK(h, launch(h, PK_REFINE, 1, [&] {
-           return ebc::launch_refine(c, c.top_idx, &c.st->top_count, K, S.part_lo, S.part_hi, S.chunk, S.nchunks);
+           return ebc::launch_bounds_list(c, c.top_idx, &c.st->top_count, K, S.part_lo, S.part_hi, S.chunk, S.nchunks);
        }));
     CK(h, launch(h, -1, 3, [&] {
            cudaError_t e = ebc::launch_fold_bounds(c, S.part_lo, S.part_hi, &c.st->top_count, K, S.top_lo, S.top_hi);
@@ -560,8 +560,8 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
            return e != cudaSuccess ? e : ebc::launch_collect_escalation(c, eta);
        }));
     CK(h, launch(h, PK_REFINE, 2, [&] {
-           cudaError_t e = ebc::launch_refine(c, c.esc_idx, &c.st->esc_count, S.cap, S.part_lo + esc_off,
-                                              S.part_hi + esc_off, S.chunk, S.nchunks);
+           cudaError_t e = ebc::launch_bounds_list(c, c.esc_idx, &c.st->esc_count, S.cap, S.part_lo + esc_off,
+                                                   S.part_hi + esc_off, S.chunk, S.nchunks);
            return e != cudaSuccess ? e : ebc::launch_refine_overflow(c, c.esc_idx, &c.st->esc_count, S.cap, c.esc_exact);
        }));
     CK(h, launch(h, -1, 2, [&] {
@@ -571,8 +571,8 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
        }));
     // level 2: exact gains of the contenders only
     CK(h, launch(h, PK_REFINE, 1, [&] {
-           return ebc::launch_refine(c, S.ctd_idx, &c.st->ctd_count, ebc::kMaxRefineK + S.cap, S.ctd_part, nullptr,
-                                     S.chunk, S.nchunks);
+           return ebc::launch_exact_list(c, S.ctd_idx, &c.st->ctd_count, ebc::kMaxRefineK + S.cap, S.ctd_part,
+                                         S.chunk, S.nchunks);
        }));
     CK(h, launch(h, -1, 2, [&] {
            cudaError_t e = ebc::launch_commit_pick(c, out_idx_base, out_f_base);

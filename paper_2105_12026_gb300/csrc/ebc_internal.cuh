@@ -13,6 +13,7 @@
 namespace ebc {
 
 constexpr int kMaxRefineK = 32;
+constexpr int kRefineTile = 64;  // points per shared-memory tile of the exact / bound kernels
 
 __host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t lmax(int64_t a, int64_t b) { return a > b ? a : b; }
@@ -133,6 +134,14 @@ cudaError_t launch_collect_escalation(Ctx &c, double eta);
 cudaError_t launch_refine_overflow(Ctx &c, const int *list, const int *count, int cap, double *out_exact);
 cudaError_t launch_refine_rows(Ctx &c, const int *list, const int *count, int list_cap, double *out,
                                double *out_hi, int64_t chunk, int nchunks);
+cudaError_t launch_bounds_fp32(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
+                               int64_t chunk, int nchunks, float kh, float kl);
+// [lo, hi] gain bounds (register-tiled FP32) / exact gains (one candidate per
+// block) of a device list with device count, as chunk partials
+cudaError_t launch_bounds_list(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
+                               int64_t chunk, int nchunks);
+cudaError_t launch_exact_list(Ctx &c, const int *list, const int *count, int cap, double *out, int64_t chunk,
+                              int nchunks);
 // two-level certified pick (k_select.cu)
 cudaError_t launch_fold_bounds(Ctx &c, const double *part_lo, const double *part_hi, const int *count, int cap,
                                double *lo, double *hi);

@@ -27,6 +27,31 @@ __device__ __forceinline__ double exact_sqdist(const float *__restrict__ v, cons
     return acc;
 }
 
+// Squared distance in double-FP32 arithmetic: each difference is split
+// exactly into s + e (TwoSum), s^2 exactly into p + pe (FMA), and the terms
+// are accumulated as an unevaluated pair (hi, lo) with TwoSum.  The result
+// hi + lo is within about d * 2^-44 relative of the exact distance, using
+// FP32 units only (FP64 throughput is a small fraction of FP32 on this GPU).
+__device__ __forceinline__ double df_sqdist(const float *__restrict__ v, const float *__restrict__ c, int d) {
+    // explicit _rn intrinsics: the compiler must not contract these into FMAs
+    float hi = 0.f, lo = 0.f;
+    for (int i = 0; i < d; ++i) {
+        const float a = v[i], b = -c[i];
+        const float s = __fadd_rn(a, b);
+        const float bp = __fsub_rn(s, a);
+        const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));  // a - c = s + e
+        const float p = __fmul_rn(s, s);
+        const float pe = __fmaf_rn(s, s, -p);                  // s^2 = p + pe exactly
+        const float t = __fmaf_rn(__fmul_rn(2.f, s), e, pe);   // + 2 s e (e^2 < 2^-48 s^2)
+        const float h = __fadd_rn(hi, p);
+        const float z = __fsub_rn(h, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(h, z)), __fsub_rn(p, z));  // hi + p = h + err
+        lo = __fadd_rn(lo, __fadd_rn(err, t));
+        hi = h;
+    }
+    return (double)hi + (double)lo;
+}
+
 // FP32 direct distance; |result - exact| <= (d + 4) * 2^-24 * exact.
 __device__ __forceinline__ float screen_sqdist(const float *__restrict__ v, const float *__restrict__ c, int d) {
     float acc = 0.f;
@@ -193,14 +218,30 @@ cudaError_t launch_merge_top(Ctx &c, int nblk, int K, double) {
 // ---------------------------------------------------------------------------
 constexpr int RB = 8;
 
-// Rigorous bounds on max(0, m_v - d) from the FP32 screen distance s, for
-// which d lies in [s / (1 + rho), s / (1 - rho)] within [s (1 - rho), s (1 + 2 rho)].
-__device__ __forceinline__ void bound_terms(double mv, float s, double rho, double &lo, double &hi) {
-    const double sd = (double)s;
-    const double th = __dsub_ru(mv, __dmul_rd(sd, 1.0 - rho));
-    const double tl = __dsub_rd(mv, __dmul_ru(sd, 1.0 + 2.0 * rho));
-    if (th > 0.0) hi += th;
-    if (tl > 0.0) lo += tl;
+// Bounds on max(0, m_v - d) from the FP32 screen distance s, for which d
+// lies in [s / (1 + rho), s / (1 - rho)], inside [s (1 - rho), s (1 + 2 rho)]:
+//   hi term max(0, mU - kh s), kh = 1 - rho rounded down, mU = m_v rounded up
+//   lo term max(0, mD - kl s), kl = 1 + 2 rho rounded up, mD = m_v rounded down
+// formed with one FP32 FMA each.  A term is off by at most one rounding and
+// a thread sums at most kBoundTermsPerThread of them in FP32, so the folded
+// sums are widened by kEta32 relative (k_select.cu) to stay rigorous.
+struct BoundConsts {
+    float kh, kl;
+};
+
+__host__ __device__ inline BoundConsts bound_consts(int d) {
+    const double rho = (double)(d + 4) * ldexp(1.0, -24);
+    BoundConsts b;
+    b.kh = (float)(1.0 - rho);
+    if ((double)b.kh > 1.0 - rho) b.kh = nextafterf(b.kh, 0.f);
+    b.kl = (float)(1.0 + 2.0 * rho);
+    if ((double)b.kl < 1.0 + 2.0 * rho) b.kl = nextafterf(b.kl, 2.f);
+    return b;
+}
+
+__device__ __forceinline__ void bound_terms(float mU, float mD, float s, BoundConsts bc, float &lo, float &hi) {
+    hi += fmaxf(fmaf(-bc.kh, s, mU), 0.f);
+    lo += fmaxf(fmaf(-bc.kl, s, mD), 0.f);
 }
 
 template <bool VEC4, bool BOUNDS>
@@ -262,7 +303,10 @@ __global__ void __launch_bounds__(256) k_refine(const float *__restrict__ V, int
             for (int k = 0; k < RB; ++k) {
                 if (k >= ng) continue;
                 if (BOUNDS) {
-                    bound_terms(mv, sd[k], rho, acc[k], acch[k]);
+                    float l = 0.f, hh = 0.f;
+                    bound_terms(__double2float_ru(mv), __double2float_rd(mv), sd[k], bound_consts(d), l, hh);
+                    acc[k] += (double)l;
+                    acch[k] += (double)hh;
                     continue;
                 }
                 if ((double)sd[k] * (1.0 - rho) >= mv) continue;  // exact distance >= m_v: term 0
@@ -294,7 +338,7 @@ __global__ void __launch_bounds__(256) k_refine(const float *__restrict__ V, int
 // 32 points a warp handles fall in distinct banks); each thread owns one
 // point of the tile and two of the group's 8 candidates, and both the FP32
 // screen and the FP64 exact distance read from shared memory.
-constexpr int RT = 64;  // points per staged tile
+constexpr int RT = kRefineTile;  // points per staged tile
 
 template <bool BOUNDS>
 __global__ void __launch_bounds__(256) k_refine_tiled(const float *__restrict__ V, int64_t n, int d,
@@ -307,8 +351,10 @@ __global__ void __launch_bounds__(256) k_refine_tiled(const float *__restrict__ 
     float *cs = sm;                 // [RB][d]
     float *ps = sm + RB * d;        // [RT][d + 1]
     __shared__ double ms[RT];
+    __shared__ float msu[RT], msd[RT];
     __shared__ double red[RB][8];
     __shared__ double redh[RB][2];
+    const BoundConsts bcst = bound_consts(d);
     const int cnt = min(*count, cap);
     const int groups = (cnt + RB - 1) / RB;
     const int64_t items = (int64_t)groups * nchunks;
@@ -327,6 +373,7 @@ __global__ void __launch_bounds__(256) k_refine_tiled(const float *__restrict__ 
         }
         const int64_t b = (int64_t)q * chunk, en = lmin(b + chunk, n);
         double acc0 = 0.0, acc1 = 0.0, hi0 = 0.0, hi1 = 0.0;
+        float fl0 = 0.f, fl1 = 0.f, fh0 = 0.f, fh1 = 0.f;  // FP32 bound sums of this item
         for (int64_t v0 = b; v0 < en; v0 += RT) {
             const int np = (int)lmin(RT, en - v0);
             __syncthreads();
@@ -334,7 +381,12 @@ __global__ void __launch_bounds__(256) k_refine_tiled(const float *__restrict__ 
                 int r = x / d, i = x % d;
                 ps[r * dp + i] = r < np ? V[(v0 + r) * d + i] : 0.f;
             }
-            if (tid < RT) ms[tid] = tid < np ? m64[v0 + tid] : -1.0;
+            if (tid < RT) {
+                const double mm = tid < np ? m64[v0 + tid] : -1.0;
+                ms[tid] = mm;
+                msu[tid] = __double2float_ru(mm);
+                msd[tid] = __double2float_rd(mm);
+            }
             __syncthreads();
             const float *pr = ps + p * dp;
             const float *c0 = cs + k0 * d;
@@ -349,8 +401,8 @@ __global__ void __launch_bounds__(256) k_refine_tiled(const float *__restrict__ 
             const double mv = ms[p];
             if (BOUNDS) {
                 if (p < np) {
-                    if (k0 < ng) bound_terms(mv, s0, rho, acc0, hi0);
-                    if (k0 + 1 < ng) bound_terms(mv, s1, rho, acc1, hi1);
+                    if (k0 < ng) bound_terms(msu[p], msd[p], s0, bcst, fl0, fh0);
+                    if (k0 + 1 < ng) bound_terms(msu[p], msd[p], s1, bcst, fl1, fh1);
                 }
             } else if (p < np) {
                 if (k0 < ng && (double)s0 * (1.0 - rho) < mv) {
@@ -362,6 +414,12 @@ __global__ void __launch_bounds__(256) k_refine_tiled(const float *__restrict__ 
                     if (t > 0.0) acc1 += t;
                 }
             }
+        }
+        if (BOUNDS) {
+            acc0 = fl0;
+            acc1 = fl1;
+            hi0 = fh0;
+            hi1 = fh1;
         }
         // threads 64 j .. 64 j + 63 hold candidates 2 j, 2 j + 1: two warps each
         for (int o = 16; o > 0; o >>= 1) {
@@ -436,6 +494,87 @@ cudaError_t launch_refine_rows(Ctx &c, const int *list, const int *count, int li
                   : refine_rows_one<false, true>(c, list, count, list_cap, out, out_hi, chunk, nchunks);
     return v4 ? refine_rows_one<true, false>(c, list, count, list_cap, out, nullptr, chunk, nchunks)
               : refine_rows_one<false, false>(c, list, count, list_cap, out, nullptr, chunk, nchunks);
+}
+
+// Exact gains of a short list (the contenders), one candidate per item:
+// out[e * nchunks + q] = sum over chunk q of max(0, m_v - d(v, c_e)), with d
+// from the double-FP32 distance for pairs the FP32 screen cannot exclude.
+// Point tiles of 128 rows are staged in shared memory (padded rows); one
+// thread per point.  For d <= 256.
+constexpr int XT = 128;
+
+__global__ void __launch_bounds__(XT) k_exact_one(const float *__restrict__ V, int64_t n, int d,
+                                                  const double *__restrict__ m64, const int *__restrict__ list,
+                                                  const int *__restrict__ count, int cap, int64_t chunk, int nchunks,
+                                                  double rho, double *__restrict__ out) {
+    extern __shared__ __align__(16) float smx[];
+    const int dp = d + 1;
+    float *cs = smx;       // [d]
+    float *ps = smx + d;   // [XT][d + 1]
+    __shared__ double red[XT / 32];
+    const int cnt = min(*count, cap);
+    const int64_t items = (int64_t)cnt * nchunks;
+    const int tid = threadIdx.x;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int e = (int)(it / nchunks);
+        const int q = (int)(it % nchunks);
+        __syncthreads();
+        for (int i = tid; i < d; i += XT) cs[i] = V[(int64_t)list[e] * d + i];
+        const int64_t b = (int64_t)q * chunk, en = lmin(b + chunk, n);
+        double acc = 0.0;
+        for (int64_t v0 = b; v0 < en; v0 += XT) {
+            const int np = (int)lmin(XT, en - v0);
+            __syncthreads();
+            for (int x = tid; x < XT * d; x += XT) {
+                int r = x / d, i = x % d;
+                ps[r * dp + i] = r < np ? V[(v0 + r) * d + i] : 0.f;
+            }
+            __syncthreads();
+            if (tid < np) {
+                const float *pr = ps + tid * dp;
+                float s = 0.f;
+                for (int i = 0; i < d; ++i) {
+                    const float df = pr[i] - cs[i];
+                    s = fmaf(df, df, s);
+                }
+                const double mv = m64[v0 + tid];
+                if ((double)s * (1.0 - rho) < mv) {
+                    const double t = mv - df_sqdist(pr, cs, d);
+                    if (t > 0.0) acc += t;
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((tid & 31) == 0) red[tid >> 5] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < XT / 32; ++w) s += red[w];
+            out[(int64_t)e * nchunks + q] = s;
+        }
+    }
+}
+
+cudaError_t launch_exact_list(Ctx &c, const int *list, const int *count, int cap, double *out, int64_t chunk,
+                              int nchunks) {
+    if (c.d > 256) return launch_refine_rows(c, list, count, cap, out, nullptr, chunk, nchunks);
+    const double rho = (double)(c.d + 4) * ldexp(1.0, -24);
+    const size_t sm = sizeof(float) * ((size_t)c.d + (size_t)XT * (c.d + 1));
+    static size_t configured = 0;
+    if (sm > 48 * 1024 && sm > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_exact_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        configured = sm;
+    }
+    k_exact_one<<<c.num_sms * 4, XT, sm, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk, nchunks, rho,
+                                                     out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds_list(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
+                               int64_t chunk, int nchunks) {
+    const BoundConsts bc = bound_consts(c.d);
+    return launch_bounds_fp32(c, list, count, cap, out_lo, out_hi, chunk, nchunks, bc.kh, bc.kl);
 }
 
 // Escalated candidates beyond the chunked buffer's capacity: one block per

@@ -147,6 +147,141 @@ cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, in
 }
 
 // ---------------------------------------------------------------------------
+// Rigorous [lo, hi] bounds of the gains of a device candidate list (count
+// read from device memory), as chunk partials:
+//   out_lo[e * nchunks + q] / out_hi[...] = sum over chunk q of the FP32
+//   bound terms max(0, mD - kl s) / max(0, mU - kh s), s the FP32 direct
+//   distance (see bound_consts in k_common.cu for the constants).
+// Same register tiling as k_gains_fp32; grid-stride over (candidate tile of
+// 64, chunk) items.  A thread adds its 8 terms per point tile in FP32, then
+// the 16 lanes of a candidate in FP32, then tiles in FP64: at most
+// 128 terms per FP32 sum.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V, int64_t n, int d,
+                                                     const double *__restrict__ m64, const int *__restrict__ list,
+                                                     const int *__restrict__ count, int cap, int64_t chunk,
+                                                     int nchunks, float kh, float kl, double *__restrict__ out_lo,
+                                                     double *__restrict__ out_hi) {
+    __shared__ __align__(16) float Cs[KC][TC];
+    __shared__ __align__(16) float Vs[KC][TV];
+    __shared__ float MsU[TV], MsD[TV];
+    __shared__ int Ci[TC];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int cnt = min(*count, cap);
+    const int ctiles = (cnt + TC - 1) / TC;
+    const int64_t items = (int64_t)ctiles * nchunks;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int ct = (int)(it / nchunks);
+        const int q = (int)(it % nchunks);
+        const int64_t vb = (int64_t)q * chunk;
+        const int64_t ve = lmin(vb + chunk, n);
+        __syncthreads();
+        if (tid < TC) {
+            const int e = ct * TC + tid;
+            Ci[tid] = e < cnt ? list[e] : -1;
+        }
+        double lod[4] = {0.0, 0.0, 0.0, 0.0}, hid[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t v0 = vb; v0 < ve; v0 += TV) {
+            __syncthreads();
+            if (tid < TV) {
+                const int64_t v = v0 + tid;
+                float mu = -INFINITY, md = -INFINITY;
+                if (v < ve) {
+                    const double mm = m64[v];
+                    mu = __double2float_ru(mm);
+                    md = __double2float_rd(mm);
+                }
+                MsU[tid] = mu;
+                MsD[tid] = md;
+            }
+            float acc[4][8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            for (int k0 = 0; k0 < d; k0 += KC) {
+                __syncthreads();
+#pragma unroll
+                for (int s = 0; s < (TC * KC) / 256; ++s) {
+                    int e = tid + 256 * s;
+                    int r = e / KC, kk = e % KC;
+                    int ci = Ci[r];
+                    Cs[kk][r] = (ci >= 0 && k0 + kk < d) ? V[(int64_t)ci * d + k0 + kk] : 0.f;
+                }
+#pragma unroll
+                for (int s = 0; s < (TV * KC) / 256; ++s) {
+                    int e = tid + 256 * s;
+                    int r = e / KC, kk = e % KC;
+                    int64_t v = v0 + r;
+                    Vs[kk][r] = (v < ve && k0 + kk < d) ? V[v * d + k0 + kk] : 0.f;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < KC; ++kk) {
+                    float4 c4 = *reinterpret_cast<const float4 *>(&Cs[kk][ty * 4]);
+                    float4 va = *reinterpret_cast<const float4 *>(&Vs[kk][tx * 4]);
+                    float4 vb4 = *reinterpret_cast<const float4 *>(&Vs[kk][64 + tx * 4]);
+                    float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                    float vv[8] = {va.x, va.y, va.z, va.w, vb4.x, vb4.y, vb4.z, vb4.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float df = vv[j] - cv[i];
+                            acc[i][j] = fmaf(df, df, acc[i][j]);
+                        }
+                }
+            }
+            float mu[8], md[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                mu[j] = MsU[tx * 4 + j];
+                mu[4 + j] = MsU[64 + tx * 4 + j];
+                md[j] = MsD[tx * 4 + j];
+                md[4 + j] = MsD[64 + tx * 4 + j];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float sl = 0.f, sh = 0.f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    sh += fmaxf(fmaf(-kh, acc[i][j], mu[j]), 0.f);
+                    sl += fmaxf(fmaf(-kl, acc[i][j], md[j]), 0.f);
+                }
+                sh += __shfl_xor_sync(0xffffffffu, sh, 1);
+                sh += __shfl_xor_sync(0xffffffffu, sh, 2);
+                sh += __shfl_xor_sync(0xffffffffu, sh, 4);
+                sh += __shfl_xor_sync(0xffffffffu, sh, 8);
+                sl += __shfl_xor_sync(0xffffffffu, sl, 1);
+                sl += __shfl_xor_sync(0xffffffffu, sl, 2);
+                sl += __shfl_xor_sync(0xffffffffu, sl, 4);
+                sl += __shfl_xor_sync(0xffffffffu, sl, 8);
+                hid[i] += (double)sh;
+                lod[i] += (double)sl;
+            }
+        }
+        if (tx == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int e = ct * TC + ty * 4 + i;
+                if (e < cnt) {
+                    out_lo[(int64_t)e * nchunks + q] = lod[i];
+                    out_hi[(int64_t)e * nchunks + q] = hid[i];
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_bounds_fp32(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
+                               int64_t chunk, int nchunks, float kh, float kl) {
+    k_bounds_fp32<<<c.num_sms * 4, 256, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk, nchunks, kh,
+                                                       kl, out_lo, out_hi);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Multi-set evaluation, FP32 direct distances.
 // Block: 128 threads, one point each; the block's 128 points are staged in
 // shared memory dimension-major (Vt[i][t]) when d <= 128, otherwise each

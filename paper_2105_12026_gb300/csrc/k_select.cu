@@ -22,16 +22,22 @@
 namespace ebc {
 
 namespace {
-// relative slack for FP64 sums of bound terms (at most ~2^31 terms of one
-// sign, each sum rounding error <= count * 2^-53)
-constexpr double kEta64 = 1e-10;
+// Relative widening of the folded bounds.  Each bound term is one FP32
+// rounding from its exact value; the bound kernel adds at most 128 terms of
+// one sign in FP32 (8 per thread, then 16 lanes) before the FP64 sums over
+// tiles and chunks, so the relative error is at most 130 * 2^-24 plus the
+// FP64 part.
+double fold_eta(int64_t chunk) {
+    (void)chunk;
+    return 131.0 * ldexp(1.0, -24) + 1e-12;
+}
 }  // namespace
 
-// lo[e] / hi[e] = (sum over chunks of the partials) / n, widened by kEta64.
+// lo[e] / hi[e] = (sum over chunks of the partials) / n, widened by eta.
 // One warp per entry, lane-strided partial sums, then a fixed tree.
 __global__ void k_fold_bounds(const double *__restrict__ part_lo, const double *__restrict__ part_hi, int nchunks,
-                              const int *__restrict__ count, int cap, double inv_n, double *__restrict__ lo,
-                              double *__restrict__ hi) {
+                              const int *__restrict__ count, int cap, double inv_n, double eta,
+                              double *__restrict__ lo, double *__restrict__ hi) {
     const int cnt = min(*count, cap);
     const int lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
@@ -46,8 +52,8 @@ __global__ void k_fold_bounds(const double *__restrict__ part_lo, const double *
             sh += __shfl_xor_sync(0xffffffffu, sh, o);
         }
         if (lane == 0) {
-            lo[e] = sl * inv_n * (1.0 - kEta64);
-            hi[e] = sh * inv_n * (1.0 + kEta64);
+            lo[e] = sl * inv_n * (1.0 - eta);
+            hi[e] = sh * inv_n * (1.0 + eta);
         }
     }
 }
@@ -55,7 +61,8 @@ __global__ void k_fold_bounds(const double *__restrict__ part_lo, const double *
 cudaError_t launch_fold_bounds(Ctx &c, const double *part_lo, const double *part_hi, const int *count, int cap,
                                double *lo, double *hi) {
     const int blocks = (int)lmin((cap + 7) / 8, (int64_t)c.num_sms * 2);
-    k_fold_bounds<<<blocks, 256, 0, c.stream>>>(part_lo, part_hi, c.cert.nchunks, count, cap, 1.0 / (double)c.n, lo, hi);
+    k_fold_bounds<<<blocks, 256, 0, c.stream>>>(part_lo, part_hi, c.cert.nchunks, count, cap, 1.0 / (double)c.n,
+                                                fold_eta(c.cert.chunk), lo, hi);
     return cudaGetLastError();
 }
 
