@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "EBC distance-evals/s, BF16-TC vs FP32 plain at matched picks; serve p99 ms"
 UNIT = "distance-evals/s"
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch of the bulk kernel from one ncu capture
+# of the current kernel (profiles/k_gains_tc_bf16_regime_n200k_d128.md), keyed
+# by (precision, n, d); None where no capture of the current kernel exists.
+NCU_TRAFFIC = {("bf16", 200_000, 128): 260.643328e6 + 11.546624e6}
 
 
 def peaks():
@@ -282,7 +286,7 @@ def main():
                 "peak_source": f"{pk['source']} bf16 sustained" + (" x2 (fp8 nominal ratio)" if args.prec == "fp8" else "")}
     achieved = flops / bulk_avg_s / 1e12 if bulk_avg_s > 0 else None
     roof.update({"achieved": achieved, "peak": peak, "frac": (achieved / peak) if achieved else None,
-                 "traffic": None, "kernel": "bulk gains", "launches": prof["bulk_launches"],
+                 "traffic": NCU_TRAFFIC.get((args.prec, n, d)), "traffic_unit": "bytes per launch (ncu)", "kernel": "bulk gains", "launches": prof["bulk_launches"],
                  "avg_ms": bulk_avg_s * 1e3, "algorithmic_flops_per_launch": flops})
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
