@@ -163,6 +163,11 @@ ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *o
  */
 ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);
 
+/* Replay Greedy rounds from a captured CUDA graph (1, the default) or issue
+ * every kernel directly (0).  Graph replay needs a non-NULL stream and is
+ * not used while profiling is on. */
+ebc_status ebc_set_graphs(ebc_t h, int32_t on);
+
 /* Host-pointer form of ebc_greedy. */
 ebc_status ebc_greedy_host(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);
 
@@ -230,6 +235,56 @@ const char *ebc_noalloc_last_error(void);
 /* Text of the last error on this handle ("" if none); h may be NULL for
  * errors from ebc_create.  The pointer stays valid until the next call. */
 const char *ebc_last_error(ebc_t h);
+
+/* Device bytes a handle for (n, d, prec) allocates (an estimate the batch
+ * runtime uses for admission); -1 for bad sizes. */
+int64_t ebc_estimate_bytes(int64_t n, int32_t d, int32_t prec);
+
+/* ------------------------------------------------------------------------
+ * Batch runtime: many independent instances on one GPU.  Not in the paper,
+ * which evaluates one optimiser at a time; it serves the many-request case
+ * its optimisers generate.  Each admitted instance gets its own handle and
+ * stream; ebc_batch_step() advances every active instance by one Greedy
+ * round, so their work overlaps on the device; finished instances free
+ * their slot and memory and queued requests are admitted first-come
+ * first-served while a slot is free and the device-memory budget allows
+ * (a request larger than the whole budget runs when nothing else does).
+ * Single host thread per batch.
+ * ---------------------------------------------------------------------- */
+typedef struct ebc_batch_ctx *ebc_batch_t;
+
+typedef struct {
+    int64_t submitted, completed, active, queued;
+    int64_t bytes_in_use, bytes_peak; /* estimated device bytes of admitted instances */
+    int64_t rounds_issued;
+} ebc_batch_info;
+
+/* max_slots concurrent instances, device_budget_bytes for their handles, K
+ * leaders re-evaluated per round (as ebc_set_precision). */
+ebc_status ebc_batch_create(int32_t max_slots, int64_t device_budget_bytes, int32_t refine_k, ebc_batch_t *out);
+
+/* Queue one Greedy summary of k picks over the host array V (n x d FP32,
+ * row-major, copied).  *ticket identifies the request.  EINVAL for bad
+ * sizes, k > n, or a tensor-core precision with d > 128. */
+ebc_status ebc_batch_submit(ebc_batch_t b, const float *V, int64_t n, int32_t d, int32_t k, ebc_prec prec,
+                            int64_t *ticket);
+
+/* Reap finished instances, admit queued ones, issue one round for every
+ * active instance.  Asynchronous; reports active and queued counts. */
+ebc_status ebc_batch_step(ebc_batch_t b, int32_t *n_active, int32_t *n_queued);
+
+/* *done = 1 and the k picks / f values copied out (out arrays of capacity
+ * cap) once the request finished; returns that request's status.  *done = 0
+ * while pending.  A finished result is handed out once. */
+ebc_status ebc_batch_poll(ebc_batch_t b, int64_t ticket, int32_t *out_idx, double *out_f, int32_t cap,
+                          int32_t *done);
+
+/* Step until every submitted request has finished. */
+ebc_status ebc_batch_run(ebc_batch_t b);
+
+ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out);
+const char *ebc_batch_last_error(ebc_batch_t b);
+ebc_status ebc_batch_destroy(ebc_batch_t b);
 
 #ifdef __cplusplus
 }

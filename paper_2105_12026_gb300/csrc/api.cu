@@ -36,6 +36,15 @@ struct ebc_ctx {
     int esc_cap = 0;        // escalated candidates with chunked partials
     double *d_scalar = nullptr;  // one device double for ebc_current_f
     int *d_bad = nullptr;
+    // one Greedy round captured as a CUDA graph, replayed for later rounds
+    int32_t *g_idx = nullptr;    // [n] picks by round (graph outputs)
+    double *g_f = nullptr;       // [n] f by round
+    cudaGraphExec_t round_exec = nullptr;
+    cudaStream_t round_stream = nullptr;  // stream the graph was captured on
+    int64_t round_launches = 0;  // kernels in one round
+    int prec_at_capture = -1;
+    bool graphs = true;          // replay rounds from a graph when possible
+    bool attrs_ready = false;    // one direct round has run (kernel attributes are set)
 };
 
 namespace {
@@ -189,13 +198,45 @@ ebc_status ensure_set_part(ebc_t h, int64_t want) {
 
 }  // namespace
 
+// Device bytes one handle allocates (create + tensor-core buffers + graph
+// outputs), mirroring the allocations of create_handle and tc_setup.
+int64_t ebc::handle_bytes(int64_t n, int32_t d, ebc_prec prec) {
+    const int64_t ch = std::max<int64_t>(4096, ((n + 63) / 64 + 127) / 128 * 128);
+    const int64_t nch = (n + ch - 1) / ch;
+    const int64_t ref_ch = std::max<int64_t>(1024, ((n + 303) / 304 + 255) / 256 * 256);
+    const int64_t nref = (n + ref_ch - 1) / ref_ch;
+    const int64_t nblk = std::min<int64_t>(512, std::max<int64_t>(1, (n + 2047) / 2048));
+    const int64_t cap = std::min<int64_t>(n, 4096);
+    const int64_t pool = ebc::kMaxRefineK + cap;
+    int64_t b = n * d * 4 + n * (8 + 4 + 8 + 1 + 8 + 4 + 8 + 4 + 4 + 8) + std::max<int64_t>(nch, 16) * n * 8;
+    b += nblk * (ebc::kMaxRefineK + 1) * 12 + 4096;
+    b += 2 * cap * 8 + 3 * pool * nref * 8 + pool * 12 + 2 * ebc::kMaxRefineK * 8;
+    if (prec == EBC_BF16 || prec == EBC_FP16) {
+        const int64_t n_pad = (n + 255) / 256 * 256, DP = (d + 63) / 64 * 64;
+        b += 3 * n_pad * DP * 2 + 3 * n_pad * 16 * 2 + n_pad * (8 + 4 + 4);
+    }
+    return b + 64 * 1024;  // allocation granularity and small buffers
+}
+
 extern "C" {
+
+int64_t ebc_estimate_bytes(int64_t n, int32_t d, int32_t prec) {
+    if (n <= 0 || d <= 0) return -1;
+    return ebc::handle_bytes(n, d, (ebc_prec)prec);
+}
 
 int32_t ebc_version(void) { return (0 << 16) | 1; }
 
 const char *ebc_last_error(ebc_t h) { return h ? h->c.last_error.c_str() : g_create_error.c_str(); }
 
 ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device, void *stream, ebc_t *out) {
+    return ebc::create_handle(V, n, d, v_on_device, stream, true, out);
+}
+
+}  // extern "C"
+
+ebc_status ebc::create_handle(const float *V, int64_t n, int32_t d, int32_t v_on_device, void *stream, bool sync,
+                              ebc_t *out) {
     g_create_error.clear();
     if (!out) return fail(nullptr, EBC_EINVAL, "ebc_create: out is NULL");
     *out = nullptr;
@@ -286,17 +327,24 @@ ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device,
                         v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream));
     CKC(ebc::launch_reset_state(c));
     CKC(ebc::launch_prologue(c));
-    CKC(cudaMemcpyAsync(c.h_err, &c.st->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-    CKC(cudaStreamSynchronize(c.stream));
-    if (c.h_err[0]) return bail(EBC_EINVAL, "ebc_create: V has a non-finite entry");
+    if (sync) {
+        CKC(cudaMemcpyAsync(c.h_err, &c.st->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        CKC(cudaStreamSynchronize(c.stream));
+        if (c.h_err[0]) return bail(EBC_EINVAL, "ebc_create: V has a non-finite entry");
+    }
 #undef CKC
     *out = h;
     return EBC_OK;
 }
 
+extern "C" {
+
 ebc_status ebc_destroy(ebc_t h) {
     if (!h) return EBC_OK;
     cudaStreamSynchronize(h->c.stream);
+    if (h->round_exec) cudaGraphExecDestroy(h->round_exec);
+    if (h->g_idx) cudaFree(h->g_idx);
+    if (h->g_f) cudaFree(h->g_f);
     for (auto &r : h->prof.pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -347,6 +395,12 @@ ebc_status ebc_set_stream(ebc_t h, void *stream) {
 }
 
 ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k) {
+    return ebc::set_precision_handle(h, prec, refine_k, true);
+}
+
+}  // extern "C"
+
+ebc_status ebc::set_precision_handle(ebc_t h, ebc_prec prec, int32_t refine_k, bool sync) {
     if (check_handle(h)) return EBC_EINVAL;
     if (refine_k < 1 || refine_k > ebc::kMaxRefineK) return fail(h, EBC_EINVAL, "ebc_set_precision: K must be in [1, 32]");
     ebc::Ctx &c = h->c;
@@ -354,16 +408,21 @@ ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k) {
         if (!ebc::tc_supported(c))
             return fail(h, EBC_EINVAL, "ebc_set_precision: the tensor-core path supports d <= 128");
         if (c.tc.prec != (int)prec) {
-            // flush earlier device errors so a quantisation failure is seen on its own
-            ebc_status s0 = ebc_sync(h);
-            if (s0 != EBC_OK) return s0;
-            CK(h, ebc::tc_setup(c, (int)prec));
-            CK(h, cudaMemcpyAsync(c.h_err, &c.st->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-            CK(h, cudaStreamSynchronize(c.stream));
-            if (c.h_err[0]) {
-                CK(h, cudaMemsetAsync(&c.st->err, 0, sizeof(int), c.stream));
-                c.tc.prec = -1;
-                return fail(h, EBC_EINVAL, "ebc_set_precision: V overflows the requested 16-bit format");
+            if (!sync) {
+                // errors (a format overflow) surface at the next ebc_sync
+                CK(h, ebc::tc_setup(c, (int)prec));
+            } else {
+                // flush earlier device errors so a quantisation failure is seen on its own
+                ebc_status s0 = ebc_sync(h);
+                if (s0 != EBC_OK) return s0;
+                CK(h, ebc::tc_setup(c, (int)prec));
+                CK(h, cudaMemcpyAsync(c.h_err, &c.st->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+                CK(h, cudaStreamSynchronize(c.stream));
+                if (c.h_err[0]) {
+                    CK(h, cudaMemsetAsync(&c.st->err, 0, sizeof(int), c.stream));
+                    c.tc.prec = -1;
+                    return fail(h, EBC_EINVAL, "ebc_set_precision: V overflows the requested 16-bit format");
+                }
             }
         }
     } else if (prec != EBC_FP32) {
@@ -373,6 +432,8 @@ ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k) {
     c.refine_k = refine_k;
     return EBC_OK;
 }
+
+extern "C" {
 
 ebc_status ebc_reset(ebc_t h) {
     if (check_handle(h)) return EBC_EINVAL;
@@ -581,6 +642,52 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
     return EBC_OK;
 }
 
+// Capture one Greedy round (outputs into the handle's by-round buffers) as a
+// graph.  A capture failure leaves direct launches in use.
+static ebc_status capture_round(ebc_t h) {
+    ebc::Ctx &c = h->c;
+    if (!h->g_idx) {
+        CK(h, dalloc(&h->g_idx, c.n));
+        CK(h, dalloc(&h->g_f, c.n));
+    }
+    if (h->round_exec) {
+        cudaGraphExecDestroy(h->round_exec);
+        h->round_exec = nullptr;
+    }
+    const int64_t launches0 = h->prof.p.launches;
+    const int64_t bulk0 = h->prof.p.bulk_launches, evals0 = h->prof.p.bulk_evals, ref0 = h->prof.p.refine_launches;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        h->graphs = false;
+        return EBC_OK;
+    }
+    ebc_status s = greedy_round(h, h->g_idx, h->g_f);
+    cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+    h->round_launches = h->prof.p.launches - launches0;
+    h->prof.p.launches = launches0;
+    h->prof.p.bulk_launches = bulk0;
+    h->prof.p.bulk_evals = evals0;
+    h->prof.p.refine_launches = ref0;
+    if (s != EBC_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        h->graphs = false;  // keep direct launches for this handle
+        return EBC_OK;
+    }
+    e = cudaGraphInstantiate(&h->round_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->round_exec = nullptr;
+        h->graphs = false;
+        return EBC_OK;
+    }
+    h->round_stream = c.stream;
+    h->prec_at_capture = (int)c.prec;
+    return EBC_OK;
+}
+
 ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) {
     if (check_handle(h)) return EBC_EINVAL;
     ebc::Ctx &c = h->c;
@@ -591,11 +698,52 @@ ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) {
     // k_commit writes out[round] with round counted since reset: shift the base
     int32_t *ib = out_idx - h->nsel;
     double *fb = out_f - h->nsel;
-    for (int32_t t = 0; t < k; ++t) {
+    int32_t t = 0;
+    // graph replay: only on a capturable stream, without per-launch events,
+    // after one direct round has set every kernel attribute
+    const bool use_graph = h->graphs && !h->prof.on && c.stream != nullptr;
+    if (use_graph && (!h->round_exec || h->round_stream != c.stream || h->prec_at_capture != (int)c.prec)) {
+        if (!h->attrs_ready) {
+            ebc_status s = greedy_round(h, ib, fb);
+            if (s) return s;
+            h->nsel += 1;
+            h->attrs_ready = true;
+            t = 1;
+        }
+        if (t < k) {
+            ebc_status s = capture_round(h);
+            if (s) return s;
+        }
+    }
+    if (use_graph && h->round_exec) {
+        const int64_t first = h->nsel;
+        for (; t < k; ++t) {
+            h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
+            h->prof.p.launches += h->round_launches;
+            h->prof.p.bulk_launches += 1;
+            CK(h, cudaGraphLaunch(h->round_exec, c.stream));
+            h->nsel += 1;
+        }
+        const int64_t cnt = h->nsel - first;
+        if (cnt > 0) {
+            CK(h, cudaMemcpyAsync(ib + first, h->g_idx + first, sizeof(int32_t) * cnt, cudaMemcpyDeviceToDevice,
+                                  c.stream));
+            CK(h, cudaMemcpyAsync(fb + first, h->g_f + first, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, c.stream));
+        }
+        return EBC_OK;
+    }
+    for (; t < k; ++t) {
         ebc_status s = greedy_round(h, ib, fb);
         if (s) return s;
         h->nsel += 1;
+        h->attrs_ready = true;
     }
+    return EBC_OK;
+}
+
+ebc_status ebc_set_graphs(ebc_t h, int32_t on) {
+    if (check_handle(h)) return EBC_EINVAL;
+    h->graphs = on != 0;
     return EBC_OK;
 }
 

@@ -1,0 +1,320 @@
+// Batch runtime: many independent summarisation instances sharing one GPU.
+//
+// Each admitted instance occupies a slot: its own handle (resident V,
+// norms, quantised copies, Greedy state) and its own non-blocking stream.
+// ebc_batch_step() advances every active instance by one Greedy round
+// (a graph replay after the first round), so rounds of different instances
+// overlap on the device; finished instances are detected with events,
+// their results copied to pinned host memory and their slot and memory
+// released; queued requests are admitted first-come first-served while a
+// slot is free and the device-memory budget allows.  This is continuous
+// batching at round granularity: a request arriving while others run is
+// admitted as soon as a slot and memory free up, without waiting for the
+// batch to drain.
+#include <string.h>
+
+#include <deque>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "ebc_internal.cuh"
+
+struct ebc_batch_ctx {
+    struct Req {
+        int64_t ticket;
+        std::vector<float> V;
+        int64_t n;
+        int32_t d, k;
+        ebc_prec prec;
+        int64_t bytes;
+    };
+    struct Slot {
+        bool busy = false, finishing = false;
+        ebc_t h = nullptr;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t done = nullptr;
+        int64_t ticket = -1;
+        int32_t k = 0, issued = 0, cap = 0;
+        int32_t *d_idx = nullptr;
+        double *d_f = nullptr;
+        int32_t *h_idx = nullptr;  // pinned
+        double *h_f = nullptr;     // pinned
+        int64_t bytes = 0;
+    };
+    struct Result {
+        ebc_status status;
+        std::vector<int32_t> idx;
+        std::vector<double> f;
+    };
+    int32_t refine_k = 8;
+    int64_t budget = 0, used = 0, peak = 0;
+    int64_t next_ticket = 1, submitted = 0, completed = 0, rounds = 0;
+    std::deque<Req> queue;
+    std::vector<Slot> slots;
+    std::unordered_map<int64_t, Result> results;
+    std::string err;
+};
+
+namespace {
+
+ebc_status bfail(ebc_batch_t b, ebc_status s, const std::string &m) {
+    if (b) b->err = m;
+    return s;
+}
+
+void release_slot(ebc_batch_ctx::Slot &s) {
+    if (s.h) ebc_destroy(s.h);
+    s.h = nullptr;
+    s.busy = s.finishing = false;
+    s.ticket = -1;
+    s.issued = s.k = 0;
+    s.bytes = 0;
+}
+
+ebc_status ensure_outputs(ebc_batch_t b, ebc_batch_ctx::Slot &s, int32_t k) {
+    if (s.cap >= k) return EBC_OK;
+    if (s.d_idx) cudaFree(s.d_idx);
+    if (s.d_f) cudaFree(s.d_f);
+    if (s.h_idx) cudaFreeHost(s.h_idx);
+    if (s.h_f) cudaFreeHost(s.h_f);
+    s.d_idx = nullptr;
+    s.d_f = nullptr;
+    s.h_idx = nullptr;
+    s.h_f = nullptr;
+    s.cap = 0;
+    if (cudaMalloc(&s.d_idx, sizeof(int32_t) * k) != cudaSuccess || cudaMalloc(&s.d_f, sizeof(double) * k) != cudaSuccess ||
+        cudaMallocHost(&s.h_idx, sizeof(int32_t) * k) != cudaSuccess ||
+        cudaMallocHost(&s.h_f, sizeof(double) * k) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, EBC_ENOMEM, "ebc_batch: output buffers");
+    }
+    s.cap = k;
+    return EBC_OK;
+}
+
+// Move finished instances to the result table and free their slots.
+void reap(ebc_batch_t b) {
+    for (auto &s : b->slots) {
+        if (!s.busy || !s.finishing) continue;
+        cudaError_t q = cudaEventQuery(s.done);
+        if (q == cudaErrorNotReady) continue;
+        ebc_batch_ctx::Result r;
+        r.status = q == cudaSuccess ? ebc_sync(s.h) : EBC_ECUDA;
+        cudaGetLastError();
+        r.idx.assign(s.h_idx, s.h_idx + s.k);
+        r.f.assign(s.h_f, s.h_f + s.k);
+        b->results[s.ticket] = std::move(r);
+        b->used -= s.bytes;
+        b->completed += 1;
+        release_slot(s);
+    }
+}
+
+// Admit queued requests first-come first-served.
+void admit(ebc_batch_t b) {
+    while (!b->queue.empty()) {
+        ebc_batch_ctx::Req &r = b->queue.front();
+        ebc_batch_ctx::Slot *free_slot = nullptr;
+        for (auto &s : b->slots)
+            if (!s.busy) {
+                free_slot = &s;
+                break;
+            }
+        if (!free_slot) return;
+        if (b->used + r.bytes > b->budget && b->used > 0) return;  // wait for memory (an oversize request runs alone)
+        ebc_batch_ctx::Slot &s = *free_slot;
+        ebc_status st = ensure_outputs(b, s, r.k);
+        ebc_t h = nullptr;
+        if (st == EBC_OK) st = ebc::create_handle(r.V.data(), r.n, r.d, 0, s.stream, false, &h);
+        if (st == EBC_OK && (r.prec != EBC_FP32 || b->refine_k != 8))
+            st = ebc::set_precision_handle(h, r.prec, b->refine_k, false);
+        if (st != EBC_OK) {
+            ebc_batch_ctx::Result res;
+            res.status = st;
+            b->results[r.ticket] = std::move(res);
+            b->completed += 1;
+            if (h) ebc_destroy(h);
+            b->queue.pop_front();
+            continue;
+        }
+        s.busy = true;
+        s.finishing = false;
+        s.h = h;
+        s.ticket = r.ticket;
+        s.k = r.k;
+        s.issued = 0;
+        s.bytes = r.bytes;
+        b->used += r.bytes;
+        if (b->used > b->peak) b->peak = b->used;
+        b->queue.pop_front();
+    }
+}
+
+// One Greedy round for every active instance; the last round also queues the
+// copy of the results and the completion event.
+ebc_status issue(ebc_batch_t b) {
+    for (auto &s : b->slots) {
+        if (!s.busy || s.finishing) continue;
+        ebc_status st = ebc_greedy(s.h, 1, s.d_idx + s.issued, s.d_f + s.issued);
+        if (st != EBC_OK) {
+            // record the failure as this instance's result
+            ebc_batch_ctx::Result res;
+            res.status = st;
+            b->results[s.ticket] = std::move(res);
+            b->used -= s.bytes;
+            b->completed += 1;
+            release_slot(s);
+            continue;
+        }
+        s.issued += 1;
+        b->rounds += 1;
+        if (s.issued == s.k) {
+            cudaMemcpyAsync(s.h_idx, s.d_idx, sizeof(int32_t) * s.k, cudaMemcpyDeviceToHost, s.stream);
+            cudaMemcpyAsync(s.h_f, s.d_f, sizeof(double) * s.k, cudaMemcpyDeviceToHost, s.stream);
+            cudaEventRecord(s.done, s.stream);
+            s.finishing = true;
+        }
+    }
+    return EBC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ebc_status ebc_batch_create(int32_t max_slots, int64_t device_budget_bytes, int32_t refine_k, ebc_batch_t *out) {
+    if (!out) return EBC_EINVAL;
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 4096 || device_budget_bytes <= 0 || refine_k < 1 || refine_k > ebc::kMaxRefineK)
+        return EBC_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return EBC_ENODEV;
+    }
+    ebc_batch_ctx *b = new (std::nothrow) ebc_batch_ctx();
+    if (!b) return EBC_ENOMEM;
+    b->budget = device_budget_bytes;
+    b->refine_k = refine_k;
+    b->slots.resize(max_slots);
+    for (auto &s : b->slots) {
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            ebc_batch_destroy(b);
+            return EBC_ECUDA;
+        }
+    }
+    *out = b;
+    return EBC_OK;
+}
+
+ebc_status ebc_batch_submit(ebc_batch_t b, const float *V, int64_t n, int32_t d, int32_t k, ebc_prec prec,
+                            int64_t *ticket) {
+    if (!b) return EBC_EINVAL;
+    if (!V || !ticket || n <= 0 || n > (int64_t)INT32_MAX - 1 || d <= 0 || d > 4096 || k < 1 || (int64_t)k > n)
+        return bfail(b, EBC_EINVAL, "ebc_batch_submit: bad V, n, d, k or ticket");
+    if (prec != EBC_FP32 && !((prec == EBC_BF16 || prec == EBC_FP16) && d <= 128))
+        return bfail(b, EBC_EINVAL, "ebc_batch_submit: unsupported precision for this d");
+    ebc_batch_ctx::Req r;
+    r.ticket = b->next_ticket++;
+    r.V.assign(V, V + (size_t)n * d);
+    r.n = n;
+    r.d = d;
+    r.k = k;
+    r.prec = prec;
+    r.bytes = ebc::handle_bytes(n, d, prec);
+    *ticket = r.ticket;
+    b->queue.push_back(std::move(r));
+    b->submitted += 1;
+    return EBC_OK;
+}
+
+ebc_status ebc_batch_step(ebc_batch_t b, int32_t *n_active, int32_t *n_queued) {
+    if (!b) return EBC_EINVAL;
+    reap(b);
+    admit(b);
+    ebc_status st = issue(b);
+    int32_t act = 0;
+    for (auto &s : b->slots) act += s.busy ? 1 : 0;
+    if (n_active) *n_active = act;
+    if (n_queued) *n_queued = (int32_t)b->queue.size();
+    return st;
+}
+
+ebc_status ebc_batch_poll(ebc_batch_t b, int64_t ticket, int32_t *out_idx, double *out_f, int32_t cap,
+                          int32_t *done) {
+    if (!b || !done) return EBC_EINVAL;
+    *done = 0;
+    auto it = b->results.find(ticket);
+    if (it == b->results.end()) {
+        if (ticket <= 0 || ticket >= b->next_ticket) return bfail(b, EBC_EINVAL, "ebc_batch_poll: unknown ticket");
+        return EBC_OK;  // pending
+    }
+    ebc_batch_ctx::Result &r = it->second;
+    if (r.status == EBC_OK) {
+        if ((int64_t)cap < (int64_t)r.idx.size() || !out_idx || !out_f)
+            return bfail(b, EBC_EINVAL, "ebc_batch_poll: output capacity below k");
+        memcpy(out_idx, r.idx.data(), sizeof(int32_t) * r.idx.size());
+        memcpy(out_f, r.f.data(), sizeof(double) * r.f.size());
+    }
+    const ebc_status st = r.status;
+    b->results.erase(it);
+    *done = 1;
+    return st;
+}
+
+ebc_status ebc_batch_run(ebc_batch_t b) {
+    if (!b) return EBC_EINVAL;
+    while (true) {
+        int32_t act = 0, q = 0;
+        ebc_status st = ebc_batch_step(b, &act, &q);
+        if (st != EBC_OK) return st;
+        if (act == 0 && q == 0) return EBC_OK;
+        // when every active instance has all its rounds queued, wait for one to end
+        bool all_finishing = true;
+        for (auto &s : b->slots)
+            if (s.busy && !s.finishing) all_finishing = false;
+        if (all_finishing)
+            for (auto &s : b->slots)
+                if (s.busy) {
+                    cudaEventSynchronize(s.done);
+                    break;
+                }
+    }
+}
+
+ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out) {
+    if (!b || !out) return EBC_EINVAL;
+    int64_t act = 0;
+    for (auto &s : b->slots) act += s.busy ? 1 : 0;
+    out->submitted = b->submitted;
+    out->completed = b->completed;
+    out->active = act;
+    out->queued = (int64_t)b->queue.size();
+    out->bytes_in_use = b->used;
+    out->bytes_peak = b->peak;
+    out->rounds_issued = b->rounds;
+    return EBC_OK;
+}
+
+const char *ebc_batch_last_error(ebc_batch_t b) { return b ? b->err.c_str() : ""; }
+
+ebc_status ebc_batch_destroy(ebc_batch_t b) {
+    if (!b) return EBC_OK;
+    for (auto &s : b->slots) {
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        release_slot(s);
+        if (s.d_idx) cudaFree(s.d_idx);
+        if (s.d_f) cudaFree(s.d_f);
+        if (s.h_idx) cudaFreeHost(s.h_idx);
+        if (s.h_f) cudaFreeHost(s.h_f);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    delete b;
+    return EBC_OK;
+}
+
+}  // extern "C"

@@ -119,6 +119,12 @@ struct Ctx {
     std::string last_error;
 };
 
+// ---- handle helpers shared with the batch runtime (api.cu) ---------------
+ebc_status create_handle(const float *V, int64_t n, int32_t d, int32_t v_on_device, void *stream, bool sync,
+                         ebc_t *out);
+ebc_status set_precision_handle(ebc_t h, ebc_prec prec, int32_t refine_k, bool sync);
+int64_t handle_bytes(int64_t n, int32_t d, ebc_prec prec);
+
 // ---- launchers (defined in the .cu files) --------------------------------
 cudaError_t launch_prologue(Ctx &c);
 cudaError_t launch_reset_state(Ctx &c);

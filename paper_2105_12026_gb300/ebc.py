@@ -45,6 +45,12 @@ class ebc_profile(ctypes.Structure):
                 ("eval_launches", ctypes.c_int64), ("eval_ms", ctypes.c_double)]
 
 
+class ebc_batch_info(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64), ("bytes_peak", ctypes.c_int64),
+                ("rounds_issued", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -66,6 +72,7 @@ _SIGS = {
     "ebc_gains_host": [_P, _P, _I64, _P],
     "ebc_greedy": [_P, _I32, _P, _P],
     "ebc_greedy_host": [_P, _I32, _P, _P],
+    "ebc_set_graphs": [_P, _I32],
     "ebc_reset": [_P],
     "ebc_sync": [_P],
     "ebc_get_stats": [_P, ctypes.POINTER(ebc_stats)],
@@ -73,6 +80,15 @@ _SIGS = {
     "ebc_last_error": [_P],
     "ebc_eval_sets_noalloc": [_P, _I64, _I32, _P, _P, _I64, _P, _P],
     "ebc_noalloc_last_error": [],
+    "ebc_estimate_bytes": [_I64, _I32, _I32],
+    "ebc_batch_create": [_I32, _I64, _I32, ctypes.POINTER(_P)],
+    "ebc_batch_submit": [_P, _P, _I64, _I32, _I32, ctypes.c_int, ctypes.POINTER(_I64)],
+    "ebc_batch_step": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
+    "ebc_batch_poll": [_P, _I64, _P, _P, _I32, ctypes.POINTER(_I32)],
+    "ebc_batch_run": [_P],
+    "ebc_batch_stats": [_P, ctypes.POINTER(ebc_batch_info)],
+    "ebc_batch_last_error": [_P],
+    "ebc_batch_destroy": [_P],
 }
 
 
@@ -95,6 +111,8 @@ def load(path: str | None = None):
                 fn.restype = ctypes.c_int
             lib.ebc_last_error.restype = ctypes.c_char_p
             lib.ebc_noalloc_last_error.restype = ctypes.c_char_p
+            lib.ebc_batch_last_error.restype = ctypes.c_char_p
+            lib.ebc_estimate_bytes.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -191,6 +209,10 @@ def ebc_gains_host(h: int, cand: np.ndarray | None, m: int | None = None) -> np.
 
 def ebc_greedy(h: int, k: int, out_idx_ptr: int, out_f_ptr: int) -> None:
     _raise(h, load().ebc_greedy(_P(h), int(k), _P(out_idx_ptr), _P(out_f_ptr)))
+
+
+def ebc_set_graphs(h: int, on: bool) -> None:
+    _raise(h, load().ebc_set_graphs(_P(h), int(bool(on))))
 
 
 def ebc_greedy_host(h: int, k: int):
@@ -351,3 +373,79 @@ class Instance:
 
     def current_f(self):
         return ebc_current_f(self.h)
+
+
+# ---------------------------------------------------------------------------
+# batch runtime (marshalling only)
+# ---------------------------------------------------------------------------
+
+def ebc_estimate_bytes(n: int, d: int, prec: int) -> int:
+    return int(load().ebc_estimate_bytes(int(n), int(d), int(prec)))
+
+
+class Batch:
+    """Many independent Greedy summaries sharing the GPU (include/ebc.h, batch runtime)."""
+
+    def __init__(self, max_slots: int = 32, budget_bytes: int = 150 << 30, refine_k: int = 8):
+        h = _P()
+        rc = load().ebc_batch_create(int(max_slots), int(budget_bytes), int(refine_k), ctypes.byref(h))
+        if rc != EBC_OK:
+            raise EbcError(rc, "ebc_batch_create")
+        self.h = h.value
+        self._k = {}
+
+    def _err(self, rc):
+        if rc != EBC_OK:
+            m = load().ebc_batch_last_error(_P(self.h))
+            raise EbcError(rc, m.decode() if m else "")
+
+    def submit(self, V: np.ndarray, k: int, precision: str = "bf16") -> int:
+        V = np.ascontiguousarray(V, dtype=np.float32)
+        t = _I64()
+        self._err(load().ebc_batch_submit(_P(self.h), V.ctypes.data_as(_P), V.shape[0], V.shape[1], int(k),
+                                          PRECISIONS[precision], ctypes.byref(t)))
+        self._k[t.value] = int(k)
+        return t.value
+
+    def step(self):
+        a, q = _I32(), _I32()
+        self._err(load().ebc_batch_step(_P(self.h), ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, ticket: int):
+        """(idx, f) when finished, else None.  Raises the request's error status."""
+        k = self._k[ticket]
+        idx = np.zeros(k, np.int32)
+        f = np.zeros(k, np.float64)
+        done = _I32()
+        rc = load().ebc_batch_poll(_P(self.h), int(ticket), idx.ctypes.data_as(_P), f.ctypes.data_as(_P), k,
+                                   ctypes.byref(done))
+        if done.value:
+            del self._k[ticket]
+        self._err(rc)
+        return (idx, f) if done.value else None
+
+    def run(self):
+        self._err(load().ebc_batch_run(_P(self.h)))
+
+    def stats(self) -> dict:
+        s = ebc_batch_info()
+        self._err(load().ebc_batch_stats(_P(self.h), ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ebc_batch_info._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ebc_batch_destroy(_P(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

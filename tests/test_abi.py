@@ -76,3 +76,20 @@ def test_no_gpu_gives_enodev_not_a_crash(lib):
     with pytest.raises(ebc.EbcError) as ei:
         ebc.ebc_create(V.ctypes.data, 4, 2, False, stream=0)
     assert ei.value.status == ebc.EBC_ENODEV
+
+
+def test_estimate_bytes(lib):
+    a = ebc.ebc_estimate_bytes(1000, 16, ebc.EBC_FP32)
+    b = ebc.ebc_estimate_bytes(100000, 16, ebc.EBC_FP32)
+    c = ebc.ebc_estimate_bytes(100000, 16, ebc.EBC_BF16)
+    assert 0 < a < b < c
+    assert ebc.ebc_estimate_bytes(0, 16, 0) == -1
+
+
+def test_batch_create_rejects_bad_arguments(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.ebc_batch_create(0, 1 << 30, 8, ctypes.byref(h)) == ebc.EBC_EINVAL
+    assert lib.ebc_batch_create(4, 0, 8, ctypes.byref(h)) == ebc.EBC_EINVAL
+    assert lib.ebc_batch_create(4, 1 << 30, 0, ctypes.byref(h)) == ebc.EBC_EINVAL
+    assert lib.ebc_batch_submit(None, None, 10, 4, 2, 0, None) == ebc.EBC_EINVAL

@@ -251,3 +251,21 @@ def test_reload_rejects_non_finite(torch):
         with pytest.raises(ebc.EbcError) as ei:
             inst.sync()
         assert ei.value.status == ebc.EBC_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_graph_replay_matches_direct(torch, prec):
+    # rounds replayed from a captured CUDA graph (non-default stream) give
+    # bitwise the same picks and f as direct launches
+    V = rand_V(5000, 48, 41, clusters=7)
+    s = torch.cuda.Stream()
+    with ebc.Instance(V, precision=prec, stream=s) as a, ebc.Instance(V, precision=prec, stream=s) as b:
+        ebc.ebc_set_graphs(b.h, False)
+        ia, fa = a.greedy_host(7)
+        ia2, fa2 = a.greedy_host(1)  # one-round calls reuse the graph
+        ia3, fa3 = a.greedy_host(1)
+        ib, fb = b.greedy_host(9)
+    np.testing.assert_array_equal(np.concatenate([ia, ia2, ia3]), ib)
+    np.testing.assert_array_equal(np.concatenate([fa, fa2, fa3]), fb)
+    ref = oracle.greedy(V, 9)
+    check_greedy(ib, fb, *ref)
