@@ -172,6 +172,138 @@ def run_reference(args):
     return 0
 
 
+def instance_evals(n: int, k: int) -> int:
+    return greedy_evals(n, k)
+
+
+def run_mix(args):
+    """256 independent Greedy instances (n log-uniform 2k..100k, d in {16,32,64,128},
+    k in 5..50) through the batch runtime; one step = submit all, run to completion."""
+    import torch
+
+    from paper_2105_12026_gb300 import ebc, synth
+    torch.cuda.set_device(0)
+    specs = synth.instance_mix(seed=args.seed, count=args.instances)
+    t0 = time.perf_counter()
+    Vs = [sp.make() for sp in specs]
+    gen_s = time.perf_counter() - t0
+    evals = sum(instance_evals(sp.n, sp.k) for sp in specs)
+
+    def one_batch():
+        with ebc.Batch(max_slots=args.slots, budget_bytes=int(args.budget_gb * (1 << 30)),
+                       refine_k=args.refine_k) as b:
+            tickets = [b.submit(V, sp.k, args.prec) for V, sp in zip(Vs, specs)]
+            b.run()
+            for t in tickets:
+                assert b.poll(t) is not None
+            return b.stats()
+
+    for _ in range(args.warmup):
+        one_batch()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        st = one_batch()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t1)
+    clk = clocks.stop()
+    tot = sum(times)
+    line = {"metric": METRIC, "value": args.steps * evals / tot, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded GMM instance mix)",
+            "config": {"workload": f"batched greedy, {len(specs)} instances: n log-uniform [2000, 100000], "
+                                   f"d in {{16,32,64,128}}, k in [5, 50]",
+                       "slots": args.slots, "budget_gb": args.budget_gb, "evals_per_step": evals,
+                       "timing": "wall clock between device synchronisations; includes host-to-device upload of "
+                                 "every instance and the result copies",
+                       "host_generation_s": gen_s},
+            "batch_stats": st, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals through the batch runtime (continuous batching at round
+    granularity); latency = completion - arrival, queueing included."""
+    import torch
+
+    from paper_2105_12026_gb300 import ebc, synth
+    torch.cuda.set_device(0)
+    trace = synth.request_trace(seed=args.seed, rate=args.rate, horizon_s=args.horizon, large_frac=args.large_frac,
+                                large_n=args.large_n)
+    t0 = time.perf_counter()
+    Vs = [r.spec.make() for r in trace]
+    gen_s = time.perf_counter() - t0
+    # warm the library (kernels, graphs) on a small instance
+    with ebc.Batch(max_slots=2) as b:
+        t = b.submit(Vs[0], min(3, trace[0].spec.k), args.prec)
+        b.run()
+        b.poll(t)
+    b = ebc.Batch(max_slots=args.slots, budget_bytes=int(args.budget_gb * (1 << 30)), refine_k=args.refine_k)
+    b.set_large(args.large_threshold, args.large_ctas, args.max_large)
+    pending = {}
+    lat = {}
+    nxt = 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    start = time.perf_counter()
+    deadline = start + args.horizon + args.drain
+    while True:
+        now = time.perf_counter() - start
+        while nxt < len(trace) and trace[nxt].t_arrive <= now:
+            pending[b.submit(Vs[nxt], trace[nxt].spec.k, args.prec)] = nxt
+            nxt += 1
+        active, queued = b.step()
+        for tk in list(pending):
+            res = b.poll(tk)
+            if res is not None:
+                i = pending.pop(tk)
+                lat[i] = (time.perf_counter() - start) - trace[i].t_arrive
+        if nxt == len(trace) and not pending:
+            break
+        if time.perf_counter() > deadline:
+            break
+        if active == 0 and queued == 0 and nxt < len(trace):
+            time.sleep(max(0.0, min(0.002, trace[nxt].t_arrive - (time.perf_counter() - start))))
+    wall = time.perf_counter() - start
+    clk = clocks.stop()
+    st = b.stats()
+    b.close()
+    done = sorted(lat)
+    lat_ms = np.array([1e3 * lat[i] for i in done]) if done else np.zeros(0)
+    small = np.array([1e3 * lat[i] for i in done if not trace[i].large])
+    large = np.array([1e3 * lat[i] for i in done if trace[i].large])
+    served_evals = sum(instance_evals(trace[i].spec.n, trace[i].spec.k) for i in done)
+    offered_evals = sum(instance_evals(r.spec.n, r.spec.k) for r in trace)
+
+    def pct(a, p):
+        return float(np.percentile(a, p)) if a.size else None
+
+    line = {"metric": "serve p99 ms", "value": pct(lat_ms, 99), "unit": "ms", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+            "data": "synthetic (seeded Poisson request trace)",
+            "config": {"workload": f"serving: Poisson {args.rate}/s over {args.horizon}s, "
+                                   f"{100 * args.large_frac:.0f}% large (n={args.large_n}, d=32), rest GMM instance mix",
+                       "slots": args.slots, "budget_gb": args.budget_gb, "large_threshold": args.large_threshold,
+                       "large_ctas": args.large_ctas, "max_large": args.max_large, "drain_s": args.drain,
+                       "host_generation_s": gen_s},
+            "latency_ms": {"p50": pct(lat_ms, 50), "p90": pct(lat_ms, 90), "p99": pct(lat_ms, 99),
+                           "max": float(lat_ms.max()) if lat_ms.size else None,
+                           "small_p50": pct(small, 50), "small_p99": pct(small, 99),
+                           "large_p50": pct(large, 50), "large_p99": pct(large, 99)},
+            "requests": {"offered": len(trace), "completed": len(done), "unfinished": len(trace) - len(done),
+                         "large_offered": sum(r.large for r in trace), "large_completed": int(large.size)},
+            "throughput": {"requests_per_s": len(done) / wall, "evals_per_s": served_evals / wall,
+                           "offered_evals_per_s": offered_evals / args.horizon, "wall_s": wall},
+            "batch_stats": st, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,7 +312,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
     ap.add_argument("--refine-k", type=int, default=8)
-    ap.add_argument("--workload", default="regime", choices=["regime", "small"])
+    ap.add_argument("--workload", default="regime", choices=["regime", "small", "mix", "serve"])
+    ap.add_argument("--instances", type=int, default=256, help="mix: number of instances")
+    ap.add_argument("--slots", type=int, default=32, help="mix/serve: concurrent instances")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="mix/serve: device-memory budget")
+    ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
+    ap.add_argument("--horizon", type=float, default=10.0, help="serve: arrival horizon in seconds")
+    ap.add_argument("--drain", type=float, default=60.0, help="serve: seconds allowed after the horizon")
+    ap.add_argument("--large-frac", type=float, default=0.05, help="serve: fraction of large requests")
+    ap.add_argument("--large-n", type=int, default=1_000_000, help="serve: n of large requests")
+    ap.add_argument("--large-threshold", type=int, default=500_000, help="serve: n from which the CTA cap applies")
+    ap.add_argument("--large-ctas", type=int, default=120, help="serve: CTA cap of large requests (0 = none)")
+    ap.add_argument("--max-large", type=int, default=2, help="serve: large requests running at once (0 = any)")
     ap.add_argument("--n", type=int, default=200_000)
     ap.add_argument("--d", type=int, default=128)
     ap.add_argument("--k", type=int, default=100)
@@ -195,6 +338,10 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "mix":
+        return run_mix(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
     import torch.distributed as dist

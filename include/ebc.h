@@ -163,6 +163,10 @@ ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *o
  */
 ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);
 
+/* Cap the CTAs of the persistent bulk kernel (0 = one per SM).  Leaves SMs
+ * free for other work on the GPU, e.g. small requests in a serving batch. */
+ebc_status ebc_set_max_ctas(ebc_t h, int32_t max_ctas);
+
 /* Replay Greedy rounds from a captured CUDA graph (1, the default) or issue
  * every kernel directly (0).  Graph replay needs a non-NULL stream and is
  * not used while profiling is on. */
@@ -246,9 +250,9 @@ int64_t ebc_estimate_bytes(int64_t n, int32_t d, int32_t prec);
  * its optimisers generate.  Each admitted instance gets its own handle and
  * stream; ebc_batch_step() advances every active instance by one Greedy
  * round, so their work overlaps on the device; finished instances free
- * their slot and memory and queued requests are admitted first-come
- * first-served while a slot is free and the device-memory budget allows
- * (a request larger than the whole budget runs when nothing else does).
+ * their slot and memory and queued requests are admitted in arrival order
+ * while a slot is free and the device-memory budget allows (a request
+ * larger than the whole budget runs when nothing else does).
  * Single host thread per batch.
  * ---------------------------------------------------------------------- */
 typedef struct ebc_batch_ctx *ebc_batch_t;
@@ -281,6 +285,13 @@ ebc_status ebc_batch_poll(ebc_batch_t b, int64_t ticket, int32_t *out_idx, doubl
 
 /* Step until every submitted request has finished. */
 ebc_status ebc_batch_run(ebc_batch_t b);
+
+/* Instances with n >= large_n ("large") run their bulk kernel on at most
+ * max_ctas CTAs (see ebc_set_max_ctas; 0 = no cap) and at most max_active
+ * of them run at once (0 = no limit), so smaller instances keep SMs and slots.
+ * Admission goes in arrival order, but a request that cannot start yet
+ * (memory or this limit) does not hold back later requests that can. */
+ebc_status ebc_batch_set_large(ebc_batch_t b, int64_t large_n, int32_t max_ctas, int32_t max_active);
 
 ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out);
 const char *ebc_batch_last_error(ebc_batch_t b);

@@ -43,6 +43,7 @@ struct ebc_ctx {
     cudaStream_t round_stream = nullptr;  // stream the graph was captured on
     int64_t round_launches = 0;  // kernels in one round
     int prec_at_capture = -1;
+    int ctas_at_capture = -1;
     bool graphs = true;          // replay rounds from a graph when possible
     bool attrs_ready = false;    // one direct round has run (kernel attributes are set)
 };
@@ -685,6 +686,7 @@ static ebc_status capture_round(ebc_t h) {
     }
     h->round_stream = c.stream;
     h->prec_at_capture = (int)c.prec;
+    h->ctas_at_capture = c.max_ctas;
     return EBC_OK;
 }
 
@@ -702,7 +704,8 @@ ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) {
     // graph replay: only on a capturable stream, without per-launch events,
     // after one direct round has set every kernel attribute
     const bool use_graph = h->graphs && !h->prof.on && c.stream != nullptr;
-    if (use_graph && (!h->round_exec || h->round_stream != c.stream || h->prec_at_capture != (int)c.prec)) {
+    if (use_graph && (!h->round_exec || h->round_stream != c.stream || h->prec_at_capture != (int)c.prec ||
+                      h->ctas_at_capture != c.max_ctas)) {
         if (!h->attrs_ready) {
             ebc_status s = greedy_round(h, ib, fb);
             if (s) return s;
@@ -738,6 +741,12 @@ ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) {
         h->nsel += 1;
         h->attrs_ready = true;
     }
+    return EBC_OK;
+}
+
+ebc_status ebc_set_max_ctas(ebc_t h, int32_t max_ctas) {
+    if (check_handle(h) || max_ctas < 0) return EBC_EINVAL;
+    h->c.max_ctas = max_ctas;
     return EBC_OK;
 }
 

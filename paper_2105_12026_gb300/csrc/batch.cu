@@ -30,7 +30,7 @@ struct ebc_batch_ctx {
         int64_t bytes;
     };
     struct Slot {
-        bool busy = false, finishing = false;
+        bool busy = false, finishing = false, large = false;
         ebc_t h = nullptr;
         cudaStream_t stream = nullptr;
         cudaEvent_t done = nullptr;
@@ -48,6 +48,9 @@ struct ebc_batch_ctx {
         std::vector<double> f;
     };
     int32_t refine_k = 8;
+    int64_t large_n = 0;      // instances with n >= large_n get at most large_ctas CTAs per kernel
+    int32_t large_ctas = 0;
+    int32_t max_large = 0;    // at most this many large instances at once (0 = no limit)
     int64_t budget = 0, used = 0, peak = 0;
     int64_t next_ticket = 1, submitted = 0, completed = 0, rounds = 0;
     std::deque<Req> queue;
@@ -111,10 +114,15 @@ void reap(ebc_batch_t b) {
     }
 }
 
-// Admit queued requests first-come first-served.
+// Admit queued requests in arrival order.  A request that cannot start yet
+// (memory, or the cap on concurrent large instances) keeps its place, and
+// later requests that fit may start before it; slots are the only hard stop.
 void admit(ebc_batch_t b) {
-    while (!b->queue.empty()) {
-        ebc_batch_ctx::Req &r = b->queue.front();
+    int32_t active_large = 0;
+    for (auto &s : b->slots)
+        if (s.busy && s.large) active_large += 1;
+    for (auto it = b->queue.begin(); it != b->queue.end();) {
+        ebc_batch_ctx::Req &r = *it;
         ebc_batch_ctx::Slot *free_slot = nullptr;
         for (auto &s : b->slots)
             if (!s.busy) {
@@ -122,24 +130,32 @@ void admit(ebc_batch_t b) {
                 break;
             }
         if (!free_slot) return;
-        if (b->used + r.bytes > b->budget && b->used > 0) return;  // wait for memory (an oversize request runs alone)
+        const bool large = b->large_n > 0 && r.n >= b->large_n;
+        const bool mem_ok = b->used + r.bytes <= b->budget || b->used == 0;  // an oversize request runs alone
+        const bool cls_ok = !large || b->max_large <= 0 || active_large < b->max_large;
+        if (!mem_ok || !cls_ok) {
+            ++it;
+            continue;
+        }
         ebc_batch_ctx::Slot &s = *free_slot;
         ebc_status st = ensure_outputs(b, s, r.k);
         ebc_t h = nullptr;
         if (st == EBC_OK) st = ebc::create_handle(r.V.data(), r.n, r.d, 0, s.stream, false, &h);
         if (st == EBC_OK && (r.prec != EBC_FP32 || b->refine_k != 8))
             st = ebc::set_precision_handle(h, r.prec, b->refine_k, false);
+        if (st == EBC_OK && large && b->large_ctas > 0) st = ebc_set_max_ctas(h, b->large_ctas);
         if (st != EBC_OK) {
             ebc_batch_ctx::Result res;
             res.status = st;
             b->results[r.ticket] = std::move(res);
             b->completed += 1;
             if (h) ebc_destroy(h);
-            b->queue.pop_front();
+            it = b->queue.erase(it);
             continue;
         }
         s.busy = true;
         s.finishing = false;
+        s.large = large;
         s.h = h;
         s.ticket = r.ticket;
         s.k = r.k;
@@ -147,7 +163,8 @@ void admit(ebc_batch_t b) {
         s.bytes = r.bytes;
         b->used += r.bytes;
         if (b->used > b->peak) b->peak = b->used;
-        b->queue.pop_front();
+        active_large += large ? 1 : 0;
+        it = b->queue.erase(it);
     }
 }
 
@@ -296,6 +313,14 @@ ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out) {
     out->bytes_in_use = b->used;
     out->bytes_peak = b->peak;
     out->rounds_issued = b->rounds;
+    return EBC_OK;
+}
+
+ebc_status ebc_batch_set_large(ebc_batch_t b, int64_t large_n, int32_t max_ctas, int32_t max_active) {
+    if (!b || large_n < 0 || max_ctas < 0 || max_active < 0) return EBC_EINVAL;
+    b->large_n = large_n;
+    b->large_ctas = max_ctas;
+    b->max_large = max_active;
     return EBC_OK;
 }
 

@@ -86,6 +86,7 @@ struct Ctx {
         CUtensorMap tmBx;         // point extension over Bext (box 16 x 256)
     } tc;
     int num_sms = 152;
+    int max_ctas = 0;  // cap on persistent-kernel CTAs (0 = one per SM)
 
     // scratch
     double *partial = nullptr;  // [nchunk_cap, n] per-V-chunk partial sums of the bulk gains

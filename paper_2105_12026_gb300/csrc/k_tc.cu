@@ -685,7 +685,7 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     a.n_vtiles = (int)(T.n_pad / BN);
     a.n_ctiles = (int)((m + BM - 1) / BM);
     // V chunks: balance the persistent grid (units = candidate tiles x chunks)
-    const int G = c.num_sms;
+    const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
     const int64_t cap = c.partial_cap / std::max<int64_t>(m, 1);
     int best = 1;
     double best_eff = 0.0;

@@ -73,6 +73,8 @@ _SIGS = {
     "ebc_greedy": [_P, _I32, _P, _P],
     "ebc_greedy_host": [_P, _I32, _P, _P],
     "ebc_set_graphs": [_P, _I32],
+    "ebc_set_max_ctas": [_P, _I32],
+    "ebc_batch_set_large": [_P, _I64, _I32, _I32],
     "ebc_reset": [_P],
     "ebc_sync": [_P],
     "ebc_get_stats": [_P, ctypes.POINTER(ebc_stats)],
@@ -209,6 +211,10 @@ def ebc_gains_host(h: int, cand: np.ndarray | None, m: int | None = None) -> np.
 
 def ebc_greedy(h: int, k: int, out_idx_ptr: int, out_f_ptr: int) -> None:
     _raise(h, load().ebc_greedy(_P(h), int(k), _P(out_idx_ptr), _P(out_f_ptr)))
+
+
+def ebc_set_max_ctas(h: int, max_ctas: int) -> None:
+    _raise(h, load().ebc_set_max_ctas(_P(h), int(max_ctas)))
 
 
 def ebc_set_graphs(h: int, on: bool) -> None:
@@ -406,6 +412,9 @@ class Batch:
                                           PRECISIONS[precision], ctypes.byref(t)))
         self._k[t.value] = int(k)
         return t.value
+
+    def set_large(self, large_n: int, max_ctas: int, max_active: int = 0):
+        self._err(load().ebc_batch_set_large(_P(self.h), int(large_n), int(max_ctas), int(max_active)))
 
     def step(self):
         a, q = _I32(), _I32()

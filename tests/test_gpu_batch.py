@@ -120,3 +120,18 @@ def test_batch_errors(torch):
         t = b.submit(np.random.default_rng(0).standard_normal((50, 4)).astype(np.float32), 3, "fp32")
         b.run()
         assert b.poll(t) is not None
+
+
+def test_batch_large_class_limits(torch):
+    # instances with n >= 5000 count as large: capped CTAs, one at a time;
+    # small ones may start while a large one waits; results as alone
+    specs = make_specs()
+    with ebc.Batch(max_slots=4) as b:
+        b.set_large(5000, 40, 1)
+        tickets = [b.submit(V, k, p) for V, k, p in specs]
+        b.run()
+        res = [b.poll(t) for t in tickets]
+    for (V, k, p), r in zip(specs, res):
+        ridx, rf = alone(V, k, p)
+        np.testing.assert_array_equal(r[0], ridx)
+        np.testing.assert_allclose(r[1], rf, rtol=1e-12)
