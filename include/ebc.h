@@ -240,6 +240,12 @@ const char *ebc_noalloc_last_error(void);
  * errors from ebc_create.  The pointer stays valid until the next call. */
 const char *ebc_last_error(ebc_t h);
 
+/* Handles allocate device memory from a stream-ordered pool owned by the
+ * library (one per device), so creating and destroying handles does not
+ * synchronise the device; freed memory stays cached for later handles.
+ * This returns the cached, unused memory of the current device's pool. */
+ebc_status ebc_release_cached_memory(void);
+
 /* Device bytes a handle for (n, d, prec) allocates (an estimate the batch
  * runtime uses for admission); -1 for bad sizes. */
 int64_t ebc_estimate_bytes(int64_t n, int32_t d, int32_t prec);

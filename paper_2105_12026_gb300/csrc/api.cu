@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -52,6 +53,30 @@ namespace {
 
 thread_local std::string g_create_error;
 
+constexpr int kPoolDevices = 64;
+cudaMemPool_t g_pools[kPoolDevices] = {};
+std::mutex g_pool_mu;
+
+cudaMemPool_t device_pool(int dev) {
+    if (dev < 0 || dev >= kPoolDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;  // keep freed memory cached for the next instance
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
 constexpr int32_t kMaxD = 4096;
 
 ebc_status fail(ebc_t h, ebc_status s, const std::string &msg) {
@@ -74,10 +99,10 @@ ebc_status cuda_fail(ebc_t h, cudaError_t e, const char *where) {
     } while (0)
 
 template <class T>
-cudaError_t dalloc(T **p, size_t count) {
+cudaError_t dalloc(T **p, size_t count, const ebc::Ctx &c) {
     *p = nullptr;
     if (count == 0) count = 1;
-    return cudaMalloc((void **)p, sizeof(T) * count);
+    return ebc::pool_alloc((void **)p, sizeof(T) * count, c.stream, c.device);
 }
 
 void free_all(ebc::Ctx &c, ebc_ctx *h) {
@@ -87,9 +112,7 @@ void free_all(ebc::Ctx &c, ebc_ctx *h) {
                     c.cert.top_lo, c.cert.top_hi, c.cert.esc_lo, c.cert.esc_hi, c.cert.part_lo, c.cert.part_hi,
                     c.cert.ctd_idx, c.cert.ctd_part, c.cert.ctd_exact,
                     h ? h->d_scalar : nullptr, h ? h->d_bad : nullptr};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
-    if (c.h_err) cudaFreeHost(c.h_err);
+    for (void *p : ptrs) ebc::pool_free(p, c.stream);
 }
 
 double bulk_eta(const ebc::Ctx &c) {
@@ -189,10 +212,10 @@ cudaError_t fold_profile(ebc_t h) {
 ebc_status ensure_set_part(ebc_t h, int64_t want) {
     ebc::Ctx &c = h->c;
     if (c.set_part_cap >= want) return EBC_OK;
-    if (c.set_part) cudaFree(c.set_part);
+    ebc::pool_free(c.set_part, c.stream);
     c.set_part = nullptr;
     c.set_part_cap = 0;
-    CK(h, dalloc(&c.set_part, (size_t)want));
+    CK(h, dalloc(&c.set_part, (size_t)want, c));
     c.set_part_cap = want;
     return EBC_OK;
 }
@@ -219,7 +242,29 @@ int64_t ebc::handle_bytes(int64_t n, int32_t d, ebc_prec prec) {
     return b + 64 * 1024;  // allocation granularity and small buffers
 }
 
+cudaError_t ebc::pool_alloc(void **p, size_t bytes, cudaStream_t s, int dev) {
+    *p = nullptr;
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, s);
+}
+
+void ebc::pool_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
 extern "C" {
+
+ebc_status ebc_release_cached_memory(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return EBC_ENODEV;
+    }
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return EBC_ECUDA;
+    return cudaMemPoolTrimTo(pool, 0) == cudaSuccess ? EBC_OK : EBC_ECUDA;
+}
 
 int64_t ebc_estimate_bytes(int64_t n, int32_t d, int32_t prec) {
     if (n <= 0 || d <= 0) return -1;
@@ -286,43 +331,42 @@ ebc_status ebc::create_handle(const float *V, int64_t n, int32_t d, int32_t v_on
             return bail(_e == cudaErrorMemoryAllocation ? EBC_ENOMEM : EBC_ECUDA,                  \
                         std::string("ebc_create: ") + #expr + ": " + cudaGetErrorString(_e));     \
     } while (0)
-    CKC(dalloc(&c.V32, (size_t)n * d));
-    CKC(dalloc(&c.nv64, n));
-    CKC(dalloc(&c.nv32, n));
-    CKC(dalloc(&c.m64, n));
-    CKC(dalloc(&c.sel, n));
-    CKC(dalloc(&c.st, 1));
+    CKC(dalloc(&c.V32, (size_t)n * d, c));
+    CKC(dalloc(&c.nv64, n, c));
+    CKC(dalloc(&c.nv32, n, c));
+    CKC(dalloc(&c.m64, n, c));
+    CKC(dalloc(&c.sel, n, c));
+    CKC(dalloc(&c.st, 1, c));
     cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
     c.partial_cap = (int64_t)std::max(h->nch, 16) * n;
-    CKC(dalloc(&c.partial, (size_t)c.partial_cap));
-    CKC(dalloc(&c.gain_up, n));
+    CKC(dalloc(&c.partial, (size_t)c.partial_cap, c));
+    CKC(dalloc(&c.gain_up, n, c));
     c.blk_cap = h->nblk * (ebc::kMaxRefineK + 1);
-    CKC(dalloc(&c.blk_idx, c.blk_cap));
-    CKC(dalloc(&c.blk_val, c.blk_cap));
-    CKC(dalloc(&c.top_idx, ebc::kMaxRefineK + 1));
-    CKC(dalloc(&c.top_val, ebc::kMaxRefineK + 1));
-    CKC(dalloc(&c.esc_idx, n));
-    CKC(dalloc(&c.esc_exact, n));
+    CKC(dalloc(&c.blk_idx, c.blk_cap, c));
+    CKC(dalloc(&c.blk_val, c.blk_cap, c));
+    CKC(dalloc(&c.top_idx, ebc::kMaxRefineK + 1, c));
+    CKC(dalloc(&c.top_val, ebc::kMaxRefineK + 1, c));
+    CKC(dalloc(&c.esc_idx, n, c));
+    CKC(dalloc(&c.esc_exact, n, c));
     {
         ebc::Ctx::Sel &S = c.cert;
         S.cap = h->esc_cap;
         S.nchunks = h->nref;
         S.chunk = h->ref_ch;
         const size_t pool = (size_t)ebc::kMaxRefineK + S.cap;
-        CKC(dalloc(&S.top_lo, ebc::kMaxRefineK));
-        CKC(dalloc(&S.top_hi, ebc::kMaxRefineK));
-        CKC(dalloc(&S.esc_lo, S.cap));
-        CKC(dalloc(&S.esc_hi, S.cap));
-        CKC(dalloc(&S.part_lo, pool * S.nchunks));
-        CKC(dalloc(&S.part_hi, pool * S.nchunks));
-        CKC(dalloc(&S.ctd_idx, pool));
-        CKC(dalloc(&S.ctd_part, pool * S.nchunks));
-        CKC(dalloc(&S.ctd_exact, pool));
+        CKC(dalloc(&S.top_lo, ebc::kMaxRefineK, c));
+        CKC(dalloc(&S.top_hi, ebc::kMaxRefineK, c));
+        CKC(dalloc(&S.esc_lo, S.cap, c));
+        CKC(dalloc(&S.esc_hi, S.cap, c));
+        CKC(dalloc(&S.part_lo, pool * S.nchunks, c));
+        CKC(dalloc(&S.part_hi, pool * S.nchunks, c));
+        CKC(dalloc(&S.ctd_idx, pool, c));
+        CKC(dalloc(&S.ctd_part, pool * S.nchunks, c));
+        CKC(dalloc(&S.ctd_exact, pool, c));
     }
-    CKC(dalloc(&c.cand_buf, n));
-    CKC(dalloc(&h->d_scalar, 1));
-    CKC(dalloc(&h->d_bad, 1));
-    CKC(cudaMallocHost((void **)&c.h_err, sizeof(int32_t) * 4));
+    CKC(dalloc(&c.cand_buf, n, c));
+    CKC(dalloc(&h->d_scalar, 1, c));
+    CKC(dalloc(&h->d_bad, 1, c));
 
     CKC(cudaMemcpyAsync(c.V32, V, sizeof(float) * (size_t)n * d,
                         v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream));
@@ -344,8 +388,8 @@ ebc_status ebc_destroy(ebc_t h) {
     if (!h) return EBC_OK;
     cudaStreamSynchronize(h->c.stream);
     if (h->round_exec) cudaGraphExecDestroy(h->round_exec);
-    if (h->g_idx) cudaFree(h->g_idx);
-    if (h->g_f) cudaFree(h->g_f);
+    ebc::pool_free(h->g_idx, h->c.stream);
+    ebc::pool_free(h->g_f, h->c.stream);
     for (auto &r : h->prof.pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -391,6 +435,7 @@ ebc_status ebc_reset_profile(ebc_t h) {
 
 ebc_status ebc_set_stream(ebc_t h, void *stream) {
     if (check_handle(h)) return EBC_EINVAL;
+    CK(h, cudaStreamSynchronize(h->c.stream));  // stream-ordered allocations become visible to the new stream
     h->c.stream = (cudaStream_t)stream;
     return EBC_OK;
 }
@@ -526,11 +571,11 @@ ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *o
             if (cand_idx[j] < 0 || (int64_t)cand_idx[j] >= c.n) return fail(h, EBC_EINDEX, "ebc_gains_host: index outside [0, n)");
     int32_t *d_c = nullptr;
     double *d_g = nullptr;
-    if (cand_idx) CK(h, dalloc(&d_c, m));
-    cudaError_t e = dalloc(&d_g, m);
+    if (cand_idx) CK(h, dalloc(&d_c, m, c));
+    cudaError_t e = dalloc(&d_g, m, c);
     if (e != cudaSuccess) {
-        if (d_c) cudaFree(d_c);
-        return cuda_fail(h, e, "ebc_gains_host: cudaMalloc");
+        ebc::pool_free(d_c, c.stream);
+        return cuda_fail(h, e, "ebc_gains_host: allocation");
     }
     ebc_status s = EBC_OK;
     if (cand_idx) e = cudaMemcpyAsync(d_c, cand_idx, sizeof(int32_t) * m, cudaMemcpyHostToDevice, c.stream);
@@ -538,8 +583,8 @@ ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *o
     if (e == cudaSuccess && s == EBC_OK)
         e = cudaMemcpyAsync(out_gain, d_g, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess && s == EBC_OK) e = cudaStreamSynchronize(c.stream);
-    cudaFree(d_g);
-    if (d_c) cudaFree(d_c);
+    ebc::pool_free(d_g, c.stream);
+    ebc::pool_free(d_c, c.stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "ebc_gains_host");
     if (s != EBC_OK) return s;
     return ebc_sync(h);
@@ -578,9 +623,9 @@ ebc_status ebc_eval_sets_host(ebc_t h, const int32_t *csr_idx, const int64_t *cs
     int32_t *d_i = nullptr;
     int64_t *d_o = nullptr;
     double *d_f = nullptr;
-    cudaError_t e = dalloc(&d_i, nnz);
-    if (e == cudaSuccess) e = dalloc(&d_o, l + 1);
-    if (e == cudaSuccess) e = dalloc(&d_f, l);
+    cudaError_t e = dalloc(&d_i, nnz, c);
+    if (e == cudaSuccess) e = dalloc(&d_o, l + 1, c);
+    if (e == cudaSuccess) e = dalloc(&d_f, l, c);
     ebc_status s = EBC_OK;
     if (e == cudaSuccess && nnz > 0)
         e = cudaMemcpyAsync(d_i, csr_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c.stream);
@@ -588,9 +633,9 @@ ebc_status ebc_eval_sets_host(ebc_t h, const int32_t *csr_idx, const int64_t *cs
     if (e == cudaSuccess) s = ebc_eval_sets(h, d_i, d_o, l, d_f);
     if (e == cudaSuccess && s == EBC_OK) e = cudaMemcpyAsync(out_f, d_f, sizeof(double) * l, cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess && s == EBC_OK) e = cudaStreamSynchronize(c.stream);
-    if (d_i) cudaFree(d_i);
-    if (d_o) cudaFree(d_o);
-    if (d_f) cudaFree(d_f);
+    ebc::pool_free(d_i, c.stream);
+    ebc::pool_free(d_o, c.stream);
+    ebc::pool_free(d_f, c.stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "ebc_eval_sets_host");
     if (s != EBC_OK) return s;
     return ebc_sync(h);
@@ -648,8 +693,8 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
 static ebc_status capture_round(ebc_t h) {
     ebc::Ctx &c = h->c;
     if (!h->g_idx) {
-        CK(h, dalloc(&h->g_idx, c.n));
-        CK(h, dalloc(&h->g_f, c.n));
+        CK(h, dalloc(&h->g_idx, c.n, c));
+        CK(h, dalloc(&h->g_f, c.n, c));
     }
     if (h->round_exec) {
         cudaGraphExecDestroy(h->round_exec);
@@ -764,15 +809,15 @@ ebc_status ebc_greedy_host(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) 
     if (!out_idx || !out_f) return fail(h, EBC_EINVAL, "ebc_greedy_host: NULL output");
     int32_t *d_i = nullptr;
     double *d_f = nullptr;
-    cudaError_t e = dalloc(&d_i, k);
-    if (e == cudaSuccess) e = dalloc(&d_f, k);
+    cudaError_t e = dalloc(&d_i, k, c);
+    if (e == cudaSuccess) e = dalloc(&d_f, k, c);
     ebc_status s = EBC_OK;
     if (e == cudaSuccess) s = ebc_greedy(h, k, d_i, d_f);
     if (e == cudaSuccess && s == EBC_OK) e = cudaMemcpyAsync(out_idx, d_i, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess && s == EBC_OK) e = cudaMemcpyAsync(out_f, d_f, sizeof(double) * k, cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess && s == EBC_OK) e = cudaStreamSynchronize(c.stream);
-    if (d_i) cudaFree(d_i);
-    if (d_f) cudaFree(d_f);
+    ebc::pool_free(d_i, c.stream);
+    ebc::pool_free(d_f, c.stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "ebc_greedy_host");
     if (s != EBC_OK) return s;
     return ebc_sync(h);

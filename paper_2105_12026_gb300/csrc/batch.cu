@@ -1,7 +1,10 @@
 // Batch runtime: many independent summarisation instances sharing one GPU.
 //
 // Each admitted instance occupies a slot: its own handle (resident V,
-// norms, quantised copies, Greedy state) and its own non-blocking stream.
+// norms, quantised copies, Greedy state) and its own non-blocking stream;
+// instances marked large (ebc_batch_set_large) use the lowest stream
+// priority, all others the highest, so ordinary requests' kernels get SMs
+// first whenever SMs free up.
 // ebc_batch_step() advances every active instance by one Greedy round
 // (a graph replay after the first round), so rounds of different instances
 // overlap on the device; finished instances are detected with events,
@@ -32,7 +35,9 @@ struct ebc_batch_ctx {
     struct Slot {
         bool busy = false, finishing = false, large = false;
         ebc_t h = nullptr;
-        cudaStream_t stream = nullptr;
+        cudaStream_t stream = nullptr;     // current instance's stream (one of the two below)
+        cudaStream_t stream_hi = nullptr;  // highest priority: ordinary instances
+        cudaStream_t stream_lo = nullptr;  // lowest priority: large instances
         cudaEvent_t done = nullptr;
         int64_t ticket = -1;
         int32_t k = 0, issued = 0, cap = 0;
@@ -75,10 +80,21 @@ void release_slot(ebc_batch_ctx::Slot &s) {
     s.bytes = 0;
 }
 
+// Per-slot output buffers, grown (rarely) to the largest k seen.  Device
+// buffers come from the library's stream-ordered pool on the slot's
+// high-priority stream; both streams of the slot wait for that stream before
+// the buffers are used.
 ebc_status ensure_outputs(ebc_batch_t b, ebc_batch_ctx::Slot &s, int32_t k) {
     if (s.cap >= k) return EBC_OK;
-    if (s.d_idx) cudaFree(s.d_idx);
-    if (s.d_f) cudaFree(s.d_f);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int32_t cap = k > 256 ? k : 256;
+    if (s.d_idx || s.d_f) {
+        cudaStreamSynchronize(s.stream_hi);
+        cudaStreamSynchronize(s.stream_lo);
+    }
+    ebc::pool_free(s.d_idx, s.stream_hi);
+    ebc::pool_free(s.d_f, s.stream_hi);
     if (s.h_idx) cudaFreeHost(s.h_idx);
     if (s.h_f) cudaFreeHost(s.h_f);
     s.d_idx = nullptr;
@@ -86,13 +102,14 @@ ebc_status ensure_outputs(ebc_batch_t b, ebc_batch_ctx::Slot &s, int32_t k) {
     s.h_idx = nullptr;
     s.h_f = nullptr;
     s.cap = 0;
-    if (cudaMalloc(&s.d_idx, sizeof(int32_t) * k) != cudaSuccess || cudaMalloc(&s.d_f, sizeof(double) * k) != cudaSuccess ||
-        cudaMallocHost(&s.h_idx, sizeof(int32_t) * k) != cudaSuccess ||
-        cudaMallocHost(&s.h_f, sizeof(double) * k) != cudaSuccess) {
+    if (ebc::pool_alloc((void **)&s.d_idx, sizeof(int32_t) * cap, s.stream_hi, dev) != cudaSuccess ||
+        ebc::pool_alloc((void **)&s.d_f, sizeof(double) * cap, s.stream_hi, dev) != cudaSuccess ||
+        cudaMallocHost(&s.h_idx, sizeof(int32_t) * cap) != cudaSuccess ||
+        cudaMallocHost(&s.h_f, sizeof(double) * cap) != cudaSuccess || cudaStreamSynchronize(s.stream_hi) != cudaSuccess) {
         cudaGetLastError();
         return bfail(b, EBC_ENOMEM, "ebc_batch: output buffers");
     }
-    s.cap = k;
+    s.cap = cap;
     return EBC_OK;
 }
 
@@ -140,6 +157,7 @@ void admit(ebc_batch_t b) {
         ebc_batch_ctx::Slot &s = *free_slot;
         ebc_status st = ensure_outputs(b, s, r.k);
         ebc_t h = nullptr;
+        s.stream = large ? s.stream_lo : s.stream_hi;
         if (st == EBC_OK) st = ebc::create_handle(r.V.data(), r.n, r.d, 0, s.stream, false, &h);
         if (st == EBC_OK && (r.prec != EBC_FP32 || b->refine_k != 8))
             st = ebc::set_precision_handle(h, r.prec, b->refine_k, false);
@@ -215,12 +233,19 @@ ebc_status ebc_batch_create(int32_t max_slots, int64_t device_budget_bytes, int3
     b->budget = device_budget_bytes;
     b->refine_k = refine_k;
     b->slots.resize(max_slots);
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
     for (auto &s : b->slots) {
-        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        if (cudaStreamCreateWithPriority(&s.stream_hi, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&s.stream_lo, cudaStreamNonBlocking, least) != cudaSuccess ||
             cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             ebc_batch_destroy(b);
             return EBC_ECUDA;
+        }
+        if (ensure_outputs(b, s, 256) != EBC_OK) {
+            ebc_batch_destroy(b);
+            return EBC_ENOMEM;
         }
     }
     *out = b;
@@ -329,14 +354,17 @@ const char *ebc_batch_last_error(ebc_batch_t b) { return b ? b->err.c_str() : ""
 ebc_status ebc_batch_destroy(ebc_batch_t b) {
     if (!b) return EBC_OK;
     for (auto &s : b->slots) {
-        if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.stream_hi) cudaStreamSynchronize(s.stream_hi);
+        if (s.stream_lo) cudaStreamSynchronize(s.stream_lo);
         release_slot(s);
-        if (s.d_idx) cudaFree(s.d_idx);
-        if (s.d_f) cudaFree(s.d_f);
+        ebc::pool_free(s.d_idx, s.stream_hi);
+        ebc::pool_free(s.d_f, s.stream_hi);
+        if (s.stream_hi) cudaStreamSynchronize(s.stream_hi);
         if (s.h_idx) cudaFreeHost(s.h_idx);
         if (s.h_f) cudaFreeHost(s.h_f);
         if (s.done) cudaEventDestroy(s.done);
-        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.stream_hi) cudaStreamDestroy(s.stream_hi);
+        if (s.stream_lo) cudaStreamDestroy(s.stream_lo);
     }
     delete b;
     return EBC_OK;

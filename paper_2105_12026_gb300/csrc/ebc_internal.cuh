@@ -102,7 +102,8 @@ struct Ctx {
     int *cand_buf = nullptr;    // [n] gathered candidate list for ebc_gains
     double *set_part = nullptr; // eval_sets partials
     int64_t set_part_cap = 0;
-    int32_t *h_err = nullptr;   // pinned host word for error read-back
+    int32_t h_err_store[4] = {0, 0, 0, 0};
+    int32_t *h_err = h_err_store;  // host words for error read-back
 
     // two-level certification of the Greedy pick (k_select.cu)
     struct Sel {
@@ -119,6 +120,13 @@ struct Ctx {
 
     std::string last_error;
 };
+
+// ---- device memory: one stream-ordered pool per device (api.cu) ----------
+// Handles allocate and free through it (cudaMallocFromPoolAsync /
+// cudaFreeAsync on their stream), so creating and destroying instances never
+// synchronises the device.  Freed memory stays cached in the pool.
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s, int dev);
+void pool_free(void *p, cudaStream_t s);
 
 // ---- handle helpers shared with the batch runtime (api.cu) ---------------
 ebc_status create_handle(const float *V, int64_t n, int32_t d, int32_t v_on_device, void *stream, bool sync,

@@ -602,8 +602,7 @@ bool tc_supported(const Ctx &c) { return c.d <= 128; }
 void tc_free(Ctx &c) {
     void *ptrs[] = {c.tc.Vq, c.tc.Vq2, c.tc.Aext, c.tc.Bext, c.tc.Cq, c.tc.Cqx, c.tc.qn64, c.tc.qerr, c.tc.qnorm,
                     c.tc.qmax};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    for (void *p : ptrs) pool_free(p, c.stream);
     c.tc = Ctx::Tc();
 }
 
@@ -627,16 +626,16 @@ cudaError_t tc_setup(Ctx &c, int prec) {
         T.DP = (c.d + KATOM - 1) / KATOM * KATOM;
         size_t rows = (size_t)T.n_pad;
         cudaError_t e;
-        if ((e = cudaMalloc(&T.Vq, rows * T.DP * 2)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.Vq2, rows * T.DP * 2)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.Aext, rows * KEXT * 2)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.Bext, rows * KEXT * 2)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.Cq, rows * T.DP * 2)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.Cqx, rows * KEXT * 2)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.qn64, rows * 8)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.qerr, rows * 4)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.qnorm, rows * 4)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&T.qmax, 2 * 4)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.Vq, rows * T.DP * 2, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.Vq2, rows * T.DP * 2, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.Aext, rows * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.Bext, rows * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.Cq, rows * T.DP * 2, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.Cqx, rows * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.qn64, rows * 8, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.qerr, rows * 4, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.qnorm, rows * 4, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.qmax, 2 * 4, c.stream, c.device)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Cq, 0, rows * T.DP * 2, c.stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Cqx, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Bext, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;

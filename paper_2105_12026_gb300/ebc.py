@@ -83,6 +83,7 @@ _SIGS = {
     "ebc_eval_sets_noalloc": [_P, _I64, _I32, _P, _P, _I64, _P, _P],
     "ebc_noalloc_last_error": [],
     "ebc_estimate_bytes": [_I64, _I32, _I32],
+    "ebc_release_cached_memory": [],
     "ebc_batch_create": [_I32, _I64, _I32, ctypes.POINTER(_P)],
     "ebc_batch_submit": [_P, _P, _I64, _I32, _I32, ctypes.c_int, ctypes.POINTER(_I64)],
     "ebc_batch_step": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
