@@ -304,6 +304,108 @@ def run_serve(args):
     return 0
 
 
+def run_sets(args):
+    """Multi-set evaluation: n=50,000, d=64, 1,024 CSR sets of size U{1..64}
+    (32-cluster anisotropic GMM).  One step = one ebc_eval_sets call over all
+    sets; one evaluation = one (point, member) pair, n * nnz per step.  The
+    tensor-core precision is timed against the FP32 plain kernel on the same
+    handle; raw error against the oracle on a sample of sets."""
+    import torch
+
+    import oracle
+    from paper_2105_12026_gb300 import ebc, synth
+    torch.cuda.set_device(0)
+    w = synth.multiset_eval(seed=args.seed, n=args.n, d=args.d, l=args.sets)
+    V, idx, off = w["V"], w["idx"], w["off"]
+    n, d = V.shape
+    l = len(off) - 1
+    nnz = int(off[-1])
+    evals = n * nnz
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", 0)
+    Vd = torch.from_numpy(V).to(dev)
+    idx_d = torch.from_numpy(idx).to(dev)
+    off_d = torch.from_numpy(off).to(dev)
+    out = torch.empty(l, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    inst = ebc.Instance(Vd, precision=args.prec, stream=stream)
+
+    def timed(prec):
+        inst.set_precision(prec)
+        for _ in range(args.warmup):
+            ebc.ebc_eval_sets(inst.h, idx_d.data_ptr(), off_d.data_ptr(), l, out.data_ptr())
+        inst.sync()
+        inst.profiling(True)
+        inst.reset_profile()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            ebc.ebc_eval_sets(inst.h, idx_d.data_ptr(), off_d.data_ptr(), l, out.data_ptr())
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        inst.sync()
+        prof = inst.profile()
+        inst.profiling(False)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        return ms, prof, out.cpu().numpy().copy()
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_tc, prof_tc, f_tc = timed(args.prec)
+    clk = clocks.stop()
+    ms_32, prof_32, f_32 = timed("fp32")
+    # e2e: host buffers through the C ABI (offsets, members in; values out)
+    inst.set_precision(args.prec)
+    inst.eval_sets_host(idx, off)
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inst.eval_sets_host(idx, off)
+        e2e.append(time.perf_counter() - t0)
+    inst.close()
+    pick = np.random.default_rng(0).choice(l, min(48, l), replace=False)
+    sub_off = np.zeros(pick.size + 1, np.int64)
+    sub_off[1:] = np.cumsum(off[pick + 1] - off[pick])
+    sub_idx = np.concatenate([idx[off[j]:off[j + 1]] for j in pick]).astype(np.int32)
+    t0 = time.perf_counter()
+    ref = oracle.eval_sets(V, sub_idx, sub_off)
+    cpu_s = time.perf_counter() - t0
+    rel_tc = np.abs(f_tc[pick] - ref) / np.maximum(ref, 1e-300)
+    rel_32 = np.abs(f_32[pick] - ref) / np.maximum(ref, 1e-300)
+    pk = peaks()
+    kern_ms = prof_tc["eval_ms"] / max(1, args.steps)
+    flops = 2.0 * d * evals
+    achieved = flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else None
+    peak = pk["bf16"]
+    line = {"metric": METRIC, "value": evals / (ms_tc / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_tc, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32"}.get(args.prec, args.prec),
+            "data": "synthetic (seeded 32-cluster anisotropic GMM, CSR sets U{1..64})",
+            "config": {"workload": f"multi-set evaluation n={n} d={d} l={l} sets of size U{{1..64}} (nnz={nnz})",
+                       "l2": "flushed between calls (256 MB write, outside the events)",
+                       "evals_per_step": evals},
+            "roofline": {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "peak_source": f"{pk['source']} bf16 burst",
+                         "kernel": "multi-set evaluation (member gather + tcgen05 sets kernel + finalize)",
+                         "avg_ms": kern_ms, "algorithmic_flops_per_launch": flops},
+            "gpu_launches": prof_tc["launches"], "clocks": clk,
+            "fp32_plain": {"value": evals / (ms_32 / 1e3), "unit": UNIT, "ms_per_step": ms_32,
+                           "tc_over_fp32": ms_32 / ms_tc},
+            "raw_rel_err_vs_oracle": {"tc_max": float(rel_tc.max()), "tc_median": float(np.median(rel_tc)),
+                                      "fp32_max": float(rel_32.max()), "sets_checked": int(pick.size)},
+            "e2e": {"value": evals * args.steps / sum(e2e), "unit": UNIT,
+                    "h2d_bytes_per_step": int(idx.nbytes + off.nbytes), "d2h_bytes_per_step": int(l * 8)},
+            "cpu_baseline": {"value": n * int(sub_off[-1]) / cpu_s, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": f"oracle eval_sets on {pick.size} sampled sets "
+                                                         f"({int(sub_off[-1])} members) x {n} points, {cpu_s:.1f}s"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,7 +414,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
     ap.add_argument("--refine-k", type=int, default=8)
-    ap.add_argument("--workload", default="regime", choices=["regime", "small", "mix", "serve"])
+    ap.add_argument("--workload", default="regime", choices=["regime", "small", "mix", "serve", "sets"])
+    ap.add_argument("--sets", type=int, default=1024, help="sets: number of CSR sets")
     ap.add_argument("--instances", type=int, default=256, help="mix: number of instances")
     ap.add_argument("--slots", type=int, default=32, help="mix/serve: concurrent instances")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="mix/serve: device-memory budget")
@@ -342,6 +445,10 @@ def main():
         return run_mix(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sets":
+        if args.n == 200_000 and args.d == 128:
+            args.n, args.d = 50_000, 64
+        return run_sets(args)
 
     import torch
     import torch.distributed as dist

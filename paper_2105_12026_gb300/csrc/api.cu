@@ -596,6 +596,25 @@ ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off
     if (l < 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: l < 0");
     if (l == 0) return EBC_OK;
     if (!csr_off || !out_f) return fail(h, EBC_EINVAL, "ebc_eval_sets: NULL argument");
+    if (c.prec != EBC_FP32) {
+        // tensor-core path: the tile plan needs the offsets on the host
+        std::vector<int64_t> off((size_t)l + 1);
+        CK(h, cudaMemcpyAsync(off.data(), csr_off, sizeof(int64_t) * (l + 1), cudaMemcpyDeviceToHost, c.stream));
+        CK(h, cudaStreamSynchronize(c.stream));
+        if (off[0] != 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: csr_off[0] != 0");
+        for (int64_t j = 0; j < l; ++j)
+            if (off[j + 1] < off[j]) return fail(h, EBC_EINVAL, "ebc_eval_sets: offsets decrease");
+        if (off[l] > 0 && !csr_idx) return fail(h, EBC_EINVAL, "ebc_eval_sets: csr_idx is NULL");
+        const int64_t npu = c.tc.n_pad / 256;
+        ebc_status s = ensure_set_part(h, std::min<int64_t>(npu * l, std::max<int64_t>(npu * 64, (int64_t)1 << 24)) +
+                                              npu * 64);
+        if (s) return s;
+        int64_t nl = 0;
+        CK(h, launch(h, PK_EVAL, 0, [&] { return ebc::launch_eval_sets_tc(c, csr_idx, csr_off, off.data(), l, out_f, &nl); }));
+        h->prof.p.launches += nl;
+        h->prof.p.eval_launches += nl;
+        return EBC_OK;
+    }
     CK(h, cudaMemsetAsync(h->d_bad, 0, sizeof(int), c.stream));
     k_check_csr<<<(unsigned)((l + 255) / 256), 256, 0, c.stream>>>(csr_off, l, c.st, h->d_bad);
     CK(h, cudaGetLastError());

@@ -84,6 +84,15 @@ struct Ctx {
         CUtensorMap tmAx_V;       // candidate extension over Aext (box 16 x 128)
         CUtensorMap tmAx_C;       // candidate extension over Cqx
         CUtensorMap tmBx;         // point extension over Bext (box 16 x 256)
+        // multi-set evaluation (ebc_eval_sets at a tensor-core precision)
+        uint16_t *Px = nullptr;   // [n_pad, 16] point-side extension: ||v||^2 - ||v_hat||^2 (static)
+        CUtensorMap tmPx;         // box 16 x 128 over Px
+        uint16_t *Mq = nullptr;   // [mcap, DP] 2 s_hat of the gathered set members, padded per set
+        uint16_t *Mx = nullptr;   // [mcap, 16] member extension: -||s_hat||^2
+        int *gset = nullptr;      // [mcap / 16] per 16-member group: 2 * (set index in its chunk) + last
+        int64_t *sets_aux = nullptr;  // padded offsets [l + 1], then chunk records
+        int64_t mcap = 0;         // rows of Mq / Mx
+        int64_t aux_cap = 0;      // int64 entries of sets_aux
     } tc;
     int num_sms = 152;
     int max_ctas = 0;  // cap on persistent-kernel CTAs (0 = one per SM)
@@ -167,6 +176,8 @@ cudaError_t launch_update(Ctx &c);
 cudaError_t launch_current_f(Ctx &c, double *d_out);
 cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,
                                   const int *bad);
+// out_f[j0 + j] = (1/n) sum over ntiles rows of set_part[row][j], j < lb
+cudaError_t launch_sets_finalize(Ctx &c, int64_t ntiles, int64_t lb, int64_t j0, int64_t l, double *out_f);
 
 // tensor-core path
 bool tc_supported(const Ctx &c);
@@ -175,6 +186,10 @@ cudaError_t tc_quantize(Ctx &c);                 // (re)quantise V into Vq
 cudaError_t launch_prep_tc(Ctx &c, bool upper);  // a_v for every point (+ max m_v)
 // bulk gains on tensor cores; returns the number of V chunks used in *nchunks
 cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int *nchunks);
+// multi-set evaluation on tensor cores; off_host is a host copy of the
+// (validated) offsets; returns cudaErrorMemoryAllocation if scratch is short
+cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_dev, const int64_t *off_host,
+                                int64_t l, double *out_f, int64_t *nlaunch);
 void tc_free(Ctx &c);
 
 }  // namespace ebc

@@ -388,6 +388,12 @@ __global__ void k_sets_finalize(const double *__restrict__ set_part, int64_t nti
     (void)lall;
 }
 
+cudaError_t launch_sets_finalize(Ctx &c, int64_t ntiles, int64_t lb, int64_t j0, int64_t l, double *out_f) {
+    k_sets_finalize<<<(unsigned)((lb + 255) / 256), 256, 0, c.stream>>>(c.set_part, ntiles, lb, j0, l,
+                                                                          1.0 / (double)c.n, out_f);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,
                                   const int *bad) {
     int64_t ntiles = (c.n + ES_T - 1) / ES_T;

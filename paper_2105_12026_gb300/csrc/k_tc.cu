@@ -55,6 +55,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "ebc_internal.cuh"
 #include "tc_ptx.cuh"
@@ -85,9 +86,37 @@ struct TcArgs {
     int na;              // candidate-tile buffers (1 or 2)
     uint32_t idesc;      // instruction descriptor, main part
     uint32_t idesc_ext;  // instruction descriptor, extension (bf16)
-    double *partial;     // [nchunks][m]
+    double *partial;     // gains: [nchunks][m]; sets: [point units][lb]
     int *err;            // device error word
+    // multi-set mode only
+    const int64_t *chunks;  // [nchunks][4]: first set, end set, first column, end column
+    const int *gset;        // per 16-column group: 2 * (set index within its chunk) + (last group of the set)
+    int64_t lb;             // sets of this launch (partial row length)
+    int64_t j0;             // first set of this launch
 };
+
+constexpr int MODE_GAINS = 0;
+constexpr int MODE_SETS = 1;
+constexpr int SETS_PER_CHUNK = 64;  // accumulator rows in shared memory ([64][8] floats)
+constexpr int SET_GROUP = 16;       // members per group: sets are padded to multiples of 16
+constexpr int64_t CHUNK_COLS = 2048;  // target member columns per chunk
+
+// Work unit u -> A tile index, chunk, first B row and number of B tiles.
+template <int MODE>
+__device__ __forceinline__ void unit_span(const TcArgs &a, int u, int &at, int &ch, int &b_row0, int &nb) {
+    at = u / a.nchunks;
+    ch = u % a.nchunks;
+    if constexpr (MODE == MODE_GAINS) {
+        const int vt0 = ch * a.vt_per_chunk;
+        const int vt1 = min(vt0 + a.vt_per_chunk, a.n_vtiles);
+        b_row0 = vt0 * BN;
+        nb = vt1 - vt0;
+    } else {
+        const int64_t *r = a.chunks + 4 * (int64_t)ch;
+        b_row0 = (int)r[2];
+        nb = (int)((r[3] - r[2] + BN - 1) / BN);
+    }
+}
 
 struct SmemLayout {
     uint32_t a_main, a_sub, a_bytes, b_main, b_bytes, off_b, off_comb, off_bar, off_misc, total;
@@ -129,9 +158,14 @@ __device__ __forceinline__ float relu_sum32(const uint32_t (&r)[32]) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_gains_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
-               const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
+// The warp-specialised TMA -> tcgen05 -> TMEM pipeline, shared by the bulk
+// gains (MODE_GAINS: A = candidates, B = points, epilogue = relu row sums)
+// and the multi-set evaluation (MODE_SETS: A = points, B = set members,
+// epilogue = per-set maxima and sums over the points).
+template <int MODE>
+__device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUtensorMap *tmAx_p,
+                                            const CUtensorMap *tmB_p, const CUtensorMap *tmBx_p, const TcArgs &args) {
+    const CUtensorMap &tmA = *tmA_p, &tmAx = *tmAx_p, &tmB = *tmB_p, &tmBx = *tmBx_p;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ns = args.nstages;
@@ -168,7 +202,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc::mbar_init(&a_full[b], 1);
             tc::mbar_init(&a_empty[b], 1);
             tc::mbar_init(&t_full[b], 1);
-            tc::mbar_init(&t_empty[b], NEPI / 32);
+            // every epilogue warp drains both regions in gains mode, half of them each in sets mode
+            tc::mbar_init(&t_empty[b], MODE == MODE_GAINS ? NEPI / 32 : NEPI / 64);
             last_afull[b] = -1;
             last_tfull[b] = -1;
         }
@@ -193,9 +228,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc::tma_prefetch_desc(&tmBx);
             int g = 0, ua = 0;
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
-                const int ct = u / args.nchunks, ch = u % args.nchunks;
-                const int vt0 = ch * args.vt_per_chunk;
-                const int vt1 = min(vt0 + args.vt_per_chunk, args.n_vtiles);
+                int ct, ch, b_row0, nb;
+                unit_span<MODE>(args, u, ct, ch, b_row0, nb);
                 const int ab = ua % na;
                 const int aph = (ua / na) & 1;
                 if (!tc::mbar_wait(&a_empty[ab], aph ^ 1, abort_flag)) {
@@ -213,9 +247,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 last_afull[ab] = aph;
                 bool ok = true;
-                for (int vt = vt0; vt < vt1; ++vt, ++g) {
+                for (int i = 0; i < nb; ++i, ++g) {
                     const int s = g % ns;
                     const int ph = (g / ns) & 1;
+                    const int brow = b_row0 + i * BN;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
                         record_timeout(args.err, abort_flag);
                         ok = false;
@@ -224,8 +259,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     uint8_t *bbuf = sB + s * L.b_bytes;
                     tc::mbar_arrive_expect_tx(&full[s], L.b_bytes);
                     for (int j = 0; j < katoms; ++j)
-                        tc::tma_load_2d(bbuf + j * (BN * 128), &tmB, &full[s], j * KATOM, vt * BN);
-                    tc::tma_load_2d(bbuf + L.b_main, &tmBx, &full[s], 0, vt * BN);
+                        tc::tma_load_2d(bbuf + j * (BN * 128), &tmB, &full[s], j * KATOM, brow);
+                    tc::tma_load_2d(bbuf + L.b_main, &tmBx, &full[s], 0, brow);
                     last_full[s] = ph;
                 }
                 if (!ok) break;
@@ -238,9 +273,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             int g = 0, t = 0, ua = 0;
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
-                const int ch = u % args.nchunks;
-                const int vt0 = ch * args.vt_per_chunk;
-                const int vt1 = min(vt0 + args.vt_per_chunk, args.n_vtiles);
+                int ct, ch, b_row0, nb;
+                unit_span<MODE>(args, u, ct, ch, b_row0, nb);
                 const int ab = ua % na;
                 if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag)) {
                     record_timeout(args.err, abort_flag);
@@ -248,7 +282,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 const uint32_t a0 = tc::smem_u32(sA + ab * L.a_bytes);
                 bool ok = true;
-                for (int vt = vt0; vt < vt1 && ok; ++vt, ++g, ++t) {
+                for (int i = 0; i < nb && ok; ++i, ++g, ++t) {
                     const int s = g % ns;
                     if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag)) {
                         record_timeout(args.err, abort_flag);
@@ -283,7 +317,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc::mma_commit(&a_empty[ab]);
             }
         }
-    } else {
+    } else if constexpr (MODE == MODE_GAINS) {
         // ------------------------------------------------------------ epilogue
         const int ew = warp - 2;        // 0..7
         const int q = warp & 3;         // TMEM lane quarter this warp may access
@@ -292,11 +326,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int t = 0;
         bool alive = true;
         for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
-            const int ct = u / args.nchunks, ch = u % args.nchunks;
-            const int vt0 = ch * args.vt_per_chunk;
-            const int vt1 = min(vt0 + args.vt_per_chunk, args.n_vtiles);
+            int ct, ch, b_row0, nb;
+            unit_span<MODE>(args, u, ct, ch, b_row0, nb);
             double acc[2] = {0.0, 0.0};
-            for (int vt = vt0; vt < vt1; ++vt, ++t) {
+            for (int i = 0; i < nb; ++i, ++t) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     if (alive) {
@@ -340,6 +373,92 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc::named_bar_sync(2, NEPI);
         }
+    } else {
+        // ------------------------------------------------------ set epilogue
+        // Warps 2-5 drain region 0 (points 0-127 of the unit), warps 6-9
+        // region 1 (points 128-255); a thread owns one point and all 256
+        // member columns of its region.  acc(v, s) = ||v||^2 - dhat(v, s), so
+        // the set's term is max(0, max over its members of acc).  Groups of
+        // 16 columns belong to one set; a set's running maximum carries over
+        // tiles; at its last group the 32 lanes' terms are summed (FP32,
+        // fixed shuffle tree) into sacc[set][warp].
+        const int ew = warp - 2;  // 0..7
+        const int q = warp & 3;
+        const int h = ew >> 2;
+        float *sacc = reinterpret_cast<float *>(comb);  // [SETS_PER_CHUNK][8]
+        const int et = threadIdx.x - 64;                // 0..255
+        int t = 0;
+        bool alive = true;
+        for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+            int at, ch, b_row0, nb;
+            unit_span<MODE>(args, u, at, ch, b_row0, nb);
+            const int64_t *rec = args.chunks + 4 * (int64_t)ch;
+            const int64_t set_b = rec[0], nsets = rec[1] - rec[0], col_e = rec[3];
+            for (int i = et; i < SETS_PER_CHUNK * 8; i += NEPI) sacc[i] = 0.f;
+            tc::named_bar_sync(2, NEPI);
+            float run = -INFINITY;
+            for (int i = 0; i < nb; ++i, ++t) {
+                const int64_t c0 = (int64_t)b_row0 + (int64_t)i * BN;
+                const int ngr = (int)(min((int64_t)BN, col_e - c0) / SET_GROUP);
+                const int ge = lane < ngr ? __ldg(args.gset + c0 / SET_GROUP + lane) : 0;
+                if (alive) {
+                    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag));
+                    if (!ok) {
+                        if (lane == 0) record_timeout(args.err, abort_flag);
+                        alive = false;
+                    }
+                }
+                if (!alive) continue;
+                tc::tc_fence_after();
+                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN);
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    if (hh * 8 < ngr) {
+                        uint32_t r[4][32];
+                        tc::tmem_ld32(taddr + hh * 128, r[0]);
+                        tc::tmem_ld32(taddr + hh * 128 + 32, r[1]);
+                        tc::tmem_ld32(taddr + hh * 128 + 64, r[2]);
+                        tc::tmem_ld32(taddr + hh * 128 + 96, r[3]);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int gg = 0; gg < 8; ++gg) {
+                            const int g = hh * 8 + gg;
+                            if (g < ngr) {
+                                const int e = __shfl_sync(0xffffffffu, ge, g);
+                                float m0 = __uint_as_float(r[gg >> 1][(gg & 1) * 16]);
+                                float m1 = __uint_as_float(r[gg >> 1][(gg & 1) * 16 + 1]);
+#pragma unroll
+                                for (int k = 2; k < 16; k += 2) {
+                                    m0 = fmaxf(m0, __uint_as_float(r[gg >> 1][(gg & 1) * 16 + k]));
+                                    m1 = fmaxf(m1, __uint_as_float(r[gg >> 1][(gg & 1) * 16 + k + 1]));
+                                }
+                                run = fmaxf(run, fmaxf(m0, m1));
+                                if (e & 1) {
+                                    float val = fmaxf(run, 0.f);
+#pragma unroll
+                                    for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                                    if (lane == 0) sacc[(e >> 1) * 8 + ew] = val;
+                                    run = -INFINITY;
+                                }
+                            }
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&t_empty[h]);
+            }
+            tc::named_bar_sync(2, NEPI);
+            if (alive) {
+                for (int sidx = et; sidx < nsets; sidx += NEPI) {
+                    double tot = 0.0;
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) tot += (double)sacc[sidx * 8 + w];
+                    args.partial[(int64_t)at * args.lb + (set_b - args.j0) + sidx] = tot;
+                }
+            }
+            tc::named_bar_sync(2, NEPI);
+        }
     }
 
     // ---------------------------------------------------------------- teardown
@@ -360,6 +479,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem_base, TMEM_COLS);
     }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gains_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+               const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
+    tc_pipeline<MODE_GAINS>(&tmA, &tmAx, &tmB, &tmBx, args);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_sets_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+              const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
+    tc_pipeline<MODE_SETS>(&tmA, &tmAx, &tmB, &tmBx, args);
 }
 
 // ---------------------------------------------------------------------------
@@ -443,11 +574,31 @@ __global__ void k_quantize(const float *__restrict__ V, int64_t n, int d, int64_
 }
 
 // Static candidate extension X and the padding rows of the point extension.
+// Also the point-side extension of the multi-set evaluation,
+// Px = [1 1 1 | b b b | 0..] with b = ||v||^2 - ||v_hat||^2 (to nearest), so
+// that with a member's [q q q | 1 1 1 | 0..], q = -||s_hat||^2, the
+// accumulator holds 2 v_hat.s_hat + b + q = ||v||^2 - ||v_hat - s_hat||^2.
+// Padding points get b = -1e30 and no ones: every term of theirs is <= 0.
 __global__ void k_make_aext(int64_t n, int64_t n_pad, const double *__restrict__ qn64, const float *__restrict__ qerr,
                             const float *__restrict__ qnorm, const float *__restrict__ qmax, double gamma,
-                            uint16_t *__restrict__ Aext, uint16_t *__restrict__ Bext) {
+                            const double *__restrict__ nv64, uint16_t *__restrict__ Aext, uint16_t *__restrict__ Bext,
+                            uint16_t *__restrict__ Px) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_pad) return;
+    {
+        __align__(16) uint16_t prow[KEXT];
+        for (int i = 0; i < KEXT; ++i) prow[i] = 0;
+        if (r < n) {
+            prow[0] = prow[1] = prow[2] = bf16_bits(__float2bfloat16_rn(1.f));
+            split3(nv64[r] - qn64[r], false, prow + 3);
+        } else {
+            prow[3] = bf16_bits(__float2bfloat16_rn(PAD_A));
+        }
+        uint4 *pd = reinterpret_cast<uint4 *>(Px + r * KEXT);
+        const uint4 *ps = reinterpret_cast<const uint4 *>(prow);
+        pd[0] = ps[0];
+        pd[1] = ps[1];
+    }
     __align__(16) uint16_t row[KEXT];
     for (int i = 0; i < KEXT; ++i) row[i] = 0;
     const uint16_t one = bf16_bits(__float2bfloat16_rn(1.f));
@@ -543,6 +694,56 @@ __global__ void k_gather_rows(const uint16_t *__restrict__ Vq, const uint16_t *_
     }
 }
 
+// Members of the sets, each set padded to a multiple of 16 columns, as
+// B rows of the multi-set evaluation: Mq = 2 s_hat (copied from Vq2) and
+// Mx = [q q q | 1 1 1 | 0..], q = -||s_hat||^2.  Padding columns get a zero
+// row and Mx = [-1e30 | 0..], so their term is -1e30 for every real point.
+// One thread per 16 bytes of a row; the set of padded column p is found by
+// binary search in the padded offsets.  Members outside [0, n) are reported
+// as EINDEX and treated as padding.
+__global__ void k_gather_members(const uint16_t *__restrict__ Vq2, const double *__restrict__ qn64, int64_t n, int DP,
+                                 const int32_t *__restrict__ idx, const int64_t *__restrict__ off,
+                                 const int64_t *__restrict__ poff, int64_t l, int64_t ncols,
+                                 uint16_t *__restrict__ Mq, uint16_t *__restrict__ Mx, int *__restrict__ err) {
+    const int per_row = DP / 8 + 2;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ncols * per_row) return;
+    const int64_t p = e / per_row;
+    const int w = (int)(e % per_row);
+    int64_t lo = 0, hi = l;  // poff[lo] <= p < poff[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (poff[mid] <= p) lo = mid;
+        else hi = mid;
+    }
+    const int64_t r = p - poff[lo];
+    const int64_t mb = off[lo];
+    int64_t src = -1;
+    if (r < off[lo + 1] - mb) {
+        src = idx[mb + r];
+        if (src < 0 || src >= n) {
+            if (w == 0) atomicCAS(err, 0, (int)EBC_EINDEX);
+            src = -1;
+        }
+    }
+    if (w < DP / 8) {
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (src >= 0) val = reinterpret_cast<const uint4 *>(Vq2 + src * DP)[w];
+        reinterpret_cast<uint4 *>(Mq + p * DP)[w] = val;
+    } else {
+        __align__(16) uint16_t row[KEXT];
+        for (int i = 0; i < KEXT; ++i) row[i] = 0;
+        if (src >= 0) {
+            split3(-qn64[src], false, row);
+            row[3] = row[4] = row[5] = bf16_bits(__float2bfloat16_rn(1.f));
+        } else {
+            row[0] = bf16_bits(__float2bfloat16_rn(PAD_A));
+        }
+        const int x = w - DP / 8;
+        reinterpret_cast<uint4 *>(Mx + p * KEXT)[x] = reinterpret_cast<const uint4 *>(row)[x];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -600,8 +801,9 @@ double gamma_for(int DP) { return ((double)(DP + KEXT) / 4.0 + 4.0) * ldexp(1.0,
 bool tc_supported(const Ctx &c) { return c.d <= 128; }
 
 void tc_free(Ctx &c) {
-    void *ptrs[] = {c.tc.Vq, c.tc.Vq2, c.tc.Aext, c.tc.Bext, c.tc.Cq, c.tc.Cqx, c.tc.qn64, c.tc.qerr, c.tc.qnorm,
-                    c.tc.qmax};
+    void *ptrs[] = {c.tc.Vq,   c.tc.Vq2,   c.tc.Aext, c.tc.Bext, c.tc.Cq,   c.tc.Cqx,      c.tc.qn64,
+                    c.tc.qerr, c.tc.qnorm, c.tc.qmax, c.tc.Px,   c.tc.Mq,   c.tc.Mx,       c.tc.gset,
+                    c.tc.sets_aux};
     for (void *p : ptrs) pool_free(p, c.stream);
     c.tc = Ctx::Tc();
 }
@@ -615,7 +817,8 @@ cudaError_t tc_quantize(Ctx &c) {
     k_quantize<<<g, th, 0, c.stream>>>(c.V32, c.n, c.d, T.n_pad, T.DP, T.prec, T.Vq, T.Vq2, T.qn64, T.qerr, T.qnorm,
                                        reinterpret_cast<unsigned int *>(T.qmax), &c.st->err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_make_aext<<<g, th, 0, c.stream>>>(c.n, T.n_pad, T.qn64, T.qerr, T.qnorm, T.qmax, gamma_for(T.DP), T.Aext, T.Bext);
+    k_make_aext<<<g, th, 0, c.stream>>>(c.n, T.n_pad, T.qn64, T.qerr, T.qnorm, T.qmax, gamma_for(T.DP), c.nv64, T.Aext,
+                                        T.Bext, T.Px);
     return cudaGetLastError();
 }
 
@@ -636,6 +839,7 @@ cudaError_t tc_setup(Ctx &c, int prec) {
         if ((e = pool_alloc((void **)&T.qerr, rows * 4, c.stream, c.device)) != cudaSuccess) return e;
         if ((e = pool_alloc((void **)&T.qnorm, rows * 4, c.stream, c.device)) != cudaSuccess) return e;
         if ((e = pool_alloc((void **)&T.qmax, 2 * 4, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.Px, rows * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Cq, 0, rows * T.DP * 2, c.stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Cqx, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Bext, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
@@ -648,6 +852,7 @@ cudaError_t tc_setup(Ctx &c, int prec) {
     if (e == cudaSuccess) e = make_map(&T.tmAx_V, T.Aext, T.n_pad, KEXT, true, KEXT, BMS, CU_TENSOR_MAP_SWIZZLE_32B);
     if (e == cudaSuccess) e = make_map(&T.tmAx_C, T.Cqx, T.n_pad, KEXT, true, KEXT, BMS, CU_TENSOR_MAP_SWIZZLE_32B);
     if (e == cudaSuccess) e = make_map(&T.tmBx, T.Bext, T.n_pad, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (e == cudaSuccess) e = make_map(&T.tmPx, T.Px, T.n_pad, KEXT, true, KEXT, BMS, CU_TENSOR_MAP_SWIZZLE_32B);
     if (e != cudaSuccess) return e;
     return tc_quantize(c);
 }
@@ -713,6 +918,134 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
                                                       T.tmBx, a);
     *nchunks_out = a.nchunks;
     return cudaGetLastError();
+}
+
+// Multi-set evaluation on the tensor cores.  Host plan (from the offsets):
+// padded offsets (each set rounded up to 16 columns), chunks of whole sets
+// (at most 64 sets and about 2048 columns each) and the group table.  Work
+// units are (256 points, chunk); set partials [point unit][set] are reduced
+// in a fixed order by k_sets_finalize.  Sets are processed in batches whose
+// partials fit the scratch.
+cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_dev, const int64_t *off_host,
+                                int64_t l, double *out_f, int64_t *nlaunch) {
+    Ctx::Tc &T = c.tc;
+    *nlaunch = 0;
+    std::vector<int64_t> aux((size_t)l + 1);
+    aux[0] = 0;
+    for (int64_t j = 0; j < l; ++j) {
+        const int64_t sz = off_host[j + 1] - off_host[j];
+        aux[j + 1] = aux[j] + (sz + SET_GROUP - 1) / SET_GROUP * SET_GROUP;
+    }
+    const int64_t ncols = aux[l];
+    if (ncols > ((int64_t)1 << 30)) return cudaErrorInvalidValue;
+    const size_t chunk0 = aux.size();
+    int64_t sb = 0, cb = 0;
+    for (int64_t j = 0; j < l; ++j) {
+        const int64_t ps = aux[j + 1] - aux[j];
+        if (j > sb && (j - sb == SETS_PER_CHUNK || aux[j] - cb + ps > CHUNK_COLS)) {
+            aux.insert(aux.end(), {sb, j, cb, aux[j]});
+            sb = j;
+            cb = aux[j];
+        }
+    }
+    aux.insert(aux.end(), {sb, l, cb, ncols});
+    const int64_t nch = (int64_t)(aux.size() - chunk0) / 4;
+    std::vector<int> gset((size_t)(ncols / SET_GROUP));
+    for (int64_t k = 0; k < nch; ++k) {
+        const int64_t *rec = aux.data() + chunk0 + 4 * k;
+        for (int64_t j = rec[0]; j < rec[1]; ++j) {
+            const int64_t g0 = aux[j] / SET_GROUP, g1 = aux[j + 1] / SET_GROUP;
+            for (int64_t g = g0; g < g1; ++g) gset[g] = (int)(2 * (j - rec[0]) + (g == g1 - 1 ? 1 : 0));
+        }
+    }
+    // scratch
+    const int64_t rows_need = std::max<int64_t>((ncols + BN - 1) / BN * BN, BN);
+    cudaError_t e;
+    if (T.mcap < rows_need) {
+        pool_free(T.Mq, c.stream);
+        pool_free(T.Mx, c.stream);
+        pool_free(T.gset, c.stream);
+        T.Mq = T.Mx = nullptr;
+        T.gset = nullptr;
+        T.mcap = 0;
+        const int64_t cap = std::max<int64_t>(rows_need, T.n_pad);
+        if ((e = pool_alloc((void **)&T.Mq, (size_t)cap * T.DP * 2, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.Mx, (size_t)cap * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&T.gset, (size_t)cap / SET_GROUP * 4, c.stream, c.device)) != cudaSuccess) return e;
+        T.mcap = cap;
+    }
+    if (T.aux_cap < (int64_t)aux.size()) {
+        pool_free(T.sets_aux, c.stream);
+        T.sets_aux = nullptr;
+        T.aux_cap = 0;
+        const int64_t cap = std::max<int64_t>((int64_t)aux.size(), 4096);
+        if ((e = pool_alloc((void **)&T.sets_aux, (size_t)cap * 8, c.stream, c.device)) != cudaSuccess) return e;
+        T.aux_cap = cap;
+    }
+    // pageable sources: the copies return once the data is staged
+    if ((e = cudaMemcpyAsync(T.sets_aux, aux.data(), aux.size() * 8, cudaMemcpyHostToDevice, c.stream)) != cudaSuccess)
+        return e;
+    if (!gset.empty() &&
+        (e = cudaMemcpyAsync(T.gset, gset.data(), gset.size() * 4, cudaMemcpyHostToDevice, c.stream)) != cudaSuccess)
+        return e;
+    const bool bf = T.prec == EBC_BF16;
+    CUtensorMap tmM, tmMx;
+    if ((e = make_map(&tmM, T.Mq, T.mcap, T.DP, bf, KATOM, BN, CU_TENSOR_MAP_SWIZZLE_128B)) != cudaSuccess) return e;
+    if ((e = make_map(&tmMx, T.Mx, T.mcap, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess) return e;
+    if (ncols > 0) {
+        const int64_t tot = ncols * (T.DP / 8 + 2);
+        k_gather_members<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(
+            T.Vq2, T.qn64, c.n, T.DP, idx, off_dev, T.sets_aux, l, ncols, T.Mq, T.Mx, &c.st->err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        *nlaunch += 1;
+    }
+    int na = 0, ns = 0;
+    pick_pipeline(T.DP, &na, &ns);
+    if (ns == 0) return cudaErrorInvalidConfiguration;
+    const SmemLayout L = smem_layout(T.DP, ns, na);
+    static int configured_smem = 0;
+    if (configured_smem < (int)L.total) {
+        if ((e = cudaFuncSetAttribute(k_sets_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total)) !=
+            cudaSuccess)
+            return e;
+        configured_smem = (int)L.total;
+    }
+    const int npu = (int)(T.n_pad / BM);
+    const int64_t max_sets = c.set_part_cap / npu;
+    if (max_sets < SETS_PER_CHUNK) return cudaErrorMemoryAllocation;
+    const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
+    for (int64_t k0 = 0; k0 < nch;) {
+        const int64_t j0 = aux[chunk0 + 4 * k0];
+        int64_t k1 = k0 + 1;
+        while (k1 < nch && aux[chunk0 + 4 * k1 + 1] - j0 <= max_sets) ++k1;
+        const int64_t lb = aux[chunk0 + 4 * (k1 - 1) + 1] - j0;
+        TcArgs a{};
+        a.m = 0;
+        a.n_vtiles = 0;
+        a.n_ctiles = npu;
+        a.nchunks = (int)(k1 - k0);
+        a.vt_per_chunk = 0;
+        a.DP = T.DP;
+        a.nstages = ns;
+        a.na = na;
+        a.idesc = tc::idesc_f16(bf ? 1u : 0u, BMS, BN);
+        a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
+        a.partial = c.set_part;
+        a.err = &c.st->err;
+        a.chunks = T.sets_aux + chunk0 + 4 * k0;
+        a.gset = T.gset;
+        a.lb = lb;
+        a.j0 = j0;
+        const int64_t units = (int64_t)npu * a.nchunks;
+        if (units > INT32_MAX) return cudaErrorInvalidValue;
+        const int grid = (int)std::min<int64_t>(units, G);
+        k_sets_tc<<<grid, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_sets_finalize(c, npu, lb, j0, l, out_f)) != cudaSuccess) return e;
+        *nlaunch += 2;
+        k0 = k1;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace ebc
