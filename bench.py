@@ -245,6 +245,7 @@ def run_serve(args):
         b.poll(t)
     b = ebc.Batch(max_slots=args.slots, budget_bytes=int(args.budget_gb * (1 << 30)), refine_k=args.refine_k)
     b.set_large(args.large_threshold, args.large_ctas, args.max_large)
+    b.set_lazy(not args.no_lazy)
     pending = {}
     lat = {}
     nxt = 0
@@ -290,6 +291,7 @@ def run_serve(args):
                                    f"{100 * args.large_frac:.0f}% large (n={args.large_n}, d=32), rest GMM instance mix",
                        "slots": args.slots, "budget_gb": args.budget_gb, "large_threshold": args.large_threshold,
                        "large_ctas": args.large_ctas, "max_large": args.max_large, "drain_s": args.drain,
+                       "greedy": "full rounds" if args.no_lazy else "lazy rounds (same picks)",
                        "host_generation_s": gen_s},
             "latency_ms": {"p50": pct(lat_ms, 50), "p90": pct(lat_ms, 90), "p99": pct(lat_ms, 99),
                            "max": float(lat_ms.max()) if lat_ms.size else None,
@@ -434,6 +436,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-lazy", action="store_true", help="regime: skip the lazy comparison; serve: full rounds")
     ap.add_argument("--fp32-rounds", type=int, default=3, help="rounds of the FP32 plain comparison")
     ap.add_argument("--ref-cands", type=int, default=64, help="reference arm: candidates per step")
     args = ap.parse_args()
@@ -580,6 +583,30 @@ def main():
         line["fp32_plain"] = {"value": v32, "unit": UNIT, "rounds": R,
                               "picks_match": bool((i32 == idx_bf[:R]).all()),
                               "tc_over_fp32": value / world / v32}
+
+    # lazy Greedy on the same workload (same picks, fewer bulk candidates) --
+    if args.prec != "fp32" and not args.no_lazy and rank == 0:
+        lz = ebc.Instance(Vd, precision=args.prec, refine_k=args.refine_k, stream=stream, lazy=True)
+        lz.greedy(k)  # warm (graph capture)
+        torch.cuda.synchronize()
+        lev = []
+        for s in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lz.reload(Vd)
+            il, fl = lz.greedy(k)
+            b.record(stream)
+            lev.append((a, b))
+        torch.cuda.synchronize()
+        lms = sum(a.elapsed_time(b) for a, b in lev) / args.steps
+        lst = lz.stats()
+        lz.close()
+        line["lazy"] = {"ms_per_step": lms, "speedup_vs_full": (t_max_ms / args.steps) / lms,
+                        "bulk_candidates_per_step": lst["bulk_candidates"],
+                        "full_candidates_per_step": sum(n - t for t in range(k)),
+                        "picks_match_full": bool((il.cpu().numpy() == idx_bf).all()),
+                        "f_match_full": bool((fl.cpu().numpy() == f_bf).all())}
 
     # end-to-end through the C ABI with host buffers ----------------------
     if not args.no_e2e:

@@ -73,6 +73,9 @@ typedef struct {
     int64_t exact_evaluations;    /* candidates whose exact FP64 gain was computed */
     int32_t prec;                 /* current ebc_prec */
     int32_t refine_k;             /* current K */
+    int64_t bulk_candidates;      /* lazy Greedy: candidates given a bulk bound, summed over rounds */
+    int32_t lazy;                 /* 1 when lazy Greedy is on (ebc_set_lazy) */
+    int32_t reserved;
 } ebc_stats;
 
 /* Library version, (major << 16) | minor. */
@@ -166,6 +169,23 @@ ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);
 /* Cap the CTAs of the persistent bulk kernel (0 = one per SM).  Leaves SMs
  * free for other work on the GPU, e.g. small requests in a serving batch. */
 ebc_status ebc_set_max_ctas(ebc_t h, int32_t max_ctas);
+
+/*
+ * Lazy Greedy (Minoux's lazy evaluation of the Greedy of Sec. 3): the handle
+ * keeps, for every candidate, an upper bound of its marginal gain from the
+ * round it was last bounded; by diminishing returns (Def. 3) such a bound
+ * stays valid as S grows.  Each round first certifies a lower bound of the
+ * best gain from the candidates with the largest stale bounds, then bounds
+ * only the candidates whose stale bound reaches it on the tensor cores, and
+ * certifies the pick among them as ebc_greedy does.  Picks and f values are
+ * the same as without it (the exact argmax, same tie rule, same exact gain);
+ * only the work per round changes.  Applies at the tensor-core precisions;
+ * at EBC_FP32 every round evaluates all candidates.  on = 1 enables, 0
+ * disables; the bounds restart from the current state when enabled, and
+ * ebc_reset / ebc_reload restart them.  Allocates 12 bytes per point on first
+ * use.
+ */
+ebc_status ebc_set_lazy(ebc_t h, int32_t on);
 
 /* Replay Greedy rounds from a captured CUDA graph (1, the default) or issue
  * every kernel directly (0).  Graph replay needs a non-NULL stream and is
@@ -298,6 +318,10 @@ ebc_status ebc_batch_run(ebc_batch_t b);
  * Admission goes in arrival order, but a request that cannot start yet
  * (memory or this limit) does not hold back later requests that can. */
 ebc_status ebc_batch_set_large(ebc_batch_t b, int64_t large_n, int32_t max_ctas, int32_t max_active);
+
+/* Lazy Greedy (ebc_set_lazy) for the instances admitted from now on
+ * (on = 1) or not (0, the default).  Results are unchanged. */
+ebc_status ebc_batch_set_lazy(ebc_batch_t b, int32_t on);
 
 ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out);
 const char *ebc_batch_last_error(ebc_batch_t b);

@@ -45,6 +45,7 @@ struct ebc_ctx {
     int64_t round_launches = 0;  // kernels in one round
     int prec_at_capture = -1;
     int ctas_at_capture = -1;
+    int lazy_at_capture = -1;
     bool graphs = true;          // replay rounds from a graph when possible
     bool attrs_ready = false;    // one direct round has run (kernel attributes are set)
 };
@@ -108,7 +109,7 @@ cudaError_t dalloc(T **p, size_t count, const ebc::Ctx &c) {
 void free_all(ebc::Ctx &c, ebc_ctx *h) {
     ebc::tc_free(c);
     void *ptrs[] = {c.V32, c.nv64, c.nv32, c.m64, c.sel, c.st, c.partial, c.gain_up, c.blk_idx, c.blk_val, c.top_idx, c.top_val,
-                    c.esc_idx, c.esc_exact, c.cand_buf, c.set_part,
+                    c.esc_idx, c.esc_exact, c.cand_buf, c.set_part, c.ub64, c.lazy_idx,
                     c.cert.top_lo, c.cert.top_hi, c.cert.esc_lo, c.cert.esc_hi, c.cert.part_lo, c.cert.part_hi,
                     c.cert.ctd_idx, c.cert.ctd_part, c.cert.ctd_exact,
                     h ? h->d_scalar : nullptr, h ? h->d_bad : nullptr};
@@ -516,6 +517,20 @@ ebc_status ebc_get_stats(ebc_t h, ebc_stats *out) {
     out->exact_evaluations = s.exact_evals;
     out->prec = (int32_t)c.prec;
     out->refine_k = c.refine_k;
+    out->bulk_candidates = s.bulk_cands;
+    out->lazy = c.lazy ? 1 : 0;
+    return EBC_OK;
+}
+
+ebc_status ebc_set_lazy(ebc_t h, int32_t on) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (on && !c.ub64) {
+        CK(h, dalloc(&c.ub64, c.n, c));
+        CK(h, dalloc(&c.lazy_idx, c.n, c));
+    }
+    if (on && !c.lazy) CK(h, ebc::launch_lazy_init(c));  // bounds restart from the current state
+    c.lazy = on != 0;
     return EBC_OK;
 }
 
@@ -665,17 +680,37 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
     const int K = c.refine_k;
     const double eta = bulk_eta(c);
     int nch = h->nch;
-    if (c.prec == EBC_FP32) {
-        CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, nullptr, c.n, true, h->ch, h->nch); }));
-    } else {
+    ebc::Ctx::Sel &S = c.cert;
+    const bool lazy = c.lazy && c.prec != EBC_FP32;
+    if (lazy) {
+        // lazy round (k_lazy.cu): certified lower bound from the largest stale
+        // bounds, then bulk bounds only for candidates whose stale bound reaches it
+        const int KP = ebc::kMaxRefineK;
+        CK(h, launch(h, -1, 2, [&] { return ebc::launch_lazy_preselect(c, h->nblk, KP); }));
+        CK(h, launch(h, PK_REFINE, 1, [&] {
+               return ebc::launch_bounds_list(c, c.top_idx, &c.st->top_count, KP, S.part_lo, S.part_hi, S.chunk,
+                                              S.nchunks);
+           }));
+        CK(h, launch(h, -1, 3, [&] {
+               cudaError_t e = ebc::launch_fold_bounds(c, S.part_lo, S.part_hi, &c.st->top_count, KP, S.top_lo, S.top_hi);
+               if (e == cudaSuccess) e = ebc::launch_lazy_threshold(c);
+               return e != cudaSuccess ? e : ebc::launch_lazy_build(c);
+           }));
         CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, true); }));
-        CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_tc(c, nullptr, c.n, true, &nch); }));
+        CK(h, launch(h, PK_BULK, 2, [&] { return ebc::launch_gains_tc_list(c, c.lazy_idx, &c.st->list_m, c.n); }));
+        CK(h, launch(h, -1, 1, [&] { return ebc::launch_lazy_select(c, eta, h->nblk); }));
+    } else {
+        if (c.prec == EBC_FP32) {
+            CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, nullptr, c.n, true, h->ch, h->nch); }));
+        } else {
+            CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, true); }));
+            CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_tc(c, nullptr, c.n, true, &nch); }));
+        }
+        h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
+        CK(h, launch(h, -1, 1, [&] { return ebc::launch_reduce_select(c, c.n, nch, nullptr, true, nullptr, h->nblk); }));
     }
-    h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
-    CK(h, launch(h, -1, 1, [&] { return ebc::launch_reduce_select(c, c.n, nch, nullptr, true, nullptr, h->nblk); }));
     CK(h, launch(h, -1, 1, [&] { return ebc::launch_merge_top(c, h->nblk, K, eta); }));
     // level 1: bounds for the top list, then for the escalated candidates
-    ebc::Ctx::Sel &S = c.cert;
     const int64_t esc_off = (int64_t)ebc::kMaxRefineK * S.nchunks;
     CK(h, launch(h, PK_REFINE, 1, [&] {
            return ebc::launch_bounds_list(c, c.top_idx, &c.st->top_count, K, S.part_lo, S.part_hi, S.chunk, S.nchunks);
@@ -683,7 +718,8 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
     CK(h, launch(h, -1, 3, [&] {
            cudaError_t e = ebc::launch_fold_bounds(c, S.part_lo, S.part_hi, &c.st->top_count, K, S.top_lo, S.top_hi);
            if (e == cudaSuccess) e = ebc::launch_decide_top(c, eta);
-           return e != cudaSuccess ? e : ebc::launch_collect_escalation(c, eta);
+           if (e != cudaSuccess) return e;
+           return lazy ? ebc::launch_lazy_collect(c, eta) : ebc::launch_collect_escalation(c, eta);
        }));
     CK(h, launch(h, PK_REFINE, 2, [&] {
            cudaError_t e = ebc::launch_bounds_list(c, c.esc_idx, &c.st->esc_count, S.cap, S.part_lo + esc_off,
@@ -751,6 +787,7 @@ static ebc_status capture_round(ebc_t h) {
     h->round_stream = c.stream;
     h->prec_at_capture = (int)c.prec;
     h->ctas_at_capture = c.max_ctas;
+    h->lazy_at_capture = c.lazy ? 1 : 0;
     return EBC_OK;
 }
 
@@ -769,7 +806,7 @@ ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) {
     // after one direct round has set every kernel attribute
     const bool use_graph = h->graphs && !h->prof.on && c.stream != nullptr;
     if (use_graph && (!h->round_exec || h->round_stream != c.stream || h->prec_at_capture != (int)c.prec ||
-                      h->ctas_at_capture != c.max_ctas)) {
+                      h->ctas_at_capture != c.max_ctas || h->lazy_at_capture != (c.lazy ? 1 : 0))) {
         if (!h->attrs_ready) {
             ebc_status s = greedy_round(h, ib, fb);
             if (s) return s;

@@ -55,6 +55,7 @@ struct ebc_batch_ctx {
     int32_t refine_k = 8;
     int64_t large_n = 0;      // instances with n >= large_n get at most large_ctas CTAs per kernel
     int32_t large_ctas = 0;
+    int32_t lazy = 0;         // lazy Greedy for admitted instances (ebc_batch_set_lazy)
     int32_t max_large = 0;    // at most this many large instances at once (0 = no limit)
     int64_t budget = 0, used = 0, peak = 0;
     int64_t next_ticket = 1, submitted = 0, completed = 0, rounds = 0;
@@ -162,6 +163,7 @@ void admit(ebc_batch_t b) {
         if (st == EBC_OK && (r.prec != EBC_FP32 || b->refine_k != 8))
             st = ebc::set_precision_handle(h, r.prec, b->refine_k, false);
         if (st == EBC_OK && large && b->large_ctas > 0) st = ebc_set_max_ctas(h, b->large_ctas);
+        if (st == EBC_OK && b->lazy) st = ebc_set_lazy(h, 1);
         if (st != EBC_OK) {
             ebc_batch_ctx::Result res;
             res.status = st;
@@ -338,6 +340,12 @@ ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out) {
     out->bytes_in_use = b->used;
     out->bytes_peak = b->peak;
     out->rounds_issued = b->rounds;
+    return EBC_OK;
+}
+
+ebc_status ebc_batch_set_lazy(ebc_batch_t b, int32_t on) {
+    if (!b) return EBC_EINVAL;
+    b->lazy = on != 0;
     return EBC_OK;
 }
 

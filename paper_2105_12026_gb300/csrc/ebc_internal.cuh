@@ -41,7 +41,37 @@ struct DevState {
     int zero_scan;          // 1 when every remaining gain is exactly 0
     int ctd_count;          // contenders needing the exact FP64 gain this round
     double best_lo;         // largest certified lower bound of the round
+    // lazy Greedy
+    double lazy_thr;        // certified lower bound of the round's best gain (pre-selection)
+    int list_m;             // candidates in this round's list (lazy mode)
+    int list_nch;           // V chunks the bulk kernel used for that list
+    long long bulk_cands;   // candidates given a bulk bound, summed over rounds
 };
+
+// V chunking of the bulk gains kernel for m candidates: the chunk count
+// (1..16, bounded by the partial buffer) that best balances
+// (candidate tiles x chunks) units over G persistent CTAs.  Used on the host
+// and, for lists whose length lives on the device, inside the kernels.
+__host__ __device__ inline int pick_chunks(int64_t m, int n_vtiles, int G, int64_t partial_cap, int *vt_per_chunk) {
+    const int64_t n_ctiles = (m + 255) / 256;
+    const int64_t cap = partial_cap / (m > 0 ? m : 1);
+    int best = 1;
+    double best_eff = 0.0;
+    const int64_t lim = lmin(16, lmin(cap, n_vtiles));
+    for (int nch = 1; nch <= lim; ++nch) {
+        const int64_t units = n_ctiles * nch;
+        const int64_t per = (units + G - 1) / G;
+        double eff = (double)units / (double)(per * lmin(G, units)) * (units < G ? (double)units / G : 1.0);
+        eff *= 1.0 - 0.003 * nch;  // per-unit candidate-tile load
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = nch;
+        }
+    }
+    const int vpc = (n_vtiles + best - 1) / best;
+    *vt_per_chunk = vpc;
+    return (n_vtiles + vpc - 1) / vpc;
+}
 
 // Scratch / resident buffers of one handle.
 struct Ctx {
@@ -109,6 +139,11 @@ struct Ctx {
     int *esc_idx = nullptr;     // [n] escalation list
     double *esc_exact = nullptr;// [n]
     int *cand_buf = nullptr;    // [n] gathered candidate list for ebc_gains
+    // lazy Greedy: stale upper bounds of every candidate's gain (gains never
+    // increase as S grows) and the round's candidate list
+    bool lazy = false;
+    double *ub64 = nullptr;     // [n]
+    int *lazy_idx = nullptr;    // [n]
     double *set_part = nullptr; // eval_sets partials
     int64_t set_part_cap = 0;
     int32_t h_err_store[4] = {0, 0, 0, 0};
@@ -149,6 +184,13 @@ cudaError_t launch_reset_state(Ctx &c);
 cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, int64_t chunk, int nchunks);
 cudaError_t launch_reduce_select(Ctx &c, int64_t m, int nchunks, const int *cand, bool greedy,
                                  double *out_gain, int nblk);
+// lazy Greedy (k_lazy.cu)
+cudaError_t launch_lazy_preselect(Ctx &c, int nblk, int K);   // top-K of ub64 among unselected -> top list
+cudaError_t launch_lazy_threshold(Ctx &c);                     // st->lazy_thr = max folded lo of the top list
+cudaError_t launch_lazy_build(Ctx &c);                         // lazy_idx = {c : ub64[c] >= lazy_thr}, st->list_m
+cudaError_t launch_lazy_select(Ctx &c, double eta, int nblk);  // list sums, ub64 update, per-block tops
+cudaError_t launch_lazy_collect(Ctx &c, double eta);           // escalation over the list
+cudaError_t launch_lazy_init(Ctx &c);                          // ub64 = +inf
 cudaError_t launch_merge_top(Ctx &c, int nblk, int K, double eta);
 // Exact FP64 gains (out_hi == nullptr) or rigorous FP32 [lo, hi] bounds of
 // the gains (out holds lo, out_hi hi) of a device list, as chunk partials.
@@ -186,6 +228,8 @@ cudaError_t tc_quantize(Ctx &c);                 // (re)quantise V into Vq
 cudaError_t launch_prep_tc(Ctx &c, bool upper);  // a_v for every point (+ max m_v)
 // bulk gains on tensor cores; returns the number of V chunks used in *nchunks
 cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int *nchunks);
+// bulk gains of the list (cand, *m_dev) whose length is on the device (m_cap bounds it)
+cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int64_t m_cap);
 // multi-set evaluation on tensor cores; off_host is a host copy of the
 // (validated) offsets; returns cudaErrorMemoryAllocation if scratch is short
 cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_dev, const int64_t *off_host,

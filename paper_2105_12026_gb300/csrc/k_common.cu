@@ -114,36 +114,9 @@ cudaError_t launch_reset_state(Ctx &c) {
     int th = 256;
     int64_t bl = (c.n + th - 1) / th;
     k_reset<<<(unsigned)bl, th, 0, c.stream>>>(c.nv64, c.m64, c.sel, c.n, c.st);
-    return cudaGetLastError();
-}
-
-// Extract the `cnt` best entries of the thread-strided range [beg, end) of
-// (val[], idx[]) in order; entries with value < 0 are never taken.
-__device__ void block_topk(const double *__restrict__ val, const int *__restrict__ idx, int64_t beg, int64_t end,
-                           int cnt, double *out_v, int *out_i) {
-    double lastv = DBL_MAX;
-    int lasti = -1;
-    for (int r = 0; r < cnt; ++r) {
-        double bv = -DBL_MAX;
-        int bi = INT_MAX;
-        for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
-            double x = val[j];
-            int xi = idx ? idx[j] : (int)j;
-            if (x < 0.0) continue;
-            if (!better(lastv, lasti, x, xi)) continue;  // already taken
-            if (better(x, xi, bv, bi)) {
-                bv = x;
-                bi = xi;
-            }
-        }
-        block_best(bv, bi);
-        if (threadIdx.x == 0) {
-            out_v[r] = bi == INT_MAX ? -1.0 : bv;
-            out_i[r] = bi == INT_MAX ? -1 : bi;
-        }
-        lastv = bv;
-        lasti = bi;
-    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && c.ub64) e = launch_lazy_init(c);
+    return e;
 }
 
 // ---------------------------------------------------------------------------

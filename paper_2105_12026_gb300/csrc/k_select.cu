@@ -140,7 +140,7 @@ __global__ void k_commit_pick(const double *__restrict__ ctd_part, int nchunks, 
                               const int *__restrict__ ctd_idx, double *__restrict__ ctd_exact,
                               const double *__restrict__ esc_exact, const int *__restrict__ esc_idx, int cap,
                               uint8_t *__restrict__ sel, int64_t n, int32_t *__restrict__ out_idx,
-                              double *__restrict__ out_f, DevState *st) {
+                              double *__restrict__ out_f, double *__restrict__ ub, DevState *st) {
     const int nc = st->ctd_count;
     const int esc_cnt = st->need_esc ? st->esc_count : 0;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -185,6 +185,7 @@ __global__ void k_commit_pick(const double *__restrict__ ctd_part, int nchunks, 
         }
         const int r = st->round;
         sel[bi] = 1;
+        if (ub) ub[bi] = -1.0;  // lazy Greedy: selected candidates leave every list
         st->f += bv;
         st->pick = bi;
         st->pick_gain = bv;
@@ -205,7 +206,7 @@ __global__ void k_commit_pick(const double *__restrict__ ctd_part, int nchunks, 
 cudaError_t launch_commit_pick(Ctx &c, int32_t *out_idx, double *out_f) {
     k_commit_pick<<<1, 256, 0, c.stream>>>(c.cert.ctd_part, c.cert.nchunks, 1.0 / (double)c.n, c.cert.ctd_idx,
                                            c.cert.ctd_exact, c.esc_exact, c.esc_idx, c.cert.cap, c.sel, c.n,
-                                           out_idx, out_f, c.st);
+                                           out_idx, out_f, c.lazy ? c.ub64 : nullptr, c.st);
     return cudaGetLastError();
 }
 

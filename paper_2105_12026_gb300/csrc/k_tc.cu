@@ -55,6 +55,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "ebc_internal.cuh"
@@ -93,6 +95,11 @@ struct TcArgs {
     const int *gset;        // per 16-column group: 2 * (set index within its chunk) + (last group of the set)
     int64_t lb;             // sets of this launch (partial row length)
     int64_t j0;             // first set of this launch
+    // gains of a list whose length is on the device (lazy Greedy)
+    const int *m_dev;       // list length, or nullptr when m and the plan above are final
+    int64_t partial_cap;    // doubles of the partial buffer
+    int G;                  // persistent CTAs
+    int *nch_out;           // chunk count used, for the reduction kernel
 };
 
 constexpr int MODE_GAINS = 0;
@@ -484,7 +491,17 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gains_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
-    tc_pipeline<MODE_GAINS>(&tmA, &tmAx, &tmB, &tmBx, args);
+    TcArgs a = args;
+    if (a.m_dev) {
+        // every CTA derives the same plan from the list length
+        a.m = *a.m_dev;
+        int vpc = 1;
+        a.nchunks = pick_chunks(a.m, a.n_vtiles, a.G, a.partial_cap, &vpc);
+        a.vt_per_chunk = vpc;
+        a.n_ctiles = (int)((a.m + BM - 1) / BM);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && a.nch_out) *a.nch_out = a.nchunks;
+    }
+    tc_pipeline<MODE_GAINS>(&tmA, &tmAx, &tmB, &tmBx, a);
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -675,9 +692,10 @@ __global__ void k_prep_tc(const double *__restrict__ m64, const double *__restri
 // Gather candidate rows of Vq and Aext into Cq / Cqx (16 bytes per thread);
 // invalid (sanitised, -1) candidates get zero rows.
 __global__ void k_gather_rows(const uint16_t *__restrict__ Vq, const uint16_t *__restrict__ Aext,
-                              const int *__restrict__ cand, int64_t m, int DP, uint16_t *__restrict__ Cq,
-                              uint16_t *__restrict__ Cqx) {
+                              const int *__restrict__ cand, int64_t m, const int *__restrict__ m_dev, int DP,
+                              uint16_t *__restrict__ Cq, uint16_t *__restrict__ Cqx) {
     const int per_row = DP / 8 + 2;  // uint4 per row: main part, then 2 for the extension
+    if (m_dev) m = lmin(m, *m_dev);
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= m * per_row) return;
     int64_t j = e / per_row;
@@ -794,6 +812,24 @@ void pick_pipeline(int DP, int *na, int *ns) {
             }
 }
 
+// Allow a kernel the largest dynamic shared memory any of its launches uses
+// (the per-CTA limit), once per (device, kernel): every launch then only
+// states its own size, whatever the order of launches with different sizes.
+cudaError_t allow_smem(const void *kernel, uint32_t bytes) {
+    if (bytes > (uint32_t)SMEM_LIMIT) return cudaErrorInvalidValue;
+    static std::mutex mu;
+    static std::vector<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &p : done)
+        if (p.first == dev && p.second == kernel) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    if (e == cudaSuccess) done.emplace_back(dev, kernel);
+    return e;
+}
+
 double gamma_for(int DP) { return ((double)(DP + KEXT) / 4.0 + 4.0) * ldexp(1.0, -22); }
 
 }  // namespace
@@ -872,39 +908,29 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     pick_pipeline(DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
     const SmemLayout L = smem_layout(DP, ns, na);
-    static int configured_smem = 0;
-    if (configured_smem < (int)L.total) {
-        cudaError_t e = cudaFuncSetAttribute(k_gains_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-        if (e != cudaSuccess) return e;
-        configured_smem = (int)L.total;
-    }
+    if (cudaError_t e = allow_smem((const void *)k_gains_tc, L.total); e != cudaSuccess) return e;
     if (cand) {
         int64_t tot = m * (DP / 8 + 2);
-        k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Vq, T.Aext, cand, m, DP, T.Cq, T.Cqx);
+        k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Vq, T.Aext, cand, m, nullptr, DP, T.Cq,
+                                                                            T.Cqx);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    TcArgs a;
+    TcArgs a{};
     a.m = m;
     a.n_vtiles = (int)(T.n_pad / BN);
     a.n_ctiles = (int)((m + BM - 1) / BM);
     // V chunks: balance the persistent grid (units = candidate tiles x chunks)
     const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
-    const int64_t cap = c.partial_cap / std::max<int64_t>(m, 1);
-    int best = 1;
-    double best_eff = 0.0;
-    for (int nch = 1; nch <= std::min<int64_t>(16, std::min<int64_t>(cap, a.n_vtiles)); ++nch) {
-        int64_t units = (int64_t)a.n_ctiles * nch;
-        int64_t per = (units + G - 1) / G;
-        double eff = (double)units / (double)(per * std::min<int64_t>(G, units)) * (units < G ? (double)units / G : 1.0);
-        eff *= 1.0 - 0.003 * nch;  // per-unit candidate-tile load
-        if (eff > best_eff + 1e-9) {
-            best_eff = eff;
-            best = nch;
-        }
-    }
-    a.vt_per_chunk = (a.n_vtiles + best - 1) / best;
-    a.nchunks = (a.n_vtiles + a.vt_per_chunk - 1) / a.vt_per_chunk;
+    a.nchunks = pick_chunks(m, a.n_vtiles, G, c.partial_cap, &a.vt_per_chunk);
+    a.m_dev = nullptr;
+    a.partial_cap = c.partial_cap;
+    a.G = G;
+    a.nch_out = nullptr;
+    a.chunks = nullptr;
+    a.gset = nullptr;
+    a.lb = 0;
+    a.j0 = 0;
     a.DP = DP;
     a.nstages = ns;
     a.na = na;
@@ -917,6 +943,45 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     k_gains_tc<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V, T.tmB_V,
                                                       T.tmBx, a);
     *nchunks_out = a.nchunks;
+    return cudaGetLastError();
+}
+
+// Bulk upper bounds of a candidate list whose length is on the device (the
+// lazy Greedy round): rows gathered for at most m_cap entries, the plan
+// (chunks) derived inside the kernel, the chunk count left in
+// st->list_nch for the reduction.
+cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int64_t m_cap) {
+    Ctx::Tc &T = c.tc;
+    const int DP = T.DP;
+    int na = 0, ns = 0;
+    pick_pipeline(DP, &na, &ns);
+    if (ns == 0) return cudaErrorInvalidConfiguration;
+    const SmemLayout L = smem_layout(DP, ns, na);
+    if (cudaError_t e = allow_smem((const void *)k_gains_tc, L.total); e != cudaSuccess) return e;
+    const int64_t tot = m_cap * (DP / 8 + 2);
+    k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Vq, T.Aext, cand, m_cap, m_dev, DP, T.Cq,
+                                                                        T.Cqx);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
+    TcArgs a{};
+    a.m = m_cap;
+    a.n_vtiles = (int)(T.n_pad / BN);
+    a.n_ctiles = 0;
+    a.nchunks = 1;
+    a.vt_per_chunk = a.n_vtiles;
+    a.DP = DP;
+    a.nstages = ns;
+    a.na = na;
+    a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, BN);
+    a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
+    a.partial = c.partial;
+    a.err = &c.st->err;
+    a.m_dev = m_dev;
+    a.partial_cap = c.partial_cap;
+    a.G = G;
+    a.nch_out = &c.st->list_nch;
+    k_gains_tc<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
     return cudaGetLastError();
 }
 
@@ -1003,13 +1068,7 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_d
     pick_pipeline(T.DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
     const SmemLayout L = smem_layout(T.DP, ns, na);
-    static int configured_smem = 0;
-    if (configured_smem < (int)L.total) {
-        if ((e = cudaFuncSetAttribute(k_sets_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total)) !=
-            cudaSuccess)
-            return e;
-        configured_smem = (int)L.total;
-    }
+    if ((e = allow_smem((const void *)k_sets_tc, L.total)) != cudaSuccess) return e;
     const int npu = (int)(T.n_pad / BM);
     const int64_t max_sets = c.set_part_cap / npu;
     if (max_sets < SETS_PER_CHUNK) return cudaErrorMemoryAllocation;

@@ -36,7 +36,8 @@ class ebc_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int64), ("certified_rounds", ctypes.c_int64),
                 ("escalated_rounds", ctypes.c_int64), ("escalated_candidates", ctypes.c_int64),
                 ("max_raw_rel_err", ctypes.c_double), ("exact_evaluations", ctypes.c_int64),
-                ("prec", ctypes.c_int32), ("refine_k", ctypes.c_int32)]
+                ("prec", ctypes.c_int32), ("refine_k", ctypes.c_int32), ("bulk_candidates", ctypes.c_int64),
+                ("lazy", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ebc_profile(ctypes.Structure):
@@ -73,8 +74,10 @@ _SIGS = {
     "ebc_greedy": [_P, _I32, _P, _P],
     "ebc_greedy_host": [_P, _I32, _P, _P],
     "ebc_set_graphs": [_P, _I32],
+    "ebc_set_lazy": [_P, _I32],
     "ebc_set_max_ctas": [_P, _I32],
     "ebc_batch_set_large": [_P, _I64, _I32, _I32],
+    "ebc_batch_set_lazy": [_P, _I32],
     "ebc_reset": [_P],
     "ebc_sync": [_P],
     "ebc_get_stats": [_P, ctypes.POINTER(ebc_stats)],
@@ -222,6 +225,10 @@ def ebc_set_graphs(h: int, on: bool) -> None:
     _raise(h, load().ebc_set_graphs(_P(h), int(bool(on))))
 
 
+def ebc_set_lazy(h: int, on: bool) -> None:
+    _raise(h, load().ebc_set_lazy(_P(h), int(bool(on))))
+
+
 def ebc_greedy_host(h: int, k: int):
     idx = np.zeros(k, dtype=np.int32)
     f = np.zeros(k, dtype=np.float64)
@@ -271,7 +278,7 @@ def ebc_last_error(h: int | None) -> str:
 class Instance:
     """One resident ground set.  ``V`` is an (n, d) float32 torch tensor or numpy array."""
 
-    def __init__(self, V, precision: str = "fp32", refine_k: int = 8, stream=None):
+    def __init__(self, V, precision: str = "fp32", refine_k: int = 8, stream=None, lazy: bool = False):
         import torch
         self._keep = None
         if isinstance(V, np.ndarray):
@@ -287,6 +294,8 @@ class Instance:
         self.precision = precision
         if precision != "fp32" or refine_k != 8:
             ebc_set_precision(self.h, PRECISIONS[precision], refine_k)
+        if lazy:
+            ebc_set_lazy(self.h, True)
 
     def close(self):
         if getattr(self, "h", None):
@@ -304,6 +313,9 @@ class Instance:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_lazy(self, on: bool = True):
+        ebc_set_lazy(self.h, on)
 
     def set_precision(self, precision: str, refine_k: int = 8):
         ebc_set_precision(self.h, PRECISIONS[precision], refine_k)
@@ -416,6 +428,9 @@ class Batch:
 
     def set_large(self, large_n: int, max_ctas: int, max_active: int = 0):
         self._err(load().ebc_batch_set_large(_P(self.h), int(large_n), int(max_ctas), int(max_active)))
+
+    def set_lazy(self, on: bool = True):
+        self._err(load().ebc_batch_set_lazy(_P(self.h), int(bool(on))))
 
     def step(self):
         a, q = _I32(), _I32()
