@@ -229,6 +229,8 @@ def run_mix(args):
 def run_serve(args):
     """Poisson arrivals through the batch runtime (continuous batching at round
     granularity); latency = completion - arrival, queueing included."""
+    # many slot streams: let each have its own hardware queue (read at context creation)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
 
     from paper_2105_12026_gb300 import ebc, synth
@@ -245,7 +247,7 @@ def run_serve(args):
         b.poll(t)
     b = ebc.Batch(max_slots=args.slots, budget_bytes=int(args.budget_gb * (1 << 30)), refine_k=args.refine_k)
     b.set_large(args.large_threshold, args.large_ctas, args.max_large)
-    b.set_lazy(not args.no_lazy)
+    b.set_lazy(not args.no_lazy, args.lazy_min_n)
     pending = {}
     lat = {}
     nxt = 0
@@ -291,7 +293,8 @@ def run_serve(args):
                                    f"{100 * args.large_frac:.0f}% large (n={args.large_n}, d=32), rest GMM instance mix",
                        "slots": args.slots, "budget_gb": args.budget_gb, "large_threshold": args.large_threshold,
                        "large_ctas": args.large_ctas, "max_large": args.max_large, "drain_s": args.drain,
-                       "greedy": "full rounds" if args.no_lazy else "lazy rounds (same picks)",
+                       "greedy": "full rounds" if args.no_lazy else f"lazy rounds (same picks) for n >= {args.lazy_min_n}",
+                       "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                        "host_generation_s": gen_s},
             "latency_ms": {"p50": pct(lat_ms, 50), "p90": pct(lat_ms, 90), "p99": pct(lat_ms, 99),
                            "max": float(lat_ms.max()) if lat_ms.size else None,
@@ -437,6 +440,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lazy", action="store_true", help="regime: skip the lazy comparison; serve: full rounds")
+    ap.add_argument("--lazy-min-n", type=int, default=100_000, help="serve: lazy rounds from this n")
     ap.add_argument("--fp32-rounds", type=int, default=3, help="rounds of the FP32 plain comparison")
     ap.add_argument("--ref-cands", type=int, default=64, help="reference arm: candidates per step")
     args = ap.parse_args()

@@ -299,8 +299,14 @@ ebc_status ebc_batch_create(int32_t max_slots, int64_t device_budget_bytes, int3
 ebc_status ebc_batch_submit(ebc_batch_t b, const float *V, int64_t n, int32_t d, int32_t k, ebc_prec prec,
                             int64_t *ticket);
 
-/* Reap finished instances, admit queued ones, issue one round for every
- * active instance.  Asynchronous; reports active and queued counts. */
+/* (Each slot has its own streams; a process serving many instances does
+ * well to set CUDA_DEVICE_MAX_CONNECTIONS=32 before its first CUDA call so
+ * that the streams do not share a few hardware queues.)
+ * Reap finished instances, admit queued ones, issue one round for every
+ * active instance that has at most one round still running (each
+ * instance's stream is kept at most two rounds deep, so short requests are
+ * not queued behind hundreds of rounds of a long one).  Asynchronous;
+ * reports active and queued counts. */
 ebc_status ebc_batch_step(ebc_batch_t b, int32_t *n_active, int32_t *n_queued);
 
 /* *done = 1 and the k picks / f values copied out (out arrays of capacity
@@ -319,9 +325,11 @@ ebc_status ebc_batch_run(ebc_batch_t b);
  * (memory or this limit) does not hold back later requests that can. */
 ebc_status ebc_batch_set_large(ebc_batch_t b, int64_t large_n, int32_t max_ctas, int32_t max_active);
 
-/* Lazy Greedy (ebc_set_lazy) for the instances admitted from now on
- * (on = 1) or not (0, the default).  Results are unchanged. */
-ebc_status ebc_batch_set_lazy(ebc_batch_t b, int32_t on);
+/* Lazy Greedy (ebc_set_lazy) for the instances admitted from now on whose
+ * n >= min_n (on = 1), or for none (on = 0, the default).  Results are
+ * unchanged; lazy rounds pay off for large n (their fixed per-round work
+ * outweighs the saving on small instances).  EINVAL if min_n < 0. */
+ebc_status ebc_batch_set_lazy(ebc_batch_t b, int32_t on, int64_t min_n);
 
 ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out);
 const char *ebc_batch_last_error(ebc_batch_t b);

@@ -39,6 +39,7 @@ struct ebc_batch_ctx {
         cudaStream_t stream_hi = nullptr;  // highest priority: ordinary instances
         cudaStream_t stream_lo = nullptr;  // lowest priority: large instances
         cudaEvent_t done = nullptr;
+        cudaEvent_t round_ev[2] = {nullptr, nullptr};  // ends of the last two issued rounds
         int64_t ticket = -1;
         int32_t k = 0, issued = 0, cap = 0;
         int32_t *d_idx = nullptr;
@@ -55,7 +56,8 @@ struct ebc_batch_ctx {
     int32_t refine_k = 8;
     int64_t large_n = 0;      // instances with n >= large_n get at most large_ctas CTAs per kernel
     int32_t large_ctas = 0;
-    int32_t lazy = 0;         // lazy Greedy for admitted instances (ebc_batch_set_lazy)
+    int32_t lazy = 0;         // lazy Greedy for admitted instances with n >= lazy_min_n (ebc_batch_set_lazy)
+    int64_t lazy_min_n = 0;
     int32_t max_large = 0;    // at most this many large instances at once (0 = no limit)
     int64_t budget = 0, used = 0, peak = 0;
     int64_t next_ticket = 1, submitted = 0, completed = 0, rounds = 0;
@@ -163,7 +165,7 @@ void admit(ebc_batch_t b) {
         if (st == EBC_OK && (r.prec != EBC_FP32 || b->refine_k != 8))
             st = ebc::set_precision_handle(h, r.prec, b->refine_k, false);
         if (st == EBC_OK && large && b->large_ctas > 0) st = ebc_set_max_ctas(h, b->large_ctas);
-        if (st == EBC_OK && b->lazy) st = ebc_set_lazy(h, 1);
+        if (st == EBC_OK && b->lazy && r.n >= b->lazy_min_n) st = ebc_set_lazy(h, 1);
         if (st != EBC_OK) {
             ebc_batch_ctx::Result res;
             res.status = st;
@@ -188,11 +190,17 @@ void admit(ebc_batch_t b) {
     }
 }
 
-// One Greedy round for every active instance; the last round also queues the
-// copy of the results and the completion event.
+// One Greedy round for every active instance that has at most one round in
+// flight; the last round also queues the copy of the results and the
+// completion event.  Keeping each stream at most two rounds deep bounds how
+// long any instance's kernels can wait behind another's in the device's
+// shared hardware queues (many streams map onto few): a request that needs
+// hundreds of rounds cannot place all of them ahead of later, shorter ones.
 ebc_status issue(ebc_batch_t b) {
     for (auto &s : b->slots) {
         if (!s.busy || s.finishing) continue;
+        if (s.issued >= 2 && cudaEventQuery(s.round_ev[s.issued & 1]) == cudaErrorNotReady) continue;
+        cudaGetLastError();
         ebc_status st = ebc_greedy(s.h, 1, s.d_idx + s.issued, s.d_f + s.issued);
         if (st != EBC_OK) {
             // record the failure as this instance's result
@@ -204,6 +212,7 @@ ebc_status issue(ebc_batch_t b) {
             release_slot(s);
             continue;
         }
+        cudaEventRecord(s.round_ev[s.issued & 1], s.stream);
         s.issued += 1;
         b->rounds += 1;
         if (s.issued == s.k) {
@@ -240,7 +249,9 @@ ebc_status ebc_batch_create(int32_t max_slots, int64_t device_budget_bytes, int3
     for (auto &s : b->slots) {
         if (cudaStreamCreateWithPriority(&s.stream_hi, cudaStreamNonBlocking, greatest) != cudaSuccess ||
             cudaStreamCreateWithPriority(&s.stream_lo, cudaStreamNonBlocking, least) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.round_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.round_ev[1], cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             ebc_batch_destroy(b);
             return EBC_ECUDA;
@@ -343,9 +354,10 @@ ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out) {
     return EBC_OK;
 }
 
-ebc_status ebc_batch_set_lazy(ebc_batch_t b, int32_t on) {
-    if (!b) return EBC_EINVAL;
+ebc_status ebc_batch_set_lazy(ebc_batch_t b, int32_t on, int64_t min_n) {
+    if (!b || min_n < 0) return EBC_EINVAL;
     b->lazy = on != 0;
+    b->lazy_min_n = min_n;
     return EBC_OK;
 }
 
@@ -371,6 +383,8 @@ ebc_status ebc_batch_destroy(ebc_batch_t b) {
         if (s.h_idx) cudaFreeHost(s.h_idx);
         if (s.h_f) cudaFreeHost(s.h_f);
         if (s.done) cudaEventDestroy(s.done);
+        for (cudaEvent_t ev : s.round_ev)
+            if (ev) cudaEventDestroy(ev);
         if (s.stream_hi) cudaStreamDestroy(s.stream_hi);
         if (s.stream_lo) cudaStreamDestroy(s.stream_lo);
     }

@@ -77,7 +77,7 @@ _SIGS = {
     "ebc_set_lazy": [_P, _I32],
     "ebc_set_max_ctas": [_P, _I32],
     "ebc_batch_set_large": [_P, _I64, _I32, _I32],
-    "ebc_batch_set_lazy": [_P, _I32],
+    "ebc_batch_set_lazy": [_P, _I32, _I64],
     "ebc_reset": [_P],
     "ebc_sync": [_P],
     "ebc_get_stats": [_P, ctypes.POINTER(ebc_stats)],
@@ -429,8 +429,8 @@ class Batch:
     def set_large(self, large_n: int, max_ctas: int, max_active: int = 0):
         self._err(load().ebc_batch_set_large(_P(self.h), int(large_n), int(max_ctas), int(max_active)))
 
-    def set_lazy(self, on: bool = True):
-        self._err(load().ebc_batch_set_lazy(_P(self.h), int(bool(on))))
+    def set_lazy(self, on: bool = True, min_n: int = 0):
+        self._err(load().ebc_batch_set_lazy(_P(self.h), int(bool(on)), int(min_n)))
 
     def step(self):
         a, q = _I32(), _I32()
