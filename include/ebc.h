@@ -113,8 +113,8 @@ ebc_status ebc_set_stream(ebc_t h, void *stream);
 
 /*
  * Select the bulk arithmetic and K, the number of leading candidates that
- * Greedy re-evaluates exactly each round (1 <= K <= 32; default FP32, K = 8).
- * EINVAL for an unsupported precision or K outside [1, 32].
+ * Greedy re-evaluates exactly each round (1 <= K <= 31; default FP32, K = 8).
+ * EINVAL for an unsupported precision or K outside [1, 31].
  */
 ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k);
 

@@ -228,7 +228,7 @@ ebc_status ensure_set_part(ebc_t h, int64_t want) {
 int64_t ebc::handle_bytes(int64_t n, int32_t d, ebc_prec prec) {
     const int64_t ch = std::max<int64_t>(4096, ((n + 63) / 64 + 127) / 128 * 128);
     const int64_t nch = (n + ch - 1) / ch;
-    const int64_t ref_ch = std::max<int64_t>(1024, ((n + 303) / 304 + 255) / 256 * 256);
+    const int64_t ref_ch = std::max<int64_t>(512, ((n + 607) / 608 + 255) / 256 * 256);
     const int64_t nref = (n + ref_ch - 1) / ref_ch;
     const int64_t nblk = std::min<int64_t>(512, std::max<int64_t>(1, (n + 2047) / 2048));
     const int64_t cap = std::min<int64_t>(n, 4096);
@@ -315,7 +315,7 @@ ebc_status ebc::create_handle(const float *V, int64_t n, int32_t d, int32_t v_on
     // chunking of the V axis
     h->ch = std::max<int64_t>(4096, ((n + 63) / 64 + 127) / 128 * 128);
     h->nch = (int)((n + h->ch - 1) / h->ch);
-    h->ref_ch = std::max<int64_t>(1024, ((n + 303) / 304 + 255) / 256 * 256);  // ~2 chunks per SM
+    h->ref_ch = std::max<int64_t>(512, ((n + 607) / 608 + 255) / 256 * 256);  // ~4 chunks per SM
     h->nref = (int)((n + h->ref_ch - 1) / h->ref_ch);
     h->esc_cap = (int)std::min<int64_t>(n, 4096);
     h->nblk = (int)std::min<int64_t>(512, std::max<int64_t>(1, (n + 2047) / 2048));
@@ -449,7 +449,7 @@ ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k) {
 
 ebc_status ebc::set_precision_handle(ebc_t h, ebc_prec prec, int32_t refine_k, bool sync) {
     if (check_handle(h)) return EBC_EINVAL;
-    if (refine_k < 1 || refine_k > ebc::kMaxRefineK) return fail(h, EBC_EINVAL, "ebc_set_precision: K must be in [1, 32]");
+    if (refine_k < 1 || refine_k > ebc::kMaxRefineK) return fail(h, EBC_EINVAL, "ebc_set_precision: K must be in [1, 31]");
     ebc::Ctx &c = h->c;
     if (prec == EBC_BF16 || prec == EBC_FP16) {
         if (!ebc::tc_supported(c))
@@ -620,9 +620,10 @@ ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off
         for (int64_t j = 0; j < l; ++j)
             if (off[j + 1] < off[j]) return fail(h, EBC_EINVAL, "ebc_eval_sets: offsets decrease");
         if (off[l] > 0 && !csr_idx) return fail(h, EBC_EINVAL, "ebc_eval_sets: csr_idx is NULL");
-        const int64_t npu = c.tc.n_pad / 256;
-        ebc_status s = ensure_set_part(h, std::min<int64_t>(npu * l, std::max<int64_t>(npu * 64, (int64_t)1 << 24)) +
-                                              npu * 64);
+        const int64_t rows = c.tc.n_pad / 256 * 8;  // (point unit, epilogue warp)
+        // partial rows x sets of one launch; a chunk holds at most 128 sets
+        ebc_status s = ensure_set_part(h, std::min<int64_t>(rows * l, std::max<int64_t>(rows * 128, (int64_t)1 << 24)) +
+                                              rows * 128);
         if (s) return s;
         int64_t nl = 0;
         CK(h, launch(h, PK_EVAL, 0, [&] { return ebc::launch_eval_sets_tc(c, csr_idx, csr_off, off.data(), l, out_f, &nl); }));
@@ -685,7 +686,7 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
     if (lazy) {
         // lazy round (k_lazy.cu): certified lower bound from the largest stale
         // bounds, then bulk bounds only for candidates whose stale bound reaches it
-        const int KP = ebc::kMaxRefineK;
+        const int KP = 8;  // one pass of the few-candidate bound kernel
         CK(h, launch(h, -1, 2, [&] { return ebc::launch_lazy_preselect(c, h->nblk, KP); }));
         CK(h, launch(h, PK_REFINE, 1, [&] {
                return ebc::launch_bounds_list(c, c.top_idx, &c.st->top_count, KP, S.part_lo, S.part_hi, S.chunk,

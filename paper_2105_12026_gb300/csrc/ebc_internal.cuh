@@ -12,7 +12,7 @@
 
 namespace ebc {
 
-constexpr int kMaxRefineK = 32;
+constexpr int kMaxRefineK = 31;  // K + 1 <= 32: one warp lane per list entry
 constexpr int kRefineTile = 64;  // points per shared-memory tile of the exact / bound kernels
 
 __host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -184,6 +184,15 @@ cudaError_t launch_reset_state(Ctx &c);
 cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, int64_t chunk, int nchunks);
 cudaError_t launch_reduce_select(Ctx &c, int64_t m, int nchunks, const int *cand, bool greedy,
                                  double *out_gain, int nblk);
+// few-candidate passes over V, one warp per point (k_few.cu); d <= 256
+bool few_supported(const Ctx &c);
+// lists longer than max_cnt are skipped (left to the tiled bound kernel)
+cudaError_t launch_few_bounds(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
+                              int64_t chunk, int nchunks, int max_cnt);
+constexpr int kFewBoundsMax = 64;  // list length up to which the few-candidate bound kernel runs
+cudaError_t launch_few_exact(Ctx &c, const int *list, const int *count, int cap, double *out, int64_t chunk,
+                             int nchunks);
+cudaError_t launch_few_update(Ctx &c);
 // lazy Greedy (k_lazy.cu)
 cudaError_t launch_lazy_preselect(Ctx &c, int nblk, int K);   // top-K of ub64 among unselected -> top list
 cudaError_t launch_lazy_threshold(Ctx &c);                     // st->lazy_thr = max folded lo of the top list
@@ -200,8 +209,9 @@ cudaError_t launch_collect_escalation(Ctx &c, double eta);
 cudaError_t launch_refine_overflow(Ctx &c, const int *list, const int *count, int cap, double *out_exact);
 cudaError_t launch_refine_rows(Ctx &c, const int *list, const int *count, int list_cap, double *out,
                                double *out_hi, int64_t chunk, int nchunks);
+// lists of at most min_cnt entries are skipped (left to the few-candidate kernel)
 cudaError_t launch_bounds_fp32(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
-                               int64_t chunk, int nchunks, float kh, float kl);
+                               int64_t chunk, int nchunks, float kh, float kl, int min_cnt);
 // [lo, hi] gain bounds (register-tiled FP32) / exact gains (one candidate per
 // block) of a device list with device count, as chunk partials
 cudaError_t launch_bounds_list(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,

@@ -530,6 +530,7 @@ __global__ void __launch_bounds__(XT) k_exact_one(const float *__restrict__ V, i
 
 cudaError_t launch_exact_list(Ctx &c, const int *list, const int *count, int cap, double *out, int64_t chunk,
                               int nchunks) {
+    if (few_supported(c)) return launch_few_exact(c, list, count, cap, out, chunk, nchunks);
     if (c.d > 256) return launch_refine_rows(c, list, count, cap, out, nullptr, chunk, nchunks);
     const double rho = (double)(c.d + 4) * ldexp(1.0, -24);
     const size_t sm = sizeof(float) * ((size_t)c.d + (size_t)XT * (c.d + 1));
@@ -546,8 +547,14 @@ cudaError_t launch_exact_list(Ctx &c, const int *list, const int *count, int cap
 
 cudaError_t launch_bounds_list(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
                                int64_t chunk, int nchunks) {
+    // short lists (the top-K, most escalations): one warp per point, 8
+    // candidates per pass; longer ones: the register-tiled kernel.  The count
+    // is on the device, so both are launched and one of them returns at once.
     const BoundConsts bc = bound_consts(c.d);
-    return launch_bounds_fp32(c, list, count, cap, out_lo, out_hi, chunk, nchunks, bc.kh, bc.kl);
+    if (!few_supported(c)) return launch_bounds_fp32(c, list, count, cap, out_lo, out_hi, chunk, nchunks, bc.kh, bc.kl, 0);
+    cudaError_t e = launch_few_bounds(c, list, count, cap, out_lo, out_hi, chunk, nchunks, kFewBoundsMax);
+    if (e != cudaSuccess || cap <= kFewBoundsMax) return e;
+    return launch_bounds_fp32(c, list, count, cap, out_lo, out_hi, chunk, nchunks, bc.kh, bc.kl, kFewBoundsMax);
 }
 
 // Escalated candidates beyond the chunked buffer's capacity: one block per
@@ -635,6 +642,7 @@ __global__ void k_update(const float *__restrict__ V, int64_t n, int d, double *
 }
 
 cudaError_t launch_update(Ctx &c) {
+    if (few_supported(c)) return launch_few_update(c);
     double rho = (double)(c.d + 4) * ldexp(1.0, -24);
     int th = 256;
     int64_t bl = (c.n + th - 1) / th;

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
                                                      const double *__restrict__ m64, const int *__restrict__ list,
                                                      const int *__restrict__ count, int cap, int64_t chunk,
                                                      int nchunks, float kh, float kl, double *__restrict__ out_lo,
-                                                     double *__restrict__ out_hi) {
+                                                     double *__restrict__ out_hi, int min_cnt) {
     __shared__ __align__(16) float Cs[KC][TC];
     __shared__ __align__(16) float Vs[KC][TV];
     __shared__ float MsU[TV], MsD[TV];
@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int cnt = min(*count, cap);
+    if (cnt <= min_cnt) return;  // short lists: the few-candidate kernel
     const int ctiles = (cnt + TC - 1) / TC;
     const int64_t items = (int64_t)ctiles * nchunks;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
@@ -275,9 +276,9 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
 }
 
 cudaError_t launch_bounds_fp32(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
-                               int64_t chunk, int nchunks, float kh, float kl) {
+                               int64_t chunk, int nchunks, float kh, float kl, int min_cnt) {
     k_bounds_fp32<<<c.num_sms * 4, 256, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk, nchunks, kh,
-                                                       kl, out_lo, out_hi);
+                                                       kl, out_lo, out_hi, min_cnt);
     return cudaGetLastError();
 }
 
@@ -378,19 +379,24 @@ __global__ void __launch_bounds__(ES_T) k_eval_sets_fp32(const float *__restrict
     }
 }
 
+// out_f[j0 + j] = (1/n) sum_q set_part[q * l + j]: one warp per set, lanes
+// take the rows in a fixed strided assignment, then a fixed xor tree.
 __global__ void k_sets_finalize(const double *__restrict__ set_part, int64_t ntiles, int64_t l, int64_t j0,
                                 int64_t lall, double inv_n, double *__restrict__ out_f) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= l) return;
+    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= l) return;  // whole warps leave together
     double s = 0.0;
-    for (int64_t q = 0; q < ntiles; ++q) s += set_part[q * l + j];
-    out_f[j0 + j] = s * inv_n;
+    for (int64_t q = lane; q < ntiles; q += 32) s += set_part[q * l + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out_f[j0 + j] = s * inv_n;
     (void)lall;
 }
 
 cudaError_t launch_sets_finalize(Ctx &c, int64_t ntiles, int64_t lb, int64_t j0, int64_t l, double *out_f) {
-    k_sets_finalize<<<(unsigned)((lb + 255) / 256), 256, 0, c.stream>>>(c.set_part, ntiles, lb, j0, l,
-                                                                          1.0 / (double)c.n, out_f);
+    k_sets_finalize<<<(unsigned)((lb * 32 + 255) / 256), 256, 0, c.stream>>>(c.set_part, ntiles, lb, j0, l,
+                                                                               1.0 / (double)c.n, out_f);
     return cudaGetLastError();
 }
 
@@ -418,9 +424,7 @@ cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off
                                                                     c.set_part, c.st, bad);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_sets_finalize<<<(unsigned)((lb + 255) / 256), 256, 0, c.stream>>>(c.set_part, ntiles, lb, j0, l,
-                                                                              1.0 / (double)c.n, out_f);
-        e = cudaGetLastError();
+        e = launch_sets_finalize(c, ntiles, lb, j0, l, out_f);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -104,7 +104,7 @@ struct TcArgs {
 
 constexpr int MODE_GAINS = 0;
 constexpr int MODE_SETS = 1;
-constexpr int SETS_PER_CHUNK = 64;  // accumulator rows in shared memory ([64][8] floats)
+constexpr int SETS_PER_CHUNK = 128;  // sets per chunk (a chunk of 2048 columns holds at most 128 non-empty sets)
 constexpr int SET_GROUP = 16;       // members per group: sets are padded to multiples of 16
 constexpr int64_t CHUNK_COLS = 2048;  // target member columns per chunk
 
@@ -149,6 +149,22 @@ __host__ __device__ inline SmemLayout smem_layout(int DP, int nstages, int na) {
 __device__ __forceinline__ void record_timeout(int *err, volatile int *abort) {
     *abort = 1;
     atomicCAS(err, 0, (int)EBC_ETIMEOUT);
+}
+
+// max of 16 consecutive accumulator words (three-input max, depth 3)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float max16(const uint32_t *x) {
+    const float a0 = fmax3(__uint_as_float(x[0]), __uint_as_float(x[1]), __uint_as_float(x[2]));
+    const float a1 = fmax3(__uint_as_float(x[3]), __uint_as_float(x[4]), __uint_as_float(x[5]));
+    const float a2 = fmax3(__uint_as_float(x[6]), __uint_as_float(x[7]), __uint_as_float(x[8]));
+    const float a3 = fmax3(__uint_as_float(x[9]), __uint_as_float(x[10]), __uint_as_float(x[11]));
+    const float a4 = fmax3(__uint_as_float(x[12]), __uint_as_float(x[13]), __uint_as_float(x[14]));
+    return fmaxf(fmax3(a0, a1, a2), fmax3(a3, a4, __uint_as_float(x[15])));
 }
 
 __device__ __forceinline__ float relu_sum32(const uint32_t (&r)[32]) {
@@ -386,23 +402,23 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         // region 1 (points 128-255); a thread owns one point and all 256
         // member columns of its region.  acc(v, s) = ||v||^2 - dhat(v, s), so
         // the set's term is max(0, max over its members of acc).  Groups of
-        // 16 columns belong to one set; a set's running maximum carries over
-        // tiles; at its last group the 32 lanes' terms are summed (FP32,
-        // fixed shuffle tree) into sacc[set][warp].
+        // 16 columns belong to one set.  The 16 group maxima of a tile are
+        // formed first (independent three-input max trees) and the region is
+        // handed back before the serial part: the set's running maximum
+        // (carried over tiles) and, at its last group, the sum of the 32
+        // lanes' terms (FP32, fixed shuffle tree), written by lane 0 as this
+        // warp's partial of the set: partial[(unit * 8 + warp)][set].
         const int ew = warp - 2;  // 0..7
         const int q = warp & 3;
         const int h = ew >> 2;
-        float *sacc = reinterpret_cast<float *>(comb);  // [SETS_PER_CHUNK][8]
-        const int et = threadIdx.x - 64;                // 0..255
         int t = 0;
         bool alive = true;
         for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
             int at, ch, b_row0, nb;
             unit_span<MODE>(args, u, at, ch, b_row0, nb);
             const int64_t *rec = args.chunks + 4 * (int64_t)ch;
-            const int64_t set_b = rec[0], nsets = rec[1] - rec[0], col_e = rec[3];
-            for (int i = et; i < SETS_PER_CHUNK * 8; i += NEPI) sacc[i] = 0.f;
-            tc::named_bar_sync(2, NEPI);
+            const int64_t set_b = rec[0], col_e = rec[3];
+            double *prow = args.partial + ((int64_t)at * 8 + ew) * args.lb + (set_b - args.j0);
             float run = -INFINITY;
             for (int i = 0; i < nb; ++i, ++t) {
                 const int64_t c0 = (int64_t)b_row0 + (int64_t)i * BN;
@@ -418,53 +434,44 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 if (!alive) continue;
                 tc::tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN);
+                uint32_t r[4][32];
+                float gm[16];
+                tc::tmem_ld32(taddr, r[0]);
+                tc::tmem_ld32(taddr + 32, r[1]);
+                tc::tmem_ld32(taddr + 64, r[2]);
+                tc::tmem_ld32(taddr + 96, r[3]);
+                tc::tmem_ld_wait();
 #pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    if (hh * 8 < ngr) {
-                        uint32_t r[4][32];
-                        tc::tmem_ld32(taddr + hh * 128, r[0]);
-                        tc::tmem_ld32(taddr + hh * 128 + 32, r[1]);
-                        tc::tmem_ld32(taddr + hh * 128 + 64, r[2]);
-                        tc::tmem_ld32(taddr + hh * 128 + 96, r[3]);
-                        tc::tmem_ld_wait();
-#pragma unroll
-                        for (int gg = 0; gg < 8; ++gg) {
-                            const int g = hh * 8 + gg;
-                            if (g < ngr) {
-                                const int e = __shfl_sync(0xffffffffu, ge, g);
-                                float m0 = __uint_as_float(r[gg >> 1][(gg & 1) * 16]);
-                                float m1 = __uint_as_float(r[gg >> 1][(gg & 1) * 16 + 1]);
-#pragma unroll
-                                for (int k = 2; k < 16; k += 2) {
-                                    m0 = fmaxf(m0, __uint_as_float(r[gg >> 1][(gg & 1) * 16 + k]));
-                                    m1 = fmaxf(m1, __uint_as_float(r[gg >> 1][(gg & 1) * 16 + k + 1]));
-                                }
-                                run = fmaxf(run, fmaxf(m0, m1));
-                                if (e & 1) {
-                                    float val = fmaxf(run, 0.f);
-#pragma unroll
-                                    for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-                                    if (lane == 0) sacc[(e >> 1) * 8 + ew] = val;
-                                    run = -INFINITY;
-                                }
-                            }
-                        }
-                    }
+                for (int gg = 0; gg < 8; ++gg) gm[gg] = max16(&r[gg >> 1][(gg & 1) * 16]);
+                if (ngr > 8) {
+                    tc::tmem_ld32(taddr + 128, r[0]);
+                    tc::tmem_ld32(taddr + 160, r[1]);
+                    tc::tmem_ld32(taddr + 192, r[2]);
+                    tc::tmem_ld32(taddr + 224, r[3]);
+                    tc::tmem_ld_wait();
                 }
                 tc::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&t_empty[h]);
-            }
-            tc::named_bar_sync(2, NEPI);
-            if (alive) {
-                for (int sidx = et; sidx < nsets; sidx += NEPI) {
-                    double tot = 0.0;
+                if (ngr > 8) {
 #pragma unroll
-                    for (int w = 0; w < 8; ++w) tot += (double)sacc[sidx * 8 + w];
-                    args.partial[(int64_t)at * args.lb + (set_b - args.j0) + sidx] = tot;
+                    for (int gg = 0; gg < 8; ++gg) gm[8 + gg] = max16(&r[gg >> 1][(gg & 1) * 16]);
+                }
+#pragma unroll
+                for (int g = 0; g < 16; ++g) {
+                    if (g < ngr) {
+                        const int e = __shfl_sync(0xffffffffu, ge, g);
+                        run = fmaxf(run, gm[g]);
+                        if (e & 1) {
+                            float val = fmaxf(run, 0.f);
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                            if (lane == 0) prow[e >> 1] = (double)val;
+                            run = -INFINITY;
+                        }
+                    }
                 }
             }
-            tc::named_bar_sync(2, NEPI);
         }
     }
 
@@ -987,9 +994,9 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
 
 // Multi-set evaluation on the tensor cores.  Host plan (from the offsets):
 // padded offsets (each set rounded up to 16 columns), chunks of whole sets
-// (at most 64 sets and about 2048 columns each) and the group table.  Work
-// units are (256 points, chunk); set partials [point unit][set] are reduced
-// in a fixed order by k_sets_finalize.  Sets are processed in batches whose
+// (at most 128 sets and about 2048 columns each) and the group table.  Work
+// units are (256 points, chunk); set partials [point unit][warp][set] are
+// reduced in a fixed order by k_sets_finalize.  Sets are processed in batches whose
 // partials fit the scratch.
 cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_dev, const int64_t *off_host,
                                 int64_t l, double *out_f, int64_t *nlaunch) {
@@ -1070,8 +1077,11 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_d
     const SmemLayout L = smem_layout(T.DP, ns, na);
     if ((e = allow_smem((const void *)k_sets_tc, L.total)) != cudaSuccess) return e;
     const int npu = (int)(T.n_pad / BM);
-    const int64_t max_sets = c.set_part_cap / npu;
-    if (max_sets < SETS_PER_CHUNK) return cudaErrorMemoryAllocation;
+    const int64_t rows = (int64_t)npu * 8;  // partial rows: (point unit, epilogue warp)
+    const int64_t max_sets = c.set_part_cap / rows;
+    int64_t chunk_sets = 0;  // every chunk's partials must fit one launch
+    for (int64_t k = 0; k < nch; ++k) chunk_sets = std::max(chunk_sets, aux[chunk0 + 4 * k + 1] - aux[chunk0 + 4 * k]);
+    if (max_sets < chunk_sets) return cudaErrorMemoryAllocation;
     const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
     for (int64_t k0 = 0; k0 < nch;) {
         const int64_t j0 = aux[chunk0 + 4 * k0];
@@ -1098,9 +1108,11 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_d
         const int64_t units = (int64_t)npu * a.nchunks;
         if (units > INT32_MAX) return cudaErrorInvalidValue;
         const int grid = (int)std::min<int64_t>(units, G);
+        // empty sets get no partial from any warp
+        if ((e = cudaMemsetAsync(c.set_part, 0, sizeof(double) * rows * lb, c.stream)) != cudaSuccess) return e;
         k_sets_tc<<<grid, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = launch_sets_finalize(c, npu, lb, j0, l, out_f)) != cudaSuccess) return e;
+        if ((e = launch_sets_finalize(c, rows, lb, j0, l, out_f)) != cudaSuccess) return e;
         *nlaunch += 2;
         k0 = k1;
     }
