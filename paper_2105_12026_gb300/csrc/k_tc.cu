@@ -167,6 +167,29 @@ __device__ __forceinline__ float max16(const uint32_t *x) {
     return fmaxf(fmax3(a0, a1, a2), fmax3(a3, a4, __uint_as_float(x[15])));
 }
 
+// Sums over the 32 lanes of 16 per-group values, as a reduce-scatter: lane l
+// ends with the total of group group_of_lane(l) (2 lanes per group); 16
+// shuffles, every total a fixed tree of 5 pair additions.
+__device__ __forceinline__ int group_of_lane(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+__device__ __forceinline__ float reduce_scatter16(const float (&v)[16], int lane) {
+    float t[8], u[4], w[2];
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4, b2 = lane & 2;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        t[j] = (b16 ? v[j + 8] : v[j]) + __shfl_xor_sync(0xffffffffu, b16 ? v[j] : v[j + 8], 16);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        u[j] = (b8 ? t[j + 4] : t[j]) + __shfl_xor_sync(0xffffffffu, b8 ? t[j] : t[j + 4], 8);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        w[j] = (b4 ? u[j + 2] : u[j]) + __shfl_xor_sync(0xffffffffu, b4 ? u[j] : u[j + 2], 4);
+    float x = (b2 ? w[1] : w[0]) + __shfl_xor_sync(0xffffffffu, b2 ? w[0] : w[1], 2);
+    return x + __shfl_xor_sync(0xffffffffu, x, 1);
+}
+
 __device__ __forceinline__ float relu_sum32(const uint32_t (&r)[32]) {
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
@@ -405,9 +428,10 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         // 16 columns belong to one set.  The 16 group maxima of a tile are
         // formed first (independent three-input max trees) and the region is
         // handed back before the serial part: the set's running maximum
-        // (carried over tiles) and, at its last group, the sum of the 32
-        // lanes' terms (FP32, fixed shuffle tree), written by lane 0 as this
-        // warp's partial of the set: partial[(unit * 8 + warp)][set].
+        // (carried over tiles) and, for every set ending in the tile, the sum
+        // of the 32 lanes' terms (FP32, one batched reduce-scatter with fixed
+        // trees), written as this warp's partial of the set:
+        // partial[(unit * 8 + warp)][set].
         const int ew = warp - 2;  // 0..7
         const int q = warp & 3;
         const int h = ew >> 2;
@@ -424,6 +448,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 const int64_t c0 = (int64_t)b_row0 + (int64_t)i * BN;
                 const int ngr = (int)(min((int64_t)BN, col_e - c0) / SET_GROUP);
                 const int ge = lane < ngr ? __ldg(args.gset + c0 / SET_GROUP + lane) : 0;
+                const unsigned lastmask = __ballot_sync(0xffffffffu, lane < ngr && (ge & 1));  // groups ending a set
                 if (alive) {
                     const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag));
                     if (!ok) {
@@ -457,19 +482,24 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
 #pragma unroll
                     for (int gg = 0; gg < 8; ++gg) gm[8 + gg] = max16(&r[gg >> 1][(gg & 1) * 16]);
                 }
+                // running maximum over the groups (reset after a set's last
+                // group); val[g] = the set's term where group g ends it
+                float val[16];
 #pragma unroll
                 for (int g = 0; g < 16; ++g) {
+                    val[g] = 0.f;
                     if (g < ngr) {
-                        const int e = __shfl_sync(0xffffffffu, ge, g);
                         run = fmaxf(run, gm[g]);
-                        if (e & 1) {
-                            float val = fmaxf(run, 0.f);
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-                            if (lane == 0) prow[e >> 1] = (double)val;
-                            run = -INFINITY;
-                        }
+                        const bool last = (lastmask >> g) & 1u;
+                        val[g] = last ? fmaxf(run, 0.f) : 0.f;
+                        run = last ? -INFINITY : run;
                     }
+                }
+                if (lastmask) {  // one batched lane reduction for all sets ending in this tile
+                    const float tot = reduce_scatter16(val, lane);
+                    const int gv = group_of_lane(lane);
+                    const int gev = __shfl_sync(0xffffffffu, ge, gv);
+                    if ((lane & 1) == 0 && ((lastmask >> gv) & 1u)) prow[gev >> 1] = (double)tot;
                 }
             }
         }
