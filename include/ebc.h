@@ -59,7 +59,9 @@ typedef enum {
     EBC_FP32 = 0,    /* direct (v - c)^2 in FP32 on the CUDA cores */
     EBC_BF16 = 1,    /* V.C^T in BF16 on tensor cores, FP32 accumulate */
     EBC_FP16 = 2,    /* V.C^T in FP16 on tensor cores, FP32 accumulate */
-    EBC_FP8E4M3 = 3  /* V.C^T in FP8 e4m3 with a per-row FP32 scale */
+    EBC_FP8E4M3 = 3  /* V.C^T in FP8 e4m3: candidate rows with a per-row power-of-two
+                        scale, points with one power-of-two scale; Greedy certifies with
+                        BF16 bounds of the candidates the FP8 bounds cannot exclude */
 } ebc_prec;
 
 /* Counters of the certified Greedy pick (see ebc_greedy). */
@@ -114,7 +116,12 @@ ebc_status ebc_set_stream(ebc_t h, void *stream);
 /*
  * Select the bulk arithmetic and K, the number of leading candidates that
  * Greedy re-evaluates exactly each round (1 <= K <= 31; default FP32, K = 8).
- * EINVAL for an unsupported precision or K outside [1, 31].
+ * The tensor-core precisions need d <= 128.  EBC_FP8E4M3 also keeps the BF16
+ * copy: ebc_gains returns the raw FP8 gains, ebc_greedy bounds every
+ * candidate with FP8 and then certifies as the lazy Greedy does with BF16
+ * bounds (same picks as every other precision), ebc_eval_sets uses BF16.
+ * EINVAL for an unsupported precision or d, K outside [1, 31], or a V that
+ * overflows the requested format (FP16) or is not finite.
  */
 ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k);
 
@@ -216,6 +223,8 @@ typedef struct {
     double refine_ms;      /* exact FP64 re-evaluation of the leaders */
     int64_t eval_launches; /* launches of the multi-set kernel */
     double eval_ms;
+    int64_t list_launches; /* lazy and FP8 Greedy: row gather + bulk bounds of the round's list */
+    double list_ms;
 } ebc_profile;
 
 /* Turn per-launch event timing on (1) or off (0); counters keep running. */

@@ -23,7 +23,7 @@ struct Prof {
     std::vector<Rec> pending;
 };
 
-enum { PK_BULK = 0, PK_REFINE = 1, PK_EVAL = 2 };
+enum { PK_BULK = 0, PK_REFINE = 1, PK_EVAL = 2, PK_LIST = 3 };
 
 struct ebc_ctx {
     ebc::Ctx c;
@@ -183,6 +183,7 @@ cudaError_t launch(ebc_t h, int kind, int64_t nlaunch, F &&fn) {
     if (kind == PK_BULK) p.p.bulk_launches += nlaunch;
     if (kind == PK_REFINE) p.p.refine_launches += nlaunch;
     if (kind == PK_EVAL) p.p.eval_launches += nlaunch;
+    if (kind == PK_LIST) p.p.list_launches += nlaunch;
     if (a && b) {
         cudaEventRecord(b, h->c.stream);
         p.pending.push_back({a, b, kind});
@@ -203,6 +204,7 @@ cudaError_t fold_profile(ebc_t h) {
         if (r.kind == PK_BULK) p.p.bulk_ms += ms;
         if (r.kind == PK_REFINE) p.p.refine_ms += ms;
         if (r.kind == PK_EVAL) p.p.eval_ms += ms;
+        if (r.kind == PK_LIST) p.p.list_ms += ms;
         p.pool.push_back(r.a);
         p.pool.push_back(r.b);
     }
@@ -236,9 +238,13 @@ int64_t ebc::handle_bytes(int64_t n, int32_t d, ebc_prec prec) {
     int64_t b = n * d * 4 + n * (8 + 4 + 8 + 1 + 8 + 4 + 8 + 4 + 4 + 8) + std::max<int64_t>(nch, 16) * n * 8;
     b += nblk * (ebc::kMaxRefineK + 1) * 12 + 4096;
     b += 2 * cap * 8 + 3 * pool * nref * 8 + pool * 12 + 2 * ebc::kMaxRefineK * 8;
-    if (prec == EBC_BF16 || prec == EBC_FP16) {
+    if (prec == EBC_BF16 || prec == EBC_FP16 || prec == EBC_FP8E4M3) {
         const int64_t n_pad = (n + 255) / 256 * 256, DP = (d + 63) / 64 * 64;
-        b += 3 * n_pad * DP * 2 + 3 * n_pad * 16 * 2 + n_pad * (8 + 4 + 4);
+        b += 3 * n_pad * DP * 2 + 4 * n_pad * 16 * 2 + n_pad * (8 + 4 + 4);
+    }
+    if (prec == EBC_FP8E4M3) {  // FP8 operands, extensions, scales, norms; lazy bounds and list
+        const int64_t n_pad = (n + 255) / 256 * 256, DP8 = (d + 127) / 128 * 128;
+        b += 3 * n_pad * DP8 + 3 * n_pad * 16 * 2 + n_pad * (4 + 4 + 8 + 8 + 4 * 4) + n * (8 + 4);
     }
     return b + 64 * 1024;  // allocation granularity and small buffers
 }
@@ -410,6 +416,7 @@ ebc_status ebc_reload(ebc_t h, const float *V, int32_t v_on_device) {
     CK(h, launch(h, -1, 1, [&] { return ebc::launch_reset_state(c); }));
     CK(h, launch(h, -1, 1, [&] { return ebc::launch_prologue(c); }));
     if (c.tc.prec >= 0) CK(h, launch(h, -1, 1, [&] { return ebc::tc_quantize(c); }));
+    if (c.tc8.ready) CK(h, launch(h, -1, 3, [&] { return ebc::tc8_setup(c); }));
     h->nsel = 0;
     return EBC_OK;
 }
@@ -472,8 +479,31 @@ ebc_status ebc::set_precision_handle(ebc_t h, ebc_prec prec, int32_t refine_k, b
                 }
             }
         }
+    } else if (prec == EBC_FP8E4M3) {
+        // FP8 bulk bounds pre-screen; the BF16 copy certifies (second level)
+        if (!ebc::tc_supported(c))
+            return fail(h, EBC_EINVAL, "ebc_set_precision: the tensor-core path supports d <= 128");
+        if (sync) {
+            ebc_status s0 = ebc_sync(h);
+            if (s0 != EBC_OK) return s0;
+        }
+        if (c.tc.prec != EBC_BF16) CK(h, ebc::tc_setup(c, EBC_BF16));
+        if (!c.tc8.ready) CK(h, ebc::tc8_setup(c));
+        if (!c.ub64) {
+            CK(h, dalloc(&c.ub64, c.n, c));
+            CK(h, dalloc(&c.lazy_idx, c.n, c));
+            CK(h, ebc::launch_lazy_init(c));
+        }
+        if (sync) {
+            CK(h, cudaMemcpyAsync(c.h_err, &c.st->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+            CK(h, cudaStreamSynchronize(c.stream));
+            if (c.h_err[0]) {
+                CK(h, cudaMemsetAsync(&c.st->err, 0, sizeof(int), c.stream));
+                return fail(h, EBC_EINVAL, "ebc_set_precision: V has a non-finite entry");
+            }
+        }
     } else if (prec != EBC_FP32) {
-        return fail(h, EBC_EINVAL, "ebc_set_precision: precision not available in this build");
+        return fail(h, EBC_EINVAL, "ebc_set_precision: unknown precision");
     }
     c.prec = prec;
     c.refine_k = refine_k;
@@ -560,11 +590,16 @@ ebc_status ebc_gains(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_ga
         CK(h, cudaGetLastError());
         h->prof.p.launches += 1;
         int nch = h->nch;
+        // all candidates in index order: no gather, the candidate is the row
+        const int *cl = cand_idx ? c.cand_buf : nullptr;
         if (c.prec == EBC_FP32) {
             CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, c.cand_buf, mb, false, h->ch, h->nch); }));
+        } else if (c.prec == EBC_FP8E4M3) {
+            CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc8(c, false); }));
+            CK(h, launch(h, PK_BULK, 2, [&] { return ebc::launch_gains_tc8(c, cl, mb, &nch); }));
         } else {
             CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, false); }));
-            CK(h, launch(h, PK_BULK, 2, [&] { return ebc::launch_gains_tc(c, c.cand_buf, mb, false, &nch); }));
+            CK(h, launch(h, PK_BULK, 2, [&] { return ebc::launch_gains_tc(c, cl, mb, false, &nch); }));
         }
         h->prof.p.bulk_evals += mb * c.n;
         CK(h, launch(h, -1, 2, [&] {
@@ -682,7 +717,21 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
     const double eta = bulk_eta(c);
     int nch = h->nch;
     ebc::Ctx::Sel &S = c.cert;
-    const bool lazy = c.lazy && c.prec != EBC_FP32;
+    const bool fp8 = c.prec == EBC_FP8E4M3;
+    const bool lazy = (c.lazy && c.prec != EBC_FP32) || fp8;
+    if (fp8) {
+        // FP8 bulk upper bounds of every candidate tighten the stale bounds;
+        // the lazy round below certifies with BF16 bounds of the candidates
+        // that can still win
+        int nch8 = 1;
+        CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc8(c, true); }));
+        CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_tc8(c, nullptr, c.n, &nch8); }));
+        h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
+        CK(h, launch(h, -1, 2, [&] {
+               cudaError_t e = ebc::launch_reduce_select(c, c.n, nch8, nullptr, true, nullptr, h->nblk);
+               return e != cudaSuccess ? e : ebc::launch_lazy_from_full(c, eta);
+           }));
+    }
     if (lazy) {
         // lazy round (k_lazy.cu): certified lower bound from the largest stale
         // bounds, then bulk bounds only for candidates whose stale bound reaches it
@@ -698,7 +747,7 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
                return e != cudaSuccess ? e : ebc::launch_lazy_build(c);
            }));
         CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, true); }));
-        CK(h, launch(h, PK_BULK, 2, [&] { return ebc::launch_gains_tc_list(c, c.lazy_idx, &c.st->list_m, c.n); }));
+        CK(h, launch(h, PK_LIST, 2, [&] { return ebc::launch_gains_tc_list(c, c.lazy_idx, &c.st->list_m, c.n); }));
         CK(h, launch(h, -1, 1, [&] { return ebc::launch_lazy_select(c, eta, h->nblk); }));
     } else {
         if (c.prec == EBC_FP32) {

@@ -124,6 +124,28 @@ struct Ctx {
         int64_t mcap = 0;         // rows of Mq / Mx
         int64_t aux_cap = 0;      // int64 entries of sets_aux
     } tc;
+    // FP8 e4m3 copy (ebc_set_precision EBC_FP8E4M3): candidate operand with a
+    // per-row power-of-two scale s_c, point operand with one power-of-two
+    // scale t; both quantised to nearest.  The certified Greedy at FP8 also
+    // uses the BF16 copy above (second level).
+    struct Tc8 {
+        bool ready = false;
+        int64_t n_pad = 0;
+        int DP = 0;                   // d rounded up to 128 (bytes per row)
+        uint8_t *Qc = nullptr;        // [n_pad, DP] candidate operand q_c = RN(c / s_c)
+        uint8_t *Qp = nullptr;        // [n_pad, DP] point operand q_v = RN(v / t)
+        uint8_t *Cq = nullptr;        // [n_pad, DP] gathered candidate rows
+        uint16_t *Aext = nullptr;     // [n_pad, 16] candidate extension / s_c
+        uint16_t *Cqx = nullptr;      // [n_pad, 16] gathered candidate extension
+        uint16_t *Bext = nullptr;     // [n_pad, 16] point extension / (2 t), per round
+        float *fc = nullptr;          // [n_pad] 2 s_c t: scale of a candidate's accumulated sums
+        float *Cfc = nullptr;         // [n_pad] gathered fc
+        double *qn_c = nullptr, *qn_p = nullptr;  // [n_pad] ||c_hat||^2, ||v_hat||^2
+        float *qerr_c = nullptr, *qerr_p = nullptr, *qnorm_c = nullptr, *qnorm_p = nullptr;  // [n_pad], rounded up
+        float *qmax = nullptr;        // [5] max qerr_c, max qnorm_c, max qerr_p, max qnorm_p, amax(V)
+        float *tscale = nullptr;      // [1] t
+        CUtensorMap tmA, tmAx, tmA_C, tmAx_C, tmB, tmBx;
+    } tc8;
     int num_sms = 152;
     int max_ctas = 0;  // cap on persistent-kernel CTAs (0 = one per SM)
 
@@ -200,6 +222,7 @@ cudaError_t launch_lazy_build(Ctx &c);                         // lazy_idx = {c 
 cudaError_t launch_lazy_select(Ctx &c, double eta, int nblk);  // list sums, ub64 update, per-block tops
 cudaError_t launch_lazy_collect(Ctx &c, double eta);           // escalation over the list
 cudaError_t launch_lazy_init(Ctx &c);                          // ub64 = +inf
+cudaError_t launch_lazy_from_full(Ctx &c, double eta);         // ub64 <- min(ub64, gain_up (1 + eta))
 cudaError_t launch_merge_top(Ctx &c, int nblk, int K, double eta);
 // Exact FP64 gains (out_hi == nullptr) or rigorous FP32 [lo, hi] bounds of
 // the gains (out holds lo, out_hi hi) of a device list, as chunk partials.
@@ -245,5 +268,9 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
 cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_dev, const int64_t *off_host,
                                 int64_t l, double *out_f, int64_t *nlaunch);
 void tc_free(Ctx &c);
+// FP8 e4m3 (k_tc.cu)
+cudaError_t tc8_setup(Ctx &c);                    // allocate, quantise, build tensor maps
+cudaError_t launch_prep_tc8(Ctx &c, bool upper);  // per-round point extension
+cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks);
 
 }  // namespace ebc

@@ -38,6 +38,20 @@ cudaError_t launch_lazy_init(Ctx &c) {
     return cudaGetLastError();
 }
 
+// ub <- min(ub, U (1 + eta)) from a full bulk pass (gain_up[c] = U_c, -1 when
+// selected): the FP8 pre-screen of the certified FP8 Greedy.
+__global__ void k_lazy_from_full(const double *__restrict__ gain_up, int64_t n, double eta, double *__restrict__ ub) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double u = gain_up[j];
+    if (u >= 0.0) ub[j] = fmin(ub[j], u * (1.0 + eta));
+}
+
+cudaError_t launch_lazy_from_full(Ctx &c, double eta) {
+    k_lazy_from_full<<<(unsigned)((c.n + 255) / 256), 256, 0, c.stream>>>(c.gain_up, c.n, eta, c.ub64);
+    return cudaGetLastError();
+}
+
 // Per-block top (K + 1) of ub among unselected candidates.
 __global__ void k_lazy_blocktop(const double *__restrict__ ub, int64_t n, int per_blk, int kk,
                                 double *__restrict__ blk_val, int *__restrict__ blk_idx) {

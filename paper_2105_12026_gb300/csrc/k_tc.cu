@@ -51,6 +51,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <float.h>
 #include <math.h>
 
@@ -83,13 +84,15 @@ struct TcArgs {
     int n_ctiles;        // candidate tiles covering m
     int nchunks;         // V chunks
     int vt_per_chunk;    // point tiles per chunk
-    int DP;              // padded K of the main part
+    int RB;              // bytes per row of the main part (whole 128-byte swizzle atoms)
+    int xatom;           // elements per 128-byte atom: the TMA x step (64 for 16-bit, 128 for 8-bit)
     int nstages;         // B ring depth
     int na;              // candidate-tile buffers (1 or 2)
     uint32_t idesc;      // instruction descriptor, main part
     uint32_t idesc_ext;  // instruction descriptor, extension (bf16)
     double *partial;     // gains: [nchunks][m]; sets: [point units][lb]
     int *err;            // device error word
+    const float *row_scale;  // FP8: factor of each A row's sums (nullptr: 1)
     // multi-set mode only
     const int64_t *chunks;  // [nchunks][4]: first set, end set, first column, end column
     const int *gset;        // per 16-column group: 2 * (set index within its chunk) + (last group of the set)
@@ -108,14 +111,43 @@ constexpr int SETS_PER_CHUNK = 128;  // sets per chunk (a chunk of 2048 columns 
 constexpr int SET_GROUP = 16;       // members per group: sets are padded to multiples of 16
 constexpr int64_t CHUNK_COLS = 2048;  // target member columns per chunk
 
+// The launch's work plan as plain values: from the arguments, or, for a
+// list whose length is on the device, derived from that length (every CTA
+// and thread computes the same plan).  The argument struct itself is never
+// modified in the kernel.
+struct Plan {
+    int64_t m;         // candidates (gains) / unused (sets)
+    int n_ctiles;      // A tiles
+    int nchunks;       // units per A tile
+    int vt_per_chunk;  // B tiles per unit (gains)
+};
+
+__device__ __forceinline__ Plan make_plan(const TcArgs &a) {
+    Plan p;
+    if (a.m_dev) {
+        p.m = *reinterpret_cast<const volatile int *>(a.m_dev);
+        int vpc = 1;
+        p.nchunks = pick_chunks(p.m, a.n_vtiles, a.G, a.partial_cap, &vpc);
+        p.vt_per_chunk = vpc;
+        p.n_ctiles = (int)((p.m + BM - 1) / BM);
+    } else {
+        p.m = a.m;
+        p.n_ctiles = a.n_ctiles;
+        p.nchunks = a.nchunks;
+        p.vt_per_chunk = a.vt_per_chunk;
+    }
+    return p;
+}
+
 // Work unit u -> A tile index, chunk, first B row and number of B tiles.
 template <int MODE>
-__device__ __forceinline__ void unit_span(const TcArgs &a, int u, int &at, int &ch, int &b_row0, int &nb) {
-    at = u / a.nchunks;
-    ch = u % a.nchunks;
+__device__ __forceinline__ void unit_span(const TcArgs &a, const Plan &P, int u, int &at, int &ch, int &b_row0,
+                                          int &nb) {
+    at = u / P.nchunks;
+    ch = u % P.nchunks;
     if constexpr (MODE == MODE_GAINS) {
-        const int vt0 = ch * a.vt_per_chunk;
-        const int vt1 = min(vt0 + a.vt_per_chunk, a.n_vtiles);
+        const int vt0 = ch * P.vt_per_chunk;
+        const int vt1 = min(vt0 + P.vt_per_chunk, a.n_vtiles);
         b_row0 = vt0 * BN;
         nb = vt1 - vt0;
     } else {
@@ -131,12 +163,12 @@ struct SmemLayout {
 
 // A buffer: sub-tile 0 (main K atoms, then its extension), sub-tile 1 (same).
 // B stage: main K atoms, then the extension.
-__host__ __device__ inline SmemLayout smem_layout(int DP, int nstages, int na) {
+__host__ __device__ inline SmemLayout smem_layout(int RB, int nstages, int na) {
     SmemLayout L;
-    L.a_main = (uint32_t)BMS * DP * 2;
+    L.a_main = (uint32_t)BMS * RB;
     L.a_sub = L.a_main + BMS * KEXT * 2;
     L.a_bytes = 2 * L.a_sub;
-    L.b_main = (uint32_t)BN * DP * 2;
+    L.b_main = (uint32_t)BN * RB;
     L.b_bytes = L.b_main + BN * KEXT * 2;
     L.off_b = na * L.a_bytes;
     L.off_comb = L.off_b + nstages * L.b_bytes;
@@ -208,7 +240,7 @@ __device__ __forceinline__ float relu_sum32(const uint32_t (&r)[32]) {
 // gains (MODE_GAINS: A = candidates, B = points, epilogue = relu row sums)
 // and the multi-set evaluation (MODE_SETS: A = points, B = set members,
 // epilogue = per-set maxima and sums over the points).
-template <int MODE>
+template <int MODE, bool F8>
 __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUtensorMap *tmAx_p,
                                             const CUtensorMap *tmB_p, const CUtensorMap *tmBx_p, const TcArgs &args) {
     const CUtensorMap &tmA = *tmA_p, &tmAx = *tmAx_p, &tmB = *tmB_p, &tmBx = *tmBx_p;
@@ -216,7 +248,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ns = args.nstages;
     const int na = args.na;
-    const SmemLayout L = smem_layout(args.DP, ns, na);
+    const SmemLayout L = smem_layout(args.RB, ns, na);
     uint8_t *sA = base;
     uint8_t *sB = base + L.off_b;
     double *comb = reinterpret_cast<double *>(base + L.off_comb);  // [2][BMS]
@@ -235,8 +267,10 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int total_units = args.n_ctiles * args.nchunks;
-    const int katoms = args.DP / KATOM;
+    const Plan P = make_plan(args);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && args.nch_out) *args.nch_out = P.nchunks;
+    const int total_units = P.n_ctiles * P.nchunks;
+    const int katoms = args.RB / 128;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < ns; ++s) {
@@ -275,7 +309,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
             int g = 0, ua = 0;
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
                 int ct, ch, b_row0, nb;
-                unit_span<MODE>(args, u, ct, ch, b_row0, nb);
+                unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
                 const int ab = ua % na;
                 const int aph = (ua / na) & 1;
                 if (!tc::mbar_wait(&a_empty[ab], aph ^ 1, abort_flag)) {
@@ -288,7 +322,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                     uint8_t *sub = abuf + h * L.a_sub;
                     const int row0 = ct * BM + h * BMS;
                     for (int j = 0; j < katoms; ++j)
-                        tc::tma_load_2d(sub + j * (BMS * 128), &tmA, &a_full[ab], j * KATOM, row0);
+                        tc::tma_load_2d(sub + j * (BMS * 128), &tmA, &a_full[ab], j * args.xatom, row0);
                     tc::tma_load_2d(sub + L.a_main, &tmAx, &a_full[ab], 0, row0);
                 }
                 last_afull[ab] = aph;
@@ -305,7 +339,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                     uint8_t *bbuf = sB + s * L.b_bytes;
                     tc::mbar_arrive_expect_tx(&full[s], L.b_bytes);
                     for (int j = 0; j < katoms; ++j)
-                        tc::tma_load_2d(bbuf + j * (BN * 128), &tmB, &full[s], j * KATOM, brow);
+                        tc::tma_load_2d(bbuf + j * (BN * 128), &tmB, &full[s], j * args.xatom, brow);
                     tc::tma_load_2d(bbuf + L.b_main, &tmBx, &full[s], 0, brow);
                     last_full[s] = ph;
                 }
@@ -320,7 +354,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
             int g = 0, t = 0, ua = 0;
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
                 int ct, ch, b_row0, nb;
-                unit_span<MODE>(args, u, ct, ch, b_row0, nb);
+                unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
                 const int ab = ua % na;
                 if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag)) {
                     record_timeout(args.err, abort_flag);
@@ -345,11 +379,15 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                         tc::tc_fence_after();
                         const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
                         const uint32_t ah = a0 + h * L.a_sub;
-                        for (int kk = 0; kk < args.DP / 16; ++kk) {
+                        // one MMA per 32 bytes of K (16 16-bit or 32 8-bit elements)
+                        for (int kk = 0; kk < args.RB / 32; ++kk) {
                             const uint32_t j = kk >> 2, w = kk & 3;
                             const uint64_t ad = tc::sdesc_sw128(ah + j * (BMS * 128) + w * 32);
                             const uint64_t bd = tc::sdesc_sw128(b0 + j * (BN * 128) + w * 32);
-                            tc::mma_f16(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
+                            if constexpr (F8)
+                                tc::mma_f8(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
+                            else
+                                tc::mma_f16(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
                         }
                         tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main),
                                     args.idesc_ext, 1u);
@@ -373,7 +411,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         bool alive = true;
         for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
             int ct, ch, b_row0, nb;
-            unit_span<MODE>(args, u, ct, ch, b_row0, nb);
+            unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
             double acc[2] = {0.0, 0.0};
             for (int i = 0; i < nb; ++i, ++t) {
 #pragma unroll
@@ -414,7 +452,11 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int64_t j = (int64_t)ct * BM + h * BMS + row;
-                    if (j < args.m) args.partial[(int64_t)ch * args.m + j] = acc[h] + comb[h * BMS + row];
+                    if (j < P.m) {
+                        double v = acc[h] + comb[h * BMS + row];
+                        if (F8) v *= (double)args.row_scale[j];  // a power of two: exact
+                        args.partial[(int64_t)ch * P.m + j] = v;
+                    }
                 }
             }
             tc::named_bar_sync(2, NEPI);
@@ -439,7 +481,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         bool alive = true;
         for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
             int at, ch, b_row0, nb;
-            unit_span<MODE>(args, u, at, ch, b_row0, nb);
+            unit_span<MODE>(args, P, u, at, ch, b_row0, nb);
             const int64_t *rec = args.chunks + 4 * (int64_t)ch;
             const int64_t set_b = rec[0], col_e = rec[3];
             double *prow = args.partial + ((int64_t)at * 8 + ew) * args.lb + (set_b - args.j0);
@@ -528,23 +570,21 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gains_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
-    TcArgs a = args;
-    if (a.m_dev) {
-        // every CTA derives the same plan from the list length
-        a.m = *a.m_dev;
-        int vpc = 1;
-        a.nchunks = pick_chunks(a.m, a.n_vtiles, a.G, a.partial_cap, &vpc);
-        a.vt_per_chunk = vpc;
-        a.n_ctiles = (int)((a.m + BM - 1) / BM);
-        if (blockIdx.x == 0 && threadIdx.x == 0 && a.nch_out) *a.nch_out = a.nchunks;
-    }
-    tc_pipeline<MODE_GAINS>(&tmA, &tmAx, &tmB, &tmBx, a);
+    tc_pipeline<MODE_GAINS, false>(&tmA, &tmAx, &tmB, &tmBx, args);
+}
+
+// FP8 e4m3 operands (kind::f8f6f4), BF16 extension step; full candidate
+// ranges or host-sized lists only.
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gains_tc8(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+                const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
+    tc_pipeline<MODE_GAINS, true>(&tmA, &tmAx, &tmB, &tmBx, args);
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_sets_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
               const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
-    tc_pipeline<MODE_SETS>(&tmA, &tmAx, &tmB, &tmBx, args);
+    tc_pipeline<MODE_SETS, false>(&tmA, &tmAx, &tmB, &tmBx, args);
 }
 
 // ---------------------------------------------------------------------------
@@ -800,6 +840,197 @@ __global__ void k_gather_members(const uint16_t *__restrict__ Vq2, const double 
 }
 
 // ---------------------------------------------------------------------------
+// FP8 e4m3.  The candidate operand is q_c = RN(c / s_c) with a per-row
+// power-of-two scale s_c (the smallest with max_i |c_i| / s_c <= 448), the
+// point operand q_v = RN(v / t) with one power-of-two scale t for all of V;
+// c_hat = s_c q_c and v_hat = t q_v exactly.  The MMA accumulates
+// q_c . q_v = c_hat . v_hat / (s_c t); the extension columns are divided by
+// s_c (candidate side) and 2 t (point side), both exact, so the accumulator
+// holds t(c, v) / (2 s_c t) and every candidate's sums are multiplied by
+// fc = 2 s_c t at the end (exact).  The rigorous slack of the BF16 path
+// applies with dc = ||c_hat - c||, dv = ||v_hat - v||.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint8_t to_e4m3(float x) {
+    return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float from_e4m3(uint8_t q) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3)));
+}
+
+// smallest power of two s with a / s <= 448 (1 for a == 0)
+__device__ __forceinline__ float e4m3_scale(float a) {
+    if (!(a > 0.f) || !isfinite(a)) return 1.f;
+    int e;
+    const float m = frexpf(a / 448.f, &e);  // a / 448 = m 2^e, m in [0.5, 1)
+    float sc = ldexpf(1.f, m == 0.5f ? e - 1 : e);
+    while (a / sc > 448.f) sc *= 2.f;  // guard against the rounding of a / 448
+    return sc;
+}
+
+__global__ void k_amax(const float *__restrict__ V, int64_t total, unsigned int *__restrict__ out_bits) {
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(V[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(m));
+}
+
+// One thread per row; FP64 norms and errors in index order.  qmax_bits:
+// [0] max qerr_c, [1] max qnorm_c, [2] max qerr_p, [3] max qnorm_p, [4] amax(V).
+__global__ void k_quantize8(const float *__restrict__ V, int64_t n, int d, int64_t n_pad, int DP,
+                            unsigned int *__restrict__ qmax_bits, uint8_t *__restrict__ Qc, uint8_t *__restrict__ Qp,
+                            float *__restrict__ fc, double *__restrict__ qn_c, double *__restrict__ qn_p,
+                            float *__restrict__ qerr_c, float *__restrict__ qerr_p, float *__restrict__ qnorm_c,
+                            float *__restrict__ qnorm_p, float *__restrict__ tscale, int *__restrict__ err) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const float t = e4m3_scale(__uint_as_float(qmax_bits[4]));
+    if (r == 0) *tscale = t;
+    if (r >= n_pad) return;
+    uint8_t *qc = Qc + r * DP, *qp = Qp + r * DP;
+    if (r >= n) {
+        for (int i = 0; i < DP; ++i) qc[i] = qp[i] = 0;
+        fc[r] = 1.f;
+        qn_c[r] = qn_p[r] = 0.0;
+        qerr_c[r] = qerr_p[r] = qnorm_c[r] = qnorm_p[r] = 0.f;
+        return;
+    }
+    const float *v = V + r * d;
+    float am = 0.f;
+    for (int i = 0; i < d; ++i) am = fmaxf(am, fabsf(v[i]));
+    const float sc = e4m3_scale(am);
+    double nc = 0.0, np = 0.0, ec = 0.0, ep = 0.0;
+    bool finite = true;
+    for (int i = 0; i < DP; ++i) {
+        const float x = i < d ? v[i] : 0.f;
+        finite = finite && isfinite(x);
+        const uint8_t a = to_e4m3(x / sc), b = to_e4m3(x / t);  // divisions by powers of two: exact
+        qc[i] = a;
+        qp[i] = b;
+        const double xc = (double)from_e4m3(a) * (double)sc, xp = (double)from_e4m3(b) * (double)t;
+        const double xd = (double)x;
+        nc = __dadd_rn(nc, __dmul_rn(xc, xc));
+        np = __dadd_rn(np, __dmul_rn(xp, xp));
+        ec = __dadd_rn(ec, __dmul_rn(xc - xd, xc - xd));
+        ep = __dadd_rn(ep, __dmul_rn(xp - xd, xp - xd));
+    }
+    if (!finite) atomicCAS(err, 0, (int)EBC_EINVAL);
+    fc[r] = 2.f * sc * t;
+    qn_c[r] = nc;
+    qn_p[r] = np;
+    const double pad = 1.0 + ldexp(1.0, -40);  // (DP + 1) roundings of 2^-53, see k_quantize
+    const float a0 = __double2float_ru(__dsqrt_ru(ec) * pad), a1 = __double2float_ru(__dsqrt_ru(nc) * pad);
+    const float a2 = __double2float_ru(__dsqrt_ru(ep) * pad), a3 = __double2float_ru(__dsqrt_ru(np) * pad);
+    qerr_c[r] = a0;
+    qnorm_c[r] = a1;
+    qerr_p[r] = a2;
+    qnorm_p[r] = a3;
+    atomicMax(&qmax_bits[0], __float_as_uint(a0));
+    atomicMax(&qmax_bits[1], __float_as_uint(a1));
+    atomicMax(&qmax_bits[2], __float_as_uint(a2));
+    atomicMax(&qmax_bits[3], __float_as_uint(a3));
+}
+
+// Candidate extension / s_c (FP8): [q q q | s s | al al al' al' | 1 1 1 | 0..] / s_c
+// with q = -||c_hat||^2, s = dc^2 + gamma (2 max||v_hat|| ||c_hat|| + ||c_hat||^2 + 1),
+// al = dc; the padding rows of the point extension as in k_make_aext.
+__global__ void k_make_aext8(int64_t n, int64_t n_pad, const double *__restrict__ qn_c, const float *__restrict__ qerr_c,
+                             const float *__restrict__ qnorm_c, const float *__restrict__ qmax, const float *__restrict__ fc,
+                             const float *__restrict__ tscale, double gamma, uint16_t *__restrict__ Aext,
+                             uint16_t *__restrict__ Bext) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_pad) return;
+    __align__(16) uint16_t row[KEXT];
+    for (int i = 0; i < KEXT; ++i) row[i] = 0;
+    if (r < n) {
+        const double inv = 1.0 / ((double)fc[r] / (2.0 * (double)*tscale));  // 1 / s_c, a power of two
+        const double qn = qn_c[r], dc = (double)qerr_c[r], qm = (double)qnorm_c[r], qmx = (double)qmax[3];
+        const double sc = __dadd_ru(__dmul_ru(dc, dc),
+                                    __dmul_ru(gamma, __dadd_ru(__dadd_ru(__dmul_ru(2.0 * qmx, qm), qn), 1.0)));
+        split3(-qn * inv, true, row + 0);
+        split2_up(sc * inv, row + 3);
+        uint16_t al[2];
+        split2_up(dc * inv, al);
+        row[5] = row[6] = al[0];
+        row[7] = row[8] = al[1];
+        row[9] = row[10] = row[11] = bf16_bits(__float2bfloat16_rn((float)inv));
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(Aext + r * KEXT);
+    const uint4 *src = reinterpret_cast<const uint4 *>(row);
+    dst[0] = src[0];
+    dst[1] = src[1];
+    if (r >= n) {
+        __align__(16) uint16_t prow[KEXT];
+        for (int i = 0; i < KEXT; ++i) prow[i] = 0;
+        prow[9] = bf16_bits(__float2bfloat16_rn(PAD_A));
+        uint4 *bd = reinterpret_cast<uint4 *>(Bext + r * KEXT);
+        const uint4 *ps = reinterpret_cast<const uint4 *>(prow);
+        bd[0] = ps[0];
+        bd[1] = ps[1];
+    }
+}
+
+// Per-round point extension / (2 t) (FP8): as k_prep_tc with the point-side
+// norms and errors and max dc of the candidate side.
+__global__ void k_prep_tc8(const double *__restrict__ m64, const double *__restrict__ qn_p,
+                           const float *__restrict__ qerr_p, const float *__restrict__ qmax,
+                           const float *__restrict__ tscale, int64_t n, int upper, double gamma,
+                           uint16_t *__restrict__ Bext) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const double inv = 1.0 / (2.0 * (double)*tscale);  // a power of two
+    __align__(16) uint16_t row[KEXT];
+    for (int i = 0; i < KEXT; ++i) row[i] = 0;
+    const uint16_t one = bf16_bits(__float2bfloat16_rn((float)inv));
+    row[0] = row[1] = row[2] = one;
+    const double mv = m64[v];
+    if (upper) {
+        const double dv = (double)qerr_p[v];
+        const double sq = __dsqrt_ru(mv);
+        const double beta = __dmul_ru(dv, __dadd_ru(__dmul_ru(2.0, sq), dv));
+        const double w = __dadd_ru(__dmul_ru(2.0, sq), __dmul_ru(2.0, dv));
+        const double base = __dsub_ru(mv, qn_p[v]);
+        const double acc = __dmul_ru(gamma, __dadd_ru(__dadd_ru(fabs(base), beta), __dmul_ru((double)qmax[0], w)));
+        const double a = __dadd_ru(__dadd_ru(base, beta), acc);
+        row[3] = row[4] = one;
+        uint16_t wp[2];
+        split2_up(w * inv, wp);
+        row[5] = wp[0];
+        row[6] = wp[1];
+        row[7] = wp[0];
+        row[8] = wp[1];
+        split3(a * inv, true, row + 9);
+    } else {
+        split3((mv - qn_p[v]) * inv, false, row + 9);
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(Bext + v * KEXT);
+    const uint4 *src = reinterpret_cast<const uint4 *>(row);
+    dst[0] = src[0];
+    dst[1] = src[1];
+}
+
+// Gather FP8 candidate rows, their extension and scale (16 bytes per thread).
+__global__ void k_gather_rows8(const uint8_t *__restrict__ Qc, const uint16_t *__restrict__ Aext,
+                               const float *__restrict__ fc, const int *__restrict__ cand, int64_t m, int DP,
+                               uint8_t *__restrict__ Cq, uint16_t *__restrict__ Cqx, float *__restrict__ Cfc) {
+    const int per_row = DP / 16 + 2;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= m * per_row) return;
+    const int64_t j = e / per_row;
+    const int w = (int)(e % per_row);
+    const int c = cand[j];
+    uint4 val = make_uint4(0, 0, 0, 0);
+    if (w < DP / 16) {
+        if (c >= 0) val = reinterpret_cast<const uint4 *>(Qc + (int64_t)c * DP)[w];
+        reinterpret_cast<uint4 *>(Cq + j * DP)[w] = val;
+    } else {
+        const int x = w - DP / 16;
+        if (c >= 0) val = reinterpret_cast<const uint4 *>(Aext + (int64_t)c * KEXT)[x];
+        reinterpret_cast<uint4 *>(Cqx + j * KEXT)[x] = val;
+        if (x == 0) Cfc[j] = c >= 0 ? fc[c] : 1.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -833,16 +1064,30 @@ cudaError_t make_map(CUtensorMap *map, void *gptr, int64_t rows, int cols, bool 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 2-D map over a row-major [rows, cols] array of bytes (FP8 operands).
+cudaError_t make_map_u8(CUtensorMap *map, void *gptr, int64_t rows, int cols, int box_cols, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, gptr, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Pipeline shape: candidate-tile buffers (na) and point-tile stages (ns).
 // Two point stages are enough (each tile feeds two sub-tiles' MMAs, twice
 // the time of its load); a second candidate buffer removes the reload
 // bubble at unit changes when it fits; deeper point rings use what is left.
-void pick_pipeline(int DP, int *na, int *ns) {
+void pick_pipeline(int RB, int *na, int *ns) {
     *na = 0;
     *ns = 0;
     for (int a = 2; a >= 1; --a)
         for (int s = 6; s >= 2; --s)
-            if ((int)smem_layout(DP, s, a).total <= SMEM_LIMIT) {
+            if ((int)smem_layout(RB, s, a).total <= SMEM_LIMIT) {
                 *na = a;
                 *ns = s;
                 return;
@@ -869,11 +1114,119 @@ cudaError_t allow_smem(const void *kernel, uint32_t bytes) {
 
 double gamma_for(int DP) { return ((double)(DP + KEXT) / 4.0 + 4.0) * ldexp(1.0, -22); }
 
+// FP8: the tensor core's internal sum of each 32-product block is assumed
+// exact to 13 bits below its largest product (32 x 2^-13 = 2^-8 of the
+// block's absolute sum), plus the FP32 accumulation of the BF16 bound.
+double gamma8_for(int DP) { return ldexp(1.0, -8) + gamma_for(DP); }
+
 }  // namespace
 
 bool tc_supported(const Ctx &c) { return c.d <= 128; }
 
+void tc8_free(Ctx &c) {
+    Ctx::Tc8 &T = c.tc8;
+    void *ptrs[] = {T.Qc, T.Qp, T.Cq, T.Aext, T.Cqx, T.Bext, T.fc, T.Cfc, T.qn_c, T.qn_p,
+                    T.qerr_c, T.qerr_p, T.qnorm_c, T.qnorm_p, T.qmax, T.tscale};
+    for (void *p : ptrs) pool_free(p, c.stream);
+    c.tc8 = Ctx::Tc8();
+}
+
+cudaError_t tc8_quantize(Ctx &c) {
+    Ctx::Tc8 &T = c.tc8;
+    cudaError_t e = cudaMemsetAsync(T.qmax, 0, 5 * sizeof(float), c.stream);
+    if (e != cudaSuccess) return e;
+    k_amax<<<c.num_sms * 4, 256, 0, c.stream>>>(c.V32, c.n * c.d, reinterpret_cast<unsigned int *>(T.qmax) + 4);
+    const int th = 128;
+    const unsigned g = (unsigned)((T.n_pad + th - 1) / th);
+    k_quantize8<<<g, th, 0, c.stream>>>(c.V32, c.n, c.d, T.n_pad, T.DP, reinterpret_cast<unsigned int *>(T.qmax), T.Qc,
+                                        T.Qp, T.fc, T.qn_c, T.qn_p, T.qerr_c, T.qerr_p, T.qnorm_c, T.qnorm_p, T.tscale,
+                                        &c.st->err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_make_aext8<<<g, th, 0, c.stream>>>(c.n, T.n_pad, T.qn_c, T.qerr_c, T.qnorm_c, T.qmax, T.fc, T.tscale,
+                                         gamma8_for(T.DP), T.Aext, T.Bext);
+    return cudaGetLastError();
+}
+
+cudaError_t tc8_setup(Ctx &c) {
+    Ctx::Tc8 &T = c.tc8;
+    if (!T.Qc) {
+        T.n_pad = (c.n + NPAD - 1) / NPAD * NPAD;
+        T.DP = (c.d + 127) / 128 * 128;
+        const size_t rows = (size_t)T.n_pad;
+        cudaError_t e;
+        void **bufs[] = {(void **)&T.Qc, (void **)&T.Qp, (void **)&T.Cq, (void **)&T.Aext, (void **)&T.Cqx,
+                         (void **)&T.Bext, (void **)&T.fc, (void **)&T.Cfc, (void **)&T.qn_c, (void **)&T.qn_p,
+                         (void **)&T.qerr_c, (void **)&T.qerr_p, (void **)&T.qnorm_c, (void **)&T.qnorm_p,
+                         (void **)&T.qmax, (void **)&T.tscale};
+        const size_t sizes[] = {rows * T.DP, rows * T.DP, rows * T.DP, rows * KEXT * 2, rows * KEXT * 2,
+                                rows * KEXT * 2, rows * 4, rows * 4, rows * 8, rows * 8, rows * 4, rows * 4,
+                                rows * 4, rows * 4, 5 * 4, 4};
+        for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i)
+            if ((e = pool_alloc(bufs[i], sizes[i], c.stream, c.device)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(T.Cq, 0, rows * T.DP, c.stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(T.Cqx, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(T.Bext, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
+        if ((e = make_map_u8(&T.tmA, T.Qc, T.n_pad, T.DP, 128, BMS)) != cudaSuccess) return e;
+        if ((e = make_map_u8(&T.tmA_C, T.Cq, T.n_pad, T.DP, 128, BMS)) != cudaSuccess) return e;
+        if ((e = make_map_u8(&T.tmB, T.Qp, T.n_pad, T.DP, 128, BN)) != cudaSuccess) return e;
+        if ((e = make_map(&T.tmAx, T.Aext, T.n_pad, KEXT, true, KEXT, BMS, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess)
+            return e;
+        if ((e = make_map(&T.tmAx_C, T.Cqx, T.n_pad, KEXT, true, KEXT, BMS, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess)
+            return e;
+        if ((e = make_map(&T.tmBx, T.Bext, T.n_pad, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess)
+            return e;
+    }
+    T.ready = true;
+    return tc8_quantize(c);
+}
+
+cudaError_t launch_prep_tc8(Ctx &c, bool upper) {
+    const int th = 256;
+    Ctx::Tc8 &T = c.tc8;
+    k_prep_tc8<<<(unsigned)((c.n + th - 1) / th), th, 0, c.stream>>>(c.m64, T.qn_p, T.qerr_p, T.qmax, T.tscale, c.n,
+                                                                      upper ? 1 : 0, gamma8_for(T.DP), T.Bext);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks_out) {
+    Ctx::Tc8 &T = c.tc8;
+    int na = 0, ns = 0;
+    pick_pipeline(T.DP, &na, &ns);
+    if (ns == 0) return cudaErrorInvalidConfiguration;
+    const SmemLayout L = smem_layout(T.DP, ns, na);
+    if (cudaError_t e = allow_smem((const void *)k_gains_tc8, L.total); e != cudaSuccess) return e;
+    if (cand) {
+        const int64_t tot = m * (T.DP / 16 + 2);
+        k_gather_rows8<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Qc, T.Aext, T.fc, cand, m, T.DP, T.Cq,
+                                                                             T.Cqx, T.Cfc);
+        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
+    }
+    TcArgs a{};
+    a.m = m;
+    a.n_vtiles = (int)(T.n_pad / BN);
+    a.n_ctiles = (int)((m + BM - 1) / BM);
+    const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
+    a.nchunks = pick_chunks(m, a.n_vtiles, G, c.partial_cap, &a.vt_per_chunk);
+    a.RB = T.DP;
+    a.xatom = 128;
+    a.nstages = ns;
+    a.na = na;
+    a.idesc = tc::idesc_f16(0u, BMS, BN);  // kind::f8f6f4 with format 0: e4m3 x e4m3
+    a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
+    a.partial = c.partial;
+    a.err = &c.st->err;
+    a.row_scale = cand ? T.Cfc : T.fc;
+    a.partial_cap = c.partial_cap;
+    a.G = G;
+    const int units = a.n_ctiles * a.nchunks;
+    k_gains_tc8<<<std::min(units, G), NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA, cand ? T.tmAx_C : T.tmAx,
+                                                                     T.tmB, T.tmBx, a);
+    *nchunks_out = a.nchunks;
+    return cudaGetLastError();
+}
+
 void tc_free(Ctx &c) {
+    tc8_free(c);
     void *ptrs[] = {c.tc.Vq,   c.tc.Vq2,   c.tc.Aext, c.tc.Bext, c.tc.Cq,   c.tc.Cqx,      c.tc.qn64,
                     c.tc.qerr, c.tc.qnorm, c.tc.qmax, c.tc.Px,   c.tc.Mq,   c.tc.Mx,       c.tc.gset,
                     c.tc.sets_aux};
@@ -942,9 +1295,9 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     Ctx::Tc &T = c.tc;
     const int DP = T.DP;
     int na = 0, ns = 0;
-    pick_pipeline(DP, &na, &ns);
+    pick_pipeline(2 * DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = smem_layout(DP, ns, na);
+    const SmemLayout L = smem_layout(2 * DP, ns, na);
     if (cudaError_t e = allow_smem((const void *)k_gains_tc, L.total); e != cudaSuccess) return e;
     if (cand) {
         int64_t tot = m * (DP / 8 + 2);
@@ -968,7 +1321,9 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     a.gset = nullptr;
     a.lb = 0;
     a.j0 = 0;
-    a.DP = DP;
+    a.RB = 2 * DP;
+    a.xatom = KATOM;
+    a.row_scale = nullptr;
     a.nstages = ns;
     a.na = na;
     a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, BN);
@@ -991,9 +1346,9 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     Ctx::Tc &T = c.tc;
     const int DP = T.DP;
     int na = 0, ns = 0;
-    pick_pipeline(DP, &na, &ns);
+    pick_pipeline(2 * DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = smem_layout(DP, ns, na);
+    const SmemLayout L = smem_layout(2 * DP, ns, na);
     if (cudaError_t e = allow_smem((const void *)k_gains_tc, L.total); e != cudaSuccess) return e;
     const int64_t tot = m_cap * (DP / 8 + 2);
     k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Vq, T.Aext, cand, m_cap, m_dev, DP, T.Cq,
@@ -1007,7 +1362,9 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     a.n_ctiles = 0;
     a.nchunks = 1;
     a.vt_per_chunk = a.n_vtiles;
-    a.DP = DP;
+    a.RB = 2 * DP;
+    a.xatom = KATOM;
+    a.row_scale = nullptr;
     a.nstages = ns;
     a.na = na;
     a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, BN);
@@ -1102,9 +1459,9 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_d
         *nlaunch += 1;
     }
     int na = 0, ns = 0;
-    pick_pipeline(T.DP, &na, &ns);
+    pick_pipeline(2 * T.DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = smem_layout(T.DP, ns, na);
+    const SmemLayout L = smem_layout(2 * T.DP, ns, na);
     if ((e = allow_smem((const void *)k_sets_tc, L.total)) != cudaSuccess) return e;
     const int npu = (int)(T.n_pad / BM);
     const int64_t rows = (int64_t)npu * 8;  // partial rows: (point unit, epilogue warp)
@@ -1124,7 +1481,9 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_d
         a.n_ctiles = npu;
         a.nchunks = (int)(k1 - k0);
         a.vt_per_chunk = 0;
-        a.DP = T.DP;
+        a.RB = 2 * T.DP;
+        a.xatom = KATOM;
+        a.row_scale = nullptr;
         a.nstages = ns;
         a.na = na;
         a.idesc = tc::idesc_f16(bf ? 1u : 0u, BMS, BN);

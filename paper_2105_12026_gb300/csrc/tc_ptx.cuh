@@ -105,6 +105,18 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64
         : "memory");
 }
 
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f8f6f4 (A, B e4m3 when the
+// instruction descriptor's formats are 0).
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive on `bar` when every tcgen05 operation issued so far by this thread
 // has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -155,8 +167,9 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: FP32 accumulator, A/B format
-// (0 = f16, 1 = bf16), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+// Instruction descriptor: FP32 accumulator, A/B format (kind::f16: 0 = f16,
+// 1 = bf16; kind::f8f6f4: 0 = e4m3), both K-major, N >> 3 at bit 17,
+// M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_format, uint32_t M, uint32_t N) {
     return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }

@@ -43,7 +43,8 @@ class ebc_stats(ctypes.Structure):
 class ebc_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("bulk_launches", ctypes.c_int64), ("bulk_ms", ctypes.c_double),
                 ("bulk_evals", ctypes.c_int64), ("refine_launches", ctypes.c_int64), ("refine_ms", ctypes.c_double),
-                ("eval_launches", ctypes.c_int64), ("eval_ms", ctypes.c_double)]
+                ("eval_launches", ctypes.c_int64), ("eval_ms", ctypes.c_double),
+                ("list_launches", ctypes.c_int64), ("list_ms", ctypes.c_double)]
 
 
 class ebc_batch_info(ctypes.Structure):
