@@ -442,6 +442,8 @@ def main():
     ap.add_argument("--no-lazy", action="store_true", help="regime: skip the lazy comparison; serve: full rounds")
     ap.add_argument("--lazy-min-n", type=int, default=100_000, help="serve: lazy rounds from this n")
     ap.add_argument("--greedy", default="full", choices=["full", "lazy"], help="regime/small: round kind timed")
+    ap.add_argument("--autotune", type=int, default=0, help="regime/small: autotune the bulk kernel first (reps)")
+    ap.add_argument("--tune-file", default="", help="save the tuning table here after autotuning")
     ap.add_argument("--fp32-rounds", type=int, default=3, help="rounds of the FP32 plain comparison")
     ap.add_argument("--ref-cands", type=int, default=64, help="reference arm: candidates per step")
     args = ap.parse_args()
@@ -485,6 +487,13 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     lazy_main = args.greedy == "lazy" and args.prec != "fp32"
     inst = ebc.Instance(Vd, precision=args.prec, refine_k=args.refine_k, stream=stream, lazy=lazy_main)
+    tuned = None
+    if args.autotune > 0 and args.prec != "fp32":
+        t0 = time.perf_counter()
+        inst.autotune(args.autotune)  # outside the timed region; results do not depend on it
+        tuned = {"reps": args.autotune, "search_s": time.perf_counter() - t0}
+        if args.tune_file:
+            ebc.ebc_tune_save(args.tune_file)
     out_idx = torch.empty(k, dtype=torch.int32, device=dev)
     out_f = torch.empty(k, dtype=torch.float64, device=dev)
 
@@ -567,6 +576,7 @@ def main():
             "config": {"workload": wname + (" (lazy rounds)" if lazy_main else ""), "n": n, "d": d, "k": k,
                        "precision": args.prec, "refine_k": args.refine_k,
                        "greedy": "lazy rounds: value counts the evaluations performed" if lazy_main else "full rounds",
+                       "autotune": tuned,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write, outside the step events)",
                        "evals_per_step": evals_step, "wall_s_timed_region": t_wall},

@@ -194,6 +194,27 @@ ebc_status ebc_set_max_ctas(ebc_t h, int32_t max_ctas);
  */
 ebc_status ebc_set_lazy(ebc_t h, int32_t on);
 
+/*
+ * Autotuner of the tensor-core bulk kernel.  The kernel's pipeline shape
+ * (candidate-tile buffers x point-tile stages that fit shared memory) and
+ * its V-chunk policy (load-balance model, twice or half as many chunks) are
+ * timed with CUDA events on this handle (reps timed launches each, fastest
+ * kept) and the fastest is stored in a process-wide table keyed by
+ * (precision, padded d, floor(log2 n)); later bulk launches of any handle in
+ * that bucket use it.  Synchronises the handle's stream; leaves the Greedy
+ * state unchanged.  Results (picks, f) do not depend on the configuration.
+ * EINVAL at EBC_FP32 or reps outside [1, 100].
+ */
+ebc_status ebc_autotune(ebc_t h, int32_t reps);
+
+/* The tuning table: save as JSON, merge a saved file (EINVAL for an
+ * unreadable or malformed file; the table is then unchanged), count and
+ * clear its entries. */
+ebc_status ebc_tune_save(const char *path);
+ebc_status ebc_tune_load(const char *path);
+int64_t ebc_tune_count(void);
+ebc_status ebc_tune_clear(void);
+
 /* Replay Greedy rounds from a captured CUDA graph (1, the default) or issue
  * every kernel directly (0).  Graph replay needs a non-NULL stream and is
  * not used while profiling is on. */
@@ -333,6 +354,11 @@ ebc_status ebc_batch_run(ebc_batch_t b);
  * Admission goes in arrival order, but a request that cannot start yet
  * (memory or this limit) does not hold back later requests that can. */
 ebc_status ebc_batch_set_large(ebc_batch_t b, int64_t large_n, int32_t max_ctas, int32_t max_active);
+
+/* Autotune (ebc_autotune with `reps`) the first instance of every new
+ * (precision, d, n bucket) at admission; 0 (the default) disables.
+ * Admitting such an instance then blocks the caller for the search. */
+ebc_status ebc_batch_set_autotune(ebc_batch_t b, int32_t reps);
 
 /* Lazy Greedy (ebc_set_lazy) for the instances admitted from now on whose
  * n >= min_n (on = 1), or for none (on = 0, the default).  Results are

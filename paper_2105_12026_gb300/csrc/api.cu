@@ -552,6 +552,70 @@ ebc_status ebc_get_stats(ebc_t h, ebc_stats *out) {
     return EBC_OK;
 }
 
+}  // extern "C"
+
+ebc_status ebc::autotune_handle(ebc_t h, int32_t reps, bool only_if_missing) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (c.prec == EBC_FP32) return fail(h, EBC_EINVAL, "ebc_autotune: the FP32 plain kernel has no tuned configuration");
+    if (reps < 1 || reps > 100) return fail(h, EBC_EINVAL, "ebc_autotune: reps must be in [1, 100]");
+    const int RB = ebc::tc_row_bytes(c);
+    if (only_if_missing && ebc::tune_has((int)c.prec, RB, c.n)) return EBC_OK;
+    const bool fp8 = c.prec == EBC_FP8E4M3;
+    CK(h, cudaStreamSynchronize(c.stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(h, cudaEventCreate(&e0));
+    cudaError_t err = cudaEventCreate(&e1);
+    double best = INFINITY;
+    ebc::TuneCfg best_cfg, cfg;
+    auto bulk = [&]() {
+        int nch = 1;
+        return fp8 ? ebc::launch_gains_tc8(c, nullptr, c.n, &nch) : ebc::launch_gains_tc(c, nullptr, c.n, true, &nch);
+    };
+    if (err == cudaSuccess) err = fp8 ? ebc::launch_prep_tc8(c, true) : ebc::launch_prep_tc(c, true);
+    // every shape that fits shared memory x every chunk policy; the fastest
+    // of reps timed launches (after one untimed) counts
+    for (int na = 1; na <= 2 && err == cudaSuccess; ++na)
+        for (int ns = 2; ns <= 6 && err == cudaSuccess; ++ns) {
+            if (!ebc::tc_config_fits(RB, na, ns)) continue;
+            for (int chunk = 0; chunk <= 2 && err == cudaSuccess; ++chunk) {
+                cfg.na = na;
+                cfg.ns = ns;
+                cfg.chunk = chunk;
+                c.tune_force = &cfg;
+                err = bulk();
+                double ms_min = INFINITY;
+                for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+                    err = cudaEventRecord(e0, c.stream);
+                    if (err == cudaSuccess) err = bulk();
+                    if (err == cudaSuccess) err = cudaEventRecord(e1, c.stream);
+                    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                    if (err == cudaSuccess) ms_min = std::min(ms_min, (double)ms);
+                }
+                if (err == cudaSuccess && ms_min < best) {
+                    best = ms_min;
+                    best_cfg = cfg;
+                }
+            }
+        }
+    c.tune_force = nullptr;
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(h, err, "ebc_autotune");
+    ebc::tune_store((int)c.prec, RB, c.n, best_cfg, best);
+    if (h->round_exec) {  // recapture rounds with the tuned configuration
+        cudaGraphExecDestroy(h->round_exec);
+        h->round_exec = nullptr;
+    }
+    return ebc_sync(h);
+}
+
+extern "C" {
+
+ebc_status ebc_autotune(ebc_t h, int32_t reps) { return ebc::autotune_handle(h, reps, false); }
+
 ebc_status ebc_set_lazy(ebc_t h, int32_t on) {
     if (check_handle(h)) return EBC_EINVAL;
     ebc::Ctx &c = h->c;

@@ -58,6 +58,7 @@ struct ebc_batch_ctx {
     int32_t large_ctas = 0;
     int32_t lazy = 0;         // lazy Greedy for admitted instances with n >= lazy_min_n (ebc_batch_set_lazy)
     int64_t lazy_min_n = 0;
+    int32_t tune_reps = 0;    // autotune each new (precision, d, n bucket) on admission (ebc_batch_set_autotune)
     int32_t max_large = 0;    // at most this many large instances at once (0 = no limit)
     int64_t budget = 0, used = 0, peak = 0;
     int64_t next_ticket = 1, submitted = 0, completed = 0, rounds = 0;
@@ -166,6 +167,7 @@ void admit(ebc_batch_t b) {
             st = ebc::set_precision_handle(h, r.prec, b->refine_k, false);
         if (st == EBC_OK && large && b->large_ctas > 0) st = ebc_set_max_ctas(h, b->large_ctas);
         if (st == EBC_OK && b->lazy && r.n >= b->lazy_min_n) st = ebc_set_lazy(h, 1);
+        if (st == EBC_OK && b->tune_reps > 0 && r.prec != EBC_FP32) st = ebc::autotune_handle(h, b->tune_reps, true);
         if (st != EBC_OK) {
             ebc_batch_ctx::Result res;
             res.status = st;
@@ -351,6 +353,12 @@ ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out) {
     out->bytes_in_use = b->used;
     out->bytes_peak = b->peak;
     out->rounds_issued = b->rounds;
+    return EBC_OK;
+}
+
+ebc_status ebc_batch_set_autotune(ebc_batch_t b, int32_t reps) {
+    if (!b || reps < 0 || reps > 100) return EBC_EINVAL;
+    b->tune_reps = reps;
     return EBC_OK;
 }
 

@@ -73,6 +73,13 @@ __host__ __device__ inline int pick_chunks(int64_t m, int n_vtiles, int G, int64
     return (n_vtiles + vpc - 1) / vpc;
 }
 
+// A tuned configuration of the tensor-core bulk kernel (tune.cu).
+struct TuneCfg {
+    int na = 0;     // candidate-tile buffers (1, 2)
+    int ns = 0;     // point-tile stages (2..6)
+    int chunk = 0;  // V-chunk policy: 0 load-balance model, 1 twice the chunks, 2 half
+};
+
 // Scratch / resident buffers of one handle.
 struct Ctx {
     int64_t n = 0;
@@ -148,6 +155,7 @@ struct Ctx {
     } tc8;
     int num_sms = 152;
     int max_ctas = 0;  // cap on persistent-kernel CTAs (0 = one per SM)
+    const TuneCfg *tune_force = nullptr;  // set by the autotuner while it times a configuration
 
     // scratch
     double *partial = nullptr;  // [nchunk_cap, n] per-V-chunk partial sums of the bulk gains
@@ -198,6 +206,9 @@ void pool_free(void *p, cudaStream_t s);
 ebc_status create_handle(const float *V, int64_t n, int32_t d, int32_t v_on_device, void *stream, bool sync,
                          ebc_t *out);
 ebc_status set_precision_handle(ebc_t h, ebc_prec prec, int32_t refine_k, bool sync);
+// time the bulk kernel's configurations for this handle's precision and n
+// bucket and store the fastest (only_if_missing: skip a bucket already tuned)
+ebc_status autotune_handle(ebc_t h, int32_t reps, bool only_if_missing);
 int64_t handle_bytes(int64_t n, int32_t d, ebc_prec prec);
 
 // ---- launchers (defined in the .cu files) --------------------------------
@@ -206,6 +217,14 @@ cudaError_t launch_reset_state(Ctx &c);
 cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, int64_t chunk, int nchunks);
 cudaError_t launch_reduce_select(Ctx &c, int64_t m, int nchunks, const int *cand, bool greedy,
                                  double *out_gain, int nblk);
+// tuning table (tune.cu)
+bool tune_lookup(const Ctx &c, int prec, int RB, int64_t n, TuneCfg *cfg);
+bool tune_has(int prec, int RB, int64_t n);
+void tune_store(int prec, int RB, int64_t n, const TuneCfg &cfg, double ms);
+int apply_chunk_mode(int nchunks, int mode, int n_vtiles, int64_t cap, int *vt_per_chunk);
+bool tc_config_fits(int RB, int na, int ns);  // k_tc.cu: shared memory of a pipeline shape fits
+int tc_row_bytes(const Ctx &c);              // k_tc.cu: row bytes of the current precision's bulk operand
+
 // few-candidate passes over V, one warp per point (k_few.cu); d <= 256
 bool few_supported(const Ctx &c);
 // lists longer than max_cnt are skipped (left to the tiled bound kernel)

@@ -1112,6 +1112,21 @@ cudaError_t allow_smem(const void *kernel, uint32_t bytes) {
     return e;
 }
 
+// Pipeline shape and chunk policy for a bulk launch: the largest shape that
+// fits shared memory, unless the tuning table (or the autotuner) says otherwise.
+void choose_config(const Ctx &c, int prec, int RB, int *na, int *ns, int *chunk_mode) {
+    pick_pipeline(RB, na, ns);
+    *chunk_mode = 0;
+    TuneCfg t;
+    if (tune_lookup(c, prec, RB, c.n, &t)) {
+        if (t.ns >= 2 && t.na >= 1 && (int)smem_layout(RB, t.ns, t.na).total <= SMEM_LIMIT) {
+            *na = t.na;
+            *ns = t.ns;
+        }
+        *chunk_mode = t.chunk;
+    }
+}
+
 double gamma_for(int DP) { return ((double)(DP + KEXT) / 4.0 + 4.0) * ldexp(1.0, -22); }
 
 // FP8: the tensor core's internal sum of each 32-product block is assumed
@@ -1122,6 +1137,15 @@ double gamma8_for(int DP) { return ldexp(1.0, -8) + gamma_for(DP); }
 }  // namespace
 
 bool tc_supported(const Ctx &c) { return c.d <= 128; }
+
+bool tc_config_fits(int RB, int na, int ns) {
+    return na >= 1 && na <= 2 && ns >= 2 && ns <= 6 && (int)smem_layout(RB, ns, na).total <= SMEM_LIMIT;
+}
+
+int tc_row_bytes(const Ctx &c) {
+    if (c.prec == EBC_FP8E4M3) return (c.d + 127) / 128 * 128;
+    return 2 * ((c.d + KATOM - 1) / KATOM * KATOM);
+}
 
 void tc8_free(Ctx &c) {
     Ctx::Tc8 &T = c.tc8;
@@ -1190,8 +1214,8 @@ cudaError_t launch_prep_tc8(Ctx &c, bool upper) {
 
 cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks_out) {
     Ctx::Tc8 &T = c.tc8;
-    int na = 0, ns = 0;
-    pick_pipeline(T.DP, &na, &ns);
+    int na = 0, ns = 0, chunk_mode = 0;
+    choose_config(c, EBC_FP8E4M3, T.DP, &na, &ns, &chunk_mode);
     if (ns == 0) return cudaErrorInvalidConfiguration;
     const SmemLayout L = smem_layout(T.DP, ns, na);
     if (cudaError_t e = allow_smem((const void *)k_gains_tc8, L.total); e != cudaSuccess) return e;
@@ -1207,6 +1231,9 @@ cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks_ou
     a.n_ctiles = (int)((m + BM - 1) / BM);
     const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
     a.nchunks = pick_chunks(m, a.n_vtiles, G, c.partial_cap, &a.vt_per_chunk);
+    if (chunk_mode)
+        a.nchunks = apply_chunk_mode(a.nchunks, chunk_mode, a.n_vtiles, c.partial_cap / std::max<int64_t>(m, 1),
+                                     &a.vt_per_chunk);
     a.RB = T.DP;
     a.xatom = 128;
     a.nstages = ns;
@@ -1294,8 +1321,8 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     (void)upper;  // the mode is carried by the point extension written by launch_prep_tc
     Ctx::Tc &T = c.tc;
     const int DP = T.DP;
-    int na = 0, ns = 0;
-    pick_pipeline(2 * DP, &na, &ns);
+    int na = 0, ns = 0, chunk_mode = 0;
+    choose_config(c, T.prec, 2 * DP, &na, &ns, &chunk_mode);
     if (ns == 0) return cudaErrorInvalidConfiguration;
     const SmemLayout L = smem_layout(2 * DP, ns, na);
     if (cudaError_t e = allow_smem((const void *)k_gains_tc, L.total); e != cudaSuccess) return e;
@@ -1313,6 +1340,9 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     // V chunks: balance the persistent grid (units = candidate tiles x chunks)
     const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
     a.nchunks = pick_chunks(m, a.n_vtiles, G, c.partial_cap, &a.vt_per_chunk);
+    if (chunk_mode)
+        a.nchunks = apply_chunk_mode(a.nchunks, chunk_mode, a.n_vtiles, c.partial_cap / std::max<int64_t>(m, 1),
+                                     &a.vt_per_chunk);
     a.m_dev = nullptr;
     a.partial_cap = c.partial_cap;
     a.G = G;

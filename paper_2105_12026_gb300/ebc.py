@@ -76,6 +76,12 @@ _SIGS = {
     "ebc_greedy_host": [_P, _I32, _P, _P],
     "ebc_set_graphs": [_P, _I32],
     "ebc_set_lazy": [_P, _I32],
+    "ebc_autotune": [_P, _I32],
+    "ebc_tune_save": [ctypes.c_char_p],
+    "ebc_tune_load": [ctypes.c_char_p],
+    "ebc_tune_count": [],
+    "ebc_tune_clear": [],
+    "ebc_batch_set_autotune": [_P, _I32],
     "ebc_set_max_ctas": [_P, _I32],
     "ebc_batch_set_large": [_P, _I64, _I32, _I32],
     "ebc_batch_set_lazy": [_P, _I32, _I64],
@@ -120,6 +126,7 @@ def load(path: str | None = None):
             lib.ebc_noalloc_last_error.restype = ctypes.c_char_p
             lib.ebc_batch_last_error.restype = ctypes.c_char_p
             lib.ebc_estimate_bytes.restype = ctypes.c_int64
+            lib.ebc_tune_count.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -226,6 +233,26 @@ def ebc_set_graphs(h: int, on: bool) -> None:
     _raise(h, load().ebc_set_graphs(_P(h), int(bool(on))))
 
 
+def ebc_autotune(h: int, reps: int = 3) -> None:
+    _raise(h, load().ebc_autotune(_P(h), int(reps)))
+
+
+def ebc_tune_save(path: str) -> None:
+    _raise(None, load().ebc_tune_save(path.encode()))
+
+
+def ebc_tune_load(path: str) -> None:
+    _raise(None, load().ebc_tune_load(path.encode()))
+
+
+def ebc_tune_count() -> int:
+    return int(load().ebc_tune_count())
+
+
+def ebc_tune_clear() -> None:
+    _raise(None, load().ebc_tune_clear())
+
+
 def ebc_set_lazy(h: int, on: bool) -> None:
     _raise(h, load().ebc_set_lazy(_P(h), int(bool(on))))
 
@@ -317,6 +344,9 @@ class Instance:
 
     def set_lazy(self, on: bool = True):
         ebc_set_lazy(self.h, on)
+
+    def autotune(self, reps: int = 3):
+        ebc_autotune(self.h, reps)
 
     def set_precision(self, precision: str, refine_k: int = 8):
         ebc_set_precision(self.h, PRECISIONS[precision], refine_k)
@@ -429,6 +459,9 @@ class Batch:
 
     def set_large(self, large_n: int, max_ctas: int, max_active: int = 0):
         self._err(load().ebc_batch_set_large(_P(self.h), int(large_n), int(max_ctas), int(max_active)))
+
+    def set_autotune(self, reps: int = 3):
+        self._err(load().ebc_batch_set_autotune(_P(self.h), int(reps)))
 
     def set_lazy(self, on: bool = True, min_n: int = 0):
         self._err(load().ebc_batch_set_lazy(_P(self.h), int(bool(on)), int(min_n)))

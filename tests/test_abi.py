@@ -93,3 +93,35 @@ def test_batch_create_rejects_bad_arguments(lib):
     assert lib.ebc_batch_create(4, 0, 8, ctypes.byref(h)) == ebc.EBC_EINVAL
     assert lib.ebc_batch_create(4, 1 << 30, 0, ctypes.byref(h)) == ebc.EBC_EINVAL
     assert lib.ebc_batch_submit(None, None, 10, 4, 2, 0, None) == ebc.EBC_EINVAL
+
+
+def test_tune_table_json_roundtrip(lib, tmp_path):
+    """The tuning table persists as JSON; malformed files are rejected and
+    leave the table unchanged (no GPU needed)."""
+    ebc.ebc_tune_clear()
+    assert ebc.ebc_tune_count() == 0
+    good = tmp_path / "tune.json"
+    good.write_text('{"version": 1, "entries": [\n'
+                    ' {"prec": 1, "rb": 256, "nbucket": 17, "na": 1, "ns": 2, "chunk": 0, "ms": 7.2},\n'
+                    ' {"ns": 3, "na": 2, "prec": 3, "rb": 128, "nbucket": 12, "chunk": 1}\n]}\n')
+    ebc.ebc_tune_load(str(good))
+    assert ebc.ebc_tune_count() == 2
+    out = tmp_path / "out.json"
+    ebc.ebc_tune_save(str(out))
+    ebc.ebc_tune_clear()
+    ebc.ebc_tune_load(str(out))
+    assert ebc.ebc_tune_count() == 2
+    text = out.read_text()
+    assert '"rb": 256' in text and '"chunk": 1' in text
+    for bad in ['{"entries": [{"prec": 1, "rb": 256}]}',
+                '{"entries": [{"prec": 9, "rb": 256, "nbucket": 3, "na": 1, "ns": 2, "chunk": 0}]}',
+                'not json']:
+        p = tmp_path / "bad.json"
+        p.write_text(bad)
+        with pytest.raises(ebc.EbcError) as ei:
+            ebc.ebc_tune_load(str(p))
+        assert ei.value.status == ebc.EBC_EINVAL
+    assert ebc.ebc_tune_count() == 2
+    with pytest.raises(ebc.EbcError):
+        ebc.ebc_tune_load(str(tmp_path / "missing.json"))
+    ebc.ebc_tune_clear()
