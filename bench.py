@@ -411,6 +411,79 @@ def run_sets(args):
     return 0
 
 
+def run_sets_sweep(args):
+    """Multi-set evaluation over the grid of the paper's runtime study (Sec. 5,
+    Fig. 2 shape: d = 100, defaults N = 50,000, l = 5,000 sets of k = 10
+    members, each of N, l, k varied), FP32 plain vs BF16 tensor cores, plus
+    the case-study shape (Greedy on n = 1,000, d = 3,524, FP32: the tensor
+    path needs d <= 128).  Synthetic GMM points and uniform random sets."""
+    import torch
+
+    from paper_2105_12026_gb300 import ebc, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    d = 100
+    grid = [(50_000, 5_000, 10)]
+    grid += [(N, 5_000, 10) for N in (1_000, 10_000, 100_000, 400_000)]
+    grid += [(50_000, l, 10) for l in (1_000, 26_070)]
+    grid += [(50_000, 5_000, k) for k in (100, 430)]
+    rows = []
+    for (N, l, k) in grid:
+        rng = np.random.default_rng(args.seed + N + l + k)
+        V = synth.zscore_to_f32(synth.gaussian_mixture(rng, N, d, 32, sigma=None))
+        idx, off = synth.random_sets(rng, N, l, k, k)
+        Vd = torch.from_numpy(V).to(dev)
+        idx_d, off_d = torch.from_numpy(idx).to(dev), torch.from_numpy(off).to(dev)
+        out = torch.empty(l, dtype=torch.float64, device=dev)
+        inst = ebc.Instance(Vd, stream=stream)
+        row = {"N": N, "l": l, "k": k, "pairs": N * int(off[-1])}
+        for prec in ("fp32", "bf16"):
+            inst.set_precision(prec)
+            ebc.ebc_eval_sets(inst.h, idx_d.data_ptr(), off_d.data_ptr(), l, out.data_ptr())
+            inst.sync()
+            ms = []
+            for _ in range(max(1, args.steps)):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ebc.ebc_eval_sets(inst.h, idx_d.data_ptr(), off_d.data_ptr(), l, out.data_ptr())
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            inst.sync()
+            row[prec + "_ms"] = min(ms)
+            row[prec + "_pairs_per_s"] = row["pairs"] / (min(ms) / 1e3)
+        row["bf16_over_fp32"] = row["fp32_ms"] / row["bf16_ms"]
+        inst.close()
+        rows.append(row)
+        del Vd, idx_d, off_d, out
+    # case-study shape: Greedy on 1,000 cycles of 3,524 features
+    rng = np.random.default_rng(args.seed)
+    Vc = synth.zscore_to_f32(synth.gaussian_mixture(rng, 1_000, 3_524, 8, sigma=None))
+    with ebc.Instance(torch.from_numpy(Vc).to(dev), stream=stream) as inst:
+        inst.greedy(10)
+        inst.reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        inst.greedy(10)
+        b.record(stream)
+        torch.cuda.synchronize()
+        case_ms = a.elapsed_time(b)
+    base = rows[0]
+    line = {"metric": METRIC, "value": base["bf16_pairs_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": base["bf16_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (32-cluster GMM, z-scored; uniform random sets)",
+            "config": {"workload": "multi-set evaluation sweep, d=100 (N, l, k grid around N=50,000 l=5,000 k=10)",
+                       "l2": "flushed between calls"},
+            "sweep": rows,
+            "case_study": {"workload": "Greedy k=10 on n=1,000 d=3,524 (FP32 plain path)", "ms": case_ms}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,7 +492,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
     ap.add_argument("--refine-k", type=int, default=8)
-    ap.add_argument("--workload", default="regime", choices=["regime", "small", "mix", "serve", "sets"])
+    ap.add_argument("--workload", default="regime", choices=["regime", "small", "mix", "serve", "sets", "sets-sweep"])
     ap.add_argument("--sets", type=int, default=1024, help="sets: number of CSR sets")
     ap.add_argument("--instances", type=int, default=256, help="mix: number of instances")
     ap.add_argument("--slots", type=int, default=32, help="mix/serve: concurrent instances")
@@ -455,6 +528,8 @@ def main():
         return run_mix(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sets-sweep":
+        return run_sets_sweep(args)
     if args.workload == "sets":
         if args.n == 200_000 and args.d == 128:
             args.n, args.d = 50_000, 64

@@ -257,6 +257,21 @@ ebc_status ebc_get_profile(ebc_t h, ebc_profile *out);
 /* Zero the counters. */
 ebc_status ebc_reset_profile(ebc_t h);
 
+/*
+ * Snapshot of the Greedy state (the per-point minima m_v of Sec. 4's
+ * incremental evaluation, the selected set S, f(S) and the round counters),
+ * for pre-empting an instance and resuming it later in this or another
+ * handle over the same V: a Greedy continued from a loaded snapshot makes the
+ * same picks with the same f as one that was never interrupted.  The buffer
+ * is host memory of ebc_state_size bytes, owned by the caller.  Save
+ * synchronises the stream (and reports a pending device error instead of
+ * saving); load checks the snapshot (EINVAL for another shape, a truncated
+ * buffer or inconsistent contents) and restarts lazy bounds.
+ */
+ebc_status ebc_state_size(ebc_t h, int64_t *bytes);
+ebc_status ebc_state_save(ebc_t h, void *host_buf, int64_t bytes);
+ebc_status ebc_state_load(ebc_t h, const void *host_buf, int64_t bytes);
+
 /* f(S) of the current Greedy state, computed on the device (synchronises). */
 ebc_status ebc_current_f(ebc_t h, double *out_f);
 

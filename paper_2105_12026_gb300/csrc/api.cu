@@ -628,6 +628,92 @@ ebc_status ebc_set_lazy(ebc_t h, int32_t on) {
     return EBC_OK;
 }
 
+// ---- Greedy state snapshot (for pre-empting and resuming an instance) ----
+// Layout: header, then m_v (f64 [n]) and the selection flags (u8 [n]).
+namespace {
+struct StateHeader {
+    uint64_t magic;  // "EBCSTATE"
+    int32_t version, d;
+    int64_t n, nsel;
+    double f;        // f(S)
+    int64_t rounds, certified, escalated_rounds, escalated_cands, exact_evals, bulk_cands;
+    int32_t round, reserved;
+};
+constexpr uint64_t kStateMagic = 0x4554415453434245ull;  // "EBCSTATE" little-endian
+}  // namespace
+
+ebc_status ebc_state_size(ebc_t h, int64_t *bytes) {
+    if (check_handle(h) || !bytes) return fail(h, EBC_EINVAL, "ebc_state_size: NULL argument");
+    *bytes = (int64_t)sizeof(StateHeader) + h->c.n * (8 + 1);
+    return EBC_OK;
+}
+
+ebc_status ebc_state_save(ebc_t h, void *host_buf, int64_t bytes) {
+    if (check_handle(h) || !host_buf) return fail(h, EBC_EINVAL, "ebc_state_save: NULL argument");
+    ebc::Ctx &c = h->c;
+    if (bytes < (int64_t)sizeof(StateHeader) + c.n * 9) return fail(h, EBC_EINVAL, "ebc_state_save: buffer too small");
+    ebc_status s0 = ebc_sync(h);  // a pending device error would make the snapshot meaningless
+    if (s0 != EBC_OK) return s0;
+    ebc::DevState st;
+    uint8_t *buf = static_cast<uint8_t *>(host_buf);
+    CK(h, cudaMemcpyAsync(&st, c.st, sizeof(st), cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaMemcpyAsync(buf + sizeof(StateHeader), c.m64, sizeof(double) * c.n, cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaMemcpyAsync(buf + sizeof(StateHeader) + 8 * c.n, c.sel, c.n, cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaStreamSynchronize(c.stream));
+    StateHeader hd;
+    memset(&hd, 0, sizeof hd);
+    hd.magic = kStateMagic;
+    hd.version = 1;
+    hd.d = c.d;
+    hd.n = c.n;
+    hd.nsel = h->nsel;
+    hd.f = st.f;
+    hd.rounds = st.rounds;
+    hd.certified = st.certified;
+    hd.escalated_rounds = st.escalated_rounds;
+    hd.escalated_cands = st.escalated_cands;
+    hd.exact_evals = st.exact_evals;
+    hd.bulk_cands = st.bulk_cands;
+    hd.round = st.round;
+    memcpy(buf, &hd, sizeof hd);
+    return EBC_OK;
+}
+
+ebc_status ebc_state_load(ebc_t h, const void *host_buf, int64_t bytes) {
+    if (check_handle(h) || !host_buf) return fail(h, EBC_EINVAL, "ebc_state_load: NULL argument");
+    ebc::Ctx &c = h->c;
+    StateHeader hd;
+    if (bytes < (int64_t)sizeof hd) return fail(h, EBC_EINVAL, "ebc_state_load: buffer too small");
+    memcpy(&hd, host_buf, sizeof hd);
+    if (hd.magic != kStateMagic || hd.version != 1) return fail(h, EBC_EINVAL, "ebc_state_load: not a state snapshot");
+    if (hd.n != c.n || hd.d != c.d) return fail(h, EBC_EINVAL, "ebc_state_load: snapshot of an instance of another shape");
+    if (bytes < (int64_t)sizeof hd + c.n * 9 || hd.nsel < 0 || hd.nsel > c.n || hd.round < 0)
+        return fail(h, EBC_EINVAL, "ebc_state_load: truncated or inconsistent snapshot");
+    const uint8_t *buf = static_cast<const uint8_t *>(host_buf);
+    int64_t nsel = 0;
+    for (int64_t i = 0; i < c.n; ++i) nsel += buf[sizeof hd + 8 * c.n + i] ? 1 : 0;
+    if (nsel != hd.nsel) return fail(h, EBC_EINVAL, "ebc_state_load: selection flags do not match the header");
+    CK(h, ebc::launch_reset_state(c));  // zero the device scalars (and restart any lazy bounds)
+    CK(h, cudaMemcpyAsync(c.m64, buf + sizeof hd, sizeof(double) * c.n, cudaMemcpyHostToDevice, c.stream));
+    CK(h, cudaMemcpyAsync(c.sel, buf + sizeof hd + 8 * c.n, c.n, cudaMemcpyHostToDevice, c.stream));
+    ebc::DevState st;
+    CK(h, cudaMemcpyAsync(&st, c.st, sizeof(st), cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaStreamSynchronize(c.stream));
+    st.f = hd.f;
+    st.rounds = hd.rounds;
+    st.certified = hd.certified;
+    st.escalated_rounds = hd.escalated_rounds;
+    st.escalated_cands = hd.escalated_cands;
+    st.exact_evals = hd.exact_evals;
+    st.bulk_cands = hd.bulk_cands;
+    st.round = hd.round;
+    CK(h, cudaMemcpyAsync(c.st, &st, sizeof(st), cudaMemcpyHostToDevice, c.stream));
+    if (c.ub64) CK(h, ebc::launch_lazy_init(c));  // after the flags: selected candidates get -1
+    CK(h, cudaStreamSynchronize(c.stream));
+    h->nsel = hd.nsel;
+    return EBC_OK;
+}
+
 ebc_status ebc_current_f(ebc_t h, double *out_f) {
     if (check_handle(h) || !out_f) return fail(h, EBC_EINVAL, "ebc_current_f: NULL argument");
     ebc::Ctx &c = h->c;

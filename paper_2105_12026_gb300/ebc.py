@@ -76,6 +76,9 @@ _SIGS = {
     "ebc_greedy_host": [_P, _I32, _P, _P],
     "ebc_set_graphs": [_P, _I32],
     "ebc_set_lazy": [_P, _I32],
+    "ebc_state_size": [_P, ctypes.POINTER(_I64)],
+    "ebc_state_save": [_P, _P, _I64],
+    "ebc_state_load": [_P, _P, _I64],
     "ebc_autotune": [_P, _I32],
     "ebc_tune_save": [ctypes.c_char_p],
     "ebc_tune_load": [ctypes.c_char_p],
@@ -347,6 +350,18 @@ class Instance:
 
     def autotune(self, reps: int = 3):
         ebc_autotune(self.h, reps)
+
+    def save_state(self) -> bytes:
+        """Snapshot of the Greedy state (m_v, S, f, counters) as bytes."""
+        size = ctypes.c_int64()
+        _raise(self.h, load().ebc_state_size(_P(self.h), ctypes.byref(size)))
+        buf = (ctypes.c_uint8 * size.value)()
+        _raise(self.h, load().ebc_state_save(_P(self.h), ctypes.cast(buf, _P), size.value))
+        return bytes(buf)
+
+    def load_state(self, snap: bytes):
+        buf = (ctypes.c_uint8 * len(snap)).from_buffer_copy(snap)
+        _raise(self.h, load().ebc_state_load(_P(self.h), ctypes.cast(buf, _P), len(snap)))
 
     def set_precision(self, precision: str, refine_k: int = 8):
         ebc_set_precision(self.h, PRECISIONS[precision], refine_k)
