@@ -99,6 +99,45 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# --- multi-rank helpers (one process per GPU; no collective on the data path) ---
+def rank_env():
+    """(world, rank, local_rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Each replica draws its own instance of the same shape."""
+    return seed + rank
+
+
+def shard(items, rank: int, world: int):
+    """Whole instances are routed to ranks round-robin: disjoint, and together
+    every instance exactly once."""
+    return list(items)[rank::world]
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Timing of the slowest rank (the job ends when the last rank does)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def greedy_evals(n: int, k: int) -> int:
     return sum((n - t) * n for t in range(k))
 
@@ -106,10 +145,10 @@ def greedy_evals(n: int, k: int) -> int:
 def make_workload(args, rank: int):
     from paper_2105_12026_gb300 import synth
     if args.workload == "regime":
-        w = synth.regime_greedy(seed=args.seed + rank, n=args.n, d=args.d, k=args.k)
+        w = synth.regime_greedy(seed=rank_seed(args.seed, rank), n=args.n, d=args.d, k=args.k)
         name = f"greedy drifting-regime features n={args.n} d={args.d} k={args.k}"
     else:
-        w = synth.plain_greedy_small(seed=args.seed + rank, n=args.n, d=args.d)
+        w = synth.plain_greedy_small(seed=rank_seed(args.seed, rank), n=args.n, d=args.d)
         w["k"] = args.k
         name = f"greedy 8-cluster GMM n={args.n} d={args.d} k={args.k}"
     return w["V"], w["k"], name
@@ -180,14 +219,20 @@ def run_mix(args):
     """256 independent Greedy instances (n log-uniform 2k..100k, d in {16,32,64,128},
     k in 5..50) through the batch runtime; one step = submit all, run to completion."""
     import torch
+    import torch.distributed as dist
 
     from paper_2105_12026_gb300 import ebc, synth
-    torch.cuda.set_device(0)
-    specs = synth.instance_mix(seed=args.seed, count=args.instances)
+    world, rank, local = rank_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    all_specs = synth.instance_mix(seed=args.seed, count=args.instances)
+    specs = shard(all_specs, rank, world)  # whole instances per rank
     t0 = time.perf_counter()
     Vs = [sp.make() for sp in specs]
     gen_s = time.perf_counter() - t0
-    evals = sum(instance_evals(sp.n, sp.k) for sp in specs)
+    evals = sum(instance_evals(sp.n, sp.k) for sp in all_specs)
 
     def one_batch():
         with ebc.Batch(max_slots=args.slots, budget_bytes=int(args.budget_gb * (1 << 30)),
@@ -201,23 +246,30 @@ def run_mix(args):
     for _ in range(args.warmup):
         one_batch()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(local)
     clocks.start()
     times = []
     for _ in range(args.steps):
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         st = one_batch()
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t1)
     clk = clocks.stop()
-    tot = sum(times)
-    line = {"metric": METRIC, "value": args.steps * evals / tot, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    tot = max_over_ranks(sum(times), world, dev)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": args.steps * evals / tot, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded GMM instance mix)",
+            "scaling": "strong", "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded GMM instance mix)",
             "config": {"workload": f"batched greedy, {len(specs)} instances: n log-uniform [2000, 100000], "
                                    f"d in {{16,32,64,128}}, k in [5, 50]",
                        "slots": args.slots, "budget_gb": args.budget_gb, "evals_per_step": evals,
+                       "parallelism": f"instances sharded over {world} GPUs" if world > 1 else "single GPU",
                        "timing": "wall clock between device synchronisations; includes host-to-device upload of "
                                  "every instance and the result copies",
                        "host_generation_s": gen_s},
@@ -541,9 +593,7 @@ def main():
     from paper_2105_12026_gb300 import build as _b
     from paper_2105_12026_gb300 import ebc
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
@@ -608,10 +658,7 @@ def main():
     f_bf = out_f.cpu().numpy().copy()
     stats = inst.stats()
 
-    t_max = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_max_ms = float(t_max.item())
+    t_max_ms = max_over_ranks(dev_ms, world, dev)
     evals_step = greedy_evals(n, k)
     if lazy_main:
         # lazy rounds: the evaluations actually performed (bulk candidates x n)
@@ -725,10 +772,8 @@ def main():
             inst.reload(Vh)  # host -> device copy of V inside the step
             hidx, hf = inst.greedy_host(k)  # device -> host read of the picks and f
             e2e_t.append(time.perf_counter() - t0)
-        e2e_s = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-        line["e2e"] = {"value": world * args.steps * evals_step / float(e2e_s.item()), "unit": UNIT,
+        e2e_s = max_over_ranks(sum(e2e_t), world, dev)
+        line["e2e"] = {"value": world * args.steps * evals_step / e2e_s, "unit": UNIT,
                        "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(k * (4 + 8))}
 
     inst.close()
