@@ -222,17 +222,38 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[16], int lane
     return x + __shfl_xor_sync(0xffffffffu, x, 1);
 }
 
-__device__ __forceinline__ float relu_sum32(const uint32_t (&r)[32]) {
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-    for (int i = 0; i < 32; i += 4) {
-        s0 += fmaxf(__uint_as_float(r[i + 0]), 0.f);
-        s1 += fmaxf(__uint_as_float(r[i + 1]), 0.f);
-        s2 += fmaxf(__uint_as_float(r[i + 2]), 0.f);
-        s3 += fmaxf(__uint_as_float(r[i + 3]), 0.f);
-    }
-    return (s0 + s1) + (s2 + s3);
+// Sum of max(0, x) over 4 x 32 accumulator words with packed FP32x2 adds
+// (two FP32 lanes per instruction, each an ordinary FP32 sum of at most 64
+// non-negative terms), then one add across the lanes and the two chains.
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
 }
+
+__device__ __forceinline__ float relu_sum128(const uint32_t (&r0)[32], const uint32_t (&r1)[32],
+                                             const uint32_t (&r2)[32], const uint32_t (&r3)[32]) {
+    unsigned long long a = pack2(0.f, 0.f), b = pack2(0.f, 0.f);
+    auto step = [&](const uint32_t (&r)[32]) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) {
+            const unsigned long long x = pack2(fmaxf(__uint_as_float(r[i]), 0.f), fmaxf(__uint_as_float(r[i + 1]), 0.f));
+            const unsigned long long y =
+                pack2(fmaxf(__uint_as_float(r[i + 2]), 0.f), fmaxf(__uint_as_float(r[i + 3]), 0.f));
+            asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(x));
+            asm("add.rn.f32x2 %0, %0, %1;" : "+l"(b) : "l"(y));
+        }
+    };
+    step(r0);
+    step(r1);
+    step(r2);
+    step(r3);
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(b));
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+    return lo + hi;
+}
+
 
 }  // namespace
 
@@ -438,7 +459,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                     tc::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&t_empty[h]);
-                    const float s = (relu_sum32(r0) + relu_sum32(r1)) + (relu_sum32(r2) + relu_sum32(r3));
+                    const float s = relu_sum128(r0, r1, r2, r3);
                     acc[h] += (double)s;
                 }
             }
