@@ -3,17 +3,18 @@
 // evaluation of Sec. 4): rigorous FP32 gain bounds of a short list, exact
 // gains of the contenders, and m_v <- min(m_v, d(v, c*)).
 //
-// One warp per point: a lane holds 4 (or 8) dimensions of the point (one
-// float4 load per 128 dimensions, coalesced) and the same dimensions of up
-// to 8 candidates in registers; the per-candidate distance is a fixed
-// xor-shuffle tree over the lanes.  Each pass over V reads every point once
-// for up to 8 candidates.
+// A group of LPP lanes holds one point: each lane 4 (or 8) of its dimensions
+// (float4 loads, coalesced) and the same dimensions of up to 8 candidates in
+// registers; a warp holds 32 / LPP points at once (LPP = 8 for d <= 32, 16
+// for d <= 64, 32 above, so that few lanes idle at small d).  Per-candidate
+// distances are fixed xor-shuffle trees within the group.  Each pass over V
+// reads every point once for up to 8 candidates.
 //
 // Rounding.  An FP32 distance formed this way has, along any term's path,
 // the difference's rounding (twice, once squared), at most 8 for the lane's
-// fused multiply-adds (fewer when the lane holds fewer non-zero terms) and 5
-// for the tree, so |s - d| <= (d + 10) 2^-24 d for every d >= 1 (the terms
-// are non-negative); the bound constants below use that.
+// fused multiply-adds (fewer when the lane holds fewer non-zero terms) and at
+// most 5 for the tree, so |s - d| <= (d + 10) 2^-24 d for every d >= 1 (the
+// terms are non-negative); the bound constants below use that.
 #include <float.h>
 #include <math.h>
 
@@ -25,25 +26,25 @@ namespace {
 constexpr int FW = 8;       // warps per block
 constexpr int FC = 8;       // candidates per pass
 constexpr int FDMAX = 256;  // largest d
-constexpr int UNR = 4;      // points in flight per warp
+constexpr int UNR = 4;      // points in flight per lane group
 
 __host__ __device__ inline double few_rho(int d) { return (double)(d + 10) * ldexp(1.0, -24); }
 
-// Lane's dimension k (0 <= k < DL) in the layouts below, or -1.
-//   VEC4: dims 128 * (k / 4) + 4 * lane + k % 4 (d a multiple of 4)
-//   else: dims 32 * k + lane
-template <bool VEC4>
-__device__ __forceinline__ int lane_dim(int k, int lane, int d) {
-    const int i = VEC4 ? 128 * (k >> 2) + 4 * lane + (k & 3) : 32 * k + lane;
+// Dimension k (0 <= k < DL) of the lane with index `sub` in its group, or -1.
+//   VEC4: dims 4 LPP (k / 4) + 4 sub + k % 4 (d a multiple of 4)
+//   else: dims LPP k + sub
+template <bool VEC4, int LPP>
+__device__ __forceinline__ int lane_dim(int k, int sub, int d) {
+    const int i = VEC4 ? 4 * LPP * (k >> 2) + 4 * sub + (k & 3) : LPP * k + sub;
     return i < d ? i : -1;
 }
 
-template <bool VEC4, int DL>
-__device__ __forceinline__ void load_point(const float *__restrict__ row, int lane, int d, float (&x)[DL]) {
+template <bool VEC4, int DL, int LPP>
+__device__ __forceinline__ void load_point(const float *__restrict__ row, int sub, int d, float (&x)[DL]) {
     if (VEC4) {
 #pragma unroll
         for (int j = 0; j < DL / 4; ++j) {
-            const int i = 128 * j + 4 * lane;
+            const int i = 4 * LPP * j + 4 * sub;
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
             if (i < d) a = __ldg(reinterpret_cast<const float4 *>(row + i));
             x[4 * j] = a.x;
@@ -54,7 +55,7 @@ __device__ __forceinline__ void load_point(const float *__restrict__ row, int la
     } else {
 #pragma unroll
         for (int k = 0; k < DL; ++k) {
-            const int i = 32 * k + lane;
+            const int i = LPP * k + sub;
             x[k] = i < d ? __ldg(row + i) : 0.f;
         }
     }
@@ -82,42 +83,51 @@ __device__ __forceinline__ void d2f_bounds(double x, float &up, float &dn) {
     }
 }
 
-// Sums over the 32 lanes of the 8 per-candidate partials s[0..7], as a
-// reduce-scatter: lane l ends with the total of candidate cand_of_lane(l)
-// (4 lanes per candidate).  9 shuffles instead of 8 x 5; every total is
-// still a fixed tree of 5 pair additions over the lanes' partials.
-__device__ __forceinline__ int cand_of_lane(int lane) {
-    return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+// Sums over the group's LPP lanes of the 8 per-candidate partials s[0..7],
+// as a reduce-scatter: offsets LPP/2, LPP/4 and LPP/8 split the candidates
+// between the two halves, smaller offsets add.  The lane with group index
+// sub ends with the total of candidate cand_of(sub) (LPP / 8 lanes per
+// candidate); every total is still a fixed tree of log2(LPP) pair additions
+// over the group's partials.
+template <int LPP>
+__device__ __forceinline__ int cand_of(int sub) {
+    return ((sub & (LPP / 2)) ? 4 : 0) + ((sub & (LPP / 4)) ? 2 : 0) + ((sub & (LPP / 8)) ? 1 : 0);
 }
 
-__device__ __forceinline__ int lane_of_cand(int e) { return ((e >> 2) & 1) * 16 + ((e >> 1) & 1) * 8 + (e & 1) * 4; }
+template <int LPP>
+__device__ __forceinline__ int sub_of_cand(int e) {
+    return ((e >> 2) & 1) * (LPP / 2) + ((e >> 1) & 1) * (LPP / 4) + (e & 1) * (LPP / 8);
+}
 
-__device__ __forceinline__ float reduce_scatter8(const float (&s)[8], int lane) {
+template <int LPP>
+__device__ __forceinline__ float reduce_scatter8(const float (&s)[8], int sub) {
     float t[4], u[2];
-    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+    const bool b1 = sub & (LPP / 2), b2 = sub & (LPP / 4), b3 = sub & (LPP / 8);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float send = b16 ? s[j] : s[j + 4];
-        const float keep = b16 ? s[j + 4] : s[j];
-        t[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        const float send = b1 ? s[j] : s[j + 4];
+        const float keep = b1 ? s[j + 4] : s[j];
+        t[j] = keep + __shfl_xor_sync(0xffffffffu, send, LPP / 2);
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        const float send = b8 ? t[j] : t[j + 2];
-        const float keep = b8 ? t[j + 2] : t[j];
-        u[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        const float send = b2 ? t[j] : t[j + 2];
+        const float keep = b2 ? t[j + 2] : t[j];
+        u[j] = keep + __shfl_xor_sync(0xffffffffu, send, LPP / 4);
     }
-    const float send = b4 ? u[0] : u[1];
-    const float keep = b4 ? u[1] : u[0];
-    float w = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    w += __shfl_xor_sync(0xffffffffu, w, 2);
-    w += __shfl_xor_sync(0xffffffffu, w, 1);
+    const float send = b3 ? u[0] : u[1];
+    const float keep = b3 ? u[1] : u[0];
+    float w = keep + __shfl_xor_sync(0xffffffffu, send, LPP / 8);
+#pragma unroll
+    for (int o = LPP / 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     return w;
 }
 
-__device__ __forceinline__ float warp_sum(float s) {
+// Sum over the group's LPP lanes (fixed xor tree).
+template <int LPP>
+__device__ __forceinline__ float group_sum(float s) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    for (int o = LPP / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 
@@ -130,11 +140,13 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float a, float b) {
     hi = h;
 }
 
-// Double-FP32 squared distance of the lane's dimensions (TwoSum / TwoProduct
-// with explicit round-to-nearest intrinsics, as in the exact gain path), then
-// a fixed xor tree whose pair additions are again TwoSum.
-template <int DL>
-__device__ __forceinline__ double df_dist_warp(const float (&x)[DL], const float (&c)[DL]) {
+// Double-FP32 squared distance of the group's point to c (TwoSum /
+// TwoProduct per dimension with explicit round-to-nearest intrinsics, as in
+// the exact gain path), then a fixed xor tree within the group whose pair
+// additions are again TwoSum.  Every lane of the warp takes part (the
+// shuffles are warp-wide); each group gets its own point's distance.
+template <int DL, int LPP>
+__device__ __forceinline__ double df_dist_group(const float (&x)[DL], const float (&c)[DL]) {
     float hi = 0.f, lo = 0.f;
 #pragma unroll
     for (int k = 0; k < DL; ++k) {
@@ -148,7 +160,7 @@ __device__ __forceinline__ double df_dist_warp(const float (&x)[DL], const float
         df_add(hi, lo, p, t);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = LPP / 2; o > 0; o >>= 1) {
         const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
         const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
         df_add(hi, lo, oh, ol);
@@ -156,8 +168,8 @@ __device__ __forceinline__ double df_dist_warp(const float (&x)[DL], const float
     return (double)hi + (double)lo;
 }
 
-// Stage the group's candidate rows and give each lane its dimensions.
-template <bool VEC4, int DL>
+// Stage the block's candidate rows and give each lane its dimensions.
+template <bool VEC4, int DL, int LPP>
 __device__ __forceinline__ void stage_candidates(const float *__restrict__ V, int d, const int *__restrict__ list,
                                                  int first, int cnt, float (*cs)[FDMAX], float (&c)[FC][DL],
                                                  int &ng) {
@@ -167,12 +179,12 @@ __device__ __forceinline__ void stage_candidates(const float *__restrict__ V, in
         cs[e][i] = e < ng ? V[(int64_t)list[first + e] * d + i] : 0.f;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int sub = threadIdx.x % LPP;
 #pragma unroll
     for (int e = 0; e < FC; ++e)
 #pragma unroll
         for (int k = 0; k < DL; ++k) {
-            const int i = lane_dim<VEC4>(k, lane, d);
+            const int i = lane_dim<VEC4, LPP>(k, sub, d);
             c[e][k] = i >= 0 ? cs[e][i] : 0.f;
         }
 }
@@ -181,17 +193,21 @@ __device__ __forceinline__ void stage_candidates(const float *__restrict__ V, in
 // Rigorous [lo, hi] bounds of the gains of a short device list, as chunk
 // partials out_lo / out_hi[e * nchunks + q] (same contract as the tiled
 // bound kernel).  Terms max(0, mU - kh s) and max(0, mD - kl s) in FP32,
-// summed per candidate by one lane, then over the block's warps in a fixed
-// order.  Lists longer than max_cnt are left to the tiled kernel.
-template <bool VEC4, int DL>
+// summed per candidate by one lane of each group in FP32 over at most 64
+// points (fewer than the 128 terms per FP32 sum the folded bounds are
+// widened for), then in FP64, then over the block's groups in a fixed order.
+// Lists longer than max_cnt are left to the tiled kernel.
+template <bool VEC4, int DL, int LPP>
 __global__ void __launch_bounds__(FW * 32) k_few_bounds(const float *__restrict__ V, int64_t n, int d,
                                                         const double *__restrict__ m64, const int *__restrict__ list,
                                                         const int *__restrict__ count, int cap, int64_t chunk,
                                                         int nchunks, float kh, float kl, double *__restrict__ out_lo,
                                                         double *__restrict__ out_hi, int max_cnt) {
+    constexpr int PPW = 32 / LPP;  // points per warp
     __shared__ __align__(16) float cs[FC][FDMAX];
-    __shared__ double rlo[FW][FC], rhi[FW][FC];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double rlo[FW][PPW][FC], rhi[FW][PPW][FC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / LPP, sub = lane % LPP;
+    const bool owner = (sub & (LPP / 8 - 1)) == 0;  // holds candidate cand_of(sub)'s total
     const int cnt = min(*count, cap);
     if (cnt > max_cnt) return;
     const int groups = (cnt + FC - 1) / FC;
@@ -201,22 +217,20 @@ __global__ void __launch_bounds__(FW * 32) k_few_bounds(const float *__restrict_
         __syncthreads();
         float c[FC][DL];
         int ng;
-        stage_candidates<VEC4, DL>(V, d, list, g * FC, cnt, cs, c, ng);
-        // lane l with l % 4 == 0: candidate cand_of_lane(l).  Terms are summed in FP32 over at most
-        // 64 points (fewer than the 128 terms per FP32 sum the folded bounds
-        // are widened for), then in FP64.
+        stage_candidates<VEC4, DL, LPP>(V, d, list, g * FC, cnt, cs, c, ng);
         double alo = 0.0, ahi = 0.0;
         float flo = 0.f, fhi = 0.f;
         int nterm = 0;
         const int64_t vb = (int64_t)q * chunk, ve = lmin(vb + chunk, n);
-        for (int64_t v0 = vb + (int64_t)warp * UNR; v0 < ve; v0 += (int64_t)FW * UNR) {
+        for (int64_t v0 = vb + (int64_t)warp * PPW * UNR; v0 < ve; v0 += (int64_t)FW * PPW * UNR) {
             float x[UNR][DL];
             double mm[UNR];
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {  // all loads first: UNR points in flight
-                const int64_t v = lmin(v0 + u, ve - 1);
-                load_point<VEC4, DL>(V + v * d, lane, d, x[u]);
-                mm[u] = v0 + u < ve ? m64[v] : -1.0;  // -1: no such point, every term 0
+            for (int u = 0; u < UNR; ++u) {  // all loads first: UNR points per group in flight
+                const int64_t p = v0 + u * PPW + grp;
+                const int64_t v = lmin(p, ve - 1);
+                load_point<VEC4, DL, LPP>(V + v * d, sub, d, x[u]);
+                mm[u] = p < ve ? m64[v] : -1.0;  // -1: no such point, every term 0
             }
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
@@ -237,8 +251,8 @@ __global__ void __launch_bounds__(FW * 32) k_few_bounds(const float *__restrict_
                     }
                     sp[e] = s;
                 }
-                const float s = reduce_scatter8(sp, lane);  // candidate cand_of_lane(lane)
-                if ((lane & 3) == 0) {
+                const float s = reduce_scatter8<LPP>(sp, sub);  // candidate cand_of(sub)
+                if (owner) {
                     fhi += fmaxf(fmaf(-kh, s, mu), 0.f);
                     flo += fmaxf(fmaf(-kl, s, md), 0.f);
                 }
@@ -253,17 +267,18 @@ __global__ void __launch_bounds__(FW * 32) k_few_bounds(const float *__restrict_
         }
         ahi += (double)fhi;
         alo += (double)flo;
-        if ((lane & 3) == 0) {
-            rlo[warp][cand_of_lane(lane)] = alo;
-            rhi[warp][cand_of_lane(lane)] = ahi;
+        if (owner) {
+            rlo[warp][grp][cand_of<LPP>(sub)] = alo;
+            rhi[warp][grp][cand_of<LPP>(sub)] = ahi;
         }
         __syncthreads();
         if (threadIdx.x < ng) {
             double sl = 0.0, sh = 0.0;
-            for (int w = 0; w < FW; ++w) {
-                sl += rlo[w][threadIdx.x];
-                sh += rhi[w][threadIdx.x];
-            }
+            for (int w = 0; w < FW; ++w)
+                for (int r = 0; r < PPW; ++r) {
+                    sl += rlo[w][r][threadIdx.x];
+                    sh += rhi[w][r][threadIdx.x];
+                }
             const int64_t e = (int64_t)g * FC + threadIdx.x;
             out_lo[e * nchunks + q] = sl;
             out_hi[e * nchunks + q] = sh;
@@ -276,14 +291,16 @@ __global__ void __launch_bounds__(FW * 32) k_few_bounds(const float *__restrict_
 // pairs the FP32 screen cannot exclude (a screen s with RD(s kh) >= m_v
 // rounded up, kh = 1 - rho rounded down, proves d >= m_v: the pair
 // contributes exactly 0).
-template <bool VEC4, int DL>
+template <bool VEC4, int DL, int LPP>
 __global__ void __launch_bounds__(FW * 32) k_few_exact(const float *__restrict__ V, int64_t n, int d,
                                                        const double *__restrict__ m64, const int *__restrict__ list,
                                                        const int *__restrict__ count, int cap, int64_t chunk,
                                                        int nchunks, float kh, double *__restrict__ out) {
+    constexpr int PPW = 32 / LPP;
     __shared__ __align__(16) float cs[FC][FDMAX];
-    __shared__ double red[FW][FC];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double red[FW][PPW][FC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / LPP, sub = lane % LPP;
+    const bool owner = (sub & (LPP / 8 - 1)) == 0;
     const int cnt = min(*count, cap);
     const int groups = (cnt + FC - 1) / FC;
     const int64_t items = (int64_t)groups * nchunks;
@@ -292,24 +309,25 @@ __global__ void __launch_bounds__(FW * 32) k_few_exact(const float *__restrict__
         __syncthreads();
         float c[FC][DL];
         int ng;
-        stage_candidates<VEC4, DL>(V, d, list, g * FC, cnt, cs, c, ng);
-        double acc = 0.0;
+        stage_candidates<VEC4, DL, LPP>(V, d, list, g * FC, cnt, cs, c, ng);
+        double acc = 0.0;  // owner lanes: candidate cand_of(sub)
         const int64_t vb = (int64_t)q * chunk, ve = lmin(vb + chunk, n);
-        for (int64_t v0 = vb + (int64_t)warp * UNR; v0 < ve; v0 += (int64_t)FW * UNR) {
+        for (int64_t v0 = vb + (int64_t)warp * PPW * UNR; v0 < ve; v0 += (int64_t)FW * PPW * UNR) {
             float x[UNR][DL];
             double mm[UNR];
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {  // all loads first: UNR points in flight
-                const int64_t v = lmin(v0 + u, ve - 1);
-                load_point<VEC4, DL>(V + v * d, lane, d, x[u]);
-                mm[u] = v0 + u < ve ? m64[v] : -1.0;  // -1: no such point, screened out
+            for (int u = 0; u < UNR; ++u) {  // all loads first: UNR points per group in flight
+                const int64_t p = v0 + u * PPW + grp;
+                const int64_t v = lmin(p, ve - 1);
+                load_point<VEC4, DL, LPP>(V + v * d, sub, d, x[u]);
+                mm[u] = p < ve ? m64[v] : -1.0;  // -1: no such point, screened out
             }
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
                 const double mv = mm[u];
-                if (__double_as_longlong(mv) < 0) continue;  // -1: past the chunk (warp-uniform)
-                float mu, md;
-                d2f_bounds(mv, mu, md);
+                const bool valid = __double_as_longlong(mv) >= 0;  // group-uniform
+                float mu = -1.f, md;
+                if (valid) d2f_bounds(mv, mu, md);
                 float sp[FC];
 #pragma unroll
                 for (int e = 0; e < FC; ++e) {
@@ -321,24 +339,26 @@ __global__ void __launch_bounds__(FW * 32) k_few_exact(const float *__restrict__
                     }
                     sp[e] = s;
                 }
-                const float sall = reduce_scatter8(sp, lane);
+                const float sall = reduce_scatter8<LPP>(sp, sub);
 #pragma unroll
                 for (int e = 0; e < FC; ++e) {
-                    if (e >= ng) break;
-                    const float s = __shfl_sync(0xffffffffu, sall, lane_of_cand(e));
+                    if (e >= ng) break;  // warp-uniform
+                    const float s = __shfl_sync(0xffffffffu, sall, grp * LPP + sub_of_cand<LPP>(e));
                     // d >= s (1 - rho) >= RD(s kh) >= mu >= m_v proves a zero term
-                    if (__fmul_rd(s, kh) < mu) {  // warp-uniform
-                        const double t = mv - df_dist_warp(x[u], c[e]);
-                        if (lane == e && t > 0.0) acc += t;
+                    const bool need = valid && __fmul_rd(s, kh) < mu;  // group-uniform
+                    if (__any_sync(0xffffffffu, need)) {               // the tree needs the whole warp
+                        const double t = mv - df_dist_group<DL, LPP>(x[u], c[e]);
+                        if (need && sub == sub_of_cand<LPP>(e) && t > 0.0) acc += t;
                     }
                 }
             }
         }
-        if (lane < FC) red[warp][lane] = acc;
+        if (owner) red[warp][grp][cand_of<LPP>(sub)] = acc;
         __syncthreads();
         if (threadIdx.x < ng) {
             double s = 0.0;
-            for (int w = 0; w < FW; ++w) s += red[w][threadIdx.x];
+            for (int w = 0; w < FW; ++w)
+                for (int r = 0; r < PPW; ++r) s += red[w][r][threadIdx.x];
             out[((int64_t)g * FC + threadIdx.x) * nchunks + q] = s;
         }
     }
@@ -347,35 +367,36 @@ __global__ void __launch_bounds__(FW * 32) k_few_exact(const float *__restrict__
 // m_v <- min(m_v, d(v, c*)) with d the double-FP32 distance (within about
 // 2^-44 relative; FP32 units only); points whose FP32 screen distance
 // proves d >= m_v keep m_v.
-template <bool VEC4, int DL>
+template <bool VEC4, int DL, int LPP>
 __global__ void __launch_bounds__(FW * 32) k_few_update(const float *__restrict__ V, int64_t n, int d,
                                                         double *__restrict__ m64, DevState *st, float kh) {
+    constexpr int PPW = 32 / LPP;
     __shared__ __align__(16) float cs[FDMAX];
     const int c = st->pick;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->mmax_bits = 0u;  // the next round recomputes max_v m_v
     if (c < 0 || (int64_t)c >= n) return;                           // no valid pick (error already recorded)
     for (int i = threadIdx.x; i < d; i += blockDim.x) cs[i] = V[(int64_t)c * d + i];
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / LPP, sub = lane % LPP;
     float cr[DL];
 #pragma unroll
     for (int k = 0; k < DL; ++k) {
-        const int i = lane_dim<VEC4>(k, lane, d);
+        const int i = lane_dim<VEC4, LPP>(k, sub, d);
         cr[k] = i >= 0 ? cs[i] : 0.f;
     }
     const int64_t gw = (int64_t)blockIdx.x * FW + warp, nw = (int64_t)gridDim.x * FW;
-    for (int64_t v0 = gw * UNR; v0 < n; v0 += nw * UNR) {
+    for (int64_t v0 = gw * PPW * UNR; v0 < n; v0 += nw * PPW * UNR) {
         float x[UNR][DL];
         double mm[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {  // all loads first: UNR points in flight
-            const int64_t v = lmin(v0 + u, n - 1);
-            load_point<VEC4, DL>(V + v * d, lane, d, x[u]);
+        for (int u = 0; u < UNR; ++u) {  // all loads first: UNR points per group in flight
+            const int64_t v = lmin(v0 + u * PPW + grp, n - 1);
+            load_point<VEC4, DL, LPP>(V + v * d, sub, d, x[u]);
             mm[u] = m64[v];
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            if (v0 + u >= n) break;  // warp-uniform
+            const int64_t p = v0 + u * PPW + grp;
             const double mv = mm[u];
             float mu, md;
             d2f_bounds(mv, mu, md);
@@ -385,43 +406,38 @@ __global__ void __launch_bounds__(FW * 32) k_few_update(const float *__restrict_
                 const float df = x[u][k] - cr[k];
                 s = fmaf(df, df, s);
             }
-            s = warp_sum(s);
-            if (__fmul_rd(s, kh) >= mu) continue;  // d >= m_v: m_v stays (warp-uniform)
-            const double de = df_dist_warp(x[u], cr);
-            if (lane == 0 && de < mv) m64[v0 + u] = de;
+            s = group_sum<LPP>(s);
+            const bool need = p < n && __fmul_rd(s, kh) < mu;  // else d >= m_v: m_v stays (group-uniform)
+            if (__any_sync(0xffffffffu, need)) {               // the tree needs the whole warp
+                const double de = df_dist_group<DL, LPP>(x[u], cr);
+                if (need && sub == 0 && de < mv) m64[p] = de;
+            }
         }
     }
 }
 
 bool few_supported(const Ctx &c) { return c.d <= FDMAX; }
 
-// Kernel variant for d: float4 lanes when d is a multiple of 4; 4
-// dimensions per lane up to d = 128, 8 up to 256.
-#define FEW_DISPATCH(CALL)                                      \
-    do {                                                        \
-        if (c.d % 4 == 0) {                                     \
-            if (c.d <= 128) { CALL(true, 4); } else { CALL(true, 8); }   \
-        } else {                                                \
-            if (c.d <= 128) { CALL(false, 4); } else { CALL(false, 8); } \
-        }                                                       \
+// Kernel variant for d: float4 lanes when d is a multiple of 4; lanes per
+// point 8 (d <= 32), 16 (d <= 64) or 32; 4 dimensions per lane, 8 above
+// d = 128.
+#define FEW_DISPATCH(CALL)                \
+    do {                                  \
+        const bool v4 = c.d % 4 == 0;     \
+        if (c.d <= 32) {                  \
+            if (v4) CALL(true, 4, 8);     \
+            else CALL(false, 4, 8);       \
+        } else if (c.d <= 64) {           \
+            if (v4) CALL(true, 4, 16);    \
+            else CALL(false, 4, 16);      \
+        } else if (c.d <= 128) {          \
+            if (v4) CALL(true, 4, 32);    \
+            else CALL(false, 4, 32);      \
+        } else {                          \
+            if (v4) CALL(true, 8, 32);    \
+            else CALL(false, 8, 32);      \
+        }                                 \
     } while (0)
-
-cudaError_t launch_few_bounds(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
-                              int64_t chunk, int nchunks, int max_cnt) {
-    // constants of the bound terms for the warp-tree rounding (see above)
-    const double rho = few_rho(c.d);
-    float kh = (float)(1.0 - rho);
-    if ((double)kh > 1.0 - rho) kh = nextafterf(kh, 0.f);
-    float kl = (float)(1.0 + 2.0 * rho);
-    if ((double)kl < 1.0 + 2.0 * rho) kl = nextafterf(kl, 2.f);
-    const int grid = c.num_sms * 4;
-#define CALL(V4, D)                                                                                             \
-    k_few_bounds<V4, D><<<grid, FW * 32, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk, nchunks, \
-                                                        kh, kl, out_lo, out_hi, max_cnt)
-    FEW_DISPATCH(CALL);
-#undef CALL
-    return cudaGetLastError();
-}
 
 // 1 - rho rounded down: the screen's scale for a proof that d >= m_v
 float few_kh(int d) {
@@ -431,13 +447,29 @@ float few_kh(int d) {
     return kh;
 }
 
+cudaError_t launch_few_bounds(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
+                              int64_t chunk, int nchunks, int max_cnt) {
+    // constants of the bound terms for the lane-tree rounding (see above)
+    const double rho = few_rho(c.d);
+    const float kh = few_kh(c.d);
+    float kl = (float)(1.0 + 2.0 * rho);
+    if ((double)kl < 1.0 + 2.0 * rho) kl = nextafterf(kl, 2.f);
+    const int grid = c.num_sms * 4;
+#define CALL(V4, D, L)                                                                                          \
+    k_few_bounds<V4, D, L><<<grid, FW * 32, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk,       \
+                                                           nchunks, kh, kl, out_lo, out_hi, max_cnt)
+    FEW_DISPATCH(CALL);
+#undef CALL
+    return cudaGetLastError();
+}
+
 cudaError_t launch_few_exact(Ctx &c, const int *list, const int *count, int cap, double *out, int64_t chunk,
                              int nchunks) {
     const int grid = c.num_sms * 4;
     const float kh = few_kh(c.d);
-#define CALL(V4, D)                                                                                            \
-    k_few_exact<V4, D><<<grid, FW * 32, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk, nchunks, \
-                                                       kh, out)
+#define CALL(V4, D, L)                                                                                         \
+    k_few_exact<V4, D, L><<<grid, FW * 32, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk,       \
+                                                          nchunks, kh, out)
     FEW_DISPATCH(CALL);
 #undef CALL
     return cudaGetLastError();
@@ -446,7 +478,7 @@ cudaError_t launch_few_exact(Ctx &c, const int *list, const int *count, int cap,
 cudaError_t launch_few_update(Ctx &c) {
     const int grid = c.num_sms * 8;
     const float kh = few_kh(c.d);
-#define CALL(V4, D) k_few_update<V4, D><<<grid, FW * 32, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, c.st, kh)
+#define CALL(V4, D, L) k_few_update<V4, D, L><<<grid, FW * 32, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, c.st, kh)
     FEW_DISPATCH(CALL);
 #undef CALL
     return cudaGetLastError();
