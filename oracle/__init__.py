@@ -17,6 +17,9 @@ one follows):
 - ``update_m(V, m, c)``         m_v <- min(m_v, d(v, c)) in place
 - ``greedy(V, k, ...)``         Greedy with smallest-index tie-break
 - ``exhaustive_opt(V, k)``      max over |S| = k of f(S), n <= 24
+- ``sieve(V, items, K, thr, patience, ...)``  threshold sieve over a stream
+- ``threshold_ladder(m, K, eps, upper)``  {(1+eps)^i : m <= (1+eps)^i <= upper K m}
+- ``three_sieves(V, items, K, eps, T, m)`` / ``sieve_streaming(V, items, K, eps, m)``
 
 Parity unpinned: none.  Every function is pinned by tests that do not call
 it to produce its own expectation (closed forms, hand-computed fixtures in
@@ -25,6 +28,7 @@ tests/golden/, brute force, invariants, a library cross-check).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -81,6 +85,9 @@ def _load():
                                        ctypes.c_int]
             lib.orc_exhaustive_opt.restype = ctypes.c_int
             lib.orc_exhaustive_opt.argtypes = [_P, _I64, _I32, _I32, _P, _P]
+            lib.orc_sieve.restype = ctypes.c_int
+            lib.orc_sieve.argtypes = [_P, _I64, _I32, _P, _I64, _I32, _P, _I32, _I64, _P, _P, _P, _P, _P, _P,
+                                      _P, _P, _P]
             lib.orc_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -200,3 +207,72 @@ def exhaustive_opt(V, k: int):
     S = np.zeros(max(k, 1), dtype=np.int32)
     _check(_load().orc_exhaustive_opt(_ptr(V), V.shape[0], V.shape[1], int(k), ctypes.byref(out), _ptr(S)))
     return out.value, S[:k].copy()
+
+
+def sieve(V, items, K: int, thresholds, patience: int, m=None, selected=None, f_start: float = 0.0,
+          level: int = 0, rejections: int = 0):
+    """Threshold sieve over the stream ``items`` (see orc_sieve).
+
+    Returns a dict with ``idx`` / ``f`` (accepted items, f after each),
+    ``margin`` (per decided stream position), ``level``, ``rejections``
+    and ``f_end``.  ``m`` / ``selected`` continue from a state and are updated
+    in place (both None: S = {}).
+    """
+    V = _f32(V)
+    n = V.shape[0]
+    items = np.ascontiguousarray(items, dtype=np.int32).ravel()
+    thr = np.ascontiguousarray(thresholds, dtype=np.float64).ravel()
+    if m is None:
+        m = norms(V)
+        selected = np.zeros(n, dtype=np.uint8)
+    assert m.dtype == np.float64 and m.flags.c_contiguous and m.size == n
+    assert selected.dtype == np.uint8 and selected.flags.c_contiguous and selected.size == n
+    idx = np.full(max(K, 1), -1, dtype=np.int32)
+    fv = np.zeros(max(K, 1), dtype=np.float64)
+    margin = np.full(max(items.size, 1), np.nan, dtype=np.float64)
+    f_io = ctypes.c_double(f_start)
+    lev = ctypes.c_int32(level)
+    rej = ctypes.c_int64(rejections)
+    cnt = ctypes.c_int32(0)
+    _check(_load().orc_sieve(_ptr(V), n, V.shape[1], _ptr(items), items.size, int(K), _ptr(thr), thr.size,
+                             int(patience), _ptr(m), _ptr(selected), ctypes.byref(f_io), ctypes.byref(lev),
+                             ctypes.byref(rej), _ptr(idx), _ptr(fv), _ptr(margin), ctypes.byref(cnt)))
+    c = cnt.value
+    return {"idx": idx[:c].copy(), "f": fv[:c].copy(), "margin": margin[:items.size].copy(),
+            "level": lev.value, "rejections": rej.value, "f_end": f_io.value}
+
+
+def threshold_ladder(m_single: float, K: int, eps: float, upper: float = 1.0) -> np.ndarray:
+    """Thresholds {(1+eps)^i : i integer, m <= (1+eps)^i <= upper K m}, largest first.
+
+    The candidate values of OPT that Sieve Streaming (upper = 2) and Three
+    Sieves (upper = 1) walk; each value is (1+eps)**i in double.
+    """
+    if not (m_single > 0.0 and eps > 0.0 and K >= 1 and upper > 0.0):
+        raise ValueError("threshold_ladder needs m > 0, eps > 0, K >= 1, upper > 0")
+    base = 1.0 + eps
+    hi = upper * K * m_single
+    i = math.floor(math.log(m_single) / math.log(base)) - 2
+    while base ** i < m_single:
+        i += 1
+    out = []
+    while base ** i <= hi:
+        out.append(base ** i)
+        i += 1
+    return np.array(out[::-1], dtype=np.float64)
+
+
+def three_sieves(V, items, K: int, eps: float, T: int, m_single: float):
+    """Three Sieves: one summary, thresholds from K m down to m, moving down
+    after T consecutive rejections."""
+    return sieve(V, items, K, threshold_ladder(m_single, K, eps, 1.0), T)
+
+
+def sieve_streaming(V, items, K: int, eps: float, m_single: float):
+    """Sieve Streaming with a known largest singleton value m: one sieve per
+    threshold of the ladder up to 2 K m; returns (best sieve's result,
+    all results, thresholds)."""
+    thr = threshold_ladder(m_single, K, eps, 2.0)
+    res = [sieve(V, items, K, [v], 0) for v in thr]
+    best = max(range(len(res)), key=lambda j: (res[j]["f_end"], -j))
+    return res[best], res, thr

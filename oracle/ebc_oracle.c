@@ -16,7 +16,10 @@
  *     scale by 1/|V|, return the difference of the two losses;
  *   - discrete derivative Delta_f(e|S) = f(S u {e}) - f(S) (Sec. 3, Def. 1);
  *   - Greedy: each step adds the not-yet-selected item of largest marginal
- *     gain (Sec. 3 and Sec. 4.1).
+ *     gain (Sec. 3 and Sec. 4.1);
+ *   - the threshold sieve of the streaming optimisers the paper names
+ *     (Sec. 2, Sec. 4.1, Fig. 4): accept a streamed item when its marginal
+ *     gain reaches (v/2 - f(S)) / (K - |S|).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - e0 is fixed to the zero vector;
@@ -320,6 +323,81 @@ int orc_exhaustive_opt(const float *V, int64_t n, int32_t d, int32_t k, double *
         }
     }
     *out_f = best;
+    return ORC_OK;
+}
+
+/*
+ * Threshold sieve over a stream: the decision rule shared by the streaming
+ * optimisers the paper names next to Greedy (Sec. 2 and Sec. 4.1: Sieve
+ * Streaming, Badanidiyuru et al. 2014; Three Sieves, Buschjaeger et al.,
+ * which the case study of Sec. 6 runs, Fig. 4), written from their
+ * published descriptions.  Items arrive in stream order;
+ * with s = |S| < K, threshold v = thr[level] and
+ *     tau = (v / 2 - f(S)) / (K - s),
+ * an item e not in S joins S when Delta_f(e | S) >= tau.  An item in S, or
+ * one whose gain is below tau, is a rejection.  After `patience` consecutive
+ * rejections the sieve moves to the next threshold (level + 1, staying on
+ * the last one) and the count restarts; patience <= 0 never moves (one
+ * fixed threshold: one sieve of Sieve Streaming).  Once |S| = K the rest of
+ * the stream is ignored.
+ *
+ * State in / out (so a stream can be fed in pieces): m_io, sel_io (length
+ * n, as orc_greedy), f_io = f(S), level_io, rej_io.  Outputs: out_idx /
+ * out_f (accepted items and f after each; capacity K), out_count, and
+ * out_margin[p] for every stream position p that was decided: |gain - tau|
+ * / max(|gain|, |tau|) (1 for items already in S, 0 when both are 0), the
+ * relative distance of the decision from a tie.
+ */
+int orc_sieve(const float *V, int64_t n, int32_t d, const int32_t *items, int64_t len, int32_t K,
+              const double *thr, int32_t nthr, int64_t patience, double *m, unsigned char *sel, double *f_io,
+              int32_t *level_io, int64_t *rej_io, int32_t *out_idx, double *out_f, double *out_margin,
+              int32_t *out_count) {
+    if (n <= 0 || d <= 0 || len < 0 || K < 0 || (int64_t)K > n || nthr < 1 || !thr || !m || !sel || !f_io ||
+        !level_io || !rej_io || !out_count)
+        return ORC_EINVAL;
+    if (*level_io < 0 || *level_io >= nthr || *rej_io < 0) return ORC_EINVAL;
+    if (check_idx(items, len, n)) return ORC_EINDEX;
+    int64_t s = 0;
+    for (int64_t i = 0; i < n; ++i) s += sel[i] ? 1 : 0;
+    if (s > (int64_t)K) return ORC_EINVAL;
+    double f = *f_io;
+    int32_t level = *level_io;
+    int64_t rej = *rej_io;
+    int32_t cnt = 0;
+    for (int64_t p = 0; p < len && s < (int64_t)K; ++p) {
+        const int32_t e = items[p];
+        int accept = 0;
+        double margin = 1.0;
+        if (!sel[e]) {
+            const double tau = (thr[level] / 2.0 - f) / (double)((int64_t)K - s);
+            const double g = gain_one(V, n, d, m, e);
+            const double scale = fmax(fabs(g), fabs(tau));
+            margin = scale > 0.0 ? fabs(g - tau) / scale : 0.0;
+            accept = g >= tau;
+            if (accept) {
+                sel[e] = 1;
+                orc_update_m(V, n, d, m, e);
+                f += g;
+                s += 1;
+                out_idx[cnt] = e;
+                out_f[cnt] = f;
+                cnt += 1;
+                rej = 0;
+            }
+        }
+        if (out_margin) out_margin[p] = margin;
+        if (!accept) {
+            rej += 1;
+            if (patience > 0 && rej >= patience) {
+                if (level + 1 < nthr) level += 1;
+                rej = 0;
+            }
+        }
+    }
+    *f_io = f;
+    *level_io = level;
+    *rej_io = rej;
+    *out_count = cnt;
     return ORC_OK;
 }
 
