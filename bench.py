@@ -463,6 +463,126 @@ def run_sets(args):
     return 0
 
 
+def run_sieve(args):
+    """Three Sieves (the streaming optimiser of the paper's case study, Sec. 6
+    Fig. 4; rule of Sec. 2 / Sec. 4.1) over the drifting-regime features,
+    stream in time order.  One step = reset to S = {} + one pass of the
+    threshold sieve over the whole stream (ebc_sieve_host: bulk tensor-core
+    upper bounds of each batch, exact gains of the items that may pass).
+    Metric: distance evaluations per second, one evaluation being one
+    (streamed item, point) pair bounded or evaluated exactly.  The largest
+    singleton value m (an input of Three Sieves) is computed once, untimed."""
+    import torch
+
+    import oracle
+    from paper_2105_12026_gb300 import ebc, synth
+    torch.cuda.set_device(0)
+    n, d, K = args.n, args.d, args.k
+    eps, T = args.sieve_eps, args.sieve_patience
+    V = synth.regime_greedy(seed=args.seed, n=n, d=d, k=K)["V"]
+    stream = np.arange(n, dtype=np.int32)
+    dev = torch.device("cuda", 0)
+    cstream = torch.cuda.current_stream()
+    Vd = torch.from_numpy(V).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    inst = ebc.Instance(Vd, precision=args.prec, stream=cstream)
+    m1 = inst.max_singleton()
+    thr = ebc.ebc_threshold_ladder(m1, K, eps, 1.0)
+
+    def one_pass():
+        inst.reset()
+        sv = inst.sieve(K, thr, T)
+        idx, f = sv.feed(stream)
+        return idx, f, sv.counters()
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    inst.profiling(True)
+    inst.reset_profile()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, evs, res = [], 0, None
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cstream)
+        idx, f, cnt = one_pass()
+        b.record(cstream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        evs += (cnt["bounded"] + cnt["exact"]) * n
+        res = (idx, f, cnt)
+    clk = clocks.stop()
+    prof = inst.profile()
+    inst.profiling(False)
+    idx, f, cnt = res
+    tot_ms = sum(ms)
+    # e2e: V from pinned host memory into the handle, the stream from host
+    # memory, accepted items and f back to the host, all inside the region
+    Vh = torch.from_numpy(V).pin_memory()
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inst.reload(Vh)
+        one_pass()
+        e2e.append(time.perf_counter() - t0)
+    # Greedy at the same K, for the quality context (lazy rounds, untimed here)
+    inst.reset()
+    inst.set_lazy(True)
+    g_idx, g_f = inst.greedy_host(K)
+    inst.close()
+    pk = peaks()
+    list_ms = prof["list_ms"] / max(1, args.steps)
+    bulk_evals = cnt["bounded"] * n
+    flops = 2.0 * d * bulk_evals
+    achieved = flops / (list_ms / 1e3) / 1e12 if list_ms > 0 else None
+    peak = pk["bf16_sustained"]
+    line = {"metric": METRIC, "value": evs / (tot_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32"}.get(args.prec, args.prec),
+            "data": "synthetic (seeded generator, drifting-regime injection-moulding-like features)",
+            "config": {"workload": f"Three Sieves over the drifting-regime features n={n} d={d} K={K} eps={eps} "
+                                   f"T={T}, stream in time order",
+                       "precision": args.prec, "thresholds": int(thr.size), "m_single": m1,
+                       "l2": "flushed between steps (256 MB write)",
+                       "evals_per_step": evs // args.steps,
+                       "timing": "CUDA events around the host-driven pass (it synchronises per batch)"},
+            "roofline": {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "peak_source": f"{pk['source']} bf16 sustained",
+                         "kernel": "bulk bounds of the streamed batches (gather + tcgen05 gains kernel)",
+                         "avg_ms": list_ms, "algorithmic_flops_per_launch": flops / max(1, prof["list_launches"]
+                                                                                      // max(1, args.steps))},
+            "gpu_launches": prof["launches"] // max(1, args.steps), "clocks": clk,
+            "sieve": {"accepted": int(idx.size), "f_final": float(f[-1]) if f.size else 0.0,
+                      "consumed": int(cnt["consumed"]), "bounded_items": int(cnt["bounded"]),
+                      "exact_items": int(cnt["exact"]), "final_level": int(cnt["level"]),
+                      "items_per_s": n / (tot_ms / args.steps / 1e3),
+                      "ms_bulk_bounds": list_ms, "ms_exact": prof["refine_ms"] / max(1, args.steps)},
+            "greedy_same_K": {"f_final": float(g_f[-1]), "ratio_sieve_over_greedy":
+                              (float(f[-1]) / float(g_f[-1])) if f.size else 0.0},
+            "e2e": {"value": evs / args.steps * len(e2e) / sum(e2e), "unit": UNIT,
+                    "h2d_bytes_per_step": int(V.nbytes + stream.nbytes),
+                    "d2h_bytes_per_step": int(idx.size * 12)}}
+    if not args.no_cpu_baseline:
+        m = oracle.norms(V)
+        t0 = time.perf_counter()
+        oracle.gains(V, m, [0])
+        per_item = max(time.perf_counter() - t0, 1e-4)
+        L = int(max(8, min(n, args.cpu_budget / per_item)))
+        t0 = time.perf_counter()
+        r = oracle.sieve(V, stream[:L], K, thr, T)
+        cpu_s = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": L * n / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"oracle Three Sieves over the first {L} stream items "
+                                          f"({r['idx'].size} accepted), {cpu_s:.1f}s, one item at a time"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_sets_sweep(args):
     """Multi-set evaluation over the grid of the paper's runtime study (Sec. 5,
     Fig. 2 shape: d = 100, defaults N = 50,000, l = 5,000 sets of k = 10
@@ -544,7 +664,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"])
     ap.add_argument("--refine-k", type=int, default=8)
-    ap.add_argument("--workload", default="regime", choices=["regime", "small", "mix", "serve", "sets", "sets-sweep"])
+    ap.add_argument("--workload", default="regime", choices=["regime", "small", "mix", "serve", "sets", "sets-sweep", "sieve"])
     ap.add_argument("--sets", type=int, default=1024, help="sets: number of CSR sets")
     ap.add_argument("--instances", type=int, default=256, help="mix: number of instances")
     ap.add_argument("--slots", type=int, default=32, help="mix/serve: concurrent instances")
@@ -557,6 +677,8 @@ def main():
     ap.add_argument("--large-threshold", type=int, default=500_000, help="serve: n from which the CTA cap applies")
     ap.add_argument("--large-ctas", type=int, default=120, help="serve: CTA cap of large requests (0 = none)")
     ap.add_argument("--max-large", type=int, default=2, help="serve: large requests running at once (0 = any)")
+    ap.add_argument("--sieve-eps", type=float, default=0.01, help="sieve: threshold ladder step")
+    ap.add_argument("--sieve-patience", type=int, default=1000, help="sieve: Three Sieves T")
     ap.add_argument("--n", type=int, default=200_000)
     ap.add_argument("--d", type=int, default=128)
     ap.add_argument("--k", type=int, default=100)
@@ -582,6 +704,8 @@ def main():
         return run_serve(args)
     if args.workload == "sets-sweep":
         return run_sets_sweep(args)
+    if args.workload == "sieve":
+        return run_sieve(args)
     if args.workload == "sets":
         if args.n == 200_000 and args.d == 128:
             args.n, args.d = 50_000, 64

@@ -223,6 +223,68 @@ ebc_status ebc_set_graphs(ebc_t h, int32_t on);
 /* Host-pointer form of ebc_greedy. */
 ebc_status ebc_greedy_host(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);
 
+/*
+ * Threshold sieve over a stream: the decision rule of the streaming
+ * optimisers the paper names beside Greedy (Sec. 2 and Sec. 4.1: Sieve
+ * Streaming, Badanidiyuru et al. 2014; Three Sieves, Buschjaeger et al.,
+ * which the case study of Sec. 6 runs for Fig. 4).  Items (indices into V)
+ * arrive in stream order.  With s = |S| < K and the current threshold
+ * v = thr[level],
+ *     tau = (v / 2 - f(S)) / (K - s),
+ * an item not in S joins S when its exact marginal gain Delta_f(e | S) >= tau
+ * (S, m_v and f then update as after a Greedy pick).  An item already in S,
+ * or one whose gain is below tau, is a rejection; after `patience`
+ * consecutive rejections the sieve moves to the next threshold (staying on
+ * the last) and the count restarts; patience <= 0 never moves.  Once
+ * |S| = K the rest of the stream is left undecided.
+ *   Three Sieves:   thr = ebc_threshold_ladder(m, K, eps, 1), patience T.
+ *   Sieve Streaming: one handle (or one reset state) per value v of
+ *                   ebc_threshold_ladder(m, K, eps, 2), thr = {v}, patience 0;
+ *                   keep the best f.
+ * Decisions use certified gains: a bulk upper bound of every streamed item
+ * (tensor cores at BF16 / FP16 / FP8, rigorous FP32 bounds at EBC_FP32)
+ * rejects the items it can, and the exact gain (as in Greedy's pick)
+ * decides the rest, so decisions and f match the FP64 definition except
+ * where the gain and tau agree to about 1e-12 relative.
+ */
+typedef struct {
+    int32_t K;           /* summary size bound, counting the points already in S */
+    int32_t nthr;        /* number of thresholds, >= 1 */
+    const double *thr;   /* host array [nthr] of threshold values v (finite), walked in order */
+    int64_t patience;    /* consecutive rejections before the next threshold; <= 0: never move */
+    int32_t level;       /* in/out: index of the current threshold, in [0, nthr) */
+    int32_t reserved;
+    int64_t rejections;  /* in/out: consecutive rejections so far, >= 0 */
+    int64_t consumed;    /* out: stream positions decided by the last call (len unless |S| reached K) */
+    int64_t bounded;     /* in/out counter: items given a bulk upper bound */
+    int64_t exact;       /* in/out counter: items whose exact gain was computed */
+} ebc_sieve_state;
+
+/*
+ * One pass of the threshold sieve over items[0 .. len) (host array),
+ * continuing from the handle's state (S, m_v, f) and from s->level /
+ * s->rejections, so a stream can be fed in pieces.  Accepted items and f
+ * after each go to out_idx / out_f (host arrays, capacity K - |S|), their
+ * number to *out_count.  Synchronises the handle's stream.
+ * EINVAL: NULL state or outputs, nthr < 1, a non-finite threshold, level or
+ * rejections out of range, K < |S| or K > n, len < 0; EINDEX: an item
+ * outside [0, n).  The state is unchanged on an argument error.
+ */
+ebc_status ebc_sieve_host(ebc_t h, ebc_sieve_state *s, const int32_t *items, int64_t len, int32_t *out_idx,
+                          double *out_f, int32_t *out_count);
+
+/*
+ * Threshold ladder of the streaming optimisers: every value (1 + eps)^i (i an
+ * integer, computed as pow(1 + eps, i) in double) with
+ * m <= (1 + eps)^i <= upper * K * m, largest first; m is the largest singleton
+ * value max_e f({e}).  Writes at most cap values to out (out may be NULL with
+ * cap 0 to size) and the full count to *count.  Host only, no device work.
+ * EINVAL: m or eps not finite and > 0, K < 1, upper not finite and > 0,
+ * count NULL, more than 1,000,000 values, or cap smaller than the count.
+ */
+ebc_status ebc_threshold_ladder(double m, int32_t K, double eps, double upper, double *out, int32_t cap,
+                                int32_t *count);
+
 /* Return the Greedy state to S = {} (m_v = ||v||^2, f = 0, counters zeroed). */
 ebc_status ebc_reset(ebc_t h);
 

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -1076,6 +1077,239 @@ ebc_status ebc_greedy_host(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) 
     ebc::pool_free(d_f, c.stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "ebc_greedy_host");
     if (s != EBC_OK) return s;
+    return ebc_sync(h);
+}
+
+}  // extern "C"
+
+// ---- threshold sieve over a stream (ebc_sieve_host) ----------------------
+
+namespace {
+
+constexpr int kSieveExact = 64;  // items per exact-gain launch
+
+// Scratch of one ebc_sieve_host call (stream-ordered pool memory), freed
+// on every return path.
+struct SieveBufs {
+    cudaStream_t stream = nullptr;
+    int32_t *list = nullptr;                // [bcap] unselected items of the batch
+    int *cnt = nullptr;                     // [2] device list counts (bounds list, exact list)
+    double *ub = nullptr;                   // [bcap] upper bounds of the gains
+    double *lo = nullptr;                   // [bcap] FP32 path: lower bounds (not used by the rule)
+    double *plo = nullptr, *phi = nullptr;  // FP32 path: [bcap * nchunks] chunk partials
+    int32_t *xlist = nullptr;               // [kSieveExact] items given the exact gain
+    double *xpart = nullptr;                // [kSieveExact * nchunks]
+    double *xg = nullptr;                   // [kSieveExact]
+    ~SieveBufs() {
+        void *ptrs[] = {list, cnt, ub, lo, plo, phi, xlist, xpart, xg};
+        for (void *q : ptrs) ebc::pool_free(q, stream);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+ebc_status ebc_threshold_ladder(double m, int32_t K, double eps, double upper, double *out, int32_t cap,
+                                int32_t *count) {
+    if (!count || !(m > 0.0) || !std::isfinite(m) || !(eps > 0.0) || !std::isfinite(eps) || K < 1 ||
+        !(upper > 0.0) || !std::isfinite(upper) || cap < 0 || (cap > 0 && !out))
+        return EBC_EINVAL;
+    const double base = 1.0 + eps;
+    const double top = upper * K * m;
+    if (!(base > 1.0) || !std::isfinite(top)) return EBC_EINVAL;
+    // smallest i with base^i >= m, then every i up to base^i <= top
+    int64_t i = (int64_t)floor(log(m) / log(base)) - 2;
+    while (pow(base, (double)i) < m) ++i;
+    int64_t lo_i = i, cnt = 0;
+    while (pow(base, (double)i) <= top) {
+        ++i;
+        if (++cnt > 1000000) return EBC_EINVAL;
+    }
+    *count = (int32_t)cnt;
+    if (cap == 0 && !out) return EBC_OK;
+    if (cap < cnt) return EBC_EINVAL;
+    for (int64_t j = 0; j < cnt; ++j) out[j] = pow(base, (double)(lo_i + cnt - 1 - j));
+    return EBC_OK;
+}
+
+ebc_status ebc_sieve_host(ebc_t h, ebc_sieve_state *s, const int32_t *items, int64_t len, int32_t *out_idx,
+                          double *out_f, int32_t *out_count) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (!s || !out_count) return fail(h, EBC_EINVAL, "ebc_sieve_host: NULL state or count");
+    if (len < 0 || (len > 0 && !items)) return fail(h, EBC_EINVAL, "ebc_sieve_host: bad stream");
+    if (s->nthr < 1 || !s->thr) return fail(h, EBC_EINVAL, "ebc_sieve_host: no thresholds");
+    for (int32_t j = 0; j < s->nthr; ++j)
+        if (!std::isfinite(s->thr[j])) return fail(h, EBC_EINVAL, "ebc_sieve_host: non-finite threshold");
+    if (s->level < 0 || s->level >= s->nthr || s->rejections < 0)
+        return fail(h, EBC_EINVAL, "ebc_sieve_host: level or rejections out of range");
+    if ((int64_t)s->K < h->nsel || (int64_t)s->K > c.n) return fail(h, EBC_EINVAL, "ebc_sieve_host: K outside [|S|, n]");
+    const int64_t room = (int64_t)s->K - h->nsel;
+    if (room > 0 && (!out_idx || !out_f)) return fail(h, EBC_EINVAL, "ebc_sieve_host: NULL output");
+    for (int64_t p = 0; p < len; ++p)
+        if (items[p] < 0 || (int64_t)items[p] >= c.n) return fail(h, EBC_EINDEX, "ebc_sieve_host: item outside [0, n)");
+    *out_count = 0;
+    s->consumed = 0;
+    if (len == 0 || room == 0) return EBC_OK;
+    if (ebc_status s0 = ebc_sync(h)) return s0;
+
+    // host mirrors of S and f(S)
+    std::vector<uint8_t> sel((size_t)c.n);
+    double f = 0.0;
+    CK(h, cudaMemcpyAsync(sel.data(), c.sel, (size_t)c.n, cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaMemcpyAsync(&f, &c.st->f, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaStreamSynchronize(c.stream));
+
+    const bool tc = c.prec != EBC_FP32;  // tensor-core bounds (FP8 certifies with its BF16 copy)
+    const int64_t bmin = tc ? 256 : 64;
+    const int64_t bcap = std::min<int64_t>(c.n, tc ? 32768 : 1024);
+    const int nchunks = c.cert.nchunks;
+    SieveBufs B;
+    B.stream = c.stream;
+    CK(h, dalloc(&B.list, (size_t)bcap, c));
+    CK(h, dalloc(&B.cnt, 2, c));
+    CK(h, dalloc(&B.ub, (size_t)bcap, c));
+    CK(h, dalloc(&B.xlist, kSieveExact, c));
+    CK(h, dalloc(&B.xpart, (size_t)kSieveExact * nchunks, c));
+    CK(h, dalloc(&B.xg, kSieveExact, c));
+    if (!tc) {
+        CK(h, dalloc(&B.lo, (size_t)bcap, c));
+        CK(h, dalloc(&B.plo, (size_t)bcap * nchunks, c));
+        CK(h, dalloc(&B.phi, (size_t)bcap * nchunks, c));
+    }
+    const double eta = bulk_eta(c);
+    const double *thr = s->thr;
+    const int32_t nthr = s->nthr, K = s->K;
+    const int64_t patience = s->patience;
+    int32_t level = s->level;
+    int64_t rej = s->rejections;
+    int64_t nsel = h->nsel;
+    int32_t cnt = 0;
+
+    std::vector<int32_t> hl, xl;
+    std::vector<int64_t> lpos;  // batch position -> list entry, -1 for items in S
+    std::vector<double> hub, xg;
+    struct Maybe {
+        int64_t pos;  // batch position
+        double tau;
+        int32_t level;
+    };
+    std::vector<Maybe> U;
+
+    int64_t p = 0, bsz = bmin;
+    while (p < len && nsel < K) {
+        const int64_t nb = std::min(bsz, len - p);
+        // level 1: bulk upper bounds of the batch's items not in S
+        hl.clear();
+        lpos.assign((size_t)nb, -1);
+        for (int64_t i = 0; i < nb; ++i) {
+            const int32_t e = items[p + i];
+            if (!sel[(size_t)e]) {
+                lpos[(size_t)i] = (int64_t)hl.size();
+                hl.push_back(e);
+            }
+        }
+        const int64_t nl = (int64_t)hl.size();
+        hub.assign((size_t)nl, 0.0);
+        if (nl > 0) {
+            CK(h, cudaMemcpyAsync(B.list, hl.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, c.stream));
+            if (tc) {
+                int nch = h->nch;
+                CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, true); }));
+                CK(h, launch(h, PK_LIST, 2, [&] { return ebc::launch_gains_tc(c, B.list, nl, true, &nch); }));
+                CK(h, launch(h, -1, 1, [&] {
+                       return ebc::launch_reduce_select(c, nl, nch, B.list, false, B.ub, h->nblk);
+                   }));
+            } else {
+                const int n32 = (int)nl;
+                CK(h, cudaMemcpyAsync(B.cnt, &n32, sizeof(int), cudaMemcpyHostToDevice, c.stream));
+                CK(h, launch(h, PK_LIST, 2, [&] {
+                       return ebc::launch_bounds_list(c, B.list, B.cnt, (int)nl, B.plo, B.phi, c.cert.chunk, nchunks);
+                   }));
+                CK(h, launch(h, -1, 1, [&] {
+                       return ebc::launch_fold_bounds(c, B.plo, B.phi, B.cnt, (int)nl, B.lo, B.ub);
+                   }));
+            }
+            CK(h, cudaMemcpyAsync(hub.data(), B.ub, sizeof(double) * nl, cudaMemcpyDeviceToHost, c.stream));
+            CK(h, cudaStreamSynchronize(c.stream));
+            s->bounded += nl;
+            if (tc)
+                for (double &u : hub) u *= 1.0 + eta;  // rigorous: partial sums carry relative error <= eta
+        }
+        // walk the batch as if every item were rejected (that is the state
+        // up to the first accept); items whose bound reaches tau may accept
+        U.clear();
+        int32_t lev = level;
+        int64_t r = rej;
+        for (int64_t i = 0; i < nb; ++i) {
+            const int64_t li = lpos[(size_t)i];
+            if (li >= 0) {
+                const double tau = (thr[lev] / 2.0 - f) / (double)((int64_t)K - nsel);
+                if (!(hub[(size_t)li] < tau)) U.push_back({i, tau, lev});
+            }
+            r += 1;
+            if (patience > 0 && r >= patience) {
+                if (lev + 1 < nthr) lev += 1;
+                r = 0;
+            }
+        }
+        // level 2: exact gains of those items in stream order, kSieveExact per
+        // launch, up to the first that reaches its tau
+        int64_t acc = -1;
+        double acc_g = 0.0;
+        int32_t acc_lev = level;
+        for (size_t u0 = 0; u0 < U.size() && acc < 0; u0 += kSieveExact) {
+            const int ng = (int)std::min<size_t>(kSieveExact, U.size() - u0);
+            xl.resize((size_t)ng);
+            for (int j = 0; j < ng; ++j) xl[(size_t)j] = items[p + U[u0 + j].pos];
+            CK(h, cudaMemcpyAsync(B.xlist, xl.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, c.stream));
+            CK(h, cudaMemcpyAsync(B.cnt + 1, &ng, sizeof(int), cudaMemcpyHostToDevice, c.stream));
+            CK(h, launch(h, PK_REFINE, 1, [&] {
+                   return ebc::launch_exact_list(c, B.xlist, B.cnt + 1, kSieveExact, B.xpart, c.cert.chunk, nchunks);
+               }));
+            CK(h, launch(h, -1, 1, [&] { return ebc::launch_sieve_fold_exact(c, B.xpart, B.cnt + 1, kSieveExact, B.xg); }));
+            xg.resize((size_t)ng);
+            CK(h, cudaMemcpyAsync(xg.data(), B.xg, sizeof(double) * ng, cudaMemcpyDeviceToHost, c.stream));
+            CK(h, cudaStreamSynchronize(c.stream));
+            s->exact += ng;
+            for (int j = 0; j < ng; ++j)
+                if (xg[(size_t)j] >= U[u0 + j].tau) {
+                    acc = U[u0 + j].pos;
+                    acc_g = xg[(size_t)j];
+                    acc_lev = U[u0 + j].level;
+                    break;
+                }
+        }
+        if (acc < 0) {  // the whole batch is rejected
+            level = lev;
+            rej = r;
+            p += nb;
+            s->consumed += nb;
+            bsz = std::min(bcap, 2 * bsz);
+            continue;
+        }
+        const int32_t item = items[p + acc];
+        CK(h, launch(h, -1, 2, [&] {
+               cudaError_t e = ebc::launch_sieve_commit(c, item, acc_g);
+               return e != cudaSuccess ? e : ebc::launch_update(c);
+           }));
+        sel[(size_t)item] = 1;
+        f += acc_g;  // the device adds the same double to the same f
+        nsel += 1;
+        h->nsel = nsel;
+        out_idx[cnt] = item;
+        out_f[cnt] = f;
+        cnt += 1;
+        level = acc_lev;
+        rej = 0;
+        p += acc + 1;
+        s->consumed += acc + 1;
+        bsz = std::min(bcap, std::max(bmin, 2 * (acc + 1)));
+    }
+    s->level = level;
+    s->rejections = rej;
+    *out_count = cnt;
     return ebc_sync(h);
 }
 

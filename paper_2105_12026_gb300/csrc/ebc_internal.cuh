@@ -267,6 +267,9 @@ cudaError_t launch_decide_top(Ctx &c, double eta_bulk);
 cudaError_t launch_decide_contenders(Ctx &c);
 cudaError_t launch_commit_pick(Ctx &c, int32_t *out_idx, double *out_f);
 cudaError_t launch_update(Ctx &c);
+// threshold sieve (k_select.cu): exact gains of a list from chunk partials; commit of an accepted item
+cudaError_t launch_sieve_fold_exact(Ctx &c, const double *part, const int *count, int cap, double *out);
+cudaError_t launch_sieve_commit(Ctx &c, int item, double gain);
 cudaError_t launch_current_f(Ctx &c, double *d_out);
 cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,
                                   const int *bad);

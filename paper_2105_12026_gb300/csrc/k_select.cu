@@ -210,4 +210,43 @@ cudaError_t launch_commit_pick(Ctx &c, int32_t *out_idx, double *out_f) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Threshold sieve over a stream (the streaming optimisers of Sec. 2 / Sec.
+// 4.1): exact gains of a short list from the exact kernel's chunk partials,
+// and the commit of an accepted item.
+// ---------------------------------------------------------------------------
+__global__ void k_sieve_fold_exact(const double *__restrict__ part, int nchunks, const int *__restrict__ count,
+                                   int cap, double inv_n, double *__restrict__ out) {
+    const int nc = min(*count, cap);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = w; e < nc; e += blockDim.x >> 5) {
+        double s = 0.0;
+        for (int q = lane; q < nchunks; q += 32) s += part[(int64_t)e * nchunks + q];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[e] = s * inv_n;
+    }
+}
+
+cudaError_t launch_sieve_fold_exact(Ctx &c, const double *part, const int *count, int cap, double *out) {
+    k_sieve_fold_exact<<<1, 256, 0, c.stream>>>(part, c.cert.nchunks, count, cap, 1.0 / (double)c.n, out);
+    return cudaGetLastError();
+}
+
+// Add item to S with its exact gain (taken by the host from the fold above);
+// the m_v update that follows reads st->pick.
+__global__ void k_sieve_commit(int item, double gain, uint8_t *__restrict__ sel, double *__restrict__ ub,
+                               DevState *st) {
+    sel[item] = 1;
+    if (ub) ub[item] = -1.0;  // lazy Greedy bounds: a selected point leaves every list
+    st->f += gain;
+    st->pick = item;
+    st->pick_gain = gain;
+    st->round += 1;
+}
+
+cudaError_t launch_sieve_commit(Ctx &c, int item, double gain) {
+    k_sieve_commit<<<1, 1, 0, c.stream>>>(item, gain, c.sel, c.ub64, c.st);
+    return cudaGetLastError();
+}
+
 }  // namespace ebc

@@ -53,6 +53,13 @@ class ebc_batch_info(ctypes.Structure):
                 ("rounds_issued", ctypes.c_int64)]
 
 
+class ebc_sieve_state(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("nthr", ctypes.c_int32), ("thr", ctypes.c_void_p),
+                ("patience", ctypes.c_int64), ("level", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rejections", ctypes.c_int64), ("consumed", ctypes.c_int64), ("bounded", ctypes.c_int64),
+                ("exact", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -74,6 +81,9 @@ _SIGS = {
     "ebc_gains_host": [_P, _P, _I64, _P],
     "ebc_greedy": [_P, _I32, _P, _P],
     "ebc_greedy_host": [_P, _I32, _P, _P],
+    "ebc_sieve_host": [_P, ctypes.POINTER(ebc_sieve_state), _P, _I64, _P, _P, ctypes.POINTER(_I32)],
+    "ebc_threshold_ladder": [ctypes.c_double, _I32, ctypes.c_double, ctypes.c_double, _P, _I32,
+                             ctypes.POINTER(_I32)],
     "ebc_set_graphs": [_P, _I32],
     "ebc_set_lazy": [_P, _I32],
     "ebc_state_size": [_P, ctypes.POINTER(_I64)],
@@ -267,6 +277,29 @@ def ebc_greedy_host(h: int, k: int):
     return idx, f
 
 
+def ebc_threshold_ladder(m: float, K: int, eps: float, upper: float = 1.0) -> np.ndarray:
+    """Thresholds (1+eps)^i in [m, upper K m], largest first (host only)."""
+    cnt = _I32()
+    _raise(None, load().ebc_threshold_ladder(float(m), int(K), float(eps), float(upper), None, 0, ctypes.byref(cnt)))
+    out = np.zeros(max(cnt.value, 1), dtype=np.float64)
+    _raise(None, load().ebc_threshold_ladder(float(m), int(K), float(eps), float(upper), out.ctypes.data_as(_P),
+                                             cnt.value, ctypes.byref(cnt)))
+    return out[:cnt.value]
+
+
+def ebc_sieve_host(h: int, state: ebc_sieve_state, items: np.ndarray):
+    """One pass of the threshold sieve over ``items``; returns the accepted
+    (idx int32, f float64) and updates ``state`` in place."""
+    items = np.ascontiguousarray(items, dtype=np.int32).ravel()
+    room = max(int(state.K), 1)
+    idx = np.zeros(room, dtype=np.int32)
+    f = np.zeros(room, dtype=np.float64)
+    cnt = _I32()
+    _raise(h, load().ebc_sieve_host(_P(h), ctypes.byref(state), items.ctypes.data_as(_P), items.size,
+                                    idx.ctypes.data_as(_P), f.ctypes.data_as(_P), ctypes.byref(cnt)))
+    return idx[:cnt.value].copy(), f[:cnt.value].copy()
+
+
 def ebc_reset(h: int) -> None:
     _raise(h, load().ebc_reset(_P(h)))
 
@@ -438,6 +471,85 @@ class Instance:
 
     def current_f(self):
         return ebc_current_f(self.h)
+
+    def max_singleton(self) -> float:
+        """max_e f({e}) over V: the exact gain of Greedy's first pick from
+        S = {} (the current state is saved and restored)."""
+        snap = self.save_state()
+        try:
+            self.reset()
+            return float(self.greedy_host(1)[1][0])
+        finally:
+            self.load_state(snap)
+
+    def sieve(self, K: int, thresholds, patience: int = 0) -> "Sieve":
+        return Sieve(self, K, thresholds, patience)
+
+
+class Sieve:
+    """Threshold sieve over a stream on one Instance (ebc_sieve_host): feed
+    items in pieces; the level / rejection state carries over."""
+
+    def __init__(self, inst: Instance, K: int, thresholds, patience: int = 0):
+        self.inst = inst
+        self.thr = np.ascontiguousarray(thresholds, dtype=np.float64).ravel()
+        self.state = ebc_sieve_state()
+        self.state.K = int(K)
+        self.state.nthr = self.thr.size
+        self.state.thr = self.thr.ctypes.data
+        self.state.patience = int(patience)
+        self.idx = []
+        self.f = []
+
+    def feed(self, items):
+        idx, f = ebc_sieve_host(self.inst.h, self.state, items)
+        self.idx.extend(idx.tolist())
+        self.f.extend(f.tolist())
+        return idx, f
+
+    @property
+    def level(self) -> int:
+        return int(self.state.level)
+
+    @property
+    def rejections(self) -> int:
+        return int(self.state.rejections)
+
+    def counters(self) -> dict:
+        s = self.state
+        return {"level": s.level, "rejections": s.rejections, "consumed": s.consumed, "bounded": s.bounded,
+                "exact": s.exact}
+
+
+def three_sieves(inst: Instance, items, K: int, eps: float, T: int, m_single: float | None = None):
+    """Three Sieves on the instance's current state: thresholds from K m down
+    to m, moving down after T consecutive rejections.  Returns (idx, f, Sieve)."""
+    if m_single is None:
+        m_single = inst.max_singleton()
+    sv = Sieve(inst, K, ebc_threshold_ladder(m_single, K, eps, 1.0), T)
+    idx, f = sv.feed(items)
+    return idx, f, sv
+
+
+def sieve_streaming(inst: Instance, items, K: int, eps: float, m_single: float | None = None):
+    """Sieve Streaming with the largest singleton value m known: one sieve per
+    ladder value up to 2 K m, each run from S = {} on the instance (reset
+    between sieves).  Returns (best idx, best f, per-sieve f_end list,
+    thresholds); the instance is left in the best sieve's state."""
+    if m_single is None:
+        m_single = inst.max_singleton()
+    thr = ebc_threshold_ladder(m_single, K, eps, 2.0)
+    best = None
+    ends = []
+    for j, v in enumerate(thr):
+        inst.reset()
+        idx, f = Sieve(inst, K, [v], 0).feed(items)
+        fe = float(f[-1]) if f.size else 0.0
+        ends.append(fe)
+        if best is None or fe > best[2]:
+            best = (idx, f, fe, inst.save_state())
+    inst.load_state(best[3])
+    return best[0], best[1], ends, thr
 
 
 # ---------------------------------------------------------------------------
