@@ -231,7 +231,7 @@ ebc_status ensure_set_part(ebc_t h, int64_t want) {
 int64_t ebc::handle_bytes(int64_t n, int32_t d, ebc_prec prec) {
     const int64_t ch = std::max<int64_t>(4096, ((n + 63) / 64 + 127) / 128 * 128);
     const int64_t nch = (n + ch - 1) / ch;
-    const int64_t ref_ch = std::max<int64_t>(512, ((n + 607) / 608 + 255) / 256 * 256);
+    const int64_t ref_ch = ebc::refine_chunk(n, d);
     const int64_t nref = (n + ref_ch - 1) / ref_ch;
     const int64_t nblk = std::min<int64_t>(512, std::max<int64_t>(1, (n + 2047) / 2048));
     const int64_t cap = std::min<int64_t>(n, 4096);
@@ -322,7 +322,7 @@ ebc_status ebc::create_handle(const float *V, int64_t n, int32_t d, int32_t v_on
     // chunking of the V axis
     h->ch = std::max<int64_t>(4096, ((n + 63) / 64 + 127) / 128 * 128);
     h->nch = (int)((n + h->ch - 1) / h->ch);
-    h->ref_ch = std::max<int64_t>(512, ((n + 607) / 608 + 255) / 256 * 256);  // ~4 chunks per SM
+    h->ref_ch = ebc::refine_chunk(n, d);
     h->nref = (int)((n + h->ref_ch - 1) / h->ref_ch);
     h->esc_cap = (int)std::min<int64_t>(n, 4096);
     h->nblk = (int)std::min<int64_t>(512, std::max<int64_t>(1, (n + 2047) / 2048));
@@ -461,7 +461,7 @@ ebc_status ebc::set_precision_handle(ebc_t h, ebc_prec prec, int32_t refine_k, b
     ebc::Ctx &c = h->c;
     if (prec == EBC_BF16 || prec == EBC_FP16) {
         if (!ebc::tc_supported(c))
-            return fail(h, EBC_EINVAL, "ebc_set_precision: the tensor-core path supports d <= 128");
+            return fail(h, EBC_EINVAL, "ebc_set_precision: the tensor-core path supports d <= 4096");
         if (c.tc.prec != (int)prec) {
             if (!sync) {
                 // errors (a format overflow) surface at the next ebc_sync
@@ -482,8 +482,8 @@ ebc_status ebc::set_precision_handle(ebc_t h, ebc_prec prec, int32_t refine_k, b
         }
     } else if (prec == EBC_FP8E4M3) {
         // FP8 bulk bounds pre-screen; the BF16 copy certifies (second level)
-        if (!ebc::tc_supported(c))
-            return fail(h, EBC_EINVAL, "ebc_set_precision: the tensor-core path supports d <= 128");
+        if (!ebc::tc_resident_supported(c))
+            return fail(h, EBC_EINVAL, "ebc_set_precision: the FP8 path supports d <= 128");
         if (sync) {
             ebc_status s0 = ebc_sync(h);
             if (s0 != EBC_OK) return s0;
@@ -605,6 +605,7 @@ ebc_status ebc::autotune_handle(ebc_t h, int32_t reps, bool only_if_missing) {
     cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_fail(h, err, "ebc_autotune");
+    if (!(best < INFINITY)) return ebc_sync(h);  // no resident shape fits: the K-blocked kernel has one shape
     ebc::tune_store((int)c.prec, RB, c.n, best_cfg, best);
     if (h->round_exec) {  // recapture rounds with the tuned configuration
         cudaGraphExecDestroy(h->round_exec);
@@ -797,7 +798,7 @@ ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off
     if (l < 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: l < 0");
     if (l == 0) return EBC_OK;
     if (!csr_off || !out_f) return fail(h, EBC_EINVAL, "ebc_eval_sets: NULL argument");
-    if (c.prec != EBC_FP32) {
+    if (c.prec != EBC_FP32 && ebc::tc_resident_supported(c)) {
         // tensor-core path: the tile plan needs the offsets on the host
         std::vector<int64_t> off((size_t)l + 1);
         CK(h, cudaMemcpyAsync(off.data(), csr_off, sizeof(int64_t) * (l + 1), cudaMemcpyDeviceToHost, c.stream));
@@ -1052,6 +1053,17 @@ ebc_status ebc_set_max_ctas(ebc_t h, int32_t max_ctas) {
     return EBC_OK;
 }
 
+ebc_status ebc_set_kblocked(ebc_t h, int32_t on) {
+    if (check_handle(h)) return EBC_EINVAL;
+    h->c.force_kb = on != 0;
+    if (h->round_exec) {  // rounds captured with the other kernel
+        cudaGraphExecDestroy(h->round_exec);
+        h->round_exec = nullptr;
+    }
+    h->attrs_ready = false;  // one direct round sets the kernel's attributes before a capture
+    return EBC_OK;
+}
+
 ebc_status ebc_set_graphs(ebc_t h, int32_t on) {
     if (check_handle(h)) return EBC_EINVAL;
     h->graphs = on != 0;
@@ -1254,13 +1266,15 @@ ebc_status ebc_sieve_host(ebc_t h, ebc_sieve_state *s, const int32_t *items, int
                 r = 0;
             }
         }
-        // level 2: exact gains of those items in stream order, kSieveExact per
-        // launch, up to the first that reaches its tau
+        // level 2: exact gains of those items in stream order, up to the first
+        // that reaches its tau; groups of 8, 16, ... kSieveExact (one pass over
+        // V serves 8 items, and the first candidates usually decide)
         int64_t acc = -1;
         double acc_g = 0.0;
         int32_t acc_lev = level;
-        for (size_t u0 = 0; u0 < U.size() && acc < 0; u0 += kSieveExact) {
-            const int ng = (int)std::min<size_t>(kSieveExact, U.size() - u0);
+        size_t group = 8;
+        for (size_t u0 = 0; u0 < U.size() && acc < 0; u0 += group, group = std::min<size_t>(2 * group, kSieveExact)) {
+            const int ng = (int)std::min<size_t>(group, U.size() - u0);
             xl.resize((size_t)ng);
             for (int j = 0; j < ng; ++j) xl[(size_t)j] = items[p + U[u0 + j].pos];
             CK(h, cudaMemcpyAsync(B.xlist, xl.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, c.stream));

@@ -272,7 +272,7 @@ ebc_status ebc_batch_submit(ebc_batch_t b, const float *V, int64_t n, int32_t d,
     if (!b) return EBC_EINVAL;
     if (!V || !ticket || n <= 0 || n > (int64_t)INT32_MAX - 1 || d <= 0 || d > 4096 || k < 1 || (int64_t)k > n)
         return bfail(b, EBC_EINVAL, "ebc_batch_submit: bad V, n, d, k or ticket");
-    if (prec != EBC_FP32 && !((prec == EBC_BF16 || prec == EBC_FP16 || prec == EBC_FP8E4M3) && d <= 128))
+    if (prec != EBC_FP32 && !(prec == EBC_BF16 || prec == EBC_FP16 || (prec == EBC_FP8E4M3 && d <= 128)))
         return bfail(b, EBC_EINVAL, "ebc_batch_submit: unsupported precision for this d");
     ebc_batch_ctx::Req r;
     r.ticket = b->next_ticket++;

@@ -48,6 +48,16 @@ struct DevState {
     long long bulk_cands;   // candidates given a bulk bound, summed over rounds
 };
 
+// Points per V chunk of the refine kernels (bounds and exact gains of short
+// lists): about 4 chunks per SM for large n; for d > 128 chunks shrink (to
+// 32 points at d >= 2048) so that a short list over a small n still spreads
+// over the SMs.
+__host__ __device__ inline int64_t refine_chunk(int64_t n, int d) {
+    const int64_t per_sm = (n + 607) / 608;
+    if (d <= 128) return lmax(512, (per_sm + 255) / 256 * 256);
+    return lmax(lmax(32, (int64_t)(65536 / d) / 32 * 32), (per_sm + 31) / 32 * 32);
+}
+
 // V chunking of the bulk gains kernel for m candidates: the chunk count
 // (1..16, bounded by the partial buffer) that best balances
 // (candidate tiles x chunks) units over G persistent CTAs.  Used on the host
@@ -172,6 +182,7 @@ struct Ctx {
     // lazy Greedy: stale upper bounds of every candidate's gain (gains never
     // increase as S grows) and the round's candidate list
     bool lazy = false;
+    bool force_kb = false;  // K-blocked bulk kernel even where whole rows fit (ebc_set_kblocked)
     double *ub64 = nullptr;     // [n]
     int *lazy_idx = nullptr;    // [n]
     double *set_part = nullptr; // eval_sets partials
@@ -277,7 +288,8 @@ cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off
 cudaError_t launch_sets_finalize(Ctx &c, int64_t ntiles, int64_t lb, int64_t j0, int64_t l, double *out_f);
 
 // tensor-core path
-bool tc_supported(const Ctx &c);
+bool tc_supported(const Ctx &c);           // 16-bit bulk bounds (K-blocked kernel above d = 128)
+bool tc_resident_supported(const Ctx &c);  // FP8 bulk and the multi-set kernel: d <= 128
 cudaError_t tc_setup(Ctx &c, int prec);          // allocate, quantise, build tensor maps
 cudaError_t tc_quantize(Ctx &c);                 // (re)quantise V into Vq
 cudaError_t launch_prep_tc(Ctx &c, bool upper);  // a_v for every point (+ max m_v)

@@ -178,6 +178,25 @@ __host__ __device__ inline SmemLayout smem_layout(int RB, int nstages, int na) {
     return L;
 }
 
+// K-blocked stage (candidate rows too long to stay resident): one 128-byte
+// K atom of both candidate sub-tiles and of the point tile, then room for
+// the three extensions, which only the last K block of a point tile loads.
+__host__ __device__ inline SmemLayout smem_layout_kb(int nstages) {
+    SmemLayout L;
+    L.a_main = 0;
+    L.a_sub = 0;
+    L.a_bytes = 0;
+    L.b_main = 2 * BMS * 128 + BN * 128;
+    L.b_bytes = L.b_main + 2 * BMS * KEXT * 2 + BN * KEXT * 2;
+    L.off_b = 0;
+    L.off_comb = nstages * L.b_bytes;
+    L.off_bar = L.off_comb + 2 * BMS * 8;
+    L.off_misc = L.off_bar + (2 * nstages + 8) * 8;
+    L.total = L.off_misc + 64 + 1024;
+    return L;
+}
+constexpr int KB_STAGES = 2;
+
 __device__ __forceinline__ void record_timeout(int *err, volatile int *abort) {
     *abort = 1;
     atomicCAS(err, 0, (int)EBC_ETIMEOUT);
@@ -261,15 +280,22 @@ __device__ __forceinline__ float relu_sum128(const uint32_t (&r0)[32], const uin
 // gains (MODE_GAINS: A = candidates, B = points, epilogue = relu row sums)
 // and the multi-set evaluation (MODE_SETS: A = points, B = set members,
 // epilogue = per-set maxima and sums over the points).
-template <int MODE, bool F8>
+//
+// KB (gains only): candidate rows longer than the resident layout allows.
+// Every stage carries one K atom of both candidate sub-tiles and of the
+// point tile; a point tile's MMAs accumulate over all K atoms (the same MMA
+// sequence, hence the same FP32 accumulation, as the resident layout) and
+// the extension step follows the last atom.
+template <int MODE, bool F8, bool KB = false>
 __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUtensorMap *tmAx_p,
                                             const CUtensorMap *tmB_p, const CUtensorMap *tmBx_p, const TcArgs &args) {
+    static_assert(!KB || (MODE == MODE_GAINS && !F8), "K-blocked layout: 16-bit gains only");
     const CUtensorMap &tmA = *tmA_p, &tmAx = *tmAx_p, &tmB = *tmB_p, &tmBx = *tmBx_p;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ns = args.nstages;
     const int na = args.na;
-    const SmemLayout L = smem_layout(args.RB, ns, na);
+    const SmemLayout L = KB ? smem_layout_kb(ns) : smem_layout(args.RB, ns, na);
     uint8_t *sA = base;
     uint8_t *sB = base + L.off_b;
     double *comb = reinterpret_cast<double *>(base + L.off_comb);  // [2][BMS]
@@ -328,6 +354,41 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
             tc::tma_prefetch_desc(&tmB);
             tc::tma_prefetch_desc(&tmBx);
             int g = 0, ua = 0;
+            if constexpr (KB) {
+                // one stage per (point tile, K atom): A atom of both
+                // sub-tiles, B atom, and at the last atom the extensions
+                for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
+                    int ct, ch, b_row0, nb;
+                    unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
+                    bool ok = true;
+                    for (int i = 0; i < nb && ok; ++i) {
+                        const int brow = b_row0 + i * BN;
+                        for (int j = 0; j < katoms; ++j, ++g) {
+                            const int s = g % ns;
+                            const int ph = (g / ns) & 1;
+                            if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                                record_timeout(args.err, abort_flag);
+                                ok = false;
+                                break;
+                            }
+                            uint8_t *st = sB + s * L.b_bytes;
+                            const bool last = j == katoms - 1;
+                            tc::mbar_arrive_expect_tx(&full[s], last ? L.b_bytes : L.b_main);
+                            for (int h = 0; h < 2; ++h)
+                                tc::tma_load_2d(st + h * (BMS * 128), &tmA, &full[s], j * args.xatom, ct * BM + h * BMS);
+                            tc::tma_load_2d(st + 2 * BMS * 128, &tmB, &full[s], j * args.xatom, brow);
+                            if (last) {
+                                for (int h = 0; h < 2; ++h)
+                                    tc::tma_load_2d(st + L.b_main + h * (BMS * KEXT * 2), &tmAx, &full[s], 0,
+                                                    ct * BM + h * BMS);
+                                tc::tma_load_2d(st + L.b_main + 2 * (BMS * KEXT * 2), &tmBx, &full[s], 0, brow);
+                            }
+                            last_full[s] = ph;
+                        }
+                    }
+                    if (!ok) break;
+                }
+            } else
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
                 int ct, ch, b_row0, nb;
                 unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
@@ -373,6 +434,54 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         // into region 1.  The epilogue drains one region while the other fills.
         if (lane == 0) {
             int g = 0, t = 0, ua = 0;
+            if constexpr (KB) {
+                // both TMEM regions accumulate one point tile over all K atoms
+                for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
+                    int ct, ch, b_row0, nb;
+                    unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
+                    bool ok = true;
+                    for (int i = 0; i < nb && ok; ++i, ++t) {
+                        for (int h = 0; h < 2 && ok; ++h)
+                            if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag)) {
+                                record_timeout(args.err, abort_flag);
+                                ok = false;
+                            }
+                        if (!ok) break;
+                        tc::tc_fence_after();
+                        for (int j = 0; j < katoms; ++j, ++g) {
+                            const int s = g % ns;
+                            if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag)) {
+                                record_timeout(args.err, abort_flag);
+                                ok = false;
+                                break;
+                            }
+                            tc::tc_fence_after();
+                            const uint32_t st = tc::smem_u32(sB + s * L.b_bytes);
+                            const uint32_t b0 = st + 2 * BMS * 128;
+                            for (int h = 0; h < 2; ++h) {
+                                const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
+                                const uint32_t ah = st + h * (BMS * 128);
+                                for (int w = 0; w < 4; ++w) {
+                                    const uint64_t ad = tc::sdesc_sw128(ah + w * 32);
+                                    const uint64_t bd = tc::sdesc_sw128(b0 + w * 32);
+                                    tc::mma_f16(d_tmem, ad, bd, args.idesc, (j > 0 || w > 0) ? 1u : 0u);
+                                }
+                                if (j == katoms - 1)
+                                    tc::mma_f16(d_tmem, tc::sdesc_sw32(st + L.b_main + h * (BMS * KEXT * 2)),
+                                                tc::sdesc_sw32(st + L.b_main + 2 * (BMS * KEXT * 2)), args.idesc_ext,
+                                                1u);
+                            }
+                            tc::mma_commit(&empty[s]);
+                        }
+                        if (!ok) break;
+                        for (int h = 0; h < 2; ++h) {
+                            tc::mma_commit(&t_full[h]);
+                            last_tfull[h] = t & 1;
+                        }
+                    }
+                    if (!ok) break;
+                }
+            } else
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
                 int ct, ch, b_row0, nb;
                 unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
@@ -592,6 +701,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     k_gains_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
     tc_pipeline<MODE_GAINS, false>(&tmA, &tmAx, &tmB, &tmBx, args);
+}
+
+// Candidate rows too long for the resident layout (d > 128 at 16 bits).
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gains_tc_kb(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+                  const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
+    tc_pipeline<MODE_GAINS, false, true>(&tmA, &tmAx, &tmB, &tmBx, args);
 }
 
 // FP8 e4m3 operands (kind::f8f6f4), BF16 extension step; full candidate
@@ -1148,6 +1264,15 @@ void choose_config(const Ctx &c, int prec, int RB, int *na, int *ns, int *chunk_
     }
 }
 
+// The K-blocked bulk kernel: when a candidate tile and two point stages of
+// whole rows do not fit shared memory (d > 128 at 16 bits), or when forced.
+bool use_kb(const Ctx &c, int RB) {
+    if (c.force_kb) return true;
+    int na = 0, ns = 0;
+    pick_pipeline(RB, &na, &ns);
+    return ns == 0;
+}
+
 double gamma_for(int DP) { return ((double)(DP + KEXT) / 4.0 + 4.0) * ldexp(1.0, -22); }
 
 // FP8: the tensor core's internal sum of each 32-product block is assumed
@@ -1157,7 +1282,10 @@ double gamma8_for(int DP) { return ldexp(1.0, -8) + gamma_for(DP); }
 
 }  // namespace
 
-bool tc_supported(const Ctx &c) { return c.d <= 128; }
+// 16-bit tensor-core bulk bounds: any d (K-blocked above 128); the FP8
+// kernel and the multi-set kernel keep whole rows resident: d <= 128.
+bool tc_supported(const Ctx &c) { return c.d <= 4096; }
+bool tc_resident_supported(const Ctx &c) { return c.d <= 128; }
 
 bool tc_config_fits(int RB, int na, int ns) {
     return na >= 1 && na <= 2 && ns >= 2 && ns <= 6 && (int)smem_layout(RB, ns, na).total <= SMEM_LIMIT;
@@ -1342,11 +1470,13 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     (void)upper;  // the mode is carried by the point extension written by launch_prep_tc
     Ctx::Tc &T = c.tc;
     const int DP = T.DP;
-    int na = 0, ns = 0, chunk_mode = 0;
-    choose_config(c, T.prec, 2 * DP, &na, &ns, &chunk_mode);
+    const bool kb = use_kb(c, 2 * DP);
+    int na = 1, ns = KB_STAGES, chunk_mode = 0;
+    if (!kb) choose_config(c, T.prec, 2 * DP, &na, &ns, &chunk_mode);
     if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = smem_layout(2 * DP, ns, na);
-    if (cudaError_t e = allow_smem((const void *)k_gains_tc, L.total); e != cudaSuccess) return e;
+    const SmemLayout L = kb ? smem_layout_kb(ns) : smem_layout(2 * DP, ns, na);
+    const void *kfn = kb ? (const void *)k_gains_tc_kb : (const void *)k_gains_tc;
+    if (cudaError_t e = allow_smem(kfn, L.total); e != cudaSuccess) return e;
     if (cand) {
         int64_t tot = m * (DP / 8 + 2);
         k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Vq, T.Aext, cand, m, nullptr, DP, T.Cq,
@@ -1383,8 +1513,12 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     a.err = &c.st->err;
     const int units = a.n_ctiles * a.nchunks;
     const int grid = std::min(units, G);
-    k_gains_tc<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V, T.tmB_V,
-                                                      T.tmBx, a);
+    if (kb)
+        k_gains_tc_kb<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V,
+                                                             T.tmB_V, T.tmBx, a);
+    else
+        k_gains_tc<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V, T.tmB_V,
+                                                          T.tmBx, a);
     *nchunks_out = a.nchunks;
     return cudaGetLastError();
 }
@@ -1396,11 +1530,13 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
 cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int64_t m_cap) {
     Ctx::Tc &T = c.tc;
     const int DP = T.DP;
-    int na = 0, ns = 0;
-    pick_pipeline(2 * DP, &na, &ns);
+    const bool kb = use_kb(c, 2 * DP);
+    int na = 1, ns = KB_STAGES;
+    if (!kb) pick_pipeline(2 * DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = smem_layout(2 * DP, ns, na);
-    if (cudaError_t e = allow_smem((const void *)k_gains_tc, L.total); e != cudaSuccess) return e;
+    const SmemLayout L = kb ? smem_layout_kb(ns) : smem_layout(2 * DP, ns, na);
+    const void *kfn = kb ? (const void *)k_gains_tc_kb : (const void *)k_gains_tc;
+    if (cudaError_t e = allow_smem(kfn, L.total); e != cudaSuccess) return e;
     const int64_t tot = m_cap * (DP / 8 + 2);
     k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Vq, T.Aext, cand, m_cap, m_dev, DP, T.Cq,
                                                                         T.Cqx);
@@ -1426,7 +1562,10 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     a.partial_cap = c.partial_cap;
     a.G = G;
     a.nch_out = &c.st->list_nch;
-    k_gains_tc<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
+    if (kb)
+        k_gains_tc_kb<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
+    else
+        k_gains_tc<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
     return cudaGetLastError();
 }
 

@@ -85,6 +85,7 @@ _SIGS = {
     "ebc_threshold_ladder": [ctypes.c_double, _I32, ctypes.c_double, ctypes.c_double, _P, _I32,
                              ctypes.POINTER(_I32)],
     "ebc_set_graphs": [_P, _I32],
+    "ebc_set_kblocked": [_P, _I32],
     "ebc_set_lazy": [_P, _I32],
     "ebc_state_size": [_P, ctypes.POINTER(_I64)],
     "ebc_state_save": [_P, _P, _I64],
@@ -380,6 +381,9 @@ class Instance:
 
     def set_lazy(self, on: bool = True):
         ebc_set_lazy(self.h, on)
+
+    def set_kblocked(self, on: bool = True):
+        _raise(self.h, load().ebc_set_kblocked(_P(self.h), int(bool(on))))
 
     def autotune(self, reps: int = 3):
         ebc_autotune(self.h, reps)

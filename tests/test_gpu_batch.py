@@ -116,7 +116,9 @@ def test_batch_errors(torch):
         with pytest.raises(ebc.EbcError):
             b.submit(V, 11)
         with pytest.raises(ebc.EbcError):
-            b.submit(np.zeros((10, 200), np.float32), 2, "bf16")
+            b.submit(np.zeros((10, 200), np.float32), 2, "fp8")   # FP8 holds d <= 128
+        with pytest.raises(ebc.EbcError):
+            b.submit(np.zeros((10, 4097), np.float32), 2, "bf16")  # d <= 4096
         t = b.submit(np.random.default_rng(0).standard_normal((50, 4)).astype(np.float32), 3, "fp32")
         b.run()
         assert b.poll(t) is not None

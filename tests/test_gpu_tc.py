@@ -173,7 +173,7 @@ def test_tc_switch_precision_and_reload(torch):
     check_greedy(ih, fh, *r2)
 
 
-def test_tc_rejects_fp16_overflow_and_large_d(torch):
+def test_tc_rejects_fp16_overflow_and_fp8_large_d(torch):
     V = gmm(100, 8, 1)
     V[3, 2] = 1e6
     with ebc.Instance(V) as inst:
@@ -184,8 +184,10 @@ def test_tc_rejects_fp16_overflow_and_large_d(torch):
         inst.greedy_host(2)
     W = gmm(50, 200, 2)
     with ebc.Instance(W) as inst:
-        with pytest.raises(ebc.EbcError):
-            inst.set_precision("bf16")
+        inst.set_precision("bf16")  # d > 128: the K-blocked kernel
+        with pytest.raises(ebc.EbcError) as ei:
+            inst.set_precision("fp8")
+        assert ei.value.status == ebc.EBC_EINVAL
 
 
 def test_tc_deterministic(torch):
