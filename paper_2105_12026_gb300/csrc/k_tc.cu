@@ -159,6 +159,7 @@ __device__ __forceinline__ void unit_span(const TcArgs &a, const Plan &P, int u,
 
 struct SmemLayout {
     uint32_t a_main, a_sub, a_bytes, b_main, b_bytes, off_b, off_comb, off_bar, off_misc, total;
+    uint32_t off_ext;  // K-blocked layout: the extension buffer
 };
 
 // A buffer: sub-tile 0 (main K atoms, then its extension), sub-tile 1 (same).
@@ -175,27 +176,30 @@ __host__ __device__ inline SmemLayout smem_layout(int RB, int nstages, int na) {
     L.off_bar = L.off_comb + 2 * BMS * 8;
     L.off_misc = L.off_bar + (2 * nstages + 8) * 8;
     L.total = L.off_misc + 64 + 1024;  // + alignment slack for the 1024-byte base
+    L.off_ext = 0;
     return L;
 }
 
-// K-blocked stage (candidate rows too long to stay resident): one 128-byte
-// K atom of both candidate sub-tiles and of the point tile, then room for
-// the three extensions, which only the last K block of a point tile loads.
+// K-blocked layout (candidate rows too long to stay resident): stages of
+// one 128-byte K atom of both candidate sub-tiles and of the point tile
+// (64 KB), then one buffer for the three extensions of a point tile (16 KB),
+// loaded with the tile's last atom.
 __host__ __device__ inline SmemLayout smem_layout_kb(int nstages) {
     SmemLayout L;
     L.a_main = 0;
     L.a_sub = 0;
-    L.a_bytes = 0;
-    L.b_main = 2 * BMS * 128 + BN * 128;
-    L.b_bytes = L.b_main + 2 * BMS * KEXT * 2 + BN * KEXT * 2;
+    L.a_bytes = 2 * BMS * KEXT * 2 + BN * KEXT * 2;  // extension buffer
+    L.b_main = 2 * BMS * 128 + BN * 128;             // one stage
+    L.b_bytes = L.b_main;
     L.off_b = 0;
-    L.off_comb = nstages * L.b_bytes;
+    L.off_ext = nstages * L.b_bytes;
+    L.off_comb = L.off_ext + L.a_bytes;
     L.off_bar = L.off_comb + 2 * BMS * 8;
     L.off_misc = L.off_bar + (2 * nstages + 8) * 8;
     L.total = L.off_misc + 64 + 1024;
     return L;
 }
-constexpr int KB_STAGES = 2;
+constexpr int KB_STAGES = 3;
 
 __device__ __forceinline__ void record_timeout(int *err, volatile int *abort) {
     *abort = 1;
@@ -356,12 +360,16 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
             int g = 0, ua = 0;
             if constexpr (KB) {
                 // one stage per (point tile, K atom): A atom of both
-                // sub-tiles, B atom, and at the last atom the extensions
+                // sub-tiles and B atom; with the tile's last atom its
+                // extensions into the extension buffer (barriers a_full[0] /
+                // a_empty[0], one phase per point tile)
+                uint8_t *sx = base + L.off_ext;
+                int tt = 0;
                 for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
                     int ct, ch, b_row0, nb;
                     unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
                     bool ok = true;
-                    for (int i = 0; i < nb && ok; ++i) {
+                    for (int i = 0; i < nb && ok; ++i, ++tt) {
                         const int brow = b_row0 + i * BN;
                         for (int j = 0; j < katoms; ++j, ++g) {
                             const int s = g % ns;
@@ -372,18 +380,23 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                                 break;
                             }
                             uint8_t *st = sB + s * L.b_bytes;
-                            const bool last = j == katoms - 1;
-                            tc::mbar_arrive_expect_tx(&full[s], last ? L.b_bytes : L.b_main);
+                            tc::mbar_arrive_expect_tx(&full[s], L.b_main);
                             for (int h = 0; h < 2; ++h)
                                 tc::tma_load_2d(st + h * (BMS * 128), &tmA, &full[s], j * args.xatom, ct * BM + h * BMS);
                             tc::tma_load_2d(st + 2 * BMS * 128, &tmB, &full[s], j * args.xatom, brow);
-                            if (last) {
-                                for (int h = 0; h < 2; ++h)
-                                    tc::tma_load_2d(st + L.b_main + h * (BMS * KEXT * 2), &tmAx, &full[s], 0,
-                                                    ct * BM + h * BMS);
-                                tc::tma_load_2d(st + L.b_main + 2 * (BMS * KEXT * 2), &tmBx, &full[s], 0, brow);
-                            }
                             last_full[s] = ph;
+                            if (j == katoms - 1) {
+                                if (!tc::mbar_wait(&a_empty[0], (tt & 1) ^ 1, abort_flag)) {
+                                    record_timeout(args.err, abort_flag);
+                                    ok = false;
+                                    break;
+                                }
+                                tc::mbar_arrive_expect_tx(&a_full[0], L.a_bytes);
+                                for (int h = 0; h < 2; ++h)
+                                    tc::tma_load_2d(sx + h * (BMS * KEXT * 2), &tmAx, &a_full[0], 0, ct * BM + h * BMS);
+                                tc::tma_load_2d(sx + 2 * (BMS * KEXT * 2), &tmBx, &a_full[0], 0, brow);
+                                last_afull[0] = tt & 1;
+                            }
                         }
                     }
                     if (!ok) break;
@@ -441,13 +454,8 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                     unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
                     bool ok = true;
                     for (int i = 0; i < nb && ok; ++i, ++t) {
-                        for (int h = 0; h < 2 && ok; ++h)
-                            if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag)) {
-                                record_timeout(args.err, abort_flag);
-                                ok = false;
-                            }
-                        if (!ok) break;
-                        tc::tc_fence_after();
+                        // region h is awaited at its first MMA of the tile: region 0
+                        // fills again while the epilogue still drains region 1
                         for (int j = 0; j < katoms; ++j, ++g) {
                             const int s = g % ns;
                             if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag)) {
@@ -458,7 +466,23 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                             tc::tc_fence_after();
                             const uint32_t st = tc::smem_u32(sB + s * L.b_bytes);
                             const uint32_t b0 = st + 2 * BMS * 128;
-                            for (int h = 0; h < 2; ++h) {
+                            const bool last = j == katoms - 1;
+                            if (last && !tc::mbar_wait(&a_full[0], t & 1, abort_flag)) {
+                                record_timeout(args.err, abort_flag);
+                                ok = false;
+                                break;
+                            }
+                            if (last) tc::tc_fence_after();
+                            const uint32_t sx = tc::smem_u32(base + L.off_ext);
+                            for (int h = 0; h < 2 && ok; ++h) {
+                                if (j == 0) {
+                                    if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag)) {
+                                        record_timeout(args.err, abort_flag);
+                                        ok = false;
+                                        break;
+                                    }
+                                    tc::tc_fence_after();
+                                }
                                 const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
                                 const uint32_t ah = st + h * (BMS * 128);
                                 for (int w = 0; w < 4; ++w) {
@@ -466,11 +490,12 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                                     const uint64_t bd = tc::sdesc_sw128(b0 + w * 32);
                                     tc::mma_f16(d_tmem, ad, bd, args.idesc, (j > 0 || w > 0) ? 1u : 0u);
                                 }
-                                if (j == katoms - 1)
-                                    tc::mma_f16(d_tmem, tc::sdesc_sw32(st + L.b_main + h * (BMS * KEXT * 2)),
-                                                tc::sdesc_sw32(st + L.b_main + 2 * (BMS * KEXT * 2)), args.idesc_ext,
-                                                1u);
+                                if (last)
+                                    tc::mma_f16(d_tmem, tc::sdesc_sw32(sx + h * (BMS * KEXT * 2)),
+                                                tc::sdesc_sw32(sx + 2 * (BMS * KEXT * 2)), args.idesc_ext, 1u);
                             }
+                            if (!ok) break;
+                            if (last) tc::mma_commit(&a_empty[0]);
                             tc::mma_commit(&empty[s]);
                         }
                         if (!ok) break;
