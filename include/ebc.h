@@ -251,11 +251,15 @@ ebc_status ebc_greedy_host(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);
  *   Sieve Streaming: one handle (or one reset state) per value v of
  *                   ebc_threshold_ladder(m, K, eps, 2), thr = {v}, patience 0;
  *                   keep the best f.
- * Decisions use certified gains: a bulk upper bound of every streamed item
- * (tensor cores at BF16 / FP16 / FP8, rigorous FP32 bounds at EBC_FP32)
- * rejects the items it can, and the exact gain (as in Greedy's pick)
- * decides the rest, so decisions and f match the FP64 definition except
- * where the gain and tau agree to about 1e-12 relative.
+ * Decisions use certified gains: upper bounds reject the items they can and
+ * the exact gain (as in Greedy's pick) decides the rest, so decisions and f
+ * match the FP64 definition except where the gain and tau agree to about
+ * 1e-12 relative.  The handle keeps an upper bound of every point's gain
+ * while S only grows (diminishing returns, Sec. 3, Def. 3): an item whose
+ * bound is below its tau is rejected without device work; the others get a
+ * fresh bulk bound (tensor cores at BF16 / FP16 / FP8, rigorous FP32 bounds
+ * at EBC_FP32) before any exact gain.  ebc_reset, ebc_reload and
+ * ebc_state_load drop the kept bounds.
  */
 typedef struct {
     int32_t K;           /* summary size bound, counting the points already in S */
@@ -268,6 +272,9 @@ typedef struct {
     int64_t consumed;    /* out: stream positions decided by the last call (len unless |S| reached K) */
     int64_t bounded;     /* in/out counter: items given a bulk upper bound */
     int64_t exact;       /* in/out counter: items whose exact gain was computed */
+    const double *bounds; /* optional host [n]: upper bounds of every point's gain valid for the
+                             current S and every larger one (e.g. ebc_gain_bounds at S = {});
+                             NULL: none */
 } ebc_sieve_state;
 
 /*
@@ -282,6 +289,18 @@ typedef struct {
  */
 ebc_status ebc_sieve_host(ebc_t h, ebc_sieve_state *s, const int32_t *items, int64_t len, int32_t *out_idx,
                           double *out_f, int32_t *out_count);
+
+/*
+ * Rigorous upper bounds of Delta_f(c | S) for m candidates (same arguments
+ * as ebc_gains): the bulk kernel in its upper-bound mode (the per-pair slack
+ * of the certified Greedy pick), widened by the relative error of its
+ * partial sums; 0 for candidates in S.  Bounds at S = {} stay valid for
+ * every S (Sec. 3, Def. 3): the ebc_sieve_state.bounds of a fresh stream.
+ */
+ebc_status ebc_gain_bounds(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_ub);
+
+/* Host-pointer form of ebc_gain_bounds. */
+ebc_status ebc_gain_bounds_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_ub);
 
 /*
  * Threshold ladder of the streaming optimisers: every value (1 + eps)^i (i an

@@ -49,6 +49,9 @@ struct ebc_ctx {
     int lazy_at_capture = -1;
     bool graphs = true;          // replay rounds from a graph when possible
     bool attrs_ready = false;    // one direct round has run (kernel attributes are set)
+    // threshold sieve: upper bounds of every point's gain, valid while S only
+    // grows (emptied whenever S is reset or replaced)
+    std::vector<double> sieve_ub;
 };
 
 namespace {
@@ -139,6 +142,11 @@ __global__ void k_sanitize(const int32_t *__restrict__ in, int64_t m, int64_t n,
 __global__ void k_zero_masked(const int32_t *__restrict__ cand, int64_t m, double *__restrict__ out) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j < m && cand[j] < 0) out[j] = 0.0;
+}
+
+__global__ void k_scale(double *__restrict__ x, int64_t m, double a) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < m) x[j] *= a;
 }
 
 __global__ void k_check_csr(const int64_t *__restrict__ off, int64_t l, ebc::DevState *st, int *bad) {
@@ -419,6 +427,7 @@ ebc_status ebc_reload(ebc_t h, const float *V, int32_t v_on_device) {
     if (c.tc.prec >= 0) CK(h, launch(h, -1, 1, [&] { return ebc::tc_quantize(c); }));
     if (c.tc8.ready) CK(h, launch(h, -1, 3, [&] { return ebc::tc8_setup(c); }));
     h->nsel = 0;
+    h->sieve_ub.clear();
     return EBC_OK;
 }
 
@@ -517,6 +526,7 @@ ebc_status ebc_reset(ebc_t h) {
     if (check_handle(h)) return EBC_EINVAL;
     CK(h, ebc::launch_reset_state(h->c));
     h->nsel = 0;
+    h->sieve_ub.clear();
     return EBC_OK;
 }
 
@@ -713,6 +723,7 @@ ebc_status ebc_state_load(ebc_t h, const void *host_buf, int64_t bytes) {
     if (c.ub64) CK(h, ebc::launch_lazy_init(c));  // after the flags: selected candidates get -1
     CK(h, cudaStreamSynchronize(c.stream));
     h->nsel = hd.nsel;
+    h->sieve_ub.clear();
     return EBC_OK;
 }
 
@@ -789,6 +800,70 @@ ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *o
     ebc::pool_free(d_c, c.stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "ebc_gains_host");
     if (s != EBC_OK) return s;
+    return ebc_sync(h);
+}
+
+ebc_status ebc_gain_bounds(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_ub) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (m < 0) return fail(h, EBC_EINVAL, "ebc_gain_bounds: m < 0");
+    if (!cand_idx && m != c.n) return fail(h, EBC_EINVAL, "ebc_gain_bounds: cand_idx NULL requires m == n");
+    if (m == 0) return EBC_OK;
+    if (!out_ub) return fail(h, EBC_EINVAL, "ebc_gain_bounds: out_ub is NULL");
+    const double scale = 1.0 + bulk_eta(c);
+    for (int64_t j0 = 0; j0 < m; j0 += c.n) {
+        const int64_t mb = std::min<int64_t>(c.n, m - j0);
+        k_sanitize<<<(unsigned)((mb + 255) / 256), 256, 0, c.stream>>>(cand_idx ? cand_idx + j0 : nullptr, mb, c.n,
+                                                                       c.cand_buf, c.st);
+        CK(h, cudaGetLastError());
+        h->prof.p.launches += 1;
+        int nch = h->nch;
+        const int *cl = cand_idx ? c.cand_buf : nullptr;
+        if (c.prec == EBC_FP32) {
+            CK(h, launch(h, PK_BULK, 1, [&] { return ebc::launch_gains_fp32(c, c.cand_buf, mb, true, h->ch, h->nch); }));
+        } else {  // upper-bound mode of the 16-bit kernel (FP8 handles use their BF16 copy)
+            CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, true); }));
+            CK(h, launch(h, PK_BULK, 2, [&] { return ebc::launch_gains_tc(c, cl, mb, true, &nch); }));
+        }
+        h->prof.p.bulk_evals += mb * c.n;
+        CK(h, launch(h, -1, 2, [&] {
+               return ebc::launch_reduce_select(c, mb, nch, c.cand_buf, false, out_ub + j0, h->nblk);
+           }));
+        k_zero_masked<<<(unsigned)((mb + 255) / 256), 256, 0, c.stream>>>(c.cand_buf, mb, out_ub + j0);
+        CK(h, cudaGetLastError());
+        k_scale<<<(unsigned)((mb + 255) / 256), 256, 0, c.stream>>>(out_ub + j0, mb, scale);
+        CK(h, cudaGetLastError());
+        h->prof.p.launches += 2;
+    }
+    return EBC_OK;
+}
+
+ebc_status ebc_gain_bounds_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_ub) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (m < 0 || (!cand_idx && m != c.n) || (m > 0 && !out_ub)) return fail(h, EBC_EINVAL, "ebc_gain_bounds_host: bad arguments");
+    if (m == 0) return EBC_OK;
+    if (cand_idx)
+        for (int64_t j = 0; j < m; ++j)
+            if (cand_idx[j] < 0 || (int64_t)cand_idx[j] >= c.n) return fail(h, EBC_EINDEX, "ebc_gain_bounds_host: index outside [0, n)");
+    int32_t *d_c = nullptr;
+    double *d_u = nullptr;
+    if (cand_idx) CK(h, dalloc(&d_c, m, c));
+    cudaError_t e = dalloc(&d_u, m, c);
+    if (e != cudaSuccess) {
+        ebc::pool_free(d_c, c.stream);
+        return cuda_fail(h, e, "ebc_gain_bounds_host: allocation");
+    }
+    ebc_status st = EBC_OK;
+    if (cand_idx) e = cudaMemcpyAsync(d_c, cand_idx, sizeof(int32_t) * m, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) st = ebc_gain_bounds(h, d_c, m, d_u);
+    if (e == cudaSuccess && st == EBC_OK)
+        e = cudaMemcpyAsync(out_ub, d_u, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess && st == EBC_OK) e = cudaStreamSynchronize(c.stream);
+    ebc::pool_free(d_u, c.stream);
+    ebc::pool_free(d_c, c.stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "ebc_gain_bounds_host");
+    if (st != EBC_OK) return st;
     return ebc_sync(h);
 }
 
@@ -1199,32 +1274,54 @@ ebc_status ebc_sieve_host(ebc_t h, ebc_sieve_state *s, const int32_t *items, int
     int64_t nsel = h->nsel;
     int32_t cnt = 0;
 
-    std::vector<int32_t> hl, xl;
-    std::vector<int64_t> lpos;  // batch position -> list entry, -1 for items in S
-    std::vector<double> hub, xg;
+    // upper bounds of every point's gain, valid while S only grows (kept by
+    // the handle across calls; diminishing returns, Def. 3): an item whose
+    // bound is below its tau is rejected without device work
+    std::vector<double> &ub = h->sieve_ub;
+    if ((int64_t)ub.size() != c.n) ub.assign((size_t)c.n, INFINITY);
+    if (s->bounds)
+        for (int64_t i = 0; i < c.n; ++i) ub[(size_t)i] = std::min(ub[(size_t)i], s->bounds[i]);
+
     struct Maybe {
-        int64_t pos;  // batch position
+        int64_t pos;  // stream position
         double tau;
         int32_t level;
     };
-    std::vector<Maybe> U;
+    std::vector<Maybe> U, X;  // positions whose cached bound reaches tau; then those still needing the exact gain
+    std::vector<int32_t> hl, xl;
+    std::vector<double> hub, xg;
 
-    int64_t p = 0, bsz = bmin;
+    // batch: up to bsz items to bound within a walk of at most wlen stream
+    // positions; both grow while nothing is accepted and restart from the
+    // distance to the last acceptance (a walk after an acceptance revisits
+    // the positions behind it with the new tau)
+    int64_t p = 0, bsz = bmin, wlen = 4096;
     while (p < len && nsel < K) {
-        const int64_t nb = std::min(bsz, len - p);
-        // level 1: bulk upper bounds of the batch's items not in S
-        hl.clear();
-        lpos.assign((size_t)nb, -1);
-        for (int64_t i = 0; i < nb; ++i) {
-            const int32_t e = items[p + i];
+        // walk from p as if every item were rejected (the state up to the
+        // first acceptance), collecting the positions whose bound reaches
+        // their tau
+        U.clear();
+        int32_t lev = level;
+        int64_t r = rej, q = p;
+        for (; q < len && (int64_t)U.size() < bsz && q - p < wlen; ++q) {
+            const int32_t e = items[q];
             if (!sel[(size_t)e]) {
-                lpos[(size_t)i] = (int64_t)hl.size();
-                hl.push_back(e);
+                const double tau = (thr[lev] / 2.0 - f) / (double)((int64_t)K - nsel);
+                if (!(ub[(size_t)e] < tau)) U.push_back({q, tau, lev});
+            }
+            r += 1;
+            if (patience > 0 && r >= patience) {
+                if (lev + 1 < nthr) lev += 1;
+                r = 0;
             }
         }
-        const int64_t nl = (int64_t)hl.size();
-        hub.assign((size_t)nl, 0.0);
-        if (nl > 0) {
+        // level 1: fresh bulk upper bounds of those items
+        X.clear();
+        if (!U.empty()) {
+            const int64_t nl = (int64_t)U.size();
+            hl.resize((size_t)nl);
+            for (int64_t i = 0; i < nl; ++i) hl[(size_t)i] = items[U[(size_t)i].pos];
+            hub.resize((size_t)nl);
             CK(h, cudaMemcpyAsync(B.list, hl.data(), sizeof(int32_t) * nl, cudaMemcpyHostToDevice, c.stream));
             if (tc) {
                 int nch = h->nch;
@@ -1246,37 +1343,26 @@ ebc_status ebc_sieve_host(ebc_t h, ebc_sieve_state *s, const int32_t *items, int
             CK(h, cudaMemcpyAsync(hub.data(), B.ub, sizeof(double) * nl, cudaMemcpyDeviceToHost, c.stream));
             CK(h, cudaStreamSynchronize(c.stream));
             s->bounded += nl;
-            if (tc)
-                for (double &u : hub) u *= 1.0 + eta;  // rigorous: partial sums carry relative error <= eta
-        }
-        // walk the batch as if every item were rejected (that is the state
-        // up to the first accept); items whose bound reaches tau may accept
-        U.clear();
-        int32_t lev = level;
-        int64_t r = rej;
-        for (int64_t i = 0; i < nb; ++i) {
-            const int64_t li = lpos[(size_t)i];
-            if (li >= 0) {
-                const double tau = (thr[lev] / 2.0 - f) / (double)((int64_t)K - nsel);
-                if (!(hub[(size_t)li] < tau)) U.push_back({i, tau, lev});
-            }
-            r += 1;
-            if (patience > 0 && r >= patience) {
-                if (lev + 1 < nthr) lev += 1;
-                r = 0;
+            for (int64_t i = 0; i < nl; ++i) {
+                // rigorous: TC partial sums carry relative error <= eta
+                const double b = tc ? hub[(size_t)i] * (1.0 + eta) : hub[(size_t)i];
+                double &u = ub[(size_t)hl[(size_t)i]];
+                u = std::min(u, b);
+                if (!(u < U[(size_t)i].tau)) X.push_back(U[(size_t)i]);
             }
         }
-        // level 2: exact gains of those items in stream order, up to the first
-        // that reaches its tau; groups of 8, 16, ... kSieveExact (one pass over
-        // V serves 8 items, and the first candidates usually decide)
+        // level 2: exact gains of the items still undecided, in stream
+        // order, up to the first that reaches its tau; groups of 8, 16, ...
+        // kSieveExact (one pass over V serves 8 items, and the first
+        // candidates usually decide)
         int64_t acc = -1;
         double acc_g = 0.0;
         int32_t acc_lev = level;
         size_t group = 8;
-        for (size_t u0 = 0; u0 < U.size() && acc < 0; u0 += group, group = std::min<size_t>(2 * group, kSieveExact)) {
-            const int ng = (int)std::min<size_t>(group, U.size() - u0);
+        for (size_t u0 = 0; u0 < X.size() && acc < 0; u0 += group, group = std::min<size_t>(2 * group, kSieveExact)) {
+            const int ng = (int)std::min<size_t>(group, X.size() - u0);
             xl.resize((size_t)ng);
-            for (int j = 0; j < ng; ++j) xl[(size_t)j] = items[p + U[u0 + j].pos];
+            for (int j = 0; j < ng; ++j) xl[(size_t)j] = items[X[u0 + j].pos];
             CK(h, cudaMemcpyAsync(B.xlist, xl.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, c.stream));
             CK(h, cudaMemcpyAsync(B.cnt + 1, &ng, sizeof(int), cudaMemcpyHostToDevice, c.stream));
             CK(h, launch(h, PK_REFINE, 1, [&] {
@@ -1288,27 +1374,29 @@ ebc_status ebc_sieve_host(ebc_t h, ebc_sieve_state *s, const int32_t *items, int
             CK(h, cudaStreamSynchronize(c.stream));
             s->exact += ng;
             for (int j = 0; j < ng; ++j)
-                if (xg[(size_t)j] >= U[u0 + j].tau) {
-                    acc = U[u0 + j].pos;
+                if (xg[(size_t)j] >= X[u0 + j].tau) {
+                    acc = X[u0 + j].pos;
                     acc_g = xg[(size_t)j];
-                    acc_lev = U[u0 + j].level;
+                    acc_lev = X[u0 + j].level;
                     break;
                 }
         }
-        if (acc < 0) {  // the whole batch is rejected
+        if (acc < 0) {  // every walked position is a rejection
             level = lev;
             rej = r;
-            p += nb;
-            s->consumed += nb;
+            s->consumed += q - p;
+            p = q;
             bsz = std::min(bcap, 2 * bsz);
+            wlen = std::min<int64_t>(len, 2 * wlen);
             continue;
         }
-        const int32_t item = items[p + acc];
+        const int32_t item = items[acc];
         CK(h, launch(h, -1, 2, [&] {
                cudaError_t e = ebc::launch_sieve_commit(c, item, acc_g);
                return e != cudaSuccess ? e : ebc::launch_update(c);
            }));
         sel[(size_t)item] = 1;
+        ub[(size_t)item] = 0.0;
         f += acc_g;  // the device adds the same double to the same f
         nsel += 1;
         h->nsel = nsel;
@@ -1317,9 +1405,12 @@ ebc_status ebc_sieve_host(ebc_t h, ebc_sieve_state *s, const int32_t *items, int
         cnt += 1;
         level = acc_lev;
         rej = 0;
-        p += acc + 1;
-        s->consumed += acc + 1;
-        bsz = std::min(bcap, std::max(bmin, 2 * (acc + 1)));
+        int64_t ua = 0;  // items bounded in this walk up to the accepted one
+        while (ua < (int64_t)U.size() && U[(size_t)ua].pos <= acc) ++ua;
+        s->consumed += acc + 1 - p;
+        bsz = std::min(bcap, std::max(bmin, 2 * ua));
+        wlen = std::max<int64_t>(4096, 2 * (acc + 1 - p));
+        p = acc + 1;
     }
     s->level = level;
     s->rejections = rej;

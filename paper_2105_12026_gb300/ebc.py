@@ -57,7 +57,7 @@ class ebc_sieve_state(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("nthr", ctypes.c_int32), ("thr", ctypes.c_void_p),
                 ("patience", ctypes.c_int64), ("level", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("rejections", ctypes.c_int64), ("consumed", ctypes.c_int64), ("bounded", ctypes.c_int64),
-                ("exact", ctypes.c_int64)]
+                ("exact", ctypes.c_int64), ("bounds", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -81,6 +81,8 @@ _SIGS = {
     "ebc_gains_host": [_P, _P, _I64, _P],
     "ebc_greedy": [_P, _I32, _P, _P],
     "ebc_greedy_host": [_P, _I32, _P, _P],
+    "ebc_gain_bounds": [_P, _P, _I64, _P],
+    "ebc_gain_bounds_host": [_P, _P, _I64, _P],
     "ebc_sieve_host": [_P, ctypes.POINTER(ebc_sieve_state), _P, _I64, _P, _P, ctypes.POINTER(_I32)],
     "ebc_threshold_ladder": [ctypes.c_double, _I32, ctypes.c_double, ctypes.c_double, _P, _I32,
                              ctypes.POINTER(_I32)],
@@ -476,6 +478,29 @@ class Instance:
     def current_f(self):
         return ebc_current_f(self.h)
 
+    def gain_bounds_host(self, cand=None) -> np.ndarray:
+        """Rigorous upper bounds of the gains of ``cand`` (all points if None)
+        relative to the current state (ebc_gain_bounds_host)."""
+        if cand is None:
+            out = np.zeros(self.n, dtype=np.float64)
+            _raise(self.h, load().ebc_gain_bounds_host(_P(self.h), None, self.n, out.ctypes.data_as(_P)))
+            return out
+        cand = np.ascontiguousarray(cand, dtype=np.int32).ravel()
+        out = np.zeros(cand.size, dtype=np.float64)
+        _raise(self.h, load().ebc_gain_bounds_host(_P(self.h), cand.ctypes.data_as(_P), cand.size,
+                                                   out.ctypes.data_as(_P)))
+        return out
+
+    def singleton_bounds(self) -> np.ndarray:
+        """Upper bounds of every point's gain valid for every S: the bounds
+        at S = {} (the current state is saved and restored)."""
+        snap = self.save_state()
+        try:
+            self.reset()
+            return self.gain_bounds_host()
+        finally:
+            self.load_state(snap)
+
     def max_singleton(self) -> float:
         """max_e f({e}) over V: the exact gain of Greedy's first pick from
         S = {} (the current state is saved and restored)."""
@@ -486,15 +511,15 @@ class Instance:
         finally:
             self.load_state(snap)
 
-    def sieve(self, K: int, thresholds, patience: int = 0) -> "Sieve":
-        return Sieve(self, K, thresholds, patience)
+    def sieve(self, K: int, thresholds, patience: int = 0, bounds=None) -> "Sieve":
+        return Sieve(self, K, thresholds, patience, bounds)
 
 
 class Sieve:
     """Threshold sieve over a stream on one Instance (ebc_sieve_host): feed
     items in pieces; the level / rejection state carries over."""
 
-    def __init__(self, inst: Instance, K: int, thresholds, patience: int = 0):
+    def __init__(self, inst: Instance, K: int, thresholds, patience: int = 0, bounds=None):
         self.inst = inst
         self.thr = np.ascontiguousarray(thresholds, dtype=np.float64).ravel()
         self.state = ebc_sieve_state()
@@ -502,6 +527,11 @@ class Sieve:
         self.state.nthr = self.thr.size
         self.state.thr = self.thr.ctypes.data
         self.state.patience = int(patience)
+        self.bounds = None
+        if bounds is not None:
+            self.bounds = np.ascontiguousarray(bounds, dtype=np.float64).ravel()
+            assert self.bounds.size == inst.n
+            self.state.bounds = self.bounds.ctypes.data
         self.idx = []
         self.f = []
 
@@ -525,36 +555,83 @@ class Sieve:
                 "exact": s.exact}
 
 
-def three_sieves(inst: Instance, items, K: int, eps: float, T: int, m_single: float | None = None):
+def three_sieves(inst: Instance, items, K: int, eps: float, T: int, m_single: float | None = None,
+                 bounds=None):
     """Three Sieves on the instance's current state: thresholds from K m down
-    to m, moving down after T consecutive rejections.  Returns (idx, f, Sieve)."""
+    to m, moving down after T consecutive rejections.  ``bounds``: optional
+    upper bounds of every point's gain (e.g. ``inst.singleton_bounds()``).
+    Returns (idx, f, Sieve)."""
     if m_single is None:
         m_single = inst.max_singleton()
-    sv = Sieve(inst, K, ebc_threshold_ladder(m_single, K, eps, 1.0), T)
+    sv = Sieve(inst, K, ebc_threshold_ladder(m_single, K, eps, 1.0), T, bounds)
     idx, f = sv.feed(items)
     return idx, f, sv
 
 
-def sieve_streaming(inst: Instance, items, K: int, eps: float, m_single: float | None = None):
+def sieve_streaming(inst: Instance, items, K: int, eps: float, m_single: float | None = None,
+                    workers: int = 1, V=None):
     """Sieve Streaming with the largest singleton value m known: one sieve per
-    ladder value up to 2 K m, each run from S = {} on the instance (reset
-    between sieves).  Returns (best idx, best f, per-sieve f_end list,
-    thresholds); the instance is left in the best sieve's state."""
+    ladder value up to 2 K m, each run from S = {} over the whole stream; the
+    summary of largest f wins (the first such threshold on ties).  Returns
+    (best idx, best f, per-sieve f_end list, thresholds); ``inst`` is left in
+    the best sieve's state.
+
+    ``workers`` > 1 runs the sieves on that many instances at once (one CUDA
+    stream and one host thread each; the binding releases the interpreter
+    lock in every library call); ``V`` (the instance's ground set, host array
+    or CUDA tensor) is then needed to create them.  Results do not depend on
+    ``workers``."""
     if m_single is None:
         m_single = inst.max_singleton()
     thr = ebc_threshold_ladder(m_single, K, eps, 2.0)
-    best = None
-    ends = []
-    for j, v in enumerate(thr):
-        inst.reset()
-        idx, f = Sieve(inst, K, [v], 0).feed(items)
-        fe = float(f[-1]) if f.size else 0.0
-        ends.append(fe)
-        if best is None or fe > best[2]:
-            best = (idx, f, fe, inst.save_state())
-    inst.load_state(best[3])
-    return best[0], best[1], ends, thr
+    items = np.ascontiguousarray(items, dtype=np.int32).ravel()
+    ub0 = inst.singleton_bounds()  # valid for every sieve's S
+    ends = [0.0] * thr.size
+    snaps = [None] * thr.size
+    idxs = [None] * thr.size
+    fs = [None] * thr.size
 
+    def run(h_inst, js):
+        for j in js:
+            h_inst.reset()
+            idx, f = Sieve(h_inst, K, [thr[j]], 0, ub0).feed(items)
+            ends[j] = float(f[-1]) if f.size else 0.0
+            idxs[j], fs[j] = idx, f
+            snaps[j] = h_inst.save_state()
+
+    workers = max(1, min(int(workers), thr.size))
+    if workers == 1:
+        run(inst, range(thr.size))
+    else:
+        import threading
+
+        import torch
+        if V is None:
+            raise ValueError("sieve_streaming with workers > 1 needs V")
+        streams = [torch.cuda.Stream() for _ in range(workers - 1)]
+        pool = [inst] + [Instance(V, precision=inst.precision, stream=st) for st in streams]
+        try:
+            errs = []
+
+            def body(w):
+                try:
+                    run(pool[w], range(w, thr.size, workers))
+                except Exception as e:  # re-raised below
+                    errs.append(e)
+
+            ts = [threading.Thread(target=body, args=(w,)) for w in range(workers)]
+            for t in ts:
+                t.start()
+            for t in ts:
+                t.join()
+            if errs:
+                raise errs[0]
+        finally:
+            for extra in pool[1:]:
+                extra.close()
+    best = max(range(thr.size), key=lambda j: (ends[j], -j))
+    inst.load_state(snaps[best])
+    return idxs[best], fs[best], ends, thr
 
 # ---------------------------------------------------------------------------
 # batch runtime (marshalling only)

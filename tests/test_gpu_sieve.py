@@ -89,6 +89,72 @@ def test_sieve_streaming_matches_oracle(torch):
     assert max(ends) == pytest.approx(rbest["f_end"], rel=F_RTOL)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp32", "fp8"])
+def test_gain_bounds_are_upper_bounds(torch, prec):
+    """ebc_gain_bounds against the oracle's exact gains, at S = {} and after
+    a few Greedy picks: every bound >= the exact gain, and close to it."""
+    n, d = 1500, 40
+    V = gmm(n, d, 14)
+    cand = np.arange(0, n, 3, dtype=np.int32)
+    m = oracle.norms(V)
+    with ebc.Instance(V, precision=prec) as inst:
+        for step in range(2):
+            ub = inst.gain_bounds_host(cand)
+            ex = oracle.gains(V, m, cand)
+            assert np.all(ub >= ex * (1 - 1e-12)), np.min(ub - ex)
+            assert np.all(ub <= ex + 0.05 * max(ex.max(), 1e-9))
+            picks, _ = inst.greedy_host(4)
+            for c in picks:
+                oracle.update_m(V, m, c)
+                ex_sel = oracle.gains(V, m, [c])
+                assert ex_sel[0] == 0.0
+        assert np.all(inst.gain_bounds_host(picks) == 0.0)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_primed_bounds_and_cache_keep_decisions(torch, prec):
+    """Singleton bounds as the sieve's starting bounds, and the bounds the
+    handle keeps across calls, change the work but not one decision."""
+    n, d, K = 2500, 32, 15
+    V = gmm(n, d, 19)
+    stream = np.random.default_rng(9).permutation(n).astype(np.int32)
+    with ebc.Instance(V, precision=prec) as a:
+        m1 = a.max_singleton()
+        thr = ebc.ebc_threshold_ladder(m1, K, 0.05, 1.0)
+        plain = a.sieve(K, thr, 40)
+        i1, f1 = plain.feed(stream)
+        a.reset()
+        primed = a.sieve(K, thr, 40, bounds=a.singleton_bounds())
+        i2, f2 = primed.feed(stream)
+        a.reset()                                   # the kept bounds are dropped
+        again = a.sieve(K, thr, 40)
+        i3, f3 = again.feed(stream)
+    np.testing.assert_array_equal(i1, i2)
+    np.testing.assert_array_equal(f1, f2)
+    np.testing.assert_array_equal(i1, i3)
+    np.testing.assert_array_equal(f1, f3)
+    assert primed.counters()["bounded"] <= plain.counters()["bounded"]
+    assert again.counters()["bounded"] == plain.counters()["bounded"]
+
+
+def test_sieve_streaming_workers_equal_sequential(torch):
+    n, d, K, eps = 3000, 48, 10, 0.15
+    V = gmm(n, d, 8)
+    stream = np.random.default_rng(6).permutation(n).astype(np.int32)
+    with ebc.Instance(V, precision="bf16") as a:
+        m1 = a.max_singleton()
+        i1, f1, e1, t1 = ebc.sieve_streaming(a, stream, K, eps, m1)
+        fa = a.current_f()
+    with ebc.Instance(V, precision="bf16") as b:
+        i4, f4, e4, t4 = ebc.sieve_streaming(b, stream, K, eps, m1, workers=4, V=V)
+        fb = b.current_f()
+    np.testing.assert_array_equal(t1, t4)
+    assert e1 == e4
+    np.testing.assert_array_equal(i1, i4)
+    np.testing.assert_array_equal(f1, f4)
+    assert fa == fb
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])
 def test_stream_in_pieces_equals_one_pass(torch, prec):
     V = gmm(3000, 48, 21)
