@@ -125,3 +125,36 @@ def test_tune_table_json_roundtrip(lib, tmp_path):
     with pytest.raises(ebc.EbcError):
         ebc.ebc_tune_load(str(tmp_path / "missing.json"))
     ebc.ebc_tune_clear()
+
+
+@pytest.mark.parametrize("m,K,eps,upper", [(0.5553, 5, 0.2, 1.0), (1.0, 10, 0.1, 2.0), (3.7e-3, 100, 0.01, 1.0),
+                                           (1.0, 1, 1.0, 1.0), (7.0, 3, 0.5, 2.0), (18.34, 100, 0.001, 1.0),
+                                           (1e-30, 7, 0.3, 2.0), (2.0 ** 40, 50, 0.05, 1.0)])
+def test_threshold_ladder_matches_oracle(lib, m, K, eps, upper):
+    """The library's ladder (host logic of the streaming optimisers) equals
+    the oracle's, value for value."""
+    import oracle
+    got = ebc.ebc_threshold_ladder(m, K, eps, upper)
+    ref = oracle.threshold_ladder(m, K, eps, upper)
+    np.testing.assert_array_equal(got, ref)
+    assert got.size >= 1 and np.all(np.diff(got) < 0)
+
+
+def test_threshold_ladder_errors(lib):
+    cnt = ctypes.c_int32()
+    f = lib.ebc_threshold_ladder
+    for args in [(0.0, 5, 0.1, 1.0), (1.0, 0, 0.1, 1.0), (1.0, 5, 0.0, 1.0), (1.0, 5, 0.1, 0.0),
+                 (float("inf"), 5, 0.1, 1.0), (float("nan"), 5, 0.1, 1.0), (1.0, 5, 1e-12, 1.0)]:
+        assert f(*args, None, 0, ctypes.byref(cnt)) == ebc.EBC_EINVAL, args
+    assert f(1.0, 5, 0.1, 1.0, None, 0, None) == ebc.EBC_EINVAL
+    assert f(1.0, 4, 1.0, 1.0, None, 0, ctypes.byref(cnt)) == ebc.EBC_OK and cnt.value == 3  # 4, 2, 1
+    out = np.zeros(2)
+    assert f(1.0, 4, 1.0, 1.0, out.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(cnt)) == ebc.EBC_EINVAL
+
+
+def test_sieve_rejects_null_handle(lib):
+    st = ebc.ebc_sieve_state()
+    cnt = ctypes.c_int32()
+    assert lib.ebc_sieve_host(None, ctypes.byref(st), None, 0, None, None, ctypes.byref(cnt)) == ebc.EBC_EINVAL
+    assert lib.ebc_gain_bounds(None, None, 0, None) == ebc.EBC_EINVAL
+    assert lib.ebc_set_kblocked(None, 1) == ebc.EBC_EINVAL
