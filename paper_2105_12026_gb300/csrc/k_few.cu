@@ -205,7 +205,7 @@ __device__ __forceinline__ void stage_candidates(const float *__restrict__ V, in
 // widened for), then in FP64, then over the block's groups in a fixed order.
 // Lists longer than max_cnt are left to the tiled kernel.
 template <bool VEC4, int DL, int LPP>
-__global__ void __launch_bounds__(FW * 32) k_few_bounds(const float *__restrict__ V, int64_t n, int d,
+__global__ void __launch_bounds__(FW * 32, DL == 4 ? 3 : 1) k_few_bounds(const float *__restrict__ V, int64_t n, int d,
                                                         const double *__restrict__ m64, const int *__restrict__ list,
                                                         const int *__restrict__ count, int cap, int64_t chunk,
                                                         int nchunks, float kh, float kl, double *__restrict__ out_lo,
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(FW * 32) k_few_bounds(const float *__restrict_
 // rounded up, kh = 1 - rho rounded down, proves d >= m_v: the pair
 // contributes exactly 0).
 template <bool VEC4, int DL, int LPP>
-__global__ void __launch_bounds__(FW * 32) k_few_exact(const float *__restrict__ V, int64_t n, int d,
+__global__ void __launch_bounds__(FW * 32, DL == 4 ? 3 : 1) k_few_exact(const float *__restrict__ V, int64_t n, int d,
                                                        const double *__restrict__ m64, const int *__restrict__ list,
                                                        const int *__restrict__ count, int cap, int64_t chunk,
                                                        int nchunks, float kh, double *__restrict__ out) {
