@@ -34,7 +34,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the bulk kernel from one ncu capture
 # of the current kernel (profiles/k_gains_tc_bf16_regime_n200k_d128.md), keyed
 # by (precision, n, d); None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("bf16", 200_000, 128): 309.266688e6 + 11.610112e6}
+NCU_TRAFFIC = {("bf16", 200_000, 128): 298.912e6 + 11.72736e6}
 
 
 def peaks():
