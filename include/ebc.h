@@ -116,9 +116,9 @@ ebc_status ebc_set_stream(ebc_t h, void *stream);
 /*
  * Select the bulk arithmetic and K, the number of leading candidates that
  * Greedy re-evaluates exactly each round (1 <= K <= 31; default FP32, K = 8).
- * EBC_BF16 / EBC_FP16 take any d (above d = 128 the bulk kernel streams the
- * rows in 64-element K blocks, see ebc_set_kblocked); EBC_FP8E4M3 needs
- * d <= 128.  EBC_FP8E4M3 also keeps the BF16
+ * EBC_BF16 / EBC_FP16 take any d (above d = 128 the bulk and multi-set
+ * kernels stream the rows in 64-element K blocks, see ebc_set_kblocked);
+ * EBC_FP8E4M3 needs d <= 128.  EBC_FP8E4M3 also keeps the BF16
  * copy: ebc_gains returns the raw FP8 gains, ebc_greedy bounds every
  * candidate with FP8 and then certifies as the lazy Greedy does with BF16
  * bounds (same picks as every other precision), ebc_eval_sets uses BF16.
@@ -137,8 +137,7 @@ ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k);
  *   out_f    device double[l]; an empty set gives 0.
  * Independent of the Greedy state.  With EBC_FP32 the distances are direct
  * FP32; with a tensor-core precision the minimum per set is formed from
- * V.S^T products (for d <= 128; larger d uses the FP32 kernel on the GPU).
- * Out-of-range members are detected on the device: the set
+ * V.S^T products (K-blocked above d = 128).  Out-of-range members are detected on the device: the set
  * is evaluated without them and ebc_sync() returns EINDEX.  l = 0 is OK.
  */
 ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off, int64_t l, double *out_f);
@@ -218,11 +217,12 @@ ebc_status ebc_tune_load(const char *path);
 int64_t ebc_tune_count(void);
 ebc_status ebc_tune_clear(void);
 
-/* Bulk kernel layout at EBC_BF16 / EBC_FP16: 1 streams the candidate and
- * point rows in 64-element K blocks through the tensor cores (always used
- * for d > 128, where whole rows do not fit shared memory); 0 (the default)
- * keeps a tile of whole candidate rows resident where it fits.  Both issue
- * the same MMA sequence, so bounds, picks and f are bitwise the same. */
+/* Tensor-core layout of the bulk and multi-set kernels at EBC_BF16 /
+ * EBC_FP16: 1 streams both operands' rows in 64-element K blocks (always
+ * used for d > 128, where whole rows do not fit shared memory); 0 (the
+ * default) keeps a tile of whole rows resident where it fits.  Both issue
+ * the same MMA sequence, so bounds, picks, f and set values are bitwise
+ * the same. */
 ebc_status ebc_set_kblocked(ebc_t h, int32_t on);
 
 /* Replay Greedy rounds from a captured CUDA graph (1, the default) or issue

@@ -801,7 +801,7 @@ ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off
     if (l < 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: l < 0");
     if (l == 0) return EBC_OK;
     if (!csr_off || !out_f) return fail(h, EBC_EINVAL, "ebc_eval_sets: NULL argument");
-    if (c.prec != EBC_FP32 && ebc::tc_resident_supported(c)) {
+    if (c.prec != EBC_FP32) {
         // tensor-core path: the tile plan needs the offsets on the host
         std::vector<int64_t> off((size_t)l + 1);
         CK(h, cudaMemcpyAsync(off.data(), csr_off, sizeof(int64_t) * (l + 1), cudaMemcpyDeviceToHost, c.stream));

@@ -288,8 +288,8 @@ cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off
 cudaError_t launch_sets_finalize(Ctx &c, int64_t ntiles, int64_t lb, int64_t j0, int64_t l, double *out_f);
 
 // tensor-core path
-bool tc_supported(const Ctx &c);           // 16-bit bulk bounds (K-blocked kernel above d = 128)
-bool tc_resident_supported(const Ctx &c);  // FP8 bulk and the multi-set kernel: d <= 128
+bool tc_supported(const Ctx &c);           // 16-bit bulk bounds and sets (K-blocked kernels above d = 128)
+bool tc_resident_supported(const Ctx &c);  // FP8 bulk: d <= 128
 cudaError_t tc_setup(Ctx &c, int prec);          // allocate, quantise, build tensor maps
 cudaError_t tc_quantize(Ctx &c);                 // (re)quantise V into Vq
 cudaError_t launch_prep_tc(Ctx &c, bool upper);  // a_v for every point (+ max m_v)

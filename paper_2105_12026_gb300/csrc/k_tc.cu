@@ -285,15 +285,15 @@ __device__ __forceinline__ float relu_sum128(const uint32_t (&r0)[32], const uin
 // and the multi-set evaluation (MODE_SETS: A = points, B = set members,
 // epilogue = per-set maxima and sums over the points).
 //
-// KB (gains only): candidate rows longer than the resident layout allows.
-// Every stage carries one K atom of both candidate sub-tiles and of the
-// point tile; a point tile's MMAs accumulate over all K atoms (the same MMA
-// sequence, hence the same FP32 accumulation, as the resident layout) and
-// the extension step follows the last atom.
+// KB: rows longer than the resident layout allows.  Every stage carries one
+// K atom of both A sub-tiles and of the B tile; a B tile's MMAs accumulate
+// over all K atoms (the same MMA sequence, hence the same FP32
+// accumulation, as the resident layout) and the extension step follows the
+// last atom.
 template <int MODE, bool F8, bool KB = false>
 __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUtensorMap *tmAx_p,
                                             const CUtensorMap *tmB_p, const CUtensorMap *tmBx_p, const TcArgs &args) {
-    static_assert(!KB || (MODE == MODE_GAINS && !F8), "K-blocked layout: 16-bit gains only");
+    static_assert(!KB || !F8, "K-blocked layout: 16-bit operands only");
     const CUtensorMap &tmA = *tmA_p, &tmAx = *tmAx_p, &tmB = *tmB_p, &tmBx = *tmBx_p;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -747,6 +747,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     k_sets_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
               const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
     tc_pipeline<MODE_SETS, false>(&tmA, &tmAx, &tmB, &tmBx, args);
+}
+
+// Multi-set evaluation with point and member rows streamed in K blocks (d > 128).
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_sets_tc_kb(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+                 const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
+    tc_pipeline<MODE_SETS, false, true>(&tmA, &tmAx, &tmB, &tmBx, args);
 }
 
 // ---------------------------------------------------------------------------
@@ -1307,8 +1314,8 @@ double gamma8_for(int DP) { return ldexp(1.0, -8) + gamma_for(DP); }
 
 }  // namespace
 
-// 16-bit tensor-core bulk bounds: any d (K-blocked above 128); the FP8
-// kernel and the multi-set kernel keep whole rows resident: d <= 128.
+// 16-bit tensor-core bulk bounds and multi-set evaluation: any d (K-blocked
+// above 128); the FP8 kernel keeps whole rows resident: d <= 128.
 bool tc_supported(const Ctx &c) { return c.d <= 4096; }
 bool tc_resident_supported(const Ctx &c) { return c.d <= 128; }
 
@@ -1673,11 +1680,13 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_d
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *nlaunch += 1;
     }
-    int na = 0, ns = 0;
-    pick_pipeline(2 * T.DP, &na, &ns);
+    const bool kb = use_kb(c, 2 * T.DP);
+    int na = 1, ns = KB_STAGES;
+    if (!kb) pick_pipeline(2 * T.DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = smem_layout(2 * T.DP, ns, na);
-    if ((e = allow_smem((const void *)k_sets_tc, L.total)) != cudaSuccess) return e;
+    const SmemLayout L = kb ? smem_layout_kb(ns) : smem_layout(2 * T.DP, ns, na);
+    const void *kfn = kb ? (const void *)k_sets_tc_kb : (const void *)k_sets_tc;
+    if ((e = allow_smem(kfn, L.total)) != cudaSuccess) return e;
     const int npu = (int)(T.n_pad / BM);
     const int64_t rows = (int64_t)npu * 8;  // partial rows: (point unit, epilogue warp)
     const int64_t max_sets = c.set_part_cap / rows;
@@ -1714,7 +1723,10 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_d
         const int grid = (int)std::min<int64_t>(units, G);
         // empty sets get no partial from any warp
         if ((e = cudaMemsetAsync(c.set_part, 0, sizeof(double) * rows * lb, c.stream)) != cudaSuccess) return e;
-        k_sets_tc<<<grid, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
+        if (kb)
+            k_sets_tc_kb<<<grid, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
+        else
+            k_sets_tc<<<grid, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = launch_sets_finalize(c, rows, lb, j0, l, out_f)) != cudaSuccess) return e;
         *nlaunch += 2;

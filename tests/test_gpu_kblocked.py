@@ -125,3 +125,30 @@ def test_large_d_batch(torch):
             ridx, rf = inst.greedy_host(k)
         np.testing.assert_array_equal(idx, ridx)
         np.testing.assert_array_equal(f, rf)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("n,d,l", [(3000, 16, 60), (2000, 64, 200), (1500, 128, 90)])
+def test_kblocked_sets_equal_resident_bitwise(torch, prec, n, d, l):
+    V = gmm(n, d, 5 * n + d)
+    idx, off = synth.random_sets(np.random.default_rng(d), n, l, 0, 70)
+    got = {}
+    for kb in (False, True):
+        with ebc.Instance(V, precision=prec) as inst:
+            inst.set_kblocked(kb)
+            got[kb] = inst.eval_sets_host(idx, off)
+    np.testing.assert_array_equal(got[False], got[True])
+
+
+@pytest.mark.parametrize("n,d,l", [(1200, 200, 80), (900, 777, 50), (1000, 3524, 40)])
+def test_large_d_sets_within_bound(torch, n, d, l):
+    from test_gpu_sets_tc import sets_error_bound
+    V = gmm(n, d, 3 * n + d)
+    idx, off = synth.random_sets(np.random.default_rng(n), n, l, 1, 40)
+    ref = oracle.eval_sets(V, idx, off)
+    with ebc.Instance(V, precision="bf16") as inst:
+        got = inst.eval_sets_host(idx, off)
+    bound = sets_error_bound(V, idx, off, "bf16", ref)
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), (np.max(err - bound), d)
+    print(d, "max err", err.max(), "max bound", bound.max())
