@@ -172,6 +172,12 @@ __device__ __forceinline__ double df_dist_group(const float (&x)[DL], const floa
         const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
         df_add(hi, lo, oh, ol);
     }
+    // df_add is not symmetric in its low parts, so the lanes of a group end
+    // with slightly different values: every lane takes the group's first
+    // lane's, and a distance never depends on which lane reads it
+    const int first = (threadIdx.x & 31) & ~(LPP - 1);
+    hi = __shfl_sync(0xffffffffu, hi, first);
+    lo = __shfl_sync(0xffffffffu, lo, first);
     return (double)hi + (double)lo;
 }
 
@@ -482,6 +488,8 @@ __device__ __forceinline__ double df_dist_wide(const float *__restrict__ row, co
         const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
         df_add(hi, lo, oh, ol);
     }
+    hi = __shfl_sync(0xffffffffu, hi, 0);  // lane 0's value for every lane (see df_dist_group)
+    lo = __shfl_sync(0xffffffffu, lo, 0);
     return (double)hi + (double)lo;
 }
 
