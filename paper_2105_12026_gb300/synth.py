@@ -134,6 +134,31 @@ def regime_greedy(seed: int = 0, n: int = 200_000, d: int = 128, k: int = 100):
     return {"V": V, "k": k}
 
 
+def case_study_series(seed: int = 0, n: int = 1_000, d: int = 3_524, regimes: int = 8):
+    """Stand-in for the case study's sensor curves (Sec. 6: n = 1,000 cycles
+    of d = 3,524 samples each): every regime a template curve
+    sum_j a_j sin(2 pi f_j t + p_j) + b t on t in [0, 1] (4 terms, a ~ U[0.5, 2],
+    f ~ U{1..20}, p ~ U[0, 2 pi], b ~ U[-1, 1]); cycles come in contiguous
+    runs of one regime (random run lengths), each its regime's curve scaled
+    by 1 + 0.05 N(0, 1) plus white noise of sigma 0.3; z-scored."""
+    rng = np.random.default_rng(seed)
+    t = np.linspace(0.0, 1.0, d)
+    tmpl = np.zeros((regimes, d))
+    for r in range(regimes):
+        a = rng.uniform(0.5, 2.0, 4)
+        f = rng.integers(1, 21, 4)
+        ph = rng.uniform(0.0, 2 * np.pi, 4)
+        tmpl[r] = (a[:, None] * np.sin(2 * np.pi * f[:, None] * t[None, :] + ph[:, None])).sum(0)
+        tmpl[r] += rng.uniform(-1.0, 1.0) * t
+    cuts = np.sort(rng.choice(np.arange(1, n), size=regimes - 1, replace=False))
+    lab = np.zeros(n, dtype=np.int64)
+    for r, c in enumerate(cuts):
+        lab[c:] = r + 1
+    scale = 1.0 + 0.05 * rng.standard_normal(n)
+    x = tmpl[lab] * scale[:, None] + 0.3 * rng.standard_normal((n, d))
+    return zscore_to_f32(x)
+
+
 @dataclass
 class InstanceSpec:
     n: int

@@ -56,3 +56,16 @@ def test_request_trace_rate():
     assert 800 < len(tr) < 1200
     assert all(a.t_arrive <= b.t_arrive for a, b in zip(tr, tr[1:]))
     assert any(r.large for r in tr)
+
+
+def test_case_study_series_shape_and_regimes():
+    a = synth.case_study_series(seed=3, n=300, d=500)
+    b = synth.case_study_series(seed=3, n=300, d=500)
+    assert a.shape == (300, 500) and a.dtype == np.float32
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_allclose(a.mean(0), 0.0, atol=1e-4)
+    np.testing.assert_allclose(a.std(0), 1.0, atol=1e-3)
+    # contiguous runs of a regime: neighbouring cycles are far more alike than random pairs
+    near = np.mean(np.sum((a[1:] - a[:-1]) ** 2, 1))
+    far = np.mean(np.sum((a[np.random.default_rng(0).permutation(300)] - a) ** 2, 1))
+    assert near < 0.5 * far
