@@ -227,6 +227,7 @@ ebc_status ebc_create(const float *V, int64_t n, int32_t d, int32_t v_on_device,
 
 ebc_status ebc::create_handle(const float *V, int64_t n, int32_t d, int32_t v_on_device, void *stream, bool sync,
                               ebc_t *out) {
+    ebc::TraceRange trace_("ebc_create");
     g_create_error.clear();
     if (!out) return fail(nullptr, EBC_EINVAL, "ebc_create: out is NULL");
     *out = nullptr;
@@ -667,6 +668,7 @@ ebc_status ebc_current_f(ebc_t h, double *out_f) {
 }
 
 ebc_status ebc_gains(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_gain) {
+    ebc::TraceRange trace_("ebc_gains");
     if (check_handle(h)) return EBC_EINVAL;
     ebc::Ctx &c = h->c;
     if (m < 0) return fail(h, EBC_EINVAL, "ebc_gains: m < 0");
@@ -732,6 +734,7 @@ ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *o
 }
 
 ebc_status ebc_gain_bounds(ebc_t h, const int32_t *cand_idx, int64_t m, double *out_ub) {
+    ebc::TraceRange trace_("ebc_gain_bounds");
     if (check_handle(h)) return EBC_EINVAL;
     ebc::Ctx &c = h->c;
     if (m < 0) return fail(h, EBC_EINVAL, "ebc_gain_bounds: m < 0");
@@ -796,6 +799,7 @@ ebc_status ebc_gain_bounds_host(ebc_t h, const int32_t *cand_idx, int64_t m, dou
 }
 
 ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off, int64_t l, double *out_f) {
+    ebc::TraceRange trace_("ebc_eval_sets");
     if (check_handle(h)) return EBC_EINVAL;
     ebc::Ctx &c = h->c;
     if (l < 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: l < 0");
@@ -997,6 +1001,7 @@ static ebc_status capture_round(ebc_t h) {
 }
 
 ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) {
+    ebc::TraceRange trace_("ebc_greedy");
     if (check_handle(h)) return EBC_EINVAL;
     ebc::Ctx &c = h->c;
     if (k < 0) return fail(h, EBC_EINVAL, "ebc_greedy: k < 0");

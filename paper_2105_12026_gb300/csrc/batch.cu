@@ -289,6 +289,7 @@ ebc_status ebc_batch_submit(ebc_batch_t b, const float *V, int64_t n, int32_t d,
 }
 
 ebc_status ebc_batch_step(ebc_batch_t b, int32_t *n_active, int32_t *n_queued) {
+    ebc::TraceRange trace_("ebc_batch_step");
     if (!b) return EBC_EINVAL;
     reap(b);
     admit(b);

@@ -9,8 +9,20 @@
 #include <string>
 
 #include "../../include/ebc.h"
+#include <nvtx3/nvToolsExt.h>
+
 
 namespace ebc {
+
+// A named NVTX range over one C-ABI call (visible in Nsight Systems; a no-op
+// without an attached tool).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
 
 constexpr int kMaxRefineK = 31;  // K + 1 <= 32: one warp lane per list entry
 constexpr int kRefineTile = 64;  // points per shared-memory tile of the exact / bound kernels

@@ -64,6 +64,7 @@ ebc_status ebc_threshold_ladder(double m, int32_t K, double eps, double upper, d
 
 ebc_status ebc_sieve_host(ebc_t h, ebc_sieve_state *s, const int32_t *items, int64_t len, int32_t *out_idx,
                           double *out_f, int32_t *out_count) {
+    ebc::TraceRange trace_("ebc_sieve_host");
     if (check_handle(h)) return EBC_EINVAL;
     ebc::Ctx &c = h->c;
     if (!s || !out_count) return fail(h, EBC_EINVAL, "ebc_sieve_host: NULL state or count");
