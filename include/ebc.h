@@ -54,7 +54,7 @@ typedef enum {
 
 /* Arithmetic used for the bulk distance work (Sec. 5 compares FP32 with
  * half precision; here the low-precision paths run on tcgen05 tensor cores
- * with FP32 accumulation and exact FP64 re-evaluation of the leaders). */
+ * with FP32 accumulation and exact re-evaluation of the leaders). */
 typedef enum {
     EBC_FP32 = 0,    /* direct (v - c)^2 in FP32 on the CUDA cores */
     EBC_BF16 = 1,    /* V.C^T in BF16 on tensor cores, FP32 accumulate */
@@ -72,7 +72,7 @@ typedef struct {
     int64_t escalated_candidates; /* total such extra candidates */
     double max_raw_rel_err;       /* max (bulk bound - lower bound) / lower bound over the top
                                      list: how loose the bulk upper bounds were */
-    int64_t exact_evaluations;    /* candidates whose exact FP64 gain was computed */
+    int64_t exact_evaluations;    /* candidates whose exact gain was computed */
     int32_t prec;                 /* current ebc_prec */
     int32_t refine_k;             /* current K */
     int64_t bulk_candidates;      /* lazy Greedy: candidates given a bulk bound, summed over rounds */
@@ -161,16 +161,25 @@ ebc_status ebc_gains_host(ebc_t h, const int32_t *cand_idx, int64_t m, double *o
 /*
  * k rounds of Greedy (Sec. 3; the step is described in Sec. 4.1): each round
  * adds the not-yet-selected point of largest marginal gain, ties to the
- * smallest index, continuing from the handle's current state.
+ * smallest index (see below for what counts as a tie), continuing from the
+ * handle's current state.
  *   out_idx  device int32[k]: the picks in order.
  *   out_f    device double[k]: out_f[t] = f(S) after pick t (cumulative).
  * Each round evaluates the gain of every unselected point with the bulk
  * precision as a rigorous upper bound; the K largest get rigorous FP32
  * direct-distance bounds [lo, hi]; if the (K+1)-th bulk bound can reach the
  * best lo, every candidate whose bulk bound reaches it gets [lo, hi] too;
- * the candidates whose hi reaches the best lo get the exact gain (FP64
- * direct distances and sums), and the pick is the best of those.  The pick
- * is therefore the exact argmax up to FP64 rounding, at every precision.
+ * the candidates whose hi reaches the best lo get the exact gain, and the
+ * pick is the best of those.  Exact gains are computed from the FP32 inputs
+ * with double-FP32 arithmetic (error-free TwoSum / TwoProduct steps, about
+ * 2^-44 relative per distance) and FP64 sums over V; an escalation of more
+ * than 4,096 candidates computes the exact gains past that capacity with
+ * FP64 distances.  Gains within 1e-10 relative of the round's largest exact
+ * gain are ties and go to the smallest index (so duplicate points and
+ * mirror-image pairs, whose gains agree in real arithmetic, are ordered by
+ * index, not by rounding); the pick is therefore the exact argmax wherever
+ * the best two gains differ by more than that, at every precision.  When
+ * every remaining gain is 0 the pick is the smallest unselected index.
  * EINVAL when k < 0 or k exceeds the number of unselected points.
  */
 ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f);
@@ -323,6 +332,18 @@ ebc_status ebc_sync(ebc_t h);
 /* Certification counters (synchronises the stream). */
 ebc_status ebc_get_stats(ebc_t h, ebc_stats *out);
 
+/*
+ * The candidates that reached the certified stage of the last Greedy round
+ * (Sec. 3's argmax, step a4): the K entries of the top list by bulk upper
+ * bound, then, when the round escalated, every candidate whose bulk bound
+ * could reach the best certified lower bound.  Every candidate left out has
+ * an upper bound below the pick's gain.  out_idx is host memory of capacity
+ * cap; *count receives the full number, and nothing is copied when cap is
+ * smaller (call with cap 0 to size).  *count = 0 before the first round.
+ * Synchronises the stream.  For inspection and tests.
+ */
+ebc_status ebc_last_round_candidates(ebc_t h, int32_t *out_idx, int64_t cap, int64_t *count);
+
 /* Launch and device-time counters of one handle.  Device times are
  * measured with CUDA events on the handle's stream around each launch while
  * profiling is on (ebc_set_profiling); launch counts are always kept. */
@@ -332,7 +353,7 @@ typedef struct {
     double bulk_ms;        /* summed device time of those launches (profiling on) */
     int64_t bulk_evals;    /* (candidate, point) pairs those launches evaluated */
     int64_t refine_launches;
-    double refine_ms;      /* exact FP64 re-evaluation of the leaders */
+    double refine_ms;      /* rigorous bounds and exact re-evaluation of the leaders */
     int64_t eval_launches; /* launches of the multi-set kernel */
     double eval_ms;
     int64_t list_launches; /* lazy and FP8 Greedy: row gather + bulk bounds of the round's list */
@@ -379,12 +400,17 @@ ebc_status ebc_current_f(ebc_t h, double *out_f);
  *   stream   cudaStream_t (NULL = legacy default stream)
  * Scratch is a static 8 MiB device array held by every GPU that loads the
  * library until exit; n may be at most 134,217,728 (1,048,576 tiles of 128
- * points), larger n is rejected with EINVAL.  All calls share the array:
- * calls whose work overlaps on the GPU race and must not be issued.  The
- * first call on a device looks up the array's address with that device
- * current; make that first call before any stream capture.  Synchronises
- * the stream and returns EINDEX / EINVAL for bad members / offsets found on
- * the device.  Text of the last failure: ebc_noalloc_last_error().
+ * points), larger n is rejected with EINVAL.  Sets are evaluated in passes
+ * that fit the array (and at most 524,280 sets per pass).  All calls share
+ * the array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU race and must not be issued.  The first call on a
+ * device looks up the array's address with that device current; make that
+ * first call before any stream capture.  Every call reads its device-side
+ * error words back into host memory and waits for the stream before it
+ * returns; it returns EINDEX for a member outside [0, n), EINVAL for offsets
+ * that do not start at 0 or decrease, or for a NULL csr_idx with a
+ * non-empty set (then no member is read).  An empty set gives 0.  Text of
+ * the last failure: ebc_noalloc_last_error().
  */
 ebc_status ebc_eval_sets_noalloc(const float *V, int64_t n, int32_t d, const int32_t *csr_idx,
                                  const int64_t *csr_off, int64_t l, double *out_f, void *stream);

@@ -492,6 +492,28 @@ ebc_status ebc_get_stats(ebc_t h, ebc_stats *out) {
     return EBC_OK;
 }
 
+ebc_status ebc_last_round_candidates(ebc_t h, int32_t *out_idx, int64_t cap, int64_t *count) {
+    if (check_handle(h) || !count || cap < 0 || (cap > 0 && !out_idx))
+        return fail(h, EBC_EINVAL, "ebc_last_round_candidates: bad arguments");
+    ebc::Ctx &c = h->c;
+    ebc::DevState s;
+    CK(h, cudaMemcpyAsync(&s, c.st, sizeof(s), cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaStreamSynchronize(c.stream));
+    if (s.rounds == 0) {
+        *count = 0;
+        return EBC_OK;
+    }
+    const int64_t ntop = std::max(0, s.top_count);
+    const int64_t nesc = s.need_esc ? std::min<int64_t>(std::max(0, s.esc_count), c.n) : 0;
+    *count = ntop + nesc;
+    if (cap < ntop + nesc) return EBC_OK;  // sizing call
+    if (ntop > 0) CK(h, cudaMemcpyAsync(out_idx, c.top_idx, sizeof(int32_t) * ntop, cudaMemcpyDeviceToHost, c.stream));
+    if (nesc > 0)
+        CK(h, cudaMemcpyAsync(out_idx + ntop, c.esc_idx, sizeof(int32_t) * nesc, cudaMemcpyDeviceToHost, c.stream));
+    CK(h, cudaStreamSynchronize(c.stream));
+    return EBC_OK;
+}
+
 }  // extern "C"
 
 ebc_status ebc::autotune_handle(ebc_t h, int32_t reps, bool only_if_missing) {

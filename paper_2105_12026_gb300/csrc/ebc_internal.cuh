@@ -26,6 +26,13 @@ struct TraceRange {
 
 constexpr int kMaxRefineK = 31;  // K + 1 <= 32: one warp lane per list entry
 constexpr int kRefineTile = 64;  // points per shared-memory tile of the exact / bound kernels
+// Exact gains whose computed values lie within this relative distance of the
+// round's largest are ties, decided by the smallest index.  The exact gains
+// are double-FP32 sums (about 2^-44 relative per term), so a tie in real
+// arithmetic (duplicate points, mirror-symmetric pairs) can come out a few
+// units apart; every threshold that decides which candidates reach the exact
+// stage is lowered by 2 kTieRel so that all tied candidates do.
+constexpr double kTieRel = 1e-10;
 
 __host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t lmax(int64_t a, int64_t b) { return a > b ? a : b; }

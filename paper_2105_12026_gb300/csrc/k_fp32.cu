@@ -404,7 +404,8 @@ cudaError_t launch_eval_sets_fp32(Ctx &c, const int32_t *idx, const int64_t *off
                                   const int *bad) {
     int64_t ntiles = (c.n + ES_T - 1) / ES_T;
     // process the sets in batches so the partials fit the scratch buffer
-    int64_t batch = c.set_part_cap / ntiles;
+    // (and the set groups the grid's y extent, at most 65,535 blocks)
+    int64_t batch = min(c.set_part_cap / ntiles, (int64_t)65535 * ES_SG);
     if (batch < 1) return cudaErrorMemoryAllocation;
     bool resident = c.d <= ES_DMAX_RES;
     size_t smem = resident ? (size_t)c.d * ES_T * 4 + (size_t)c.d * 16 : (size_t)min(c.d, ES_DC) * 16;

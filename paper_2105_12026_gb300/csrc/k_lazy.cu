@@ -68,7 +68,8 @@ cudaError_t launch_lazy_preselect(Ctx &c, int nblk, int K) {
     return launch_merge_top(c, nblk, K, 0.0);
 }
 
-// thr = max lo over the pre-selected list; tighten their ub with hi.
+// thr = max lo over the pre-selected list (lowered by the tie margin);
+// tighten their ub with hi.
 __global__ void k_lazy_threshold(const double *__restrict__ top_lo, const double *__restrict__ top_hi,
                                  const int *__restrict__ top_idx, double *__restrict__ ub, DevState *st) {
     if (threadIdx.x != 0) return;
@@ -79,7 +80,7 @@ __global__ void k_lazy_threshold(const double *__restrict__ top_lo, const double
         const int c = top_idx[e];
         if (c >= 0) ub[c] = fmin(ub[c], top_hi[e]);
     }
-    st->lazy_thr = thr;
+    st->lazy_thr = thr * (1.0 - 2.0 * kTieRel);  // candidates tied with the best stay in the list
     st->list_m = 0;
 }
 

@@ -45,9 +45,13 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles + 2];
 double *g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-__global__ void k_na_check_csr(const int64_t *__restrict__ off, int64_t l, int *__restrict__ err) {
+// Offsets must start at 0 and never decrease; a NULL member list is only
+// valid when every set is empty.  Either failure sets err[1], after which the
+// evaluation kernels read no member.
+__global__ void k_na_check_csr(const int32_t *__restrict__ idx, const int64_t *__restrict__ off, int64_t l,
+                               int *__restrict__ err) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if ((j == 0 && off[0] != 0) || (j < l && off[j + 1] < off[j])) {
+    if ((j == 0 && (off[0] != 0 || (idx == nullptr && off[l] != 0))) || (j < l && off[j + 1] < off[j])) {
         atomicCAS(&err[0], 0, (int)EBC_EINVAL);
         atomicExch(&err[1], 1);
     }
@@ -185,8 +189,10 @@ extern "C" ebc_status ebc_eval_sets_noalloc(const float *V, int64_t n, int32_t d
     int *err = reinterpret_cast<int *>(scratch + kScratchDoubles);
     if (cudaMemsetAsync(err, 0, 2 * sizeof(int), st) != cudaSuccess)
         return na_fail(EBC_ECUDA, "ebc_eval_sets_noalloc: clearing the error words failed");
-    k_na_check_csr<<<(unsigned)((l + 255) / 256), 256, 0, st>>>(csr_off, l, err);
-    const int64_t batch = kScratchDoubles / ntiles;  // sets per pass that fit the partials
+    k_na_check_csr<<<(unsigned)((l + 255) / 256), 256, 0, st>>>(csr_idx, csr_off, l, err);
+    // sets per pass: the partials must fit the array and the set groups the
+    // grid's y extent (at most 65,535 blocks)
+    const int64_t batch = lmin(kScratchDoubles / ntiles, (int64_t)65535 * NA_SG);
     for (int64_t j0 = 0; j0 < l; j0 += batch) {
         const int64_t lb = lmin(batch, l - j0);
         dim3 grid((unsigned)ntiles, (unsigned)((lb + NA_SG - 1) / NA_SG));
@@ -200,6 +206,8 @@ extern "C" ebc_status ebc_eval_sets_noalloc(const float *V, int64_t n, int32_t d
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return na_fail(EBC_ECUDA, cudaGetErrorString(e));
     if (herr[0] == EBC_EINDEX) return na_fail(EBC_EINDEX, "ebc_eval_sets_noalloc: index outside [0, n)");
-    if (herr[0] != 0) return na_fail((ebc_status)herr[0], "ebc_eval_sets_noalloc: offsets not non-decreasing from 0");
+    if (herr[0] != 0)
+        return na_fail((ebc_status)herr[0],
+                       "ebc_eval_sets_noalloc: offsets not non-decreasing from 0, or NULL csr_idx with members");
     return EBC_OK;
 }

@@ -10,10 +10,11 @@
 //     (escalation) and gets bounds the same way.
 //  3. Contenders = pool entries with hi >= best_lo (usually one or two).
 //     Only these get the exact gain (FP64 direct distances).
-//  4. The pick is the contender of largest exact gain (smallest index on
-//     ties).  Any other candidate has gain <= hi < best_lo <= the exact gain
-//     of the entry attaining best_lo, itself a contender: the pick is the
-//     exact argmax.
+//  4. The pick is the contender of largest exact gain, the smallest index
+//     among the contenders within kTieRel of it (ties).  Any other candidate
+//     has gain <= hi < best_lo (1 - 2 kTieRel) <= the exact gain of the entry
+//     attaining best_lo, itself a contender: the pick is the exact argmax, and
+//     every candidate tied with it is a contender.
 // When every remaining gain is exactly 0 the pick is the smallest
 // unselected index.
 #include "ebc_internal.cuh"
@@ -83,8 +84,9 @@ __global__ void k_decide_top(const double *__restrict__ top_lo, const int *__res
     const double thr = st->top_thr;  // (K+1)-th bulk bound, -1 when no other candidate
     // outside candidates have gain <= U (1 + eta_bulk) <= thr (1 + eta_bulk); a
     // zero bound means a zero gain, which can only matter for the all-zero case
-    st->need_esc = (thr > 0.0 && thr * (1.0 + eta_bulk) >= best_lo) ? 1 : 0;
-    st->esc_thr = best_lo;
+    const double tie_lo = best_lo * (1.0 - 2.0 * kTieRel);
+    st->need_esc = (thr > 0.0 && thr * (1.0 + eta_bulk) >= tie_lo) ? 1 : 0;
+    st->esc_thr = tie_lo;
     st->best_lo = best_lo;
     st->esc_count = 0;
     st->ctd_count = 0;
@@ -117,10 +119,11 @@ __global__ void k_decide_contenders(const double *__restrict__ top_hi, const dou
     __syncthreads();
     double best_lo = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) best_lo = fmax(best_lo, sbest[w]);
+    const double tie_lo = best_lo * (1.0 - 2.0 * kTieRel);
     for (int e = threadIdx.x; e < top_cnt; e += blockDim.x)
-        if (top_hi[e] >= best_lo) ctd_idx[atomicAdd(&sn, 1)] = top_idx[e];
+        if (top_hi[e] >= tie_lo) ctd_idx[atomicAdd(&sn, 1)] = top_idx[e];
     for (int e = threadIdx.x; e < in_cap; e += blockDim.x)
-        if (esc_hi[e] >= best_lo) ctd_idx[atomicAdd(&sn, 1)] = esc_idx[e];
+        if (esc_hi[e] >= tie_lo) ctd_idx[atomicAdd(&sn, 1)] = esc_idx[e];
     __syncthreads();
     if (threadIdx.x == 0) {
         st->best_lo = best_lo;
@@ -151,19 +154,35 @@ __global__ void k_commit_pick(const double *__restrict__ ctd_part, int nchunks, 
         if (lane == 0) ctd_exact[e] = s * inv_n;
     }
     __syncthreads();
+    // largest exact gain, then the smallest index among the entries within
+    // kTieRel of it (the pick's own exact gain goes into f)
+    double mv = -1.0;
+    int mi = INT_MAX;
+    for (int e = threadIdx.x; e < nc; e += blockDim.x)
+        if (better(ctd_exact[e], ctd_idx[e], mv, mi)) {
+            mv = ctd_exact[e];
+            mi = ctd_idx[e];
+        }
+    for (int e = cap + threadIdx.x; e < esc_cnt; e += blockDim.x)
+        if (better(esc_exact[e], esc_idx[e], mv, mi)) {
+            mv = esc_exact[e];
+            mi = esc_idx[e];
+        }
+    block_best(mv, mi);
+    const double tie = mv * (1.0 - kTieRel);
     double bv = -1.0;
     int bi = INT_MAX;
     for (int e = threadIdx.x; e < nc; e += blockDim.x)
-        if (better(ctd_exact[e], ctd_idx[e], bv, bi)) {
+        if (ctd_exact[e] >= tie && ctd_idx[e] < bi) {
             bv = ctd_exact[e];
             bi = ctd_idx[e];
         }
     for (int e = cap + threadIdx.x; e < esc_cnt; e += blockDim.x)
-        if (better(esc_exact[e], esc_idx[e], bv, bi)) {
+        if (esc_exact[e] >= tie && esc_idx[e] < bi) {
             bv = esc_exact[e];
             bi = esc_idx[e];
         }
-    block_best(bv, bi);
+    block_min_index(bv, bi);
     // every remaining gain is 0 (no escalation, outside bounds 0): smallest unselected index
     const bool zero_scan = bv == 0.0 && st->top_thr >= 0.0 && !st->need_esc;
     if (zero_scan) {

@@ -55,6 +55,48 @@ __device__ __forceinline__ void block_best(double &v, int &i) {
     __syncthreads();
 }
 
+// Block-wide minimum index (the value travels with it; INT_MAX = none).
+__device__ __forceinline__ void block_min_index(double &v, int &i) {
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (oi < i) {
+            v = ov;
+            i = oi;
+        }
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sv[w] = v;
+        si[w] = i;
+    }
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    if (w == 0) {
+        v = lane < nw ? sv[lane] : -1.0;
+        i = lane < nw ? si[lane] : INT_MAX;
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, v, o);
+            int oi = __shfl_xor_sync(0xffffffffu, i, o);
+            if (oi < i) {
+                v = ov;
+                i = oi;
+            }
+        }
+        if (lane == 0) {
+            sv[0] = v;
+            si[0] = i;
+        }
+    }
+    __syncthreads();
+    v = sv[0];
+    i = si[0];
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Top-L selection (L <= 32) in the order above, with per-warp sorted lists:
 // lane r of a warp holds the warp's r-th best entry so far.  A batch of 32

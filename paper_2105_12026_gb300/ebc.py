@@ -105,6 +105,7 @@ _SIGS = {
     "ebc_sync": [_P],
     "ebc_get_stats": [_P, ctypes.POINTER(ebc_stats)],
     "ebc_current_f": [_P, ctypes.POINTER(ctypes.c_double)],
+    "ebc_last_round_candidates": [_P, _P, _I64, ctypes.POINTER(_I64)],
     "ebc_last_error": [_P],
     "ebc_eval_sets_noalloc": [_P, _I64, _I32, _P, _P, _I64, _P, _P],
     "ebc_noalloc_last_error": [],
@@ -317,6 +318,15 @@ def ebc_get_stats(h: int) -> dict:
     return {k: getattr(s, k) for k, _ in ebc_stats._fields_}
 
 
+def ebc_last_round_candidates(h: int) -> np.ndarray:
+    """Candidates that reached the certified stage of the last Greedy round."""
+    cnt = _I64()
+    _raise(h, load().ebc_last_round_candidates(_P(h), None, 0, ctypes.byref(cnt)))
+    out = np.zeros(max(cnt.value, 1), dtype=np.int32)
+    _raise(h, load().ebc_last_round_candidates(_P(h), out.ctypes.data_as(_P), out.size, ctypes.byref(cnt)))
+    return out[:cnt.value].copy()
+
+
 def ebc_current_f(h: int) -> float:
     v = ctypes.c_double()
     _raise(h, load().ebc_current_f(_P(h), ctypes.byref(v)))
@@ -477,6 +487,9 @@ class Instance:
 
     def current_f(self):
         return ebc_current_f(self.h)
+
+    def last_round_candidates(self) -> np.ndarray:
+        return ebc_last_round_candidates(self.h)
 
     def gain_bounds_host(self, cand=None) -> np.ndarray:
         """Rigorous upper bounds of the gains of ``cand`` (all points if None)

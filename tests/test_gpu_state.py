@@ -1,9 +1,11 @@
 """Greedy state snapshots (ebc_state_save / ebc_state_load): a Greedy
 resumed from a snapshot, in the same or another handle over the same V,
-continues with bitwise the picks and f of an uninterrupted run."""
+continues with bitwise the picks and f of an uninterrupted run, and with the
+picks and f of the FP64 oracle continued from the same state (S, m_v, f)."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2105_12026_gb300 import ebc, synth
 
 pytestmark = pytest.mark.gpu
@@ -45,6 +47,38 @@ def test_resume_equals_uninterrupted(torch, prec, lazy):
         np.testing.assert_array_equal(np.concatenate([ib1, idx]), ia)
         np.testing.assert_array_equal(np.concatenate([fb1, f]), fa)
     assert st_c["rounds"] == st_a["rounds"] == 12
+
+
+def _oracle_continue(V, picks, k):
+    """The oracle's Greedy continued for k rounds from the state the picks
+    reach (m_v updated by the oracle's own distances, f its own f(S))."""
+    m = oracle.norms(V)
+    sel = np.zeros(V.shape[0], dtype=np.uint8)
+    for c in picks:
+        oracle.update_m(V, m, int(c))
+        sel[int(c)] = 1
+    return oracle.greedy(V, k, m=m, selected=sel, f_start=oracle.f(V, picks))
+
+
+@pytest.mark.parametrize("prec,lazy", [("fp32", False), ("bf16", False), ("bf16", True), ("fp16", False),
+                                       ("fp8", False)])
+def test_resume_matches_oracle(torch, prec, lazy):
+    V = gmm(5000, 24, 33)
+    with ebc.Instance(V, precision=prec, lazy=lazy) as b:
+        i1, f1 = b.greedy_host(6)
+        snap = b.save_state()
+    ref_i, ref_f, ref_gap = _oracle_continue(V, i1, 9)
+    with ebc.Instance(V, precision=prec, lazy=lazy) as c:
+        c.load_state(snap)
+        assert abs(c.current_f() - oracle.f(V, i1)) <= 1e-5 * oracle.f(V, i1)
+        i2, f2 = c.greedy_host(9)
+    for t in range(9):
+        if ref_gap[t] > 1e-6:
+            assert i2[t] == ref_i[t], (prec, t, i2.tolist(), ref_i.tolist())
+        if i2[t] != ref_i[t]:
+            break  # a legal divergence at a near-tie: compare f from here on
+    np.testing.assert_allclose(f2, ref_f, rtol=1e-5)
+    np.testing.assert_allclose(f2[-1], oracle.f(V, np.concatenate([i1, i2])), rtol=1e-5)
 
 
 def test_state_errors(torch):
