@@ -418,6 +418,30 @@ ebc_status ebc_eval_sets_noalloc(const float *V, int64_t n, int32_t d, const int
 /* Text of the last ebc_eval_sets_noalloc failure on this host thread. */
 const char *ebc_noalloc_last_error(void);
 
+/*
+ * Failure injection, for testing how callers handle the library's error
+ * paths without faulting the GPU (the paper has no counterpart).
+ *
+ * ebc_set_wait_limit_ns: the limit of each wait inside the tensor-core
+ * kernels (a CTA waiting for its TMA copies, its MMAs or its epilogue; 0
+ * restores the default of 1 s, at most 60 s).  A wait that runs out makes
+ * the CTA record EBC_ETIMEOUT, stop issuing work, wait (with the default
+ * limit) for the copies and MMAs it already issued, free its tensor memory
+ * and return; the next ebc_sync() of the handle returns EBC_ETIMEOUT, the
+ * results of that call are undefined, and the handle stays usable (a Greedy
+ * state that saw a timeout should be reset).  Applies to kernels launched
+ * after the call (a captured Greedy round is captured again).  Process-wide.
+ *
+ * ebc_inject_alloc_failure: the device allocation after `after` more
+ * successful ones (all of the library's device memory comes from one pool)
+ * fails as if the device were out of memory, once; -1 disarms.  Calls that
+ * allocate return EBC_ENOMEM and leave nothing allocated behind; a batch
+ * request whose admission fails finishes with EBC_ENOMEM (ebc_batch_poll)
+ * while the other requests go on.  Process-wide.  EINVAL for after < -1.
+ */
+ebc_status ebc_set_wait_limit_ns(int64_t ns);
+ebc_status ebc_inject_alloc_failure(int64_t after);
+
 /* Text of the last error on this handle ("" if none); h may be NULL for
  * errors from ebc_create.  The pointer stays valid until the next call. */
 const char *ebc_last_error(ebc_t h);

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -107,6 +108,18 @@ cudaError_t fold_profile(ebc_t h) {
     return cudaSuccess;
 }
 
+// Lazy Greedy bounds and list, both or neither.
+cudaError_t alloc_lazy(ebc::Ctx &c) {
+    cudaError_t e = dalloc(&c.ub64, c.n, c);
+    if (e == cudaSuccess) e = dalloc(&c.lazy_idx, c.n, c);
+    if (e != cudaSuccess) {
+        ebc::pool_free(c.ub64, c.stream);
+        c.ub64 = nullptr;
+        c.lazy_idx = nullptr;
+    }
+    return e;
+}
+
 ebc_status ensure_set_part(ebc_t h, int64_t want) {
     ebc::Ctx &c = h->c;
     if (c.set_part_cap >= want) return EBC_OK;
@@ -186,8 +199,23 @@ int64_t ebc::handle_bytes(int64_t n, int32_t d, ebc_prec prec) {
     return b + 64 * 1024;  // allocation granularity and small buffers
 }
 
+namespace {
+// Injected allocation failure: the allocation after this many more
+// successful ones fails (-1: none).
+std::atomic<int64_t> g_alloc_fail_after{-1};
+std::atomic<uint64_t> g_wait_limit_ns{1000000000ull};
+}  // namespace
+
+uint64_t ebc::wait_limit_ns() { return g_wait_limit_ns.load(std::memory_order_relaxed); }
+
 cudaError_t ebc::pool_alloc(void **p, size_t bytes, cudaStream_t s, int dev) {
     *p = nullptr;
+    for (int64_t a = g_alloc_fail_after.load(); a >= 0;) {
+        if (g_alloc_fail_after.compare_exchange_weak(a, a - 1)) {
+            if (a == 0) return cudaErrorMemoryAllocation;  // the injected failure (now disarmed)
+            break;
+        }
+    }
     cudaMemPool_t pool = device_pool(dev);
     if (!pool) return cudaErrorMemoryAllocation;
     return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, s);
@@ -198,6 +226,18 @@ void ebc::pool_free(void *p, cudaStream_t s) {
 }
 
 extern "C" {
+
+ebc_status ebc_inject_alloc_failure(int64_t after) {
+    if (after < -1) return EBC_EINVAL;
+    g_alloc_fail_after.store(after);
+    return EBC_OK;
+}
+
+ebc_status ebc_set_wait_limit_ns(int64_t ns) {
+    if (ns < 0 || ns > 60000000000ll) return EBC_EINVAL;
+    g_wait_limit_ns.store(ns == 0 ? 1000000000ull : (uint64_t)ns);
+    return EBC_OK;
+}
 
 ebc_status ebc_release_cached_memory(void) {
     int dev = 0;
@@ -429,8 +469,7 @@ ebc_status ebc::set_precision_handle(ebc_t h, ebc_prec prec, int32_t refine_k, b
         if (c.tc.prec != EBC_BF16) CK(h, ebc::tc_setup(c, EBC_BF16));
         if (!c.tc8.ready) CK(h, ebc::tc8_setup(c));
         if (!c.ub64) {
-            CK(h, dalloc(&c.ub64, c.n, c));
-            CK(h, dalloc(&c.lazy_idx, c.n, c));
+            CK(h, alloc_lazy(c));
             CK(h, ebc::launch_lazy_init(c));
         }
         if (sync) {
@@ -468,7 +507,10 @@ ebc_status ebc_sync(ebc_t h) {
     if (err) {
         CK(h, cudaMemsetAsync(&c.st->err, 0, sizeof(int), c.stream));
         CK(h, cudaStreamSynchronize(c.stream));
-        return fail(h, (ebc_status)err, err == EBC_EINDEX ? "device: index outside [0, n)" : "device: invalid argument");
+        return fail(h, (ebc_status)err,
+                    err == EBC_EINDEX     ? "device: index outside [0, n)"
+                    : err == EBC_ETIMEOUT ? "device: a bounded wait in the tensor-core pipeline ran out"
+                                          : "device: invalid argument");
     }
     return EBC_OK;
 }
@@ -582,10 +624,7 @@ ebc_status ebc_autotune(ebc_t h, int32_t reps) { return ebc::autotune_handle(h, 
 ebc_status ebc_set_lazy(ebc_t h, int32_t on) {
     if (check_handle(h)) return EBC_EINVAL;
     ebc::Ctx &c = h->c;
-    if (on && !c.ub64) {
-        CK(h, dalloc(&c.ub64, c.n, c));
-        CK(h, dalloc(&c.lazy_idx, c.n, c));
-    }
+    if (on && !c.ub64) CK(h, alloc_lazy(c));
     if (on && !c.lazy) CK(h, ebc::launch_lazy_init(c));  // bounds restart from the current state
     c.lazy = on != 0;
     return EBC_OK;
@@ -979,8 +1018,14 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
 static ebc_status capture_round(ebc_t h) {
     ebc::Ctx &c = h->c;
     if (!h->g_idx) {
-        CK(h, dalloc(&h->g_idx, c.n, c));
-        CK(h, dalloc(&h->g_f, c.n, c));
+        cudaError_t e = dalloc(&h->g_idx, c.n, c);
+        if (e == cudaSuccess) e = dalloc(&h->g_f, c.n, c);
+        if (e != cudaSuccess) {  // both or neither
+            ebc::pool_free(h->g_idx, c.stream);
+            h->g_idx = nullptr;
+            h->g_f = nullptr;
+            CK(h, e);
+        }
     }
     if (h->round_exec) {
         cudaGraphExecDestroy(h->round_exec);
@@ -1019,6 +1064,7 @@ static ebc_status capture_round(ebc_t h) {
     h->prec_at_capture = (int)c.prec;
     h->ctas_at_capture = c.max_ctas;
     h->lazy_at_capture = c.lazy ? 1 : 0;
+    h->wait_at_capture = ebc::wait_limit_ns();
     return EBC_OK;
 }
 
@@ -1038,7 +1084,8 @@ ebc_status ebc_greedy(ebc_t h, int32_t k, int32_t *out_idx, double *out_f) {
     // after one direct round has set every kernel attribute
     const bool use_graph = h->graphs && !h->prof.on && c.stream != nullptr;
     if (use_graph && (!h->round_exec || h->round_stream != c.stream || h->prec_at_capture != (int)c.prec ||
-                      h->ctas_at_capture != c.max_ctas || h->lazy_at_capture != (c.lazy ? 1 : 0))) {
+                      h->ctas_at_capture != c.max_ctas || h->lazy_at_capture != (c.lazy ? 1 : 0) ||
+                      h->wait_at_capture != ebc::wait_limit_ns())) {
         if (!h->attrs_ready) {
             ebc_status s = greedy_round(h, ib, fb);
             if (s) return s;

@@ -34,6 +34,10 @@ constexpr int kRefineTile = 64;  // points per shared-memory tile of the exact /
 // stage is lowered by 2 kTieRel so that all tied candidates do.
 constexpr double kTieRel = 1e-10;
 
+// Limit of each wait inside the tensor-core pipeline, in ns (1 s unless
+// ebc_set_wait_limit_ns changed it); read when a kernel is launched.
+uint64_t wait_limit_ns();
+
 __host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t lmax(int64_t a, int64_t b) { return a > b ? a : b; }
 constexpr int kNumSMsHint = 152;

@@ -43,6 +43,7 @@ struct ebc_ctx {
     int prec_at_capture = -1;
     int ctas_at_capture = -1;
     int lazy_at_capture = -1;
+    uint64_t wait_at_capture = 0;  // pipeline wait limit baked into the captured round
     bool graphs = true;          // replay rounds from a graph when possible
     bool attrs_ready = false;    // one direct round has run (kernel attributes are set)
     // threshold sieve: upper bounds of every point's gain, valid while S only

@@ -103,6 +103,7 @@ struct TcArgs {
     int64_t partial_cap;    // doubles of the partial buffer
     int G;                  // persistent CTAs
     int *nch_out;           // chunk count used, for the reduction kernel
+    uint64_t wait_ns;       // limit of each pipeline wait (wait_limit_ns())
 };
 
 constexpr int MODE_GAINS = 0;
@@ -315,9 +316,12 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
     int *last_full = reinterpret_cast<int *>(base + L.off_misc + 8);  // [ns] (ns <= 8)
     int *last_afull = last_full + 8;                                    // [2]
     int *last_tfull = last_afull + 2;                                   // [2]
+    // teardown: one commit after every MMA this CTA issued (misc + 56 .. 64)
+    uint64_t *fin = reinterpret_cast<uint64_t *>(base + L.off_misc + 56);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const uint64_t wait_ns = args.wait_ns;  // limit of every pipeline wait (the teardown keeps kWaitNs)
     const Plan P = make_plan(args);
     if (blockIdx.x == 0 && threadIdx.x == 0 && args.nch_out) *args.nch_out = P.nchunks;
     const int total_units = P.n_ctiles * P.nchunks;
@@ -338,6 +342,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
             last_afull[b] = -1;
             last_tfull[b] = -1;
         }
+        tc::mbar_init(fin, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -374,7 +379,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                         for (int j = 0; j < katoms; ++j, ++g) {
                             const int s = g % ns;
                             const int ph = (g / ns) & 1;
-                            if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                            if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, wait_ns)) {
                                 record_timeout(args.err, abort_flag);
                                 ok = false;
                                 break;
@@ -386,7 +391,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                             tc::tma_load_2d(st + 2 * BMS * 128, &tmB, &full[s], j * args.xatom, brow);
                             last_full[s] = ph;
                             if (j == katoms - 1) {
-                                if (!tc::mbar_wait(&a_empty[0], (tt & 1) ^ 1, abort_flag)) {
+                                if (!tc::mbar_wait(&a_empty[0], (tt & 1) ^ 1, abort_flag, wait_ns)) {
                                     record_timeout(args.err, abort_flag);
                                     ok = false;
                                     break;
@@ -407,7 +412,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
                 const int ab = ua % na;
                 const int aph = (ua / na) & 1;
-                if (!tc::mbar_wait(&a_empty[ab], aph ^ 1, abort_flag)) {
+                if (!tc::mbar_wait(&a_empty[ab], aph ^ 1, abort_flag, wait_ns)) {
                     record_timeout(args.err, abort_flag);
                     break;
                 }
@@ -426,7 +431,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                     const int s = g % ns;
                     const int ph = (g / ns) & 1;
                     const int brow = b_row0 + i * BN;
-                    if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, wait_ns)) {
                         record_timeout(args.err, abort_flag);
                         ok = false;
                         break;
@@ -458,7 +463,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                         // fills again while the epilogue still drains region 1
                         for (int j = 0; j < katoms; ++j, ++g) {
                             const int s = g % ns;
-                            if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag)) {
+                            if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag, wait_ns)) {
                                 record_timeout(args.err, abort_flag);
                                 ok = false;
                                 break;
@@ -467,7 +472,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                             const uint32_t st = tc::smem_u32(sB + s * L.b_bytes);
                             const uint32_t b0 = st + 2 * BMS * 128;
                             const bool last = j == katoms - 1;
-                            if (last && !tc::mbar_wait(&a_full[0], t & 1, abort_flag)) {
+                            if (last && !tc::mbar_wait(&a_full[0], t & 1, abort_flag, wait_ns)) {
                                 record_timeout(args.err, abort_flag);
                                 ok = false;
                                 break;
@@ -476,7 +481,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                             const uint32_t sx = tc::smem_u32(base + L.off_ext);
                             for (int h = 0; h < 2 && ok; ++h) {
                                 if (j == 0) {
-                                    if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag)) {
+                                    if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag, wait_ns)) {
                                         record_timeout(args.err, abort_flag);
                                         ok = false;
                                         break;
@@ -511,7 +516,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 int ct, ch, b_row0, nb;
                 unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
                 const int ab = ua % na;
-                if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag)) {
+                if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag, wait_ns)) {
                     record_timeout(args.err, abort_flag);
                     break;
                 }
@@ -519,14 +524,14 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 bool ok = true;
                 for (int i = 0; i < nb && ok; ++i, ++g, ++t) {
                     const int s = g % ns;
-                    if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag)) {
+                    if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag, wait_ns)) {
                         record_timeout(args.err, abort_flag);
                         ok = false;
                         break;
                     }
                     const uint32_t b0 = tc::smem_u32(sB + s * L.b_bytes);
                     for (int h = 0; h < 2; ++h) {
-                        if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag)) {
+                        if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag, wait_ns)) {
                             record_timeout(args.err, abort_flag);
                             ok = false;
                             break;
@@ -573,7 +578,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 for (int h = 0; h < 2; ++h) {
                     if (alive) {
                         // the TMEM loads below are warp-collective: decide per warp
-                        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag));
+                        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag, wait_ns));
                         if (!ok) {
                             if (lane == 0) record_timeout(args.err, abort_flag);
                             alive = false;
@@ -647,7 +652,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 const int ge = lane < ngr ? __ldg(args.gset + c0 / SET_GROUP + lane) : 0;
                 const unsigned lastmask = __ballot_sync(0xffffffffu, lane < ngr && (ge & 1));  // groups ending a set
                 if (alive) {
-                    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag));
+                    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag, wait_ns));
                     if (!ok) {
                         if (lane == 0) record_timeout(args.err, abort_flag);
                         alive = false;
@@ -704,6 +709,14 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
 
     // ---------------------------------------------------------------- teardown
     __syncthreads();
+    if (warp == 1 && lane == 0) {
+        // every MMA this thread issued, committed or not (a timeout can stop
+        // the issuer between a region's MMAs and their commit), completes
+        // before the tensor memory is released
+        volatile int never = 0;
+        tc::mma_commit(fin);
+        tc::mbar_wait(fin, 0u, &never);
+    }
     if (threadIdx.x == 0) {
         // nothing may still write shared memory or TMEM when the CTA leaves:
         // wait (bounded) for the last issued phase of every barrier
@@ -1367,7 +1380,14 @@ cudaError_t tc8_setup(Ctx &c) {
                                 rows * KEXT * 2, rows * 4, rows * 4, rows * 8, rows * 8, rows * 4, rows * 4,
                                 rows * 4, rows * 4, 5 * 4, 4};
         for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i)
-            if ((e = pool_alloc(bufs[i], sizes[i], c.stream, c.device)) != cudaSuccess) return e;
+            if ((e = pool_alloc(bufs[i], sizes[i], c.stream, c.device)) != cudaSuccess) {
+                // leave no half-built set: the next call allocates all of them again
+                for (size_t j = 0; j < i; ++j) {
+                    pool_free(*bufs[j], c.stream);
+                    *bufs[j] = nullptr;
+                }
+                return e;
+            }
         if ((e = cudaMemsetAsync(T.Cq, 0, rows * T.DP, c.stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Cqx, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Bext, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
@@ -1407,6 +1427,7 @@ cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks_ou
         if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
     }
     TcArgs a{};
+    a.wait_ns = wait_limit_ns();
     a.m = m;
     a.n_vtiles = (int)(T.n_pad / BN);
     a.n_ctiles = (int)((m + BM - 1) / BM);
@@ -1463,17 +1484,21 @@ cudaError_t tc_setup(Ctx &c, int prec) {
         T.DP = (c.d + KATOM - 1) / KATOM * KATOM;
         size_t rows = (size_t)T.n_pad;
         cudaError_t e;
-        if ((e = pool_alloc((void **)&T.Vq, rows * T.DP * 2, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.Vq2, rows * T.DP * 2, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.Aext, rows * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.Bext, rows * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.Cq, rows * T.DP * 2, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.Cqx, rows * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.qn64, rows * 8, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.qerr, rows * 4, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.qnorm, rows * 4, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.qmax, 2 * 4, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.Px, rows * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
+        void **bufs[] = {(void **)&T.Vq,   (void **)&T.Vq2,  (void **)&T.Aext,  (void **)&T.Bext,
+                         (void **)&T.Cq,   (void **)&T.Cqx,  (void **)&T.qn64,  (void **)&T.qerr,
+                         (void **)&T.qnorm, (void **)&T.qmax, (void **)&T.Px};
+        const size_t sizes[] = {rows * T.DP * 2, rows * T.DP * 2, rows * KEXT * 2, rows * KEXT * 2,
+                                rows * T.DP * 2, rows * KEXT * 2, rows * 8,        rows * 4,
+                                rows * 4,        2 * 4,           rows * KEXT * 2};
+        for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i)
+            if ((e = pool_alloc(bufs[i], sizes[i], c.stream, c.device)) != cudaSuccess) {
+                // leave no half-built set: the next call allocates all of them again
+                for (size_t j = 0; j < i; ++j) {
+                    pool_free(*bufs[j], c.stream);
+                    *bufs[j] = nullptr;
+                }
+                return e;
+            }
         if ((e = cudaMemsetAsync(T.Cq, 0, rows * T.DP * 2, c.stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Cqx, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(T.Bext, 0, rows * KEXT * 2, c.stream)) != cudaSuccess) return e;
@@ -1517,6 +1542,7 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
         if (e != cudaSuccess) return e;
     }
     TcArgs a{};
+    a.wait_ns = wait_limit_ns();
     a.m = m;
     a.n_vtiles = (int)(T.n_pad / BN);
     a.n_ctiles = (int)((m + BM - 1) / BM);
@@ -1576,6 +1602,7 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     if (e != cudaSuccess) return e;
     const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
     TcArgs a{};
+    a.wait_ns = wait_limit_ns();
     a.m = m_cap;
     a.n_vtiles = (int)(T.n_pad / BN);
     a.n_ctiles = 0;
@@ -1700,6 +1727,7 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_d
         while (k1 < nch && aux[chunk0 + 4 * k1 + 1] - j0 <= max_sets) ++k1;
         const int64_t lb = aux[chunk0 + 4 * (k1 - 1) + 1] - j0;
         TcArgs a{};
+        a.wait_ns = wait_limit_ns();
         a.m = 0;
         a.n_vtiles = 0;
         a.n_ctiles = npu;

@@ -1,7 +1,8 @@
 // Inline-PTX helpers for sm_103a: mbarriers, TMA tile loads, tcgen05 MMA,
 // tensor memory (TMEM) allocation and loads.  Every wait is bounded: it
-// gives up after kWaitNs of %globaltimer time or when the CTA's abort flag
-// is raised, so a kernel can record an error and shut down cleanly.
+// gives up after a limit of %globaltimer time (kWaitNs unless the caller
+// passes another) or when the CTA's abort flag is raised, so a kernel can
+// record an error and shut down cleanly.
 #pragma once
 
 #include <cuda.h>
@@ -48,15 +49,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase of `parity` to complete.  Returns false on timeout or
-// when *abort is raised by another thread of the CTA.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+// Wait for the phase of `parity` to complete.  Returns false after limit_ns
+// of %globaltimer time or when *abort is raised by another thread of the CTA.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                          uint64_t limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
-        if (gtimer() - t0 > kWaitNs) return false;
+        if (gtimer() - t0 > limit_ns) return false;
     }
 }
 

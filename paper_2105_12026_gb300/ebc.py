@@ -87,6 +87,8 @@ _SIGS = {
     "ebc_threshold_ladder": [ctypes.c_double, _I32, ctypes.c_double, ctypes.c_double, _P, _I32,
                              ctypes.POINTER(_I32)],
     "ebc_set_graphs": [_P, _I32],
+    "ebc_set_wait_limit_ns": [_I64],
+    "ebc_inject_alloc_failure": [_I64],
     "ebc_set_kblocked": [_P, _I32],
     "ebc_set_lazy": [_P, _I32],
     "ebc_state_size": [_P, ctypes.POINTER(_I64)],
@@ -248,6 +250,20 @@ def ebc_set_max_ctas(h: int, max_ctas: int) -> None:
 
 def ebc_set_graphs(h: int, on: bool) -> None:
     _raise(h, load().ebc_set_graphs(_P(h), int(bool(on))))
+
+
+def ebc_set_wait_limit_ns(ns: int) -> None:
+    """Limit of each tensor-core pipeline wait (0: the default of 1 s)."""
+    rc = load().ebc_set_wait_limit_ns(int(ns))
+    if rc != EBC_OK:
+        raise EbcError(rc, "ebc_set_wait_limit_ns: out of range")
+
+
+def ebc_inject_alloc_failure(after: int) -> None:
+    """Make the device allocation after `after` more successful ones fail (-1: disarm)."""
+    rc = load().ebc_inject_alloc_failure(int(after))
+    if rc != EBC_OK:
+        raise EbcError(rc, "ebc_inject_alloc_failure: after < -1")
 
 
 def ebc_autotune(h: int, reps: int = 3) -> None:
@@ -649,6 +665,13 @@ def sieve_streaming(inst: Instance, items, K: int, eps: float, m_single: float |
 # ---------------------------------------------------------------------------
 # batch runtime (marshalling only)
 # ---------------------------------------------------------------------------
+
+def ebc_release_cached_memory() -> None:
+    """Return the library pool's cached, unused device memory (current device)."""
+    rc = load().ebc_release_cached_memory()
+    if rc != EBC_OK:
+        raise EbcError(rc, "ebc_release_cached_memory")
+
 
 def ebc_estimate_bytes(n: int, d: int, prec: int) -> int:
     return int(load().ebc_estimate_bytes(int(n), int(d), int(prec)))
