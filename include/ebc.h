@@ -457,6 +457,48 @@ ebc_status ebc_release_cached_memory(void);
 int64_t ebc_estimate_bytes(int64_t n, int32_t d, int32_t prec);
 
 /* ------------------------------------------------------------------------
+ * Groups: Greedy on many handles with one persistent bulk launch per round.
+ * Not in the paper, which runs one optimiser at a time; this is the Greedy
+ * step of Sec. 4.1 batched over an uneven mix of instances.  Each round, the
+ * bulk gains of every handle still running are computed by ONE persistent
+ * tensor-core launch whose work units (handle, 256-candidate tile, V chunk)
+ * are handed out largest first from a device queue; each handle's tensor
+ * maps are read from device memory.  The certified pick and the m_v update
+ * of each handle then run on that handle's own stream.
+ * ---------------------------------------------------------------------- */
+typedef struct ebc_group_ctx *ebc_group_t;
+
+/* A group on the current device (its own stream and tables).  One host
+ * thread at a time per group. */
+ebc_status ebc_group_create(ebc_group_t *out);
+
+/*
+ * k[i] Greedy rounds on handle h[i] for i < count, continuing from each
+ * handle's state, exactly as ebc_greedy(h[i], k[i], out_idx[i], out_f[i])
+ * would: the same picks (certified exact argmax, same tie rule) and the same
+ * f values.  out_idx[i] / out_f[i] are device arrays of k[i] entries.
+ * Handles at EBC_BF16 / EBC_FP16 with d <= 128, lazy Greedy off and no CTA
+ * cap share the launches; any other handle runs its rounds through
+ * ebc_greedy on its own stream.  Handles on their own streams overlap their
+ * per-round tails; handles sharing one stream serialise them.
+ * Asynchronous: a handle's outputs are ready when its stream reaches them
+ * (ebc_sync); a timeout in a shared launch is reported by ebc_sync of every
+ * handle in it.  EINVAL for a NULL or repeated handle, a handle on another
+ * device, k[i] < 0 or above the handle's unselected points, or a NULL
+ * output with k[i] > 0; on any error the handles' Greedy states are
+ * undefined (reset them).
+ */
+ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *h, int32_t count, const int32_t *k, int32_t *const *out_idx,
+                            double *const *out_f);
+
+/* Shared launches issued, work units they processed and rounds, summed over
+ * the group's calls (any pointer may be NULL). */
+ebc_status ebc_group_stats(ebc_group_t g, int64_t *launches, int64_t *units, int64_t *rounds);
+const char *ebc_group_last_error(ebc_group_t g);
+/* Waits for the group's stream, then frees it (NULL is accepted). */
+ebc_status ebc_group_destroy(ebc_group_t g);
+
+/* ------------------------------------------------------------------------
  * Batch runtime: many independent instances on one GPU.  Not in the paper,
  * which evaluates one optimiser at a time; it serves the many-request case
  * its optimisers generate.  Each admitted instance gets its own handle and

@@ -979,6 +979,19 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
         h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
         CK(h, launch(h, -1, 1, [&] { return ebc::launch_reduce_select(c, c.n, nch, nullptr, true, nullptr, h->nblk); }));
     }
+    return ebc::round_certify(h, out_idx_base, out_f_base, lazy);
+}
+
+}  // extern "C"
+
+// The certified pick of a round whose bulk bounds are in place (per-block
+// top lists from the reduction of the bulk partials, or the lazy list's),
+// then the m_v update.
+ebc_status ebc::round_certify(ebc_t h, int32_t *out_idx_base, double *out_f_base, bool lazy) {
+    ebc::Ctx &c = h->c;
+    const int K = c.refine_k;
+    const double eta = bulk_eta(c);
+    ebc::Ctx::Sel &S = c.cert;
     CK(h, launch(h, -1, 1, [&] { return ebc::launch_merge_top(c, h->nblk, K, eta); }));
     // level 1: bounds for the top list, then for the escalated candidates
     const int64_t esc_off = (int64_t)ebc::kMaxRefineK * S.nchunks;
@@ -1012,6 +1025,8 @@ static ebc_status greedy_round(ebc_t h, int32_t *out_idx_base, double *out_f_bas
        }));
     return EBC_OK;
 }
+
+extern "C" {
 
 // Capture one Greedy round (outputs into the handle's by-round buffers) as a
 // graph.  A capture failure leaves direct launches in use.

@@ -325,6 +325,36 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
 cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_dev, const int64_t *off_host,
                                 int64_t l, double *out_f, int64_t *nlaunch);
 void tc_free(Ctx &c);
+
+// ---- one persistent bulk launch over several handles (k_tc.cu, group.cu) ----
+// A handle's part of a shared Greedy round: its tensor maps (read by TMA from
+// device memory) and the plan of its bulk gains over all n candidates.  The
+// maps keep CUtensorMap's own alignment (at least the 64 bytes TMA needs).
+struct GroupInst {
+    CUtensorMap tmA, tmAx, tmB, tmBx;  // candidate rows / extension, point rows / extension
+    double *partial;                   // [nchunks][m] the handle's chunk partials
+    int *err;                          // the handle's device error word
+    int64_t m;                         // candidates: every point (selected ones are masked later)
+    int n_vtiles;                      // point tiles of 256
+    int vt_per_chunk;                  // point tiles per V chunk
+    int nchunks;                       // V chunks
+    int RB;                            // bytes per row of the main part (128 or 256)
+    uint32_t idesc, idesc_ext;         // MMA instruction descriptors (precision), extension (BF16)
+};
+// One work unit: a 256-candidate tile of one handle against one of its V chunks.
+struct GroupUnit {
+    int inst, ctile, chunk, ntiles;  // ntiles = point tiles of the chunk (the unit's cost)
+};
+bool tc_group_supported(const Ctx &c);  // BF16 / FP16 with whole rows resident (d <= 128)
+int tc_group_row_bytes(const Ctx &c);   // RB of the handle (2 * padded d)
+void group_inst_fill(const Ctx &c, int nchunks, int vt_per_chunk, GroupInst *out);
+// the persistent kernel over units [0, total_units) handed out by *d_counter
+// (zero on entry); a timeout is recorded in *d_err
+cudaError_t launch_gains_tc_group(const GroupInst *d_inst, const GroupUnit *d_units, int total_units,
+                                  int *d_counter, int *d_err, int RBmax, int G, cudaStream_t s);
+// copy a nonzero *d_err into the error word of handles [0, count) of d_inst
+cudaError_t launch_group_err(const GroupInst *d_inst, int count, const int *d_err, cudaStream_t s);
+
 // FP8 e4m3 (k_tc.cu)
 cudaError_t tc8_setup(Ctx &c);                    // allocate, quantise, build tensor maps
 cudaError_t launch_prep_tc8(Ctx &c, bool upper);  // per-round point extension

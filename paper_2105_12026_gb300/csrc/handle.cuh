@@ -99,6 +99,11 @@ cudaError_t launch(ebc_t h, int kind, int64_t nlaunch, F &&fn) {
 }
 
 }  // namespace hx
+
+// The certified pick of a Greedy round whose bulk bounds are reduced into the
+// per-block top lists (or the lazy list's), then the m_v update (api.cu).
+ebc_status round_certify(ebc_t h, int32_t *out_idx_base, double *out_f_base, bool lazy);
+
 }  // namespace ebc
 
 #define CK(h, expr)                                   \

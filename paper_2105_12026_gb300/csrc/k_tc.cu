@@ -770,6 +770,330 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// One persistent launch over the Greedy rounds of several handles (the
+// instance-batched bulk gains of an uneven mix of ground sets).
+//
+// The same warp roles and MMA sequence as the resident MODE_GAINS pipeline,
+// with the work units of all handles in one table: a unit is (handle,
+// candidate tile, V chunk).  The producer takes the next unit from a device
+// counter (the table is ordered largest first, so the last units to start are
+// short) and passes its index to the MMA issuer and the epilogue warps
+// through a small ring of shared-memory slots; each handle's tensor maps are
+// read by TMA from device memory.  Shared-memory buffers are laid out for the
+// widest row of the launch (RBmax); a unit of narrower rows fills only the
+// first K atoms of each buffer and expects only its own bytes, so its MMAs,
+// and hence its sums, are those of the single-handle kernel.
+//
+// Every wait is bounded; a CTA that gives up records EBC_ETIMEOUT in the
+// launch's error word and stops, and the other warps of the CTA see its
+// abort flag at their next wait.  The two column halves of a unit are joined
+// through mbarriers (no block-wide barrier), so an aborted warp cannot leave
+// the others waiting.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int UR = 4;                // unit ring slots
+constexpr uint32_t GROUP_EXTRA = 128;  // shared bytes past the resident layout: ring and join barriers
+
+struct GroupArgs {
+    const GroupInst *inst;
+    const GroupUnit *units;
+    int total_units;
+    int *counter;
+    int *err;
+    int RBmax, nstages, na;
+    uint64_t wait_ns;
+};
+}  // namespace
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int ns = args.nstages;
+    const int na = args.na;
+    const uint64_t wait_ns = args.wait_ns;
+    const SmemLayout L = smem_layout(args.RBmax, ns, na);
+    uint8_t *sA = base;
+    uint8_t *sB = base + L.off_b;
+    double *comb = reinterpret_cast<double *>(base + L.off_comb);  // [2][BMS]
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + L.off_bar);
+    uint64_t *empty = full + ns;
+    uint64_t *a_full = empty + ns;
+    uint64_t *a_empty = a_full + 2;
+    uint64_t *t_full = a_empty + 2;
+    uint64_t *t_empty = t_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + L.off_misc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(base + L.off_misc + 4);
+    int *last_full = reinterpret_cast<int *>(base + L.off_misc + 8);  // [ns] (ns <= 8)
+    int *last_afull = last_full + 8;                                    // [2]
+    int *last_tfull = last_afull + 2;                                   // [2]
+    uint64_t *fin = reinterpret_cast<uint64_t *>(base + L.off_misc + 56);
+    uint64_t *u_full = reinterpret_cast<uint64_t *>(base + L.off_misc + 64);  // [UR]
+    uint64_t *u_empty = u_full + UR;                                          // [UR]
+    uint64_t *c_full = u_empty + UR;   // column half 1 -> half 0: comb written
+    uint64_t *c_empty = c_full + 1;    // half 0 -> half 1: comb read
+    volatile int *u_id = reinterpret_cast<volatile int *>(c_empty + 1);  // [UR]
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ns; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+            last_full[s] = -1;
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&a_full[b], 1);
+            tc::mbar_init(&a_empty[b], 1);
+            tc::mbar_init(&t_full[b], 1);
+            tc::mbar_init(&t_empty[b], NEPI / 32);
+            last_afull[b] = -1;
+            last_tfull[b] = -1;
+        }
+        for (int r = 0; r < UR; ++r) {
+            tc::mbar_init(&u_full[r], 1);
+            tc::mbar_init(&u_empty[r], 1 + NEPI / 32);  // the MMA issuer and every epilogue warp
+        }
+        tc::mbar_init(c_full, NEPI / 2);  // every thread of the column-half-1 warps
+        tc::mbar_init(c_empty, NEPI / 2);
+        tc::mbar_init(fin, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int g = 0, ua = 0, last_inst = -1;
+            for (int i = 0;; ++i) {
+                const int r = i % UR;
+                if (!tc::mbar_wait(&u_empty[r], ((i / UR) & 1) ^ 1, abort_flag, wait_ns)) {
+                    record_timeout(args.err, abort_flag);
+                    break;
+                }
+                int u = atomicAdd(args.counter, 1);
+                if (u >= args.total_units) u = -1;
+                u_id[r] = u;
+                tc::mbar_arrive(&u_full[r]);  // release: the slot's index is visible to its waiters
+                if (u < 0) break;
+                const GroupUnit w = args.units[u];
+                const GroupInst *I = args.inst + w.inst;
+                const int RB = I->RB;
+                const int katoms = RB / 128;
+                const uint32_t a_tx = 2u * (uint32_t)(BMS * RB + BMS * KEXT * 2);
+                const uint32_t b_tx = (uint32_t)(BN * RB + BN * KEXT * 2);
+                if (w.inst != last_inst) {  // maps written by a copy before the launch
+                    tc::tensormap_acquire(&I->tmA);
+                    tc::tensormap_acquire(&I->tmAx);
+                    tc::tensormap_acquire(&I->tmB);
+                    tc::tensormap_acquire(&I->tmBx);
+                    last_inst = w.inst;
+                }
+                const int ab = ua % na;
+                const int aph = (ua / na) & 1;
+                if (!tc::mbar_wait(&a_empty[ab], aph ^ 1, abort_flag, wait_ns)) {
+                    record_timeout(args.err, abort_flag);
+                    break;
+                }
+                uint8_t *abuf = sA + ab * L.a_bytes;
+                tc::mbar_arrive_expect_tx(&a_full[ab], a_tx);
+                for (int h = 0; h < 2; ++h) {
+                    uint8_t *sub = abuf + h * L.a_sub;
+                    const int row0 = w.ctile * BM + h * BMS;
+                    for (int j = 0; j < katoms; ++j)
+                        tc::tma_load_2d(sub + j * (BMS * 128), &I->tmA, &a_full[ab], j * KATOM, row0);
+                    tc::tma_load_2d(sub + L.a_main, &I->tmAx, &a_full[ab], 0, row0);
+                }
+                last_afull[ab] = aph;
+                bool ok = true;
+                const int vt0 = w.chunk * I->vt_per_chunk;
+                for (int t = 0; t < w.ntiles; ++t, ++g) {
+                    const int s = g % ns;
+                    const int ph = (g / ns) & 1;
+                    const int brow = (vt0 + t) * BN;
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, wait_ns)) {
+                        record_timeout(args.err, abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *bbuf = sB + s * L.b_bytes;
+                    tc::mbar_arrive_expect_tx(&full[s], b_tx);
+                    for (int j = 0; j < katoms; ++j)
+                        tc::tma_load_2d(bbuf + j * (BN * 128), &I->tmB, &full[s], j * KATOM, brow);
+                    tc::tma_load_2d(bbuf + L.b_main, &I->tmBx, &full[s], 0, brow);
+                    last_full[s] = ph;
+                }
+                if (!ok) break;
+                ++ua;
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int g = 0, t = 0, ua = 0;
+            for (int i = 0;; ++i) {
+                const int r = i % UR;
+                if (!tc::mbar_wait(&u_full[r], (i / UR) & 1, abort_flag, wait_ns)) {
+                    record_timeout(args.err, abort_flag);
+                    break;
+                }
+                const int u = u_id[r];
+                tc::mbar_arrive(&u_empty[r]);
+                if (u < 0) break;
+                const GroupUnit w = args.units[u];
+                const GroupInst *I = args.inst + w.inst;
+                const int nmma = I->RB / 32;  // one MMA per 32 bytes of K
+                const uint32_t idesc = I->idesc, idesc_ext = I->idesc_ext;
+                const int ab = ua % na;
+                if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag, wait_ns)) {
+                    record_timeout(args.err, abort_flag);
+                    break;
+                }
+                const uint32_t a0 = tc::smem_u32(sA + ab * L.a_bytes);
+                bool ok = true;
+                for (int tt = 0; tt < w.ntiles && ok; ++tt, ++g, ++t) {
+                    const int s = g % ns;
+                    if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag, wait_ns)) {
+                        record_timeout(args.err, abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t b0 = tc::smem_u32(sB + s * L.b_bytes);
+                    for (int h = 0; h < 2; ++h) {
+                        if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag, wait_ns)) {
+                            record_timeout(args.err, abort_flag);
+                            ok = false;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
+                        const uint32_t ah = a0 + h * L.a_sub;
+                        for (int kk = 0; kk < nmma; ++kk) {
+                            const uint32_t j = kk >> 2, w4 = kk & 3;
+                            const uint64_t ad = tc::sdesc_sw128(ah + j * (BMS * 128) + w4 * 32);
+                            const uint64_t bd = tc::sdesc_sw128(b0 + j * (BN * 128) + w4 * 32);
+                            tc::mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        }
+                        tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main), idesc_ext,
+                                    1u);
+                        tc::mma_commit(&t_full[h]);
+                        last_tfull[h] = t & 1;
+                    }
+                    if (!ok) break;
+                    tc::mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&a_empty[ab]);
+                ++ua;
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int ew = warp - 2;        // 0..7
+        const int q = warp & 3;         // TMEM lane quarter this warp may access
+        const int half = ew >> 2;       // column half of a region
+        const int row = q * 32 + lane;  // candidate row within a sub-tile
+        int t = 0, ie = 0;
+        for (int i = 0;; ++i) {
+            const int r = i % UR;
+            int u = -1;
+            bool ok = true;
+            if (lane == 0) {
+                ok = tc::mbar_wait(&u_full[r], (i / UR) & 1, abort_flag, wait_ns);
+                if (ok) {
+                    u = u_id[r];
+                    tc::mbar_arrive(&u_empty[r]);
+                } else {
+                    record_timeout(args.err, abort_flag);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (!ok || u < 0) break;
+            const GroupUnit w = args.units[u];
+            const GroupInst *I = args.inst + w.inst;
+            double acc[2] = {0.0, 0.0};
+            for (int tt = 0; tt < w.ntiles && ok; ++tt, ++t) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    // the TMEM loads below are warp-collective: decide per warp
+                    if (!__all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag, wait_ns))) {
+                        if (lane == 0) record_timeout(args.err, abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN + half * 128);
+                    uint32_t r0[32], r1[32], r2[32], r3[32];
+                    tc::tmem_ld32(taddr, r0);
+                    tc::tmem_ld32(taddr + 32, r1);
+                    tc::tmem_ld32(taddr + 64, r2);
+                    tc::tmem_ld32(taddr + 96, r3);
+                    tc::tmem_ld_wait();
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&t_empty[h]);
+                    acc[h] += (double)relu_sum128(r0, r1, r2, r3);
+                }
+            }
+            if (!ok) break;
+            // join the column halves in a fixed order: half 1 hands its sums to half 0
+            const uint32_t cph = ie & 1;
+            if (half == 1) {
+                if (!tc::mbar_wait(c_empty, cph ^ 1, abort_flag, wait_ns)) {
+                    record_timeout(args.err, abort_flag);
+                    break;
+                }
+                comb[row] = acc[0];
+                comb[BMS + row] = acc[1];
+                tc::mbar_arrive(c_full);
+            } else {
+                if (!tc::mbar_wait(c_full, cph, abort_flag, wait_ns)) {
+                    record_timeout(args.err, abort_flag);
+                    break;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t j = (int64_t)w.ctile * BM + h * BMS + row;
+                    if (j < I->m) I->partial[(int64_t)w.chunk * I->m + j] = acc[h] + comb[h * BMS + row];
+                }
+                tc::mbar_arrive(c_empty);
+            }
+            ++ie;
+        }
+    }
+
+    // ---------------------------------------------------------------- teardown
+    __syncthreads();
+    if (warp == 1 && lane == 0) {
+        volatile int never = 0;
+        tc::mma_commit(fin);
+        tc::mbar_wait(fin, 0u, &never);
+    }
+    if (threadIdx.x == 0) {
+        volatile int never = 0;
+        for (int s = 0; s < ns; ++s)
+            if (last_full[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)last_full[s], &never);
+        for (int b = 0; b < 2; ++b) {
+            if (last_afull[b] >= 0) tc::mbar_wait(&a_full[b], (uint32_t)last_afull[b], &never);
+            if (last_tfull[b] >= 0) tc::mbar_wait(&t_full[b], (uint32_t)last_tfull[b], &never);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // bf16 pieces.  hi is the nearest bf16; each residual is exact in FP64
 // (Sterbenz); the last piece is rounded up (or to nearest) so that the sum of
 // the pieces is >= x with an error of about 2^-24 |x|.
@@ -1578,6 +1902,72 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
         k_gains_tc<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V, T.tmB_V,
                                                           T.tmBx, a);
     *nchunks_out = a.nchunks;
+    return cudaGetLastError();
+}
+
+bool tc_group_supported(const Ctx &c) {
+    return (c.tc.prec == EBC_BF16 || c.tc.prec == EBC_FP16) && !use_kb(c, 2 * c.tc.DP);
+}
+
+int tc_group_row_bytes(const Ctx &c) { return 2 * c.tc.DP; }
+
+void group_inst_fill(const Ctx &c, int nchunks, int vt_per_chunk, GroupInst *out) {
+    const Ctx::Tc &T = c.tc;
+    out->tmA = T.tmA_V;
+    out->tmAx = T.tmAx_V;
+    out->tmB = T.tmB_V;
+    out->tmBx = T.tmBx;
+    out->partial = c.partial;
+    out->err = &c.st->err;
+    out->m = c.n;
+    out->n_vtiles = (int)(T.n_pad / BN);
+    out->vt_per_chunk = vt_per_chunk;
+    out->nchunks = nchunks;
+    out->RB = 2 * T.DP;
+    out->idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, BN);
+    out->idesc_ext = tc::idesc_f16(1u, BMS, BN);
+}
+
+// A timeout anywhere in the shared launch leaves units of any handle
+// unfinished: every handle of the launch gets the error.
+__global__ void k_group_err(const GroupInst *__restrict__ inst, int count, const int *__restrict__ err) {
+    const int e = *err;
+    if (e == 0) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        atomicCAS(inst[i].err, 0, e);
+}
+
+cudaError_t launch_group_err(const GroupInst *d_inst, int count, const int *d_err, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    k_group_err<<<(count + 255) / 256, 256, 0, s>>>(d_inst, count, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gains_tc_group(const GroupInst *d_inst, const GroupUnit *d_units, int total_units,
+                                  int *d_counter, int *d_err, int RBmax, int G, cudaStream_t s) {
+    if (total_units <= 0) return cudaSuccess;
+    int na = 0, ns = 0;
+    for (int a = 2; a >= 1 && ns == 0; --a)
+        for (int st = 6; st >= 2; --st)
+            if (smem_layout(RBmax, st, a).total + GROUP_EXTRA <= (uint32_t)SMEM_LIMIT) {
+                na = a;
+                ns = st;
+                break;
+            }
+    if (ns == 0) return cudaErrorInvalidConfiguration;
+    const uint32_t bytes = smem_layout(RBmax, ns, na).total + GROUP_EXTRA;
+    if (cudaError_t e = allow_smem((const void *)k_gains_tc_group, bytes); e != cudaSuccess) return e;
+    GroupArgs a{};
+    a.inst = d_inst;
+    a.units = d_units;
+    a.total_units = total_units;
+    a.counter = d_counter;
+    a.err = d_err;
+    a.RBmax = RBmax;
+    a.nstages = ns;
+    a.na = na;
+    a.wait_ns = wait_limit_ns();
+    k_gains_tc_group<<<std::min(total_units, G), NTHREADS, bytes, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -67,6 +67,13 @@ __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Acquire a tensor map that lives in global memory (written by an earlier
+// copy) for the tensor-map proxy, so TMA never uses a stale cached copy.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 // 2-D tiled load of the box at (x = inner element offset, y = row) into
 // shared memory, completing `bytes` on the mbarrier.  x * element size must be
 // a multiple of 16 bytes (callers pass multiples of 64 elements).

@@ -113,6 +113,11 @@ _SIGS = {
     "ebc_noalloc_last_error": [],
     "ebc_estimate_bytes": [_I64, _I32, _I32],
     "ebc_release_cached_memory": [],
+    "ebc_group_create": [ctypes.POINTER(_P)],
+    "ebc_group_greedy": [_P, _P, _I32, _P, _P, _P],
+    "ebc_group_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+    "ebc_group_last_error": [_P],
+    "ebc_group_destroy": [_P],
     "ebc_batch_create": [_I32, _I64, _I32, ctypes.POINTER(_P)],
     "ebc_batch_submit": [_P, _P, _I64, _I32, _I32, ctypes.c_int, ctypes.POINTER(_I64)],
     "ebc_batch_step": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
@@ -144,6 +149,7 @@ def load(path: str | None = None):
             lib.ebc_last_error.restype = ctypes.c_char_p
             lib.ebc_noalloc_last_error.restype = ctypes.c_char_p
             lib.ebc_batch_last_error.restype = ctypes.c_char_p
+            lib.ebc_group_last_error.restype = ctypes.c_char_p
             lib.ebc_estimate_bytes.restype = ctypes.c_int64
             lib.ebc_tune_count.restype = ctypes.c_int64
             _lib = lib
@@ -675,6 +681,71 @@ def ebc_release_cached_memory() -> None:
 
 def ebc_estimate_bytes(n: int, d: int, prec: int) -> int:
     return int(load().ebc_estimate_bytes(int(n), int(d), int(prec)))
+
+
+class Group:
+    """Greedy on many instances with one persistent bulk launch per round
+    (include/ebc.h, ebc_group_*)."""
+
+    def __init__(self):
+        h = _P()
+        rc = load().ebc_group_create(ctypes.byref(h))
+        if rc != EBC_OK:
+            raise EbcError(rc, "ebc_group_create")
+        self.h = h.value
+
+    def _err(self, rc):
+        if rc != EBC_OK:
+            m = load().ebc_group_last_error(_P(self.h))
+            raise EbcError(rc, m.decode() if m else "")
+
+    def greedy(self, instances, ks):
+        """Enqueue k rounds on every instance; returns per-instance device
+        tensors (idx int32[k], f float64[k]), valid once each instance's
+        stream reaches them (Instance.sync)."""
+        import torch
+        n = len(instances)
+        outs = [(torch.empty(max(int(k), 1), dtype=torch.int32, device="cuda"),
+                 torch.empty(max(int(k), 1), dtype=torch.float64, device="cuda")) for k in ks]
+        harr = (_P * n)(*[inst.h for inst in instances])
+        karr = (_I32 * n)(*[int(k) for k in ks])
+        iarr = (_P * n)(*[o[0].data_ptr() for o in outs])
+        farr = (_P * n)(*[o[1].data_ptr() for o in outs])
+        self._err(load().ebc_group_greedy(_P(self.h), ctypes.cast(harr, _P), n, ctypes.cast(karr, _P),
+                                          ctypes.cast(iarr, _P), ctypes.cast(farr, _P)))
+        self._keep = outs
+        return [(o[0][:int(k)], o[1][:int(k)]) for o, k in zip(outs, ks)]
+
+    def greedy_host(self, instances, ks):
+        """As greedy, then wait for every instance; numpy results."""
+        outs = self.greedy(instances, ks)
+        res = []
+        for inst, (i, f) in zip(instances, outs):
+            inst.sync()
+            res.append((i.cpu().numpy(), f.cpu().numpy()))
+        return res
+
+    def stats(self) -> dict:
+        a, b, c = _I64(), _I64(), _I64()
+        self._err(load().ebc_group_stats(_P(self.h), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"launches": a.value, "units": b.value, "rounds": c.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ebc_group_destroy(_P(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
