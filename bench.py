@@ -307,7 +307,7 @@ def run_mix_resident(args):
              for V in Vs]
     outs = [(torch.empty(k, dtype=torch.int32, device=dev), torch.empty(k, dtype=torch.float64, device=dev))
             for k in ks]
-    group = ebc.Group()
+    group = ebc.Group(lanes=args.group_lanes)
 
     def one_step():
         for inst, V in zip(insts, Vs):
@@ -354,7 +354,7 @@ def run_mix_resident(args):
             "scaling": "strong", "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded GMM instance mix)",
             "config": {"workload": f"batched greedy, {len(specs)} instances: n log-uniform [2000, 100000], "
                                    f"d in {{16,32,64,128}}, k in [5, 50]",
-                       "mix_mode": args.mix_mode, "evals_per_step": evals,
+                       "mix_mode": args.mix_mode, "group_lanes": args.group_lanes, "evals_per_step": evals,
                        "parallelism": f"instances sharded over {world} GPUs" if world > 1 else "single GPU",
                        "timing": "wall clock between device synchronisations; every step uploads each instance's "
                                  "V from pinned host memory into its resident handle (ebc_reload: prologue and "
@@ -852,6 +852,7 @@ def main():
     ap.add_argument("--mix-mode", default="group", choices=["group", "streams", "batch"],
                     help="mix: one shared bulk launch per round (group), per-instance rounds on own streams "
                          "(streams) or the batch runtime (batch)")
+    ap.add_argument("--group-lanes", type=int, default=2, help="mix: lanes of the shared-launch group")
     ap.add_argument("--slots", type=int, default=32, help="mix/serve: concurrent instances")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="mix/serve: device-memory budget")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")

@@ -491,6 +491,12 @@ ebc_status ebc_group_create(ebc_group_t *out);
 ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *h, int32_t count, const int32_t *k, int32_t *const *out_idx,
                             double *const *out_f);
 
+/* Lanes (1 to 4, default 2): the handles of a call are dealt round-robin to
+ * this many lanes, each with its own stream and shared launch per round, so
+ * the per-handle picks of one lane overlap the shared launch of another.
+ * Results do not depend on it.  EINVAL outside [1, 4]. */
+ebc_status ebc_group_set_lanes(ebc_group_t g, int32_t lanes);
+
 /* Shared launches issued, work units they processed and rounds, summed over
  * the group's calls (any pointer may be NULL). */
 ebc_status ebc_group_stats(ebc_group_t g, int64_t *launches, int64_t *units, int64_t *rounds);

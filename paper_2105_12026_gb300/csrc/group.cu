@@ -25,14 +25,14 @@
 
 using namespace ebc::hx;
 
-struct ebc_group_ctx {
-    int device = 0;
-    int num_sms = 152;
+// One lane: a stream with its own tables; the handles of a call are dealt
+// round-robin to the lanes, whose rounds interleave on the device (the
+// per-handle tails of one lane overlap the shared launch of another).
+struct GroupLane {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_bulk = nullptr;    // end of the current round's shared launch
     cudaEvent_t ev_staged = nullptr;  // the staging buffers' last upload finished
     bool staged_pending = false;
-    std::vector<cudaEvent_t> ev_inst;  // per handle: its point extension is ready
     ebc::GroupInst *h_inst = nullptr;  // pinned staging
     ebc::GroupUnit *h_units = nullptr;
     int64_t h_inst_cap = 0, h_unit_cap = 0;
@@ -40,6 +40,14 @@ struct ebc_group_ctx {
     ebc::GroupUnit *d_units = nullptr;
     int64_t d_inst_cap = 0, d_unit_cap = 0;
     int *d_words = nullptr;  // [0] next unit, [1] error of the launch
+};
+
+struct ebc_group_ctx {
+    int device = 0;
+    int num_sms = 152;
+    int nlanes = 2;
+    GroupLane lanes[4];
+    std::vector<cudaEvent_t> ev_inst;  // per handle: its point extension is ready
     int64_t launches = 0, units = 0, rounds = 0;
     std::string err;
 };
@@ -71,50 +79,45 @@ bool group_eligible(ebc_t h) {
            ebc::tc_group_supported(c);
 }
 
-// staging and device tables large enough for ni handles and nu units
-ebc_status ensure_tables(ebc_group_t g, int64_t ni, int64_t nu) {
-    if (g->staged_pending) {  // the previous call's upload still reads the staging buffers
-        GK(g, cudaEventSynchronize(g->ev_staged));
-        g->staged_pending = false;
+// staging and device tables of a lane large enough for ni handles and nu units
+ebc_status ensure_tables(ebc_group_t g, GroupLane *l, int64_t ni, int64_t nu) {
+    if (l->staged_pending) {  // the previous call's upload still reads the staging buffers
+        GK(g, cudaEventSynchronize(l->ev_staged));
+        l->staged_pending = false;
     }
-    if (g->h_inst_cap < ni) {
-        if (g->h_inst) cudaFreeHost(g->h_inst);
-        g->h_inst = nullptr;
-        g->h_inst_cap = 0;
+    if (l->h_inst_cap < ni) {
+        if (l->h_inst) cudaFreeHost(l->h_inst);
+        l->h_inst = nullptr;
+        l->h_inst_cap = 0;
         const int64_t cap = std::max<int64_t>(ni, 64);
-        GK(g, cudaMallocHost((void **)&g->h_inst, sizeof(ebc::GroupInst) * cap));
-        g->h_inst_cap = cap;
+        GK(g, cudaMallocHost((void **)&l->h_inst, sizeof(ebc::GroupInst) * cap));
+        l->h_inst_cap = cap;
     }
-    if (g->h_unit_cap < nu) {
-        if (g->h_units) cudaFreeHost(g->h_units);
-        g->h_units = nullptr;
-        g->h_unit_cap = 0;
+    if (l->h_unit_cap < nu) {
+        if (l->h_units) cudaFreeHost(l->h_units);
+        l->h_units = nullptr;
+        l->h_unit_cap = 0;
         const int64_t cap = std::max<int64_t>(nu, 4096);
-        GK(g, cudaMallocHost((void **)&g->h_units, sizeof(ebc::GroupUnit) * cap));
-        g->h_unit_cap = cap;
+        GK(g, cudaMallocHost((void **)&l->h_units, sizeof(ebc::GroupUnit) * cap));
+        l->h_unit_cap = cap;
     }
-    if (g->d_inst_cap < ni) {
-        ebc::pool_free(g->d_inst, g->stream);
-        g->d_inst = nullptr;
-        g->d_inst_cap = 0;
+    if (l->d_inst_cap < ni) {
+        ebc::pool_free(l->d_inst, l->stream);
+        l->d_inst = nullptr;
+        l->d_inst_cap = 0;
         const int64_t cap = std::max<int64_t>(ni, 64);
-        GK(g, ebc::pool_alloc((void **)&g->d_inst, sizeof(ebc::GroupInst) * cap, g->stream, g->device));
-        g->d_inst_cap = cap;
+        GK(g, ebc::pool_alloc((void **)&l->d_inst, sizeof(ebc::GroupInst) * cap, l->stream, g->device));
+        l->d_inst_cap = cap;
     }
-    if (g->d_unit_cap < nu) {
-        ebc::pool_free(g->d_units, g->stream);
-        g->d_units = nullptr;
-        g->d_unit_cap = 0;
+    if (l->d_unit_cap < nu) {
+        ebc::pool_free(l->d_units, l->stream);
+        l->d_units = nullptr;
+        l->d_unit_cap = 0;
         const int64_t cap = std::max<int64_t>(nu, 4096);
-        GK(g, ebc::pool_alloc((void **)&g->d_units, sizeof(ebc::GroupUnit) * cap, g->stream, g->device));
-        g->d_unit_cap = cap;
+        GK(g, ebc::pool_alloc((void **)&l->d_units, sizeof(ebc::GroupUnit) * cap, l->stream, g->device));
+        l->d_unit_cap = cap;
     }
-    if (!g->d_words) GK(g, ebc::pool_alloc((void **)&g->d_words, 2 * sizeof(int), g->stream, g->device));
-    while ((int64_t)g->ev_inst.size() < ni) {
-        cudaEvent_t ev = nullptr;
-        GK(g, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        g->ev_inst.push_back(ev);
-    }
+    if (!l->d_words) GK(g, ebc::pool_alloc((void **)&l->d_words, 2 * sizeof(int), l->stream, g->device));
     return EBC_OK;
 }
 
@@ -134,14 +137,21 @@ ebc_status ebc_group_create(ebc_group_t *out) {
     if (!g) return EBC_ENOMEM;
     g->device = dev;
     cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&g->ev_bulk, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&g->ev_staged, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        ebc_group_destroy(g);
-        return EBC_ECUDA;
-    }
+    for (GroupLane &l : g->lanes)
+        if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&l.ev_bulk, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&l.ev_staged, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            ebc_group_destroy(g);
+            return EBC_ECUDA;
+        }
     *out = g;
+    return EBC_OK;
+}
+
+ebc_status ebc_group_set_lanes(ebc_group_t g, int32_t lanes) {
+    if (!g || lanes < 1 || lanes > 4) return EBC_EINVAL;
+    g->nlanes = lanes;
     return EBC_OK;
 }
 
@@ -174,53 +184,75 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
         if (s != EBC_OK) return gfail(g, s, std::string("ebc_group_greedy: ") + ebc_last_error(hs[i]));
     }
     if (shared.empty()) return EBC_OK;
-    // most rounds first: the handles running in round r are a prefix
+    // most rounds first; dealt round-robin to the lanes, so in every lane the
+    // handles running in round r are a prefix
     std::stable_sort(shared.begin(), shared.end(), [&](int a, int b) { return k[a] > k[b]; });
     const int ni = (int)shared.size();
-    std::vector<int> nch(ni), vpc(ni), RB(ni);
-    std::vector<int64_t> first_unit(ni + 1, 0);
-    for (int e = 0; e < ni; ++e) {
-        const ebc::Ctx &c = hs[shared[e]]->c;
-        const int n_vtiles = (int)(c.tc.n_pad / 256);
-        const int n_ctiles = (int)((c.n + 255) / 256);
-        const int max_ch = (int)std::max<int64_t>(1, std::min<int64_t>(c.partial_cap / c.n, n_vtiles));
-        int want = std::min(max_ch, std::max(1, (n_vtiles + kTilesPerUnit - 1) / kTilesPerUnit));
-        vpc[e] = (n_vtiles + want - 1) / want;
-        nch[e] = (n_vtiles + vpc[e] - 1) / vpc[e];
-        RB[e] = ebc::tc_group_row_bytes(c);
-        first_unit[e + 1] = first_unit[e] + (int64_t)n_ctiles * nch[e];
+    const int L = std::min(g->nlanes, ni);
+    while ((int)g->ev_inst.size() < ni) {
+        cudaEvent_t ev = nullptr;
+        GK(g, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        g->ev_inst.push_back(ev);
     }
-    const int64_t nu = first_unit[ni];
-    if (nu > INT32_MAX / 2) return gfail(g, EBC_EINVAL, "ebc_group_greedy: too many work units");
-    ebc_status s = ensure_tables(g, ni, nu);
-    if (s != EBC_OK) return s;
-    // unit table: handles in order of rounds, within equal rounds largest units first
-    {
+    struct LanePlan {
+        std::vector<int> members;  // indices into `shared`, rounds descending
+        std::vector<int> nch, vpc, RB;
+        std::vector<int64_t> first_unit;
+    };
+    std::vector<LanePlan> plan(L);
+    for (int e = 0; e < ni; ++e) plan[e % L].members.push_back(e);
+    for (int li = 0; li < L; ++li) {
+        LanePlan &P = plan[li];
+        GroupLane &lane = g->lanes[li];
+        const int nm = (int)P.members.size();
+        P.nch.resize(nm);
+        P.vpc.resize(nm);
+        P.RB.resize(nm);
+        P.first_unit.assign(nm + 1, 0);
+        for (int x = 0; x < nm; ++x) {
+            const ebc::Ctx &c = hs[shared[P.members[x]]]->c;
+            const int n_vtiles = (int)(c.tc.n_pad / 256);
+            const int n_ctiles = (int)((c.n + 255) / 256);
+            const int max_ch = (int)std::max<int64_t>(1, std::min<int64_t>(c.partial_cap / c.n, n_vtiles));
+            const int want = std::min(max_ch, std::max(1, (n_vtiles + kTilesPerUnit - 1) / kTilesPerUnit));
+            P.vpc[x] = (n_vtiles + want - 1) / want;
+            P.nch[x] = (n_vtiles + P.vpc[x] - 1) / P.vpc[x];
+            P.RB[x] = ebc::tc_group_row_bytes(c);
+            P.first_unit[x + 1] = P.first_unit[x] + (int64_t)n_ctiles * P.nch[x];
+        }
+        const int64_t nu = P.first_unit[nm];
+        if (nu > INT32_MAX / 2) return gfail(g, EBC_EINVAL, "ebc_group_greedy: too many work units");
+        ebc_status s = ensure_tables(g, &lane, nm, nu);
+        if (s != EBC_OK) return s;
+        // unit table: handles in order of rounds, within equal rounds largest units first
         int64_t w = 0;
-        for (int e0 = 0; e0 < ni;) {
-            int e1 = e0;
-            while (e1 < ni && k[shared[e1]] == k[shared[e0]]) ++e1;
+        for (int x0 = 0; x0 < nm;) {
+            int x1 = x0;
+            while (x1 < nm && k[shared[P.members[x1]]] == k[shared[P.members[x0]]]) ++x1;
             const int64_t b = w;
-            for (int e = e0; e < e1; ++e) {
-                const ebc::Ctx &c = hs[shared[e]]->c;
+            for (int x = x0; x < x1; ++x) {
+                const ebc::Ctx &c = hs[shared[P.members[x]]]->c;
                 const int n_vtiles = (int)(c.tc.n_pad / 256);
                 const int n_ctiles = (int)((c.n + 255) / 256);
                 for (int ct = 0; ct < n_ctiles; ++ct)
-                    for (int ch = 0; ch < nch[e]; ++ch) {
-                        const int vt0 = ch * vpc[e];
-                        g->h_units[w++] = {e, ct, ch, std::min(vt0 + vpc[e], n_vtiles) - vt0};
+                    for (int ch = 0; ch < P.nch[x]; ++ch) {
+                        const int vt0 = ch * P.vpc[x];
+                        lane.h_units[w++] = {x, ct, ch, std::min(vt0 + P.vpc[x], n_vtiles) - vt0};
                     }
             }
-            std::stable_sort(g->h_units + b, g->h_units + w,
-                             [](const ebc::GroupUnit &x, const ebc::GroupUnit &y) { return x.ntiles > y.ntiles; });
-            e0 = e1;
+            std::stable_sort(lane.h_units + b, lane.h_units + w,
+                             [](const ebc::GroupUnit &a, const ebc::GroupUnit &c) { return a.ntiles > c.ntiles; });
+            x0 = x1;
         }
+        for (int x = 0; x < nm; ++x)
+            ebc::group_inst_fill(hs[shared[P.members[x]]]->c, P.nch[x], P.vpc[x], &lane.h_inst[x]);
+        GK(g, cudaMemcpyAsync(lane.d_inst, lane.h_inst, sizeof(ebc::GroupInst) * nm, cudaMemcpyHostToDevice,
+                              lane.stream));
+        GK(g, cudaMemcpyAsync(lane.d_units, lane.h_units, sizeof(ebc::GroupUnit) * nu, cudaMemcpyHostToDevice,
+                              lane.stream));
+        GK(g, cudaEventRecord(lane.ev_staged, lane.stream));
+        lane.staged_pending = true;
     }
-    for (int e = 0; e < ni; ++e) ebc::group_inst_fill(hs[shared[e]]->c, nch[e], vpc[e], &g->h_inst[e]);
-    GK(g, cudaMemcpyAsync(g->d_inst, g->h_inst, sizeof(ebc::GroupInst) * ni, cudaMemcpyHostToDevice, g->stream));
-    GK(g, cudaMemcpyAsync(g->d_units, g->h_units, sizeof(ebc::GroupUnit) * nu, cudaMemcpyHostToDevice, g->stream));
-    GK(g, cudaEventRecord(g->ev_staged, g->stream));
-    g->staged_pending = true;
 
     // output bases: the commit kernel writes out[round since reset]
     std::vector<int32_t *> ib(ni);
@@ -231,40 +263,49 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
         fb[e] = out_f[shared[e]] - h->nsel;
     }
     const int kmax = k[shared[0]];
-    int active = ni;
+    std::vector<int> active(L);
+    for (int li = 0; li < L; ++li) active[li] = (int)plan[li].members.size();
     for (int r = 0; r < kmax; ++r) {
-        while (active > 0 && k[shared[active - 1]] <= r) --active;
-        int RBmax = 0;
-        for (int e = 0; e < active; ++e) RBmax = std::max(RBmax, RB[e]);
-        for (int e = 0; e < active; ++e) {
-            ebc_t h = hs[shared[e]];
-            CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(h->c, true); }));
-            GK(g, cudaEventRecord(g->ev_inst[e], h->c.stream));
-            GK(g, cudaStreamWaitEvent(g->stream, g->ev_inst[e], 0));
+        for (int li = 0; li < L; ++li) {
+            LanePlan &P = plan[li];
+            GroupLane &lane = g->lanes[li];
+            int &na = active[li];
+            while (na > 0 && k[shared[P.members[na - 1]]] <= r) --na;
+            if (na == 0) continue;
+            int RBmax = 0;
+            for (int x = 0; x < na; ++x) RBmax = std::max(RBmax, P.RB[x]);
+            for (int x = 0; x < na; ++x) {
+                const int e = P.members[x];
+                ebc_t h = hs[shared[e]];
+                CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(h->c, true); }));
+                GK(g, cudaEventRecord(g->ev_inst[e], h->c.stream));
+                GK(g, cudaStreamWaitEvent(lane.stream, g->ev_inst[e], 0));
+            }
+            GK(g, cudaMemsetAsync(lane.d_words, 0, 2 * sizeof(int), lane.stream));
+            GK(g, ebc::launch_gains_tc_group(lane.d_inst, lane.d_units, (int)P.first_unit[na], lane.d_words,
+                                             lane.d_words + 1, RBmax, g->num_sms, lane.stream));
+            GK(g, ebc::launch_group_err(lane.d_inst, na, lane.d_words + 1, lane.stream));
+            GK(g, cudaEventRecord(lane.ev_bulk, lane.stream));
+            g->launches += 1;
+            g->units += P.first_unit[na];
+            for (int x = 0; x < na; ++x) {
+                const int e = P.members[x];
+                ebc_t h = hs[shared[e]];
+                ebc::Ctx &c = h->c;
+                GK(g, cudaStreamWaitEvent(c.stream, lane.ev_bulk, 0));
+                h->prof.p.bulk_launches += 1;
+                h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
+                const int nchunks = P.nch[x];
+                CK(h, launch(h, -1, 1, [&] {
+                       return ebc::launch_reduce_select(c, c.n, nchunks, nullptr, true, nullptr, h->nblk);
+                   }));
+                ebc_status s = ebc::round_certify(h, ib[e], fb[e], false);
+                if (s != EBC_OK) return gfail(g, s, std::string("ebc_group_greedy: ") + ebc_last_error(h));
+                h->nsel += 1;
+                h->attrs_ready = true;
+            }
         }
-        GK(g, cudaMemsetAsync(g->d_words, 0, 2 * sizeof(int), g->stream));
-        GK(g, ebc::launch_gains_tc_group(g->d_inst, g->d_units, (int)first_unit[active], g->d_words, g->d_words + 1,
-                                         RBmax, g->num_sms, g->stream));
-        GK(g, ebc::launch_group_err(g->d_inst, active, g->d_words + 1, g->stream));
-        GK(g, cudaEventRecord(g->ev_bulk, g->stream));
-        g->launches += 1;
-        g->units += first_unit[active];
         g->rounds += 1;
-        for (int e = 0; e < active; ++e) {
-            ebc_t h = hs[shared[e]];
-            ebc::Ctx &c = h->c;
-            GK(g, cudaStreamWaitEvent(c.stream, g->ev_bulk, 0));
-            h->prof.p.bulk_launches += 1;
-            h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
-            const int nchunks = nch[e];
-            CK(h, launch(h, -1, 1, [&] {
-                   return ebc::launch_reduce_select(c, c.n, nchunks, nullptr, true, nullptr, h->nblk);
-               }));
-            s = ebc::round_certify(h, ib[e], fb[e], false);
-            if (s != EBC_OK) return gfail(g, s, std::string("ebc_group_greedy: ") + ebc_last_error(h));
-            h->nsel += 1;
-            h->attrs_ready = true;
-        }
     }
     return EBC_OK;
 }
@@ -281,19 +322,21 @@ const char *ebc_group_last_error(ebc_group_t g) { return g ? g->err.c_str() : ""
 
 ebc_status ebc_group_destroy(ebc_group_t g) {
     if (!g) return EBC_OK;
-    if (g->stream) cudaStreamSynchronize(g->stream);
-    ebc::pool_free(g->d_inst, g->stream);
-    ebc::pool_free(g->d_units, g->stream);
-    ebc::pool_free(g->d_words, g->stream);
-    if (g->stream) {
-        cudaStreamSynchronize(g->stream);
-        cudaStreamDestroy(g->stream);
+    for (GroupLane &l : g->lanes) {
+        if (l.stream) cudaStreamSynchronize(l.stream);
+        ebc::pool_free(l.d_inst, l.stream);
+        ebc::pool_free(l.d_units, l.stream);
+        ebc::pool_free(l.d_words, l.stream);
+        if (l.stream) {
+            cudaStreamSynchronize(l.stream);
+            cudaStreamDestroy(l.stream);
+        }
+        if (l.h_inst) cudaFreeHost(l.h_inst);
+        if (l.h_units) cudaFreeHost(l.h_units);
+        if (l.ev_bulk) cudaEventDestroy(l.ev_bulk);
+        if (l.ev_staged) cudaEventDestroy(l.ev_staged);
     }
-    if (g->h_inst) cudaFreeHost(g->h_inst);
-    if (g->h_units) cudaFreeHost(g->h_units);
     for (cudaEvent_t ev : g->ev_inst) cudaEventDestroy(ev);
-    if (g->ev_bulk) cudaEventDestroy(g->ev_bulk);
-    if (g->ev_staged) cudaEventDestroy(g->ev_staged);
     delete g;
     return EBC_OK;
 }

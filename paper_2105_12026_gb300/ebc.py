@@ -116,6 +116,7 @@ _SIGS = {
     "ebc_group_create": [ctypes.POINTER(_P)],
     "ebc_group_greedy": [_P, _P, _I32, _P, _P, _P],
     "ebc_group_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+    "ebc_group_set_lanes": [_P, _I32],
     "ebc_group_last_error": [_P],
     "ebc_group_destroy": [_P],
     "ebc_batch_create": [_I32, _I64, _I32, ctypes.POINTER(_P)],
@@ -687,12 +688,13 @@ class Group:
     """Greedy on many instances with one persistent bulk launch per round
     (include/ebc.h, ebc_group_*)."""
 
-    def __init__(self):
+    def __init__(self, lanes: int = 2):
         h = _P()
         rc = load().ebc_group_create(ctypes.byref(h))
         if rc != EBC_OK:
             raise EbcError(rc, "ebc_group_create")
         self.h = h.value
+        self._err(load().ebc_group_set_lanes(_P(self.h), int(lanes)))
 
     def _err(self, rc):
         if rc != EBC_OK:

@@ -47,7 +47,7 @@ def test_group_equals_alone_64(torch):
     specs = _mix(64, seed=3)
     precs = ["bf16" if i % 5 else "fp16" for i in range(len(specs))]
     insts = _instances(torch, specs, precs)
-    with ebc.Group() as g:
+    with ebc.Group(lanes=1) as g:
         got = g.greedy_host(insts, [k for _, k in specs])
         st = g.stats()
     for inst in insts:
@@ -81,7 +81,7 @@ def test_group_mixed_paths_and_continuation(torch):
     insts = _instances(torch, specs, precs, lazy)
     k1 = [max(1, k // 2) for _, k in specs]
     k2 = [k - a for (_, k), a in zip(specs, k1)]
-    with ebc.Group() as g:
+    with ebc.Group(lanes=3) as g:
         first = g.greedy_host(insts, k1)
         second = g.greedy_host(insts, k2)
     for inst in insts:
