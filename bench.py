@@ -307,7 +307,7 @@ def run_mix_resident(args):
              for V in Vs]
     outs = [(torch.empty(k, dtype=torch.int32, device=dev), torch.empty(k, dtype=torch.float64, device=dev))
             for k in ks]
-    group = ebc.Group(lanes=args.group_lanes)
+    group = ebc.Group(lanes=args.group_lanes, by_row_width=args.group_by_width)
 
     def one_step():
         for inst, V in zip(insts, Vs):
@@ -326,6 +326,8 @@ def run_mix_resident(args):
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
+    group.profiling(True)  # event pairs around the shared launches only
+    group.reset_profile()
     clocks = ClockSampler(local)
     clocks.start()
     times = []
@@ -340,6 +342,7 @@ def run_mix_resident(args):
     clk = clocks.stop()
     picks = [r[0].cpu().numpy().tolist() for r in res[:4]]
     gst = group.stats()
+    gprof = group.profile()
     group.close()
     for inst in insts:
         inst.close()
@@ -360,7 +363,11 @@ def run_mix_resident(args):
                                  "V from pinned host memory into its resident handle (ebc_reload: prologue and "
                                  "quantisation included) and runs all its Greedy rounds",
                        "h2d_bytes_per_step": h2d, "host_generation_s": gen_s},
-            "group_stats": gst if args.mix_mode == "group" else None, "first_picks": picks, "clocks": clk}
+            "group_stats": gst if args.mix_mode == "group" else None,
+            "shared_launches": ({"ms_per_step": gprof["launch_ms"] / args.steps,
+                                 "pairs_per_s": gprof["pairs"] / (gprof["launch_ms"] * 1e-3)}
+                                if args.mix_mode == "group" and gprof["launch_ms"] > 0 else None),
+            "first_picks": picks, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -852,7 +859,8 @@ def main():
     ap.add_argument("--mix-mode", default="group", choices=["group", "streams", "batch"],
                     help="mix: one shared bulk launch per round (group), per-instance rounds on own streams "
                          "(streams) or the batch runtime (batch)")
-    ap.add_argument("--group-lanes", type=int, default=2, help="mix: lanes of the shared-launch group")
+    ap.add_argument("--group-lanes", type=int, default=1, help="mix: lanes of the shared-launch group")
+    ap.add_argument("--group-by-width", action="store_true", help="mix: group lanes by row width")
     ap.add_argument("--slots", type=int, default=32, help="mix/serve: concurrent instances")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="mix/serve: device-memory budget")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")

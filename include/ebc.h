@@ -491,11 +491,22 @@ ebc_status ebc_group_create(ebc_group_t *out);
 ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *h, int32_t count, const int32_t *k, int32_t *const *out_idx,
                             double *const *out_f);
 
-/* Lanes (1 to 4, default 2): the handles of a call are dealt round-robin to
+/* Lanes (1 to 4, default 1): the handles of a call are dealt round-robin to
  * this many lanes, each with its own stream and shared launch per round, so
  * the per-handle picks of one lane overlap the shared launch of another.
- * Results do not depend on it.  EINVAL outside [1, 4]. */
+ * ebc_group_set_lanes_by_row_width(g, 1) instead uses two lanes by row width
+ * (d <= 64 and 64 < d <= 128), each launch laid out for its own rows.
+ * Results do not depend on either.  EINVAL outside [1, 4]. */
 ebc_status ebc_group_set_lanes(ebc_group_t g, int32_t lanes);
+ebc_status ebc_group_set_lanes_by_row_width(ebc_group_t g, int32_t on);
+
+/* Time every shared launch with CUDA events on its lane's stream (on = 1);
+ * ebc_group_profile waits for the timed launches and returns their summed
+ * device time and the (candidate, point) pairs they evaluated;
+ * ebc_group_reset_profile zeroes both. */
+ebc_status ebc_group_set_profiling(ebc_group_t g, int32_t on);
+ebc_status ebc_group_profile(ebc_group_t g, double *launch_ms, int64_t *pairs);
+ebc_status ebc_group_reset_profile(ebc_group_t g);
 
 /* Shared launches issued, work units they processed and rounds, summed over
  * the group's calls (any pointer may be NULL). */

@@ -45,10 +45,16 @@ struct GroupLane {
 struct ebc_group_ctx {
     int device = 0;
     int num_sms = 152;
-    int nlanes = 2;
+    int nlanes = 1;
+    bool by_row_width = false;  // lanes by row width (d <= 64 / d <= 128) instead of round-robin
     GroupLane lanes[4];
     std::vector<cudaEvent_t> ev_inst;  // per handle: its point extension is ready
     int64_t launches = 0, units = 0, rounds = 0;
+    // shared-launch timing (ebc_group_set_profiling): event pairs not yet folded
+    bool prof = false;
+    double launch_ms = 0.0;
+    int64_t launch_evals = 0;  // (candidate, point) pairs of the timed launches
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending, spare;
     std::string err;
 };
 
@@ -184,11 +190,12 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
         if (s != EBC_OK) return gfail(g, s, std::string("ebc_group_greedy: ") + ebc_last_error(hs[i]));
     }
     if (shared.empty()) return EBC_OK;
-    // most rounds first; dealt round-robin to the lanes, so in every lane the
-    // handles running in round r are a prefix
+    // most rounds first; dealt to the lanes in that order, so in every lane
+    // the handles running in round r are a prefix
     std::stable_sort(shared.begin(), shared.end(), [&](int a, int b) { return k[a] > k[b]; });
     const int ni = (int)shared.size();
-    const int L = std::min(g->nlanes, ni);
+    int L = std::min(g->nlanes, ni);
+    if (g->by_row_width) L = 2;
     while ((int)g->ev_inst.size() < ni) {
         cudaEvent_t ev = nullptr;
         GK(g, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -200,11 +207,15 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
         std::vector<int64_t> first_unit;
     };
     std::vector<LanePlan> plan(L);
-    for (int e = 0; e < ni; ++e) plan[e % L].members.push_back(e);
+    for (int e = 0; e < ni; ++e) {
+        const int lane = g->by_row_width ? (ebc::tc_group_row_bytes(hs[shared[e]]->c) > 128 ? 0 : 1) : e % L;
+        plan[lane].members.push_back(e);
+    }
     for (int li = 0; li < L; ++li) {
         LanePlan &P = plan[li];
         GroupLane &lane = g->lanes[li];
         const int nm = (int)P.members.size();
+        if (nm == 0) continue;
         P.nch.resize(nm);
         P.vpc.resize(nm);
         P.RB.resize(nm);
@@ -269,6 +280,7 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
         for (int li = 0; li < L; ++li) {
             LanePlan &P = plan[li];
             GroupLane &lane = g->lanes[li];
+            if (P.members.empty()) continue;
             int &na = active[li];
             while (na > 0 && k[shared[P.members[na - 1]]] <= r) --na;
             if (na == 0) continue;
@@ -282,8 +294,27 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
                 GK(g, cudaStreamWaitEvent(lane.stream, g->ev_inst[e], 0));
             }
             GK(g, cudaMemsetAsync(lane.d_words, 0, 2 * sizeof(int), lane.stream));
+            std::pair<cudaEvent_t, cudaEvent_t> evp{nullptr, nullptr};
+            if (g->prof) {
+                if (!g->spare.empty()) {
+                    evp = g->spare.back();
+                    g->spare.pop_back();
+                } else {
+                    GK(g, cudaEventCreate(&evp.first));
+                    GK(g, cudaEventCreate(&evp.second));
+                }
+                GK(g, cudaEventRecord(evp.first, lane.stream));
+            }
             GK(g, ebc::launch_gains_tc_group(lane.d_inst, lane.d_units, (int)P.first_unit[na], lane.d_words,
                                              lane.d_words + 1, RBmax, g->num_sms, lane.stream));
+            if (g->prof) {
+                GK(g, cudaEventRecord(evp.second, lane.stream));
+                g->pending.push_back(evp);
+                for (int x = 0; x < na; ++x) {
+                    const ebc::Ctx &c = hs[shared[P.members[x]]]->c;
+                    g->launch_evals += c.n * c.n;
+                }
+            }
             GK(g, ebc::launch_group_err(lane.d_inst, na, lane.d_words + 1, lane.stream));
             GK(g, cudaEventRecord(lane.ev_bulk, lane.stream));
             g->launches += 1;
@@ -318,6 +349,42 @@ ebc_status ebc_group_stats(ebc_group_t g, int64_t *launches, int64_t *units, int
     return EBC_OK;
 }
 
+ebc_status ebc_group_set_profiling(ebc_group_t g, int32_t on) {
+    if (!g) return EBC_EINVAL;
+    g->prof = on != 0;
+    return EBC_OK;
+}
+
+ebc_status ebc_group_set_lanes_by_row_width(ebc_group_t g, int32_t on) {
+    if (!g) return EBC_EINVAL;
+    g->by_row_width = on != 0;
+    return EBC_OK;
+}
+
+ebc_status ebc_group_profile(ebc_group_t g, double *launch_ms, int64_t *pairs) {
+    if (!g) return EBC_EINVAL;
+    for (auto &p : g->pending) {
+        if (cudaEventSynchronize(p.second) != cudaSuccess) return gcuda(g, cudaGetLastError(), "ebc_group_profile");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.first, p.second);
+        g->launch_ms += ms;
+        g->spare.push_back(p);
+    }
+    g->pending.clear();
+    if (launch_ms) *launch_ms = g->launch_ms;
+    if (pairs) *pairs = g->launch_evals;
+    return EBC_OK;
+}
+
+ebc_status ebc_group_reset_profile(ebc_group_t g) {
+    if (!g) return EBC_EINVAL;
+    double ms = 0.0;
+    ebc_status s = ebc_group_profile(g, &ms, nullptr);
+    g->launch_ms = 0.0;
+    g->launch_evals = 0;
+    return s;
+}
+
 const char *ebc_group_last_error(ebc_group_t g) { return g ? g->err.c_str() : ""; }
 
 ebc_status ebc_group_destroy(ebc_group_t g) {
@@ -337,6 +404,11 @@ ebc_status ebc_group_destroy(ebc_group_t g) {
         if (l.ev_staged) cudaEventDestroy(l.ev_staged);
     }
     for (cudaEvent_t ev : g->ev_inst) cudaEventDestroy(ev);
+    for (auto *v : {&g->pending, &g->spare})
+        for (auto &p : *v) {
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
     delete g;
     return EBC_OK;
 }

@@ -117,6 +117,10 @@ _SIGS = {
     "ebc_group_greedy": [_P, _P, _I32, _P, _P, _P],
     "ebc_group_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "ebc_group_set_lanes": [_P, _I32],
+    "ebc_group_set_lanes_by_row_width": [_P, _I32],
+    "ebc_group_set_profiling": [_P, _I32],
+    "ebc_group_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
+    "ebc_group_reset_profile": [_P],
     "ebc_group_last_error": [_P],
     "ebc_group_destroy": [_P],
     "ebc_batch_create": [_I32, _I64, _I32, ctypes.POINTER(_P)],
@@ -688,13 +692,25 @@ class Group:
     """Greedy on many instances with one persistent bulk launch per round
     (include/ebc.h, ebc_group_*)."""
 
-    def __init__(self, lanes: int = 2):
+    def __init__(self, lanes: int = 1, by_row_width: bool = False):
         h = _P()
         rc = load().ebc_group_create(ctypes.byref(h))
         if rc != EBC_OK:
             raise EbcError(rc, "ebc_group_create")
         self.h = h.value
         self._err(load().ebc_group_set_lanes(_P(self.h), int(lanes)))
+        self._err(load().ebc_group_set_lanes_by_row_width(_P(self.h), int(bool(by_row_width))))
+
+    def profiling(self, on: bool = True):
+        self._err(load().ebc_group_set_profiling(_P(self.h), int(bool(on))))
+
+    def profile(self) -> dict:
+        ms, pairs = ctypes.c_double(), _I64()
+        self._err(load().ebc_group_profile(_P(self.h), ctypes.byref(ms), ctypes.byref(pairs)))
+        return {"launch_ms": ms.value, "pairs": pairs.value}
+
+    def reset_profile(self):
+        self._err(load().ebc_group_reset_profile(_P(self.h)))
 
     def _err(self, rc):
         if rc != EBC_OK:
