@@ -365,6 +365,7 @@ def run_mix_resident(args):
                        "h2d_bytes_per_step": h2d, "host_generation_s": gen_s},
             "group_stats": gst if args.mix_mode == "group" else None,
             "shared_launches": ({"ms_per_step": gprof["launch_ms"] / args.steps,
+                                 "gap_ms_per_step": gprof["gap_ms"] / args.steps,
                                  "pairs_per_s": gprof["pairs"] / (gprof["launch_ms"] * 1e-3)}
                                 if args.mix_mode == "group" and gprof["launch_ms"] > 0 else None),
             "first_picks": picks, "clocks": clk}

@@ -502,10 +502,13 @@ ebc_status ebc_group_set_lanes_by_row_width(ebc_group_t g, int32_t on);
 
 /* Time every shared launch with CUDA events on its lane's stream (on = 1);
  * ebc_group_profile waits for the timed launches and returns their summed
- * device time and the (candidate, point) pairs they evaluated;
- * ebc_group_reset_profile zeroes both. */
+ * device time, the summed time from the end of one timed launch to the start
+ * of the next (in issue order: with one lane, the time the shared launches
+ * wait for the per-handle picks and preparations) and the (candidate, point)
+ * pairs they evaluated; ebc_group_reset_profile zeroes all three.  Any
+ * output may be NULL. */
 ebc_status ebc_group_set_profiling(ebc_group_t g, int32_t on);
-ebc_status ebc_group_profile(ebc_group_t g, double *launch_ms, int64_t *pairs);
+ebc_status ebc_group_profile(ebc_group_t g, double *launch_ms, double *gap_ms, int64_t *pairs);
 ebc_status ebc_group_reset_profile(ebc_group_t g);
 
 /* Shared launches issued, work units they processed and rounds, summed over

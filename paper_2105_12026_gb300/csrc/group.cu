@@ -53,6 +53,8 @@ struct ebc_group_ctx {
     // shared-launch timing (ebc_group_set_profiling): event pairs not yet folded
     bool prof = false;
     double launch_ms = 0.0;
+    double gap_ms = 0.0;  // from the end of one shared launch to the start of the next (lane 0)
+    cudaEvent_t last_end = nullptr;
     int64_t launch_evals = 0;  // (candidate, point) pairs of the timed launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending, spare;
     std::string err;
@@ -361,17 +363,25 @@ ebc_status ebc_group_set_lanes_by_row_width(ebc_group_t g, int32_t on) {
     return EBC_OK;
 }
 
-ebc_status ebc_group_profile(ebc_group_t g, double *launch_ms, int64_t *pairs) {
+ebc_status ebc_group_profile(ebc_group_t g, double *launch_ms, double *gap_ms, int64_t *pairs) {
     if (!g) return EBC_EINVAL;
     for (auto &p : g->pending) {
         if (cudaEventSynchronize(p.second) != cudaSuccess) return gcuda(g, cudaGetLastError(), "ebc_group_profile");
         float ms = 0.f;
         cudaEventElapsedTime(&ms, p.first, p.second);
         g->launch_ms += ms;
-        g->spare.push_back(p);
+        if (g->last_end) {
+            float gms = 0.f;
+            if (cudaEventElapsedTime(&gms, g->last_end, p.first) == cudaSuccess && gms >= 0.f) g->gap_ms += gms;
+            cudaGetLastError();
+        }
+        g->last_end = p.second;
     }
+    for (auto &p : g->pending) g->spare.push_back(p);
     g->pending.clear();
+    g->last_end = nullptr;
     if (launch_ms) *launch_ms = g->launch_ms;
+    if (gap_ms) *gap_ms = g->gap_ms;
     if (pairs) *pairs = g->launch_evals;
     return EBC_OK;
 }
@@ -379,8 +389,9 @@ ebc_status ebc_group_profile(ebc_group_t g, double *launch_ms, int64_t *pairs) {
 ebc_status ebc_group_reset_profile(ebc_group_t g) {
     if (!g) return EBC_EINVAL;
     double ms = 0.0;
-    ebc_status s = ebc_group_profile(g, &ms, nullptr);
+    ebc_status s = ebc_group_profile(g, &ms, nullptr, nullptr);
     g->launch_ms = 0.0;
+    g->gap_ms = 0.0;
     g->launch_evals = 0;
     return s;
 }

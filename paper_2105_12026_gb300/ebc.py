@@ -119,7 +119,8 @@ _SIGS = {
     "ebc_group_set_lanes": [_P, _I32],
     "ebc_group_set_lanes_by_row_width": [_P, _I32],
     "ebc_group_set_profiling": [_P, _I32],
-    "ebc_group_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
+    "ebc_group_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(_I64)],
     "ebc_group_reset_profile": [_P],
     "ebc_group_last_error": [_P],
     "ebc_group_destroy": [_P],
@@ -705,9 +706,9 @@ class Group:
         self._err(load().ebc_group_set_profiling(_P(self.h), int(bool(on))))
 
     def profile(self) -> dict:
-        ms, pairs = ctypes.c_double(), _I64()
-        self._err(load().ebc_group_profile(_P(self.h), ctypes.byref(ms), ctypes.byref(pairs)))
-        return {"launch_ms": ms.value, "pairs": pairs.value}
+        ms, gap, pairs = ctypes.c_double(), ctypes.c_double(), _I64()
+        self._err(load().ebc_group_profile(_P(self.h), ctypes.byref(ms), ctypes.byref(gap), ctypes.byref(pairs)))
+        return {"launch_ms": ms.value, "gap_ms": gap.value, "pairs": pairs.value}
 
     def reset_profile(self):
         self._err(load().ebc_group_reset_profile(_P(self.h)))
