@@ -847,6 +847,10 @@ def run_case_study(args):
 
 
 def main():
+    if any(w in sys.argv for w in ("mix", "serve")):
+        # many instance streams: give them their own hardware queues (read at
+        # the first CUDA call, which has not happened yet)
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
