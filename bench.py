@@ -542,13 +542,15 @@ def run_sets(args):
             "roofline": {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
                          "frac": achieved / peak if achieved else None, "traffic": None,
                          "peak_source": f"{pk['source']} bf16 burst",
-                         "kernel": "multi-set evaluation (member gather + tcgen05 sets kernel + finalize)",
+                         "kernel": "multi-set evaluation (device plan + tcgen05 sets kernel with in-kernel member "
+                                   "gather + finalize)",
                          "avg_ms": kern_ms, "algorithmic_flops_per_launch": flops},
             "gpu_launches": prof_tc["launches"], "clocks": clk,
             "fp32_plain": {"value": evals / (ms_32 / 1e3), "unit": UNIT, "ms_per_step": ms_32,
                            "tc_over_fp32": ms_32 / ms_tc},
             "raw_rel_err_vs_oracle": {"tc_max": float(rel_tc.max()), "tc_median": float(np.median(rel_tc)),
-                                      "fp32_max": float(rel_32.max()), "sets_checked": int(pick.size)},
+                                      "fp32_max": float(rel_32.max()), "sets_checked": int(pick.size),
+                                      "tc_per_set": {str(int(j)): float(r) for j, r in zip(pick, rel_tc)}},
             "e2e": {"value": evals * args.steps / sum(e2e), "unit": UNIT,
                     "h2d_bytes_per_step": int(idx.nbytes + off.nbytes), "d2h_bytes_per_step": int(l * 8)},
             "cpu_baseline": {"value": n * int(sub_off[-1]) / cpu_s, "unit": UNIT, "cores": oracle.num_threads(),

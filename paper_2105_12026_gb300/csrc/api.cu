@@ -190,7 +190,7 @@ int64_t ebc::handle_bytes(int64_t n, int32_t d, ebc_prec prec) {
     b += 2 * cap * 8 + 3 * pool * nref * 8 + pool * 12 + 2 * ebc::kMaxRefineK * 8;
     if (prec == EBC_BF16 || prec == EBC_FP16 || prec == EBC_FP8E4M3) {
         const int64_t n_pad = (n + 255) / 256 * 256, DP = (d + 63) / 64 * 64;
-        b += 3 * n_pad * DP * 2 + 4 * n_pad * 16 * 2 + n_pad * (8 + 4 + 4);
+        b += 3 * n_pad * DP * 2 + 5 * n_pad * 16 * 2 + n_pad * (8 + 4 + 4);
     }
     if (prec == EBC_FP8E4M3) {  // FP8 operands, extensions, scales, norms; lazy bounds and list
         const int64_t n_pad = (n + 255) / 256 * 256, DP8 = (d + 127) / 128 * 128;
@@ -866,8 +866,19 @@ ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off
     if (l < 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: l < 0");
     if (l == 0) return EBC_OK;
     if (!csr_off || !out_f) return fail(h, EBC_EINVAL, "ebc_eval_sets: NULL argument");
+    if (c.prec != EBC_FP32 && ebc::tc_sets_device_planned(c)) {
+        // tensor-core path planned on the device: asynchronous, no host read
+        const int64_t rows = c.tc.n_pad / 256 * 8;  // (point unit, epilogue warp)
+        ebc_status s = ensure_set_part(h, rows * std::min<int64_t>(l, std::max<int64_t>(128, ((int64_t)1 << 24) / rows)));
+        if (s) return s;
+        int64_t nl = 0;
+        CK(h, launch(h, PK_EVAL, 0, [&] { return ebc::launch_eval_sets_tc_dev(c, csr_idx, csr_off, l, out_f, &nl); }));
+        h->prof.p.launches += nl;
+        h->prof.p.eval_launches += nl;
+        return EBC_OK;
+    }
     if (c.prec != EBC_FP32) {
-        // tensor-core path: the tile plan needs the offsets on the host
+        // K-blocked rows (d > 128): the tile plan is made on the host from the offsets
         std::vector<int64_t> off((size_t)l + 1);
         CK(h, cudaMemcpyAsync(off.data(), csr_off, sizeof(int64_t) * (l + 1), cudaMemcpyDeviceToHost, c.stream));
         CK(h, cudaStreamSynchronize(c.stream));

@@ -156,6 +156,13 @@ struct Ctx {
         CUtensorMap tmBx;         // point extension over Bext (box 16 x 256)
         // multi-set evaluation (ebc_eval_sets at a tensor-core precision)
         uint16_t *Px = nullptr;   // [n_pad, 16] point-side extension: ||v||^2 - ||v_hat||^2 (static)
+        uint16_t *Sx = nullptr;   // [n_pad + 1, 16] member-side extension of every point: -||v_hat||^2
+                                  // (static); row n_pad: the padding column's (-1e30)
+        int64_t *sp_beg = nullptr;    // device plan of a multi-set batch: padded start column of each
+        int *sp_set = nullptr;        //   non-empty set ([lb + 1]), its index ([lb]),
+        int *sp_chunk = nullptr;      //   the first compacted set of each chunk ([lb + 1]),
+        int *sp_cnt = nullptr;        //   [0] chunks, [1] non-empty sets, [2] bad offsets
+        int64_t sp_cap = 0;           // sets per batch the plan buffers hold
         CUtensorMap tmPx;         // box 16 x 128 over Px
         uint16_t *Mq = nullptr;   // [mcap, DP] 2 s_hat of the gathered set members, padded per set
         uint16_t *Mx = nullptr;   // [mcap, 16] member extension: -||s_hat||^2
@@ -325,6 +332,11 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
 cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_dev, const int64_t *off_host,
                                 int64_t l, double *out_f, int64_t *nlaunch);
 void tc_free(Ctx &c);
+// multi-set evaluation planned on the device (whole rows resident, d <= 128):
+// asynchronous, no host read; set_part must hold at least 8 * n_pad / 256 rows
+bool tc_sets_device_planned(const Ctx &c);
+cudaError_t launch_eval_sets_tc_dev(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,
+                                    int64_t *nlaunch);
 
 // ---- one persistent bulk launch over several handles (k_tc.cu, group.cu) ----
 // A handle's part of a shared Greedy round: its tensor maps (read by TMA from

@@ -173,3 +173,71 @@ def test_sets_tc_multiset_workload_sampled(torch):
     assert (err <= bound).all()
     np.testing.assert_allclose(f32[pick], ref, rtol=1e-5)
     print("C1 sample: max rel err bf16", (err / ref).max(), "fp32", (np.abs(f32[pick] - ref) / ref).max())
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_sets_tc_device_plan_async_and_capturable(torch, prec):
+    """At d <= 128 the set plan is made on the device: the call reads nothing
+    back to the host, so it can be captured in a CUDA graph; the replay gives
+    the same values as the direct call, which equal the K-blocked kernel's
+    (planned on the host) bitwise, and cover empty sets, sets spanning many
+    tiles and several chunks."""
+    rng = np.random.default_rng(21)
+    n, d = 20_000, 48
+    V = synth.zscore_to_f32(rng.standard_normal((n, d)))
+    sizes = rng.integers(0, 70, size=600)
+    sizes[::37] = 0                    # empty sets, some in runs
+    sizes[5] = 1500                    # a set spanning six tiles
+    sizes[6:9] = 0
+    off = np.zeros(sizes.size + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    idx = rng.integers(0, n, size=int(off[-1])).astype(np.int32)
+    l = sizes.size
+    s = torch.cuda.Stream()
+    with ebc.Instance(V, precision=prec, stream=s) as inst:
+        idx_d, off_d = torch.from_numpy(idx).cuda(), torch.from_numpy(off).cuda()
+        out = torch.zeros(l, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        ebc.ebc_eval_sets(inst.h, idx_d.data_ptr(), off_d.data_ptr(), l, out.data_ptr())  # set-up outside capture
+        inst.sync()
+        direct = out.cpu().numpy().copy()
+        out.zero_()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ebc.ebc_eval_sets(inst.h, idx_d.data_ptr(), off_d.data_ptr(), l, out.data_ptr())
+        g.replay()
+        s.synchronize()
+        inst.sync()
+        replay = out.cpu().numpy().copy()
+        inst.set_kblocked(True)
+        kb = inst.eval_sets_host(idx, off)
+    np.testing.assert_array_equal(replay, direct)
+    np.testing.assert_array_equal(direct, kb)
+    assert np.all(direct[sizes == 0] == 0.0)
+    ref = oracle.eval_sets(V, idx, off)
+    bound = sets_error_bound(V, idx, off, prec, ref)
+    assert np.all(np.abs(direct - ref) <= bound), np.max(np.abs(direct - ref) - bound)
+
+
+def test_sets_tc_device_plan_errors(torch):
+    V = synth.plain_greedy_small(seed=4)["V"]
+    with ebc.Instance(V, precision="bf16") as inst:
+        out = torch.zeros(2, dtype=torch.float64, device="cuda")
+        idx = torch.tensor([1, 2, 3], dtype=torch.int32, device="cuda")
+        for bad in ([1, 2, 3], [0, 3, 2]):
+            off = torch.tensor(bad, dtype=torch.int64, device="cuda")
+            ebc.ebc_eval_sets(inst.h, idx.data_ptr(), off.data_ptr(), 2, out.data_ptr())
+            with pytest.raises(ebc.EbcError) as ei:
+                inst.sync()
+            assert ei.value.status == ebc.EBC_EINVAL
+        off = torch.tensor([0, 2, 3], dtype=torch.int64, device="cuda")
+        bad_idx = torch.tensor([1, 5000, 3], dtype=torch.int32, device="cuda")
+        ebc.ebc_eval_sets(inst.h, bad_idx.data_ptr(), off.data_ptr(), 2, out.data_ptr())
+        with pytest.raises(ebc.EbcError) as ei:
+            inst.sync()
+        assert ei.value.status == ebc.EBC_EINDEX
+        # a good call afterwards
+        got = inst.eval_sets_host(np.array([1, 2, 3], np.int32), np.array([0, 2, 3], np.int64))
+        ref = oracle.eval_sets(V, np.array([1, 2, 3], np.int32), np.array([0, 2, 3], np.int64))
+        np.testing.assert_allclose(got, ref, rtol=1e-2)
