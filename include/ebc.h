@@ -137,8 +137,14 @@ ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k);
  *   out_f    device double[l]; an empty set gives 0.
  * Independent of the Greedy state.  With EBC_FP32 the distances are direct
  * FP32; with a tensor-core precision the minimum per set is formed from
- * V.S^T products (K-blocked above d = 128).  Out-of-range members are detected on the device: the set
- * is evaluated without them and ebc_sync() returns EINDEX.  l = 0 is OK.
+ * V.S^T products (K-blocked above d = 128).  Asynchronous, with nothing read
+ * back to the host, except at a tensor-core precision with d > 128, where the
+ * tile plan is made on the host from the offsets (the call then waits for
+ * the stream once).  Offsets that do not start at 0 or decrease, or a NULL
+ * csr_idx with members, give EINVAL (from the next ebc_sync(), or from the
+ * call on the host-planned path) and no member is read; out-of-range
+ * members are detected on the device: the set is evaluated without them and
+ * ebc_sync() returns EINDEX.  l = 0 is OK.
  */
 ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off, int64_t l, double *out_f);
 

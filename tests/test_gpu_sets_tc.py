@@ -139,11 +139,12 @@ def test_sets_tc_errors_and_determinism(torch):
             inst.eval_sets(torch.from_numpy(bad), torch.from_numpy(off))
             inst.sync()
         assert ei.value.status == ebc.EBC_EINDEX
-        # decreasing offsets: EINVAL before any launch
+        # decreasing offsets: EINVAL, found by the device plan and returned by the next sync
         off2 = off.copy()
         off2[3], off2[4] = off2[4], off2[3]
         with pytest.raises(ebc.EbcError) as ei:
             inst.eval_sets(torch.from_numpy(idx), torch.from_numpy(off2))
+            inst.sync()
         assert ei.value.status == ebc.EBC_EINVAL
         np.testing.assert_array_equal(inst.eval_sets_host(idx, off), a)
         # the FP32 path on the same handle agrees within the bound
