@@ -137,16 +137,28 @@ ebc_status ebc_set_precision(ebc_t h, ebc_prec prec, int32_t refine_k);
  *   out_f    device double[l]; an empty set gives 0.
  * Independent of the Greedy state.  With EBC_FP32 the distances are direct
  * FP32; with a tensor-core precision the minimum per set is formed from
- * V.S^T products (K-blocked above d = 128).  Asynchronous, with nothing read
- * back to the host, except at a tensor-core precision with d > 128, where the
- * tile plan is made on the host from the offsets (the call then waits for
- * the stream once).  Offsets that do not start at 0 or decrease, or a NULL
- * csr_idx with members, give EINVAL (from the next ebc_sync(), or from the
- * call on the host-planned path) and no member is read; out-of-range
- * members are detected on the device: the set is evaluated without them and
- * ebc_sync() returns EINDEX.  l = 0 is OK.
+ * V.S^T products (K-blocked above d = 128), the members padded per set to
+ * 16-column groups; the plan (padding, chunks, member gather) is made on the
+ * device.  Asynchronous at EBC_FP32; at a tensor-core precision too when a
+ * reservation (ebc_reserve_sets) covers l sets, and then nothing is read back
+ * to the host, so the call can be captured in a CUDA graph; without one the
+ * call first reads csr_off[l] (8 bytes, one wait for the stream) to size its
+ * buffers.  Offsets that do not start at 0 or decrease, a NULL csr_idx with
+ * members, or more members than a reservation holds give EINVAL from the
+ * next ebc_sync() and no member is read; out-of-range members are detected
+ * on the device: the set is evaluated without them and ebc_sync() returns
+ * EINDEX.  l = 0 is OK.
  */
 ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off, int64_t l, double *out_f);
+
+/*
+ * Reserve the device buffers of ebc_eval_sets at a tensor-core precision for
+ * calls of up to max_sets sets with up to max_members members in all
+ * (csr_off[l]).  Such calls then allocate nothing and read nothing back to
+ * the host.  max_sets = 0 drops the reservation (the buffers stay).  EINVAL
+ * for negative sizes or at EBC_FP32; ENOMEM when the buffers do not fit.
+ */
+ebc_status ebc_reserve_sets(ebc_t h, int64_t max_sets, int64_t max_members);
 
 /* Host-pointer form of ebc_eval_sets; validates offsets and indices on the host. */
 ebc_status ebc_eval_sets_host(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off, int64_t l, double *out_f);

@@ -190,7 +190,7 @@ int64_t ebc::handle_bytes(int64_t n, int32_t d, ebc_prec prec) {
     b += 2 * cap * 8 + 3 * pool * nref * 8 + pool * 12 + 2 * ebc::kMaxRefineK * 8;
     if (prec == EBC_BF16 || prec == EBC_FP16 || prec == EBC_FP8E4M3) {
         const int64_t n_pad = (n + 255) / 256 * 256, DP = (d + 63) / 64 * 64;
-        b += 3 * n_pad * DP * 2 + 5 * n_pad * 16 * 2 + n_pad * (8 + 4 + 4);
+        b += 3 * n_pad * DP * 2 + 4 * n_pad * 16 * 2 + n_pad * (8 + 4 + 4);
     }
     if (prec == EBC_FP8E4M3) {  // FP8 operands, extensions, scales, norms; lazy bounds and list
         const int64_t n_pad = (n + 255) / 256 * 256, DP8 = (d + 127) / 128 * 128;
@@ -866,33 +866,23 @@ ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off
     if (l < 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: l < 0");
     if (l == 0) return EBC_OK;
     if (!csr_off || !out_f) return fail(h, EBC_EINVAL, "ebc_eval_sets: NULL argument");
-    if (c.prec != EBC_FP32 && ebc::tc_sets_device_planned(c)) {
-        // tensor-core path planned on the device: asynchronous, no host read
+    if (c.prec != EBC_FP32) {
+        // tensor cores, planned on the device.  The member buffers must hold
+        // csr_off[l] members: a reservation covering l sets says how many;
+        // without one the count is read from the device (8 bytes, one wait).
+        int64_t members = c.tc.res_members;
+        if (l > c.tc.res_sets || members <= 0) {
+            CK(h, cudaMemcpyAsync(c.h_err, csr_off + l, sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
+            CK(h, cudaStreamSynchronize(c.stream));
+            memcpy(&members, c.h_err, sizeof(int64_t));
+            if (members < 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: csr_off[l] < 0");
+            if (members > 0 && !csr_idx) return fail(h, EBC_EINVAL, "ebc_eval_sets: csr_idx is NULL");
+        }
         const int64_t rows = c.tc.n_pad / 256 * 8;  // (point unit, epilogue warp)
         ebc_status s = ensure_set_part(h, rows * std::min<int64_t>(l, std::max<int64_t>(128, ((int64_t)1 << 24) / rows)));
         if (s) return s;
         int64_t nl = 0;
-        CK(h, launch(h, PK_EVAL, 0, [&] { return ebc::launch_eval_sets_tc_dev(c, csr_idx, csr_off, l, out_f, &nl); }));
-        h->prof.p.launches += nl;
-        h->prof.p.eval_launches += nl;
-        return EBC_OK;
-    }
-    if (c.prec != EBC_FP32) {
-        // K-blocked rows (d > 128): the tile plan is made on the host from the offsets
-        std::vector<int64_t> off((size_t)l + 1);
-        CK(h, cudaMemcpyAsync(off.data(), csr_off, sizeof(int64_t) * (l + 1), cudaMemcpyDeviceToHost, c.stream));
-        CK(h, cudaStreamSynchronize(c.stream));
-        if (off[0] != 0) return fail(h, EBC_EINVAL, "ebc_eval_sets: csr_off[0] != 0");
-        for (int64_t j = 0; j < l; ++j)
-            if (off[j + 1] < off[j]) return fail(h, EBC_EINVAL, "ebc_eval_sets: offsets decrease");
-        if (off[l] > 0 && !csr_idx) return fail(h, EBC_EINVAL, "ebc_eval_sets: csr_idx is NULL");
-        const int64_t rows = c.tc.n_pad / 256 * 8;  // (point unit, epilogue warp)
-        // partial rows x sets of one launch; a chunk holds at most 128 sets
-        ebc_status s = ensure_set_part(h, std::min<int64_t>(rows * l, std::max<int64_t>(rows * 128, (int64_t)1 << 24)) +
-                                              rows * 128);
-        if (s) return s;
-        int64_t nl = 0;
-        CK(h, launch(h, PK_EVAL, 0, [&] { return ebc::launch_eval_sets_tc(c, csr_idx, csr_off, off.data(), l, out_f, &nl); }));
+        CK(h, launch(h, PK_EVAL, 0, [&] { return ebc::launch_eval_sets_tc(c, csr_idx, csr_off, l, members, out_f, &nl); }));
         h->prof.p.launches += nl;
         h->prof.p.eval_launches += nl;
         return EBC_OK;
@@ -906,6 +896,24 @@ ebc_status ebc_eval_sets(ebc_t h, const int32_t *csr_idx, const int64_t *csr_off
     if (s) return s;
     h->prof.p.launches += 1;
     CK(h, launch(h, PK_EVAL, 2, [&] { return ebc::launch_eval_sets_fp32(c, csr_idx, csr_off, l, out_f, h->d_bad); }));
+    return EBC_OK;
+}
+
+ebc_status ebc_reserve_sets(ebc_t h, int64_t max_sets, int64_t max_members) {
+    if (check_handle(h)) return EBC_EINVAL;
+    ebc::Ctx &c = h->c;
+    if (max_sets < 0 || max_members < 0) return fail(h, EBC_EINVAL, "ebc_reserve_sets: negative size");
+    if (c.prec == EBC_FP32 || c.tc.prec < 0)
+        return fail(h, EBC_EINVAL, "ebc_reserve_sets: needs a tensor-core precision (ebc_set_precision)");
+    if (max_sets > 0) {
+        const int64_t rows = c.tc.n_pad / 256 * 8;
+        ebc_status s = ensure_set_part(
+            h, rows * std::min<int64_t>(max_sets, std::max<int64_t>(128, ((int64_t)1 << 24) / rows)));
+        if (s) return s;
+        CK(h, ebc::tc_sets_reserve(c, max_sets, max_members));
+    }
+    c.tc.res_sets = max_sets;
+    c.tc.res_members = max_members;
     return EBC_OK;
 }
 

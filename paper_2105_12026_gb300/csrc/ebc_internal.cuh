@@ -156,20 +156,17 @@ struct Ctx {
         CUtensorMap tmBx;         // point extension over Bext (box 16 x 256)
         // multi-set evaluation (ebc_eval_sets at a tensor-core precision)
         uint16_t *Px = nullptr;   // [n_pad, 16] point-side extension: ||v||^2 - ||v_hat||^2 (static)
-        uint16_t *Sx = nullptr;   // [n_pad + 1, 16] member-side extension of every point: -||v_hat||^2
-                                  // (static); row n_pad: the padding column's (-1e30)
-        int64_t *sp_beg = nullptr;    // device plan of a multi-set batch: padded start column of each
-        int *sp_set = nullptr;        //   non-empty set ([lb + 1]), its index ([lb]),
-        int *sp_chunk = nullptr;      //   the first compacted set of each chunk ([lb + 1]),
-        int *sp_cnt = nullptr;        //   [0] chunks, [1] non-empty sets, [2] bad offsets
-        int64_t sp_cap = 0;           // sets per batch the plan buffers hold
+        // device plan of a multi-set call (k_sets_plan): padded offsets [l + 1], chunk records
+        // [l + 1][4], each set's chunk [l], first chunk of each launch batch [batches + 1]
+        int64_t *sp_aux = nullptr, *sp_rec = nullptr;
+        int *sp_cj = nullptr, *sp_bf = nullptr;
+        int64_t sp_sets = 0, sp_batches = 0;  // capacities
+        int64_t res_sets = 0, res_members = 0;  // ebc_reserve_sets
         CUtensorMap tmPx;         // box 16 x 128 over Px
         uint16_t *Mq = nullptr;   // [mcap, DP] 2 s_hat of the gathered set members, padded per set
         uint16_t *Mx = nullptr;   // [mcap, 16] member extension: -||s_hat||^2
         int *gset = nullptr;      // [mcap / 16] per 16-member group: 2 * (set index in its chunk) + last
-        int64_t *sets_aux = nullptr;  // padded offsets [l + 1], then chunk records
         int64_t mcap = 0;         // rows of Mq / Mx
-        int64_t aux_cap = 0;      // int64 entries of sets_aux
     } tc;
     // FP8 e4m3 copy (ebc_set_precision EBC_FP8E4M3): candidate operand with a
     // per-row power-of-two scale s_c, point operand with one power-of-two
@@ -327,16 +324,14 @@ cudaError_t launch_prep_tc(Ctx &c, bool upper);  // a_v for every point (+ max m
 cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int *nchunks);
 // bulk gains of the list (cand, *m_dev) whose length is on the device (m_cap bounds it)
 cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int64_t m_cap);
-// multi-set evaluation on tensor cores; off_host is a host copy of the
-// (validated) offsets; returns cudaErrorMemoryAllocation if scratch is short
-cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_dev, const int64_t *off_host,
-                                int64_t l, double *out_f, int64_t *nlaunch);
+// multi-set evaluation on tensor cores, planned on the device: `members` is
+// an upper bound of off[l] (more members record EINVAL and evaluate nothing);
+// set_part must hold at least 8 n_pad / 256 rows
+cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, int64_t members,
+                                double *out_f, int64_t *nlaunch);
+// grow the multi-set buffers for `sets` sets of `members` members in all
+cudaError_t tc_sets_reserve(Ctx &c, int64_t sets, int64_t members);
 void tc_free(Ctx &c);
-// multi-set evaluation planned on the device (whole rows resident, d <= 128):
-// asynchronous, no host read; set_part must hold at least 8 * n_pad / 256 rows
-bool tc_sets_device_planned(const Ctx &c);
-cudaError_t launch_eval_sets_tc_dev(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,
-                                    int64_t *nlaunch);
 
 // ---- one persistent bulk launch over several handles (k_tc.cu, group.cu) ----
 // A handle's part of a shared Greedy round: its tensor maps (read by TMA from

@@ -104,6 +104,10 @@ struct TcArgs {
     int G;                  // persistent CTAs
     int *nch_out;           // chunk count used, for the reduction kernel
     uint64_t wait_ns;       // limit of each pipeline wait (wait_limit_ns())
+    // multi-set mode, plan on the device: this launch's chunks are records
+    // [sets_bf[sets_batch], sets_bf[sets_batch + 1]) of `chunks`
+    const int *sets_bf;
+    int sets_batch;
 };
 
 constexpr int MODE_GAINS = 0;
@@ -121,6 +125,7 @@ struct Plan {
     int n_ctiles;      // A tiles
     int nchunks;       // units per A tile
     int vt_per_chunk;  // B tiles per unit (gains)
+    int chunk0;        // sets: first chunk record of the launch
 };
 
 __device__ __forceinline__ Plan make_plan(const TcArgs &a) {
@@ -137,6 +142,12 @@ __device__ __forceinline__ Plan make_plan(const TcArgs &a) {
         p.nchunks = a.nchunks;
         p.vt_per_chunk = a.vt_per_chunk;
     }
+    p.chunk0 = 0;
+    if (a.sets_bf) {
+        const volatile int *bf = a.sets_bf;
+        p.chunk0 = bf[a.sets_batch];
+        p.nchunks = bf[a.sets_batch + 1] - p.chunk0;
+    }
     return p;
 }
 
@@ -152,7 +163,7 @@ __device__ __forceinline__ void unit_span(const TcArgs &a, const Plan &P, int u,
         b_row0 = vt0 * BN;
         nb = vt1 - vt0;
     } else {
-        const int64_t *r = a.chunks + 4 * (int64_t)ch;
+        const int64_t *r = a.chunks + 4 * ((int64_t)P.chunk0 + ch);
         b_row0 = (int)r[2];
         nb = (int)((r[3] - r[2] + BN - 1) / BN);
     }
@@ -642,7 +653,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
             int at, ch, b_row0, nb;
             unit_span<MODE>(args, P, u, at, ch, b_row0, nb);
-            const int64_t *rec = args.chunks + 4 * (int64_t)ch;
+            const int64_t *rec = args.chunks + 4 * ((int64_t)P.chunk0 + ch);
             const int64_t set_b = rec[0], col_e = rec[3];
             double *prow = args.partial + ((int64_t)at * 8 + ew) * args.lb + (set_b - args.j0);
             float run = -INFINITY;
@@ -1094,505 +1105,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs 
 }
 
 // ---------------------------------------------------------------------------
-// Multi-set evaluation planned on the device (Sec. 4.2's work matrix rows,
-// sets as CSR index lists; the paper packs the sets on the host).
-//
-// k_sets_plan (one block, per batch of sets [j0, j0 + lb)): the padded column
-// start of every non-empty set (members padded to 16-column groups),
-// compacted in set order (sp_set: the set, sp_beg: its start, sp_beg[cnt] =
-// total columns), and chunks: runs of compacted sets whose start falls in
-// one window of SP_WIN columns (sp_chunk: the first set of each, then the
-// count).  It also checks the offsets; bad offsets leave zero chunks and the
-// bad flag set, and nothing reads a member.
-//
-// k_sets_tc_g: the tcgen05 multi-set kernel for whole rows resident (d <=
-// 128) without a host plan: a unit is (256-point tile, chunk); the producer
-// warp gathers every 256-member tile itself, each lane copying eight member
-// rows of 2 v_hat (and their extension row) from the resident quantised V
-// with cp.async into the 128-byte-swizzled layout the MMA reads, padding
-// columns zero-filled with the -1e30 extension; the epilogue finds the set
-// of each 16-column group with warp ballots over the compacted set starts.
-// ---------------------------------------------------------------------------
-namespace {
-constexpr int64_t SP_WIN = 2048;  // columns per chunk window
-constexpr int SP_T = 1024;        // plan block
-
-struct SetsGArgs {
-    const int32_t *idx;
-    const int64_t *off;     // CSR offsets of the batch's sets (off[0] = the batch's first set)
-    const uint16_t *Vq2;    // [n_pad, DP] 2 v_hat
-    const uint16_t *Sx;     // [n_pad + 1, 16] member extension rows
-    const int64_t *beg;     // plan: padded start column of each compacted set, [cnt + 1]
-    const int *set;         // plan: batch-relative index of each compacted set
-    const int *chunk;       // plan: first compacted set of each chunk, [nck + 1]
-    const int *cnt;         // plan: [0] chunks, [1] compacted sets, [2] bad offsets
-    double *partial;        // [(point unit * 8 + epilogue warp)][lb]
-    int *err;
-    int64_t n, lb;
-    int n_pad, DP, npu;
-    int nstages, na;
-    uint32_t idesc, idesc_ext;
-    uint64_t wait_ns;
-};
-
-// Exclusive block scan (SP_T threads) of one value per thread; returns the
-// prefix and writes the block total to *total (shared).
-template <class T>
-__device__ __forceinline__ T block_excl_scan(T v, T *warp_tot, T *total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    T x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const T y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        T t = lane < SP_T / 32 ? warp_tot[lane] : (T)0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const T y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        if (lane < SP_T / 32) warp_tot[lane] = t;  // inclusive warp prefix
-        if (lane == SP_T / 32 - 1) *total = t;
-    }
-    __syncthreads();
-    const T r = (w > 0 ? warp_tot[w - 1] : (T)0) + x - v;
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-// generic-proxy writes of this thread (here: completed cp.async copies)
-// become visible to later async-proxy reads (the MMA)
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-}  // namespace
-
-__global__ void __launch_bounds__(SP_T) k_sets_plan(const int32_t *__restrict__ idx, const int64_t *__restrict__ off,
-                                                    int64_t lb, int64_t nnz_check, int64_t *__restrict__ beg,
-                                                    int *__restrict__ set, int *__restrict__ chunk,
-                                                    int *__restrict__ cnt, int *__restrict__ err) {
-    __shared__ int64_t wt64[SP_T / 32];
-    __shared__ int wt32[SP_T / 32];
-    __shared__ int64_t tot64;
-    __shared__ int tot32;
-    __shared__ int s_bad;
-    const int t = threadIdx.x;
-    if (t == 0) {
-        // the first batch checks off[0] = 0; every batch a NULL member list
-        // against a non-empty batch (nnz_check < 0: not the first batch)
-        s_bad = (nnz_check >= 0 && off[0] != 0) || (idx == nullptr && off[lb] != off[0]);
-    }
-    __syncthreads();
-    int64_t col = 0;
-    int q0 = 0;
-    for (int64_t base = 0; base < lb; base += SP_T) {
-        const int64_t j = base + t;
-        int64_t pad = 0;
-        if (j < lb) {
-            const int64_t o0 = off[j], o1 = off[j + 1];
-            if (o1 < o0) s_bad = 1;  // any thread may set it; all write the same value
-            else pad = (o1 - o0 + 15) / 16 * 16;
-        }
-        const int ne = pad > 0 ? 1 : 0;
-        const int64_t c = block_excl_scan<int64_t>(pad, wt64, &tot64);
-        const int q = block_excl_scan<int>(ne, wt32, &tot32);
-        if (ne) {
-            beg[q0 + q] = col + c;
-            set[q0 + q] = (int)j;
-        }
-        col += tot64;
-        q0 += tot32;
-        __syncthreads();
-    }
-    if (t == 0) beg[q0] = col;
-    __syncthreads();
-    __threadfence_block();
-    // chunks over the compacted sets
-    int k0 = 0;
-    for (int base = 0; base < q0; base += SP_T) {
-        const int q = base + t;
-        int flag = 0;
-        if (q < q0) flag = (q == 0) || (beg[q] / SP_WIN != beg[q - 1] / SP_WIN);
-        const int pos = block_excl_scan<int>(flag, wt32, &tot32);
-        if (flag) chunk[k0 + pos] = q;
-        k0 += tot32;
-        __syncthreads();
-    }
-    if (t == 0) {
-        chunk[k0] = q0;
-        const int bad = s_bad;
-        cnt[0] = bad ? 0 : k0;
-        cnt[1] = q0;
-        cnt[2] = bad;
-        if (bad) atomicCAS(err, 0, (int)EBC_EINVAL);
-    }
-}
-
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_sets_tc_g(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx, const SetsGArgs args) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int ns = args.nstages;
-    const int na = args.na;
-    const uint64_t wait_ns = args.wait_ns;
-    const int RB = 2 * args.DP;
-    const SmemLayout L = smem_layout(RB, ns, na);
-    uint8_t *sA = base;
-    uint8_t *sB = base + L.off_b;
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + L.off_bar);
-    uint64_t *empty = full + ns;
-    uint64_t *a_full = empty + ns;
-    uint64_t *a_empty = a_full + 2;
-    uint64_t *t_full = a_empty + 2;
-    uint64_t *t_empty = t_full + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + L.off_misc);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(base + L.off_misc + 4);
-    int *last_full = reinterpret_cast<int *>(base + L.off_misc + 8);  // [ns] (ns <= 8)
-    int *last_afull = last_full + 8;                                    // [2]
-    int *last_tfull = last_afull + 2;                                   // [2]
-    uint64_t *fin = reinterpret_cast<uint64_t *>(base + L.off_misc + 56);
-
-    const int nck = args.cnt[0];
-    const int total_units = args.npu * nck;
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < ns; ++s) {
-            tc::mbar_init(&full[s], 32);  // every producer lane, after its copies
-            tc::mbar_init(&empty[s], 1);
-            last_full[s] = -1;
-        }
-        for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&a_full[b], 1);
-            tc::mbar_init(&a_empty[b], 1);
-            tc::mbar_init(&t_full[b], 1);
-            tc::mbar_init(&t_empty[b], NEPI / 64);
-            last_afull[b] = -1;
-            last_tfull[b] = -1;
-        }
-        tc::mbar_init(fin, 1);
-        *abort_flag = 0;
-        tc::fence_mbar_init();
-    }
-    if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, TMEM_COLS);
-        tc::tmem_relinquish();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-    const uint32_t tmem_base = *tmem_slot;
-    const int64_t *cbeg = args.beg;
-
-    if (warp == 0) {
-        // ------------------------------------------------------------ producer
-        // lane 0: the point tile by TMA; all lanes: the member tiles by cp.async
-        int g = 0, ua = 0;
-        int pend = -1;  // stage whose copies are issued but not yet signalled
-        bool alive = true;
-        if (lane == 0) {
-            tc::tma_prefetch_desc(&tmA);
-            tc::tma_prefetch_desc(&tmAx);
-        }
-        const uint32_t rowb = (uint32_t)RB;
-        const int nmain = RB / 16;  // 16-byte pieces of a member row
-        for (int u = blockIdx.x; u < total_units && alive; u += gridDim.x) {
-            const int at = u / nck, k = u % nck;
-            const int qb = args.chunk[k], qe = args.chunk[k + 1];
-            const int64_t c_beg = cbeg[qb], c_end = cbeg[qe];
-            const int nb = (int)((c_end - c_beg + BN - 1) / BN);
-            if (nb == 0) continue;
-            const int ab = ua % na;
-            const int aph = (ua / na) & 1;
-            int ok = 1;
-            if (lane == 0) {
-                if (!tc::mbar_wait(&a_empty[ab], aph ^ 1, abort_flag, wait_ns)) {
-                    record_timeout(args.err, abort_flag);
-                    ok = 0;
-                } else {
-                    uint8_t *abuf = sA + ab * L.a_bytes;
-                    tc::mbar_arrive_expect_tx(&a_full[ab], L.a_bytes);
-                    for (int h = 0; h < 2; ++h) {
-                        uint8_t *sub = abuf + h * L.a_sub;
-                        const int row0 = at * BM + h * BMS;
-                        for (int j = 0; j < RB / 128; ++j)
-                            tc::tma_load_2d(sub + j * (BMS * 128), &tmA, &a_full[ab], j * KATOM, row0);
-                        tc::tma_load_2d(sub + L.a_main, &tmAx, &a_full[ab], 0, row0);
-                    }
-                    last_afull[ab] = aph;
-                }
-            }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) {
-                alive = false;
-                break;
-            }
-            ++ua;
-            int cur = qb;  // compacted set holding the tile's first column
-            for (int i = 0; i < nb; ++i, ++g) {
-                const int s = g % ns;
-                const int ph = (g / ns) & 1;
-                const int64_t c0 = c_beg + (int64_t)i * BN;
-                // set ends ahead of the current set: e = start of compacted set cur + 1 + lane
-                const int qa = cur + 1 + lane;
-                const int64_t e = qa <= qe ? cbeg[qa] : INT64_MAX;
-                int okw = 1;
-                if (lane == 0 && !tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, wait_ns)) {
-                    record_timeout(args.err, abort_flag);
-                    okw = 0;
-                }
-                if (!__shfl_sync(0xffffffffu, okw, 0)) {
-                    alive = false;
-                    break;
-                }
-                // the set of this lane's 16-column group (lanes 2g, 2g + 1: group g)
-                const int grp = lane >> 1;
-                int mycnt = 0;
-#pragma unroll
-                for (int gg = 0; gg < 16; ++gg) {
-                    const unsigned b = __ballot_sync(0xffffffffu, e <= c0 + 16 * gg);
-                    if (gg == grp) mycnt = __popc(b);
-                }
-                const int q = cur + mycnt;
-                const int64_t gcol = c0 + 16 * grp;
-                int64_t m0 = 0, m1 = 0, sb = 0;
-                if (gcol < c_end) {
-                    const int jj = args.set[q];
-                    m0 = args.off[jj];
-                    m1 = args.off[jj + 1];
-                    sb = cbeg[q];
-                }
-                uint8_t *bbuf = sB + s * L.b_bytes;
-                const uint32_t bb = tc::smem_u32(bbuf);
-                for (int rr = 0; rr < 8; ++rr) {
-                    const int r = 16 * grp + (lane & 1) * 8 + rr;  // tile row = member column
-                    const int64_t col = c0 + r;
-                    int64_t src = -1;
-                    if (col < c_end) {
-                        const int64_t p = m0 + (col - sb);
-                        if (p < m1) {
-                            const int x = args.idx[p];
-                            if (x >= 0 && (int64_t)x < args.n) src = x;
-                            else atomicCAS(args.err, 0, (int)EBC_EINDEX);
-                        }
-                    }
-                    const uint8_t *vrow = reinterpret_cast<const uint8_t *>(args.Vq2) + (src >= 0 ? src : 0) * (int64_t)rowb;
-                    const uint32_t vbytes = src >= 0 ? 16u : 0u;  // 0: zero fill
-                    // main part: 128-byte K atoms of BN rows, 128-byte swizzle
-                    for (int piece = 0; piece < nmain; ++piece) {
-                        const int atom = piece >> 3, qd = piece & 7;
-                        const uint32_t dst = bb + (uint32_t)(atom * (BN * 128) + (r >> 3) * 1024 + (r & 7) * 128 +
-                                                             ((qd ^ (r & 7)) << 4));
-                        cp_async16(dst, vrow + piece * 16, vbytes);
-                    }
-                    // extension row (32 bytes), 32-byte swizzle
-                    const uint16_t *xrow = args.Sx + (int64_t)(src >= 0 ? src : args.n_pad) * KEXT;
-                    for (int qd = 0; qd < 2; ++qd) {
-                        const uint32_t dst = bb + L.b_main +
-                                             (uint32_t)((r >> 3) * 256 + (r & 7) * 32 + ((qd ^ ((r >> 2) & 1)) << 4));
-                        cp_async16(dst, xrow + qd * 8, 16u);
-                    }
-                }
-                cp_async_commit();
-                if (pend >= 0) {
-                    cp_async_wait_1();  // the previous stage's copies are complete
-                    fence_proxy_async();
-                    tc::mbar_arrive(&full[pend]);
-                }
-                pend = s;
-                last_full[s] = ph;
-                // next tile: skip the sets that end at or before its first column
-                cur += __popc(__ballot_sync(0xffffffffu, e <= c0 + BN));
-            }
-            // signal the unit's last stage before the next unit waits for a
-            // candidate buffer (the MMA frees it only after that stage)
-            cp_async_wait_0();
-            if (pend >= 0) {
-                fence_proxy_async();
-                tc::mbar_arrive(&full[pend]);
-                pend = -1;
-            }
-        }
-        cp_async_wait_0();  // no copy may still write shared memory at the teardown
-        if (pend >= 0) {
-            fence_proxy_async();
-            tc::mbar_arrive(&full[pend]);
-        }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            int g = 0, t = 0, ua = 0;
-            for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
-                const int k = u % nck;
-                const int64_t c_beg = cbeg[args.chunk[k]], c_end = cbeg[args.chunk[k + 1]];
-                const int nb = (int)((c_end - c_beg + BN - 1) / BN);
-                if (nb == 0) continue;
-                const int ab = ua % na;
-                if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag, wait_ns)) {
-                    record_timeout(args.err, abort_flag);
-                    break;
-                }
-                const uint32_t a0 = tc::smem_u32(sA + ab * L.a_bytes);
-                bool ok = true;
-                for (int i = 0; i < nb && ok; ++i, ++g, ++t) {
-                    const int s = g % ns;
-                    if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag, wait_ns)) {
-                        record_timeout(args.err, abort_flag);
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t b0 = tc::smem_u32(sB + s * L.b_bytes);
-                    for (int h = 0; h < 2; ++h) {
-                        if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag, wait_ns)) {
-                            record_timeout(args.err, abort_flag);
-                            ok = false;
-                            break;
-                        }
-                        tc::tc_fence_after();
-                        const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
-                        const uint32_t ah = a0 + h * L.a_sub;
-                        for (int kk = 0; kk < RB / 32; ++kk) {
-                            const uint32_t j = kk >> 2, w4 = kk & 3;
-                            const uint64_t ad = tc::sdesc_sw128(ah + j * (BMS * 128) + w4 * 32);
-                            const uint64_t bd = tc::sdesc_sw128(b0 + j * (BN * 128) + w4 * 32);
-                            tc::mma_f16(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
-                        }
-                        tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main),
-                                    args.idesc_ext, 1u);
-                        tc::mma_commit(&t_full[h]);
-                        last_tfull[h] = t & 1;
-                    }
-                    if (!ok) break;
-                    tc::mma_commit(&empty[s]);
-                }
-                if (!ok) break;
-                tc::mma_commit(&a_empty[ab]);
-                ++ua;
-            }
-        }
-    } else {
-        // ------------------------------------------------------ set epilogue
-        // as in tc_pipeline's set epilogue; the set of each 16-column group
-        // comes from the compacted set starts
-        const int ew = warp - 2;  // 0..7
-        const int q4 = warp & 3;
-        const int h = ew >> 2;
-        int t = 0;
-        bool alive = true;
-        for (int u = blockIdx.x; u < total_units && alive; u += gridDim.x) {
-            const int at = u / nck, k = u % nck;
-            const int qb = args.chunk[k], qe = args.chunk[k + 1];
-            const int64_t c_beg = cbeg[qb], c_end = cbeg[qe];
-            const int nb = (int)((c_end - c_beg + BN - 1) / BN);
-            double *prow = args.partial + ((int64_t)at * 8 + ew) * args.lb;
-            float run = -INFINITY;
-            int cur = qb;
-            for (int i = 0; i < nb; ++i, ++t) {
-                const int64_t c0 = c_beg + (int64_t)i * BN;
-                const int ngr = (int)(min((int64_t)BN, c_end - c0) / SET_GROUP);
-                const int qa = cur + 1 + lane;
-                const int64_t e = qa <= qe ? cbeg[qa] : INT64_MAX;  // end of compacted set cur + lane
-                const int sj = cur + lane < qe ? args.set[cur + lane] : 0;
-                int mycnt = 0;
-#pragma unroll
-                for (int gg = 0; gg < 16; ++gg) {
-                    const unsigned b = __ballot_sync(0xffffffffu, e <= c0 + 16 * gg);
-                    if (gg == lane) mycnt = __popc(b);
-                }
-                // group `lane` (< ngr) lies in compacted set cur + mycnt; it ends that set when the set's end
-                // is the group's end
-                const int64_t e_mine = __shfl_sync(0xffffffffu, e, mycnt & 31);
-                const int j_mine = __shfl_sync(0xffffffffu, sj, mycnt & 31);
-                const bool is_last = lane < ngr && e_mine == c0 + 16 * lane + 16;
-                const unsigned lastmask = __ballot_sync(0xffffffffu, is_last);
-                const int ge = j_mine;  // batch-relative set index of group `lane`
-                if (alive) {
-                    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag, wait_ns));
-                    if (!ok) {
-                        if (lane == 0) record_timeout(args.err, abort_flag);
-                        alive = false;
-                    }
-                }
-                if (!alive) break;
-                tc::tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * BN);
-                uint32_t r[4][32];
-                float gm[16];
-                tc::tmem_ld32(taddr, r[0]);
-                tc::tmem_ld32(taddr + 32, r[1]);
-                tc::tmem_ld32(taddr + 64, r[2]);
-                tc::tmem_ld32(taddr + 96, r[3]);
-                tc::tmem_ld_wait();
-#pragma unroll
-                for (int gg = 0; gg < 8; ++gg) gm[gg] = max16(&r[gg >> 1][(gg & 1) * 16]);
-                if (ngr > 8) {
-                    tc::tmem_ld32(taddr + 128, r[0]);
-                    tc::tmem_ld32(taddr + 160, r[1]);
-                    tc::tmem_ld32(taddr + 192, r[2]);
-                    tc::tmem_ld32(taddr + 224, r[3]);
-                    tc::tmem_ld_wait();
-                }
-                tc::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&t_empty[h]);
-                if (ngr > 8) {
-#pragma unroll
-                    for (int gg = 0; gg < 8; ++gg) gm[8 + gg] = max16(&r[gg >> 1][(gg & 1) * 16]);
-                }
-                float val[16];
-#pragma unroll
-                for (int gg = 0; gg < 16; ++gg) {
-                    val[gg] = 0.f;
-                    if (gg < ngr) {
-                        run = fmaxf(run, gm[gg]);
-                        const bool last = (lastmask >> gg) & 1u;
-                        val[gg] = last ? fmaxf(run, 0.f) : 0.f;
-                        run = last ? -INFINITY : run;
-                    }
-                }
-                if (lastmask) {
-                    const float tot = reduce_scatter16(val, lane);
-                    const int gv = group_of_lane(lane);
-                    const int gev = __shfl_sync(0xffffffffu, ge, gv);
-                    if ((lane & 1) == 0 && ((lastmask >> gv) & 1u)) prow[gev] = (double)tot;
-                }
-                cur += __popc(__ballot_sync(0xffffffffu, e <= c0 + BN));
-            }
-        }
-    }
-
-    // ---------------------------------------------------------------- teardown
-    __syncthreads();
-    if (warp == 1 && lane == 0) {
-        volatile int never = 0;
-        tc::mma_commit(fin);
-        tc::mbar_wait(fin, 0u, &never);
-    }
-    if (threadIdx.x == 0) {
-        volatile int never = 0;
-        for (int s = 0; s < ns; ++s)
-            if (last_full[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)last_full[s], &never);
-        for (int b = 0; b < 2; ++b) {
-            if (last_afull[b] >= 0) tc::mbar_wait(&a_full[b], (uint32_t)last_afull[b], &never);
-            if (last_tfull[b] >= 0) tc::mbar_wait(&t_full[b], (uint32_t)last_tfull[b], &never);
-        }
-    }
-    __syncthreads();
-    if (warp == 1) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(tmem_base, TMEM_COLS);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // bf16 pieces.  hi is the nearest bf16; each residual is exact in FP64
 // (Sterbenz); the last piece is rounded up (or to nearest) so that the sum of
 // the pieces is >= x with an error of about 2^-24 |x|.
@@ -1681,25 +1193,9 @@ __global__ void k_quantize(const float *__restrict__ V, int64_t n, int d, int64_
 __global__ void k_make_aext(int64_t n, int64_t n_pad, const double *__restrict__ qn64, const float *__restrict__ qerr,
                             const float *__restrict__ qnorm, const float *__restrict__ qmax, double gamma,
                             const double *__restrict__ nv64, uint16_t *__restrict__ Aext, uint16_t *__restrict__ Bext,
-                            uint16_t *__restrict__ Px, uint16_t *__restrict__ Sx) {
+                            uint16_t *__restrict__ Px) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r > n_pad) return;
-    {
-        // member side of the multi-set evaluation: [-||v_hat||^2 in three
-        // pieces | 1 1 1 | 0..], or the padding column's [-1e30 | 0..]
-        __align__(16) uint16_t srow[KEXT];
-        for (int i = 0; i < KEXT; ++i) srow[i] = 0;
-        if (r < n) {
-            split3(-qn64[r], false, srow);
-            srow[3] = srow[4] = srow[5] = bf16_bits(__float2bfloat16_rn(1.f));
-        } else {
-            srow[0] = bf16_bits(__float2bfloat16_rn(PAD_A));
-        }
-        uint4 *sd = reinterpret_cast<uint4 *>(Sx + r * KEXT);
-        sd[0] = reinterpret_cast<const uint4 *>(srow)[0];
-        sd[1] = reinterpret_cast<const uint4 *>(srow)[1];
-    }
-    if (r == n_pad) return;
+    if (r >= n_pad) return;
     {
         __align__(16) uint16_t prow[KEXT];
         for (int i = 0; i < KEXT; ++i) prow[i] = 0;
@@ -1817,46 +1313,184 @@ __global__ void k_gather_rows(const uint16_t *__restrict__ Vq, const uint16_t *_
 // One thread per 16 bytes of a row; the set of padded column p is found by
 // binary search in the padded offsets.  Members outside [0, n) are reported
 // as EINDEX and treated as padding.
+// Member rows of the sets, padded per set to 16-column groups: column p of
+// Mq holds 2 s_hat of its set's member (zeros for padding), Mx its
+// extension [-||s_hat||^2 in three pieces | 1 1 1 | 0..] (padding: -1e30).
+// The column count is the device plan's poff[l]; grid-stride over columns.
 __global__ void k_gather_members(const uint16_t *__restrict__ Vq2, const double *__restrict__ qn64, int64_t n, int DP,
                                  const int32_t *__restrict__ idx, const int64_t *__restrict__ off,
-                                 const int64_t *__restrict__ poff, int64_t l, int64_t ncols,
+                                 const int64_t *__restrict__ poff, int64_t l, int64_t ncap,
                                  uint16_t *__restrict__ Mq, uint16_t *__restrict__ Mx, int *__restrict__ err) {
     const int per_row = DP / 8 + 2;
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= ncols * per_row) return;
-    const int64_t p = e / per_row;
-    const int w = (int)(e % per_row);
-    int64_t lo = 0, hi = l;  // poff[lo] <= p < poff[hi]
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (poff[mid] <= p) lo = mid;
-        else hi = mid;
-    }
-    const int64_t r = p - poff[lo];
-    const int64_t mb = off[lo];
-    int64_t src = -1;
-    if (r < off[lo + 1] - mb) {
-        src = idx[mb + r];
-        if (src < 0 || src >= n) {
-            if (w == 0) atomicCAS(err, 0, (int)EBC_EINDEX);
-            src = -1;
+    const int64_t ncols = min(poff[l], ncap);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncols * per_row;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / per_row;
+        const int w = (int)(e % per_row);
+        int64_t lo = 0, hi = l;  // the last set with poff[set] <= p (the non-empty one holding p)
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (poff[mid] <= p) lo = mid;
+            else hi = mid;
         }
-    }
-    if (w < DP / 8) {
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (src >= 0) val = reinterpret_cast<const uint4 *>(Vq2 + src * DP)[w];
-        reinterpret_cast<uint4 *>(Mq + p * DP)[w] = val;
-    } else {
-        __align__(16) uint16_t row[KEXT];
-        for (int i = 0; i < KEXT; ++i) row[i] = 0;
-        if (src >= 0) {
-            split3(-qn64[src], false, row);
-            row[3] = row[4] = row[5] = bf16_bits(__float2bfloat16_rn(1.f));
+        const int64_t r = p - poff[lo];
+        const int64_t mb = off[lo];
+        int64_t src = -1;
+        if (r < off[lo + 1] - mb) {
+            src = idx[mb + r];
+            if (src < 0 || src >= n) {
+                if (w == 0) atomicCAS(err, 0, (int)EBC_EINDEX);
+                src = -1;
+            }
+        }
+        if (w < DP / 8) {
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (src >= 0) val = reinterpret_cast<const uint4 *>(Vq2 + src * DP)[w];
+            reinterpret_cast<uint4 *>(Mq + p * DP)[w] = val;
         } else {
-            row[0] = bf16_bits(__float2bfloat16_rn(PAD_A));
+            __align__(16) uint16_t row[KEXT];
+            for (int i = 0; i < KEXT; ++i) row[i] = 0;
+            if (src >= 0) {
+                split3(-qn64[src], false, row);
+                row[3] = row[4] = row[5] = bf16_bits(__float2bfloat16_rn(1.f));
+            } else {
+                row[0] = bf16_bits(__float2bfloat16_rn(PAD_A));
+            }
+            const int x = w - DP / 8;
+            reinterpret_cast<uint4 *>(Mx + p * KEXT)[x] = reinterpret_cast<const uint4 *>(row)[x];
         }
-        const int x = w - DP / 8;
-        reinterpret_cast<uint4 *>(Mx + p * KEXT)[x] = reinterpret_cast<const uint4 *>(row)[x];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Device plan of a multi-set evaluation (one block; nothing is read back to
+// the host).  The sets are the rows of the work matrix of Sec. 4.2 given as
+// CSR index lists; each set's members are padded to 16-column groups.
+//  1. poff[j]: padded start column of set j (exclusive scan, poff[l] = total);
+//     offsets that do not start at 0 or decrease, a NULL member list with
+//     members, or more columns than the buffers hold leave no work (poff[l] =
+//     0, no chunks) and record EINVAL.
+//  2. chunks: a run of sets starts a new chunk where the set's start column
+//     enters a new window of SP_WIN columns, and at every launch batch's
+//     first set (batches of lbmax sets); rec[k] = {first set, end set, first
+//     column, end column}, cj[j] = chunk of set j, bf[b] = first chunk of
+//     batch b (bf[batches] = chunk count).
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t SP_WIN = 2048;
+constexpr int SP_T = 1024;
+
+// Exclusive scan over the block (SP_T threads) of one value per thread; the
+// block total goes to *total.
+template <class T>
+__device__ __forceinline__ T block_excl_scan(T v, T *warp_tot, T *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        T t = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;  // inclusive prefix of the warp totals
+        if (lane == 31) *total = t;
+    }
+    __syncthreads();
+    const T r = (w > 0 ? warp_tot[w - 1] : (T)0) + x - v;
+    __syncthreads();
+    return r;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(SP_T) k_sets_plan(const int32_t *__restrict__ idx, const int64_t *__restrict__ off,
+                                                    int64_t l, int64_t lbmax, int64_t col_cap,
+                                                    int64_t *__restrict__ poff, int64_t *__restrict__ rec,
+                                                    int *__restrict__ cj, int *__restrict__ bf, int64_t nbatch,
+                                                    int *__restrict__ err) {
+    __shared__ int64_t wt64[32];
+    __shared__ int wt32[32];
+    __shared__ int64_t tot64;
+    __shared__ int tot32;
+    __shared__ int s_bad;
+    const int t = threadIdx.x;
+    if (t == 0) s_bad = off[0] != 0 || (idx == nullptr && off[l] != off[0]);
+    __syncthreads();
+    int64_t col = 0;
+    for (int64_t base = 0; base < l; base += SP_T) {
+        const int64_t j = base + t;
+        int64_t pad = 0;
+        if (j < l) {
+            const int64_t o0 = off[j], o1 = off[j + 1];
+            if (o1 < o0) s_bad = 1;  // every writer writes 1
+            else pad = (o1 - o0 + 15) / 16 * 16;
+        }
+        const int64_t c = block_excl_scan<int64_t>(pad, wt64, &tot64);
+        if (j < l) poff[j] = col + c;
+        col += tot64;
+        __syncthreads();
+    }
+    if (t == 0 && col > col_cap) s_bad = 1;
+    __syncthreads();
+    if (s_bad) {
+        if (t == 0) {
+            poff[l] = 0;
+            atomicCAS(err, 0, (int)EBC_EINVAL);
+        }
+        for (int64_t b = t; b <= nbatch; b += SP_T) bf[b] = 0;
+        return;
+    }
+    if (t == 0) poff[l] = col;
+    __syncthreads();
+    int kbase = 0;
+    for (int64_t base = 0; base < l; base += SP_T) {
+        const int64_t j = base + t;
+        int flag = 0;
+        if (j < l) flag = (j % lbmax == 0) || (poff[j] / SP_WIN != poff[j - 1] / SP_WIN);
+        const int pos = block_excl_scan<int>(flag, wt32, &tot32);
+        if (j < l) {
+            const int k = kbase + pos + flag - 1;  // chunk of set j
+            cj[j] = k;
+            if (flag) {
+                rec[4 * (int64_t)k] = j;
+                rec[4 * (int64_t)k + 2] = poff[j];
+                if (j % lbmax == 0) bf[j / lbmax] = k;
+            }
+        }
+        kbase += tot32;
+        __syncthreads();
+    }
+    if (t == 0) bf[nbatch] = kbase;
+    __syncthreads();
+    for (int k = t; k < kbase; k += SP_T) {
+        const int64_t se = k + 1 < kbase ? rec[4 * (int64_t)(k + 1)] : l;
+        rec[4 * (int64_t)k + 1] = se;
+        rec[4 * (int64_t)k + 3] = poff[se];
+    }
+}
+
+// Per 16-column group of the padded members: 2 * (its set's index within the
+// set's chunk) + 1 if it is the set's last group.
+__global__ void k_sets_gset(const int64_t *__restrict__ poff, int64_t l, const int64_t *__restrict__ rec,
+                            const int *__restrict__ cj, int64_t gcap, int *__restrict__ gset) {
+    const int64_t ng = min(poff[l] / 16, gcap);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = g * 16;
+        int64_t lo = 0, hi = l;  // the last set with poff[set] <= col
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (poff[mid] <= col) lo = mid;
+            else hi = mid;
+        }
+        const int64_t sb = rec[4 * (int64_t)cj[lo]];
+        gset[g] = (int)(2 * (lo - sb) + (col + 16 == poff[lo + 1] ? 1 : 0));
     }
 }
 
@@ -2297,7 +1931,7 @@ void tc_free(Ctx &c) {
     tc8_free(c);
     void *ptrs[] = {c.tc.Vq,   c.tc.Vq2,   c.tc.Aext, c.tc.Bext, c.tc.Cq,   c.tc.Cqx,      c.tc.qn64,
                     c.tc.qerr, c.tc.qnorm, c.tc.qmax, c.tc.Px,   c.tc.Mq,   c.tc.Mx,       c.tc.gset,
-                    c.tc.sets_aux, c.tc.Sx, c.tc.sp_beg, c.tc.sp_set, c.tc.sp_chunk, c.tc.sp_cnt};
+                    c.tc.sp_aux, c.tc.sp_rec, c.tc.sp_cj, c.tc.sp_bf};
     for (void *p : ptrs) pool_free(p, c.stream);
     c.tc = Ctx::Tc();
 }
@@ -2311,9 +1945,8 @@ cudaError_t tc_quantize(Ctx &c) {
     k_quantize<<<g, th, 0, c.stream>>>(c.V32, c.n, c.d, T.n_pad, T.DP, T.prec, T.Vq, T.Vq2, T.qn64, T.qerr, T.qnorm,
                                        reinterpret_cast<unsigned int *>(T.qmax), &c.st->err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const unsigned g1 = (unsigned)((T.n_pad + 1 + th - 1) / th);
-    k_make_aext<<<g1, th, 0, c.stream>>>(c.n, T.n_pad, T.qn64, T.qerr, T.qnorm, T.qmax, gamma_for(T.DP), c.nv64,
-                                         T.Aext, T.Bext, T.Px, T.Sx);
+    k_make_aext<<<g, th, 0, c.stream>>>(c.n, T.n_pad, T.qn64, T.qerr, T.qnorm, T.qmax, gamma_for(T.DP), c.nv64, T.Aext,
+                                        T.Bext, T.Px);
     return cudaGetLastError();
 }
 
@@ -2326,10 +1959,10 @@ cudaError_t tc_setup(Ctx &c, int prec) {
         cudaError_t e;
         void **bufs[] = {(void **)&T.Vq,   (void **)&T.Vq2,  (void **)&T.Aext,  (void **)&T.Bext,
                          (void **)&T.Cq,   (void **)&T.Cqx,  (void **)&T.qn64,  (void **)&T.qerr,
-                         (void **)&T.qnorm, (void **)&T.qmax, (void **)&T.Px,   (void **)&T.Sx};
+                         (void **)&T.qnorm, (void **)&T.qmax, (void **)&T.Px};
         const size_t sizes[] = {rows * T.DP * 2, rows * T.DP * 2, rows * KEXT * 2, rows * KEXT * 2,
                                 rows * T.DP * 2, rows * KEXT * 2, rows * 8,        rows * 4,
-                                rows * 4,        2 * 4,           rows * KEXT * 2, (rows + 1) * KEXT * 2};
+                                rows * 4,        2 * 4,           rows * KEXT * 2};
         for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i)
             if ((e = pool_alloc(bufs[i], sizes[i], c.stream, c.device)) != cudaSuccess) {
                 // leave no half-built set: the next call allocates all of them again
@@ -2487,79 +2120,6 @@ cudaError_t launch_gains_tc_group(const GroupInst *d_inst, const GroupUnit *d_un
     return cudaGetLastError();
 }
 
-bool tc_sets_device_planned(const Ctx &c) { return c.tc.prec >= 0 && !use_kb(c, 2 * c.tc.DP); }
-
-cudaError_t launch_eval_sets_tc_dev(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, double *out_f,
-                                    int64_t *nlaunch) {
-    Ctx::Tc &T = c.tc;
-    *nlaunch = 0;
-    if (l <= 0) return cudaSuccess;
-    const int RB = 2 * T.DP;
-    int na = 0, ns = 0;
-    pick_pipeline(RB, &na, &ns);
-    if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = smem_layout(RB, ns, na);
-    cudaError_t e = allow_smem((const void *)k_sets_tc_g, L.total);
-    if (e != cudaSuccess) return e;
-    const int npu = (int)(T.n_pad / BM);
-    const int64_t rows = (int64_t)npu * 8;  // partial rows: (point unit, epilogue warp)
-    const int64_t lbmax = std::min<int64_t>(l, std::min<int64_t>(c.set_part_cap / rows, (int64_t)1 << 30));
-    if (lbmax < 1) return cudaErrorMemoryAllocation;
-    if (T.sp_cap < lbmax) {
-        void *old[] = {T.sp_beg, T.sp_set, T.sp_chunk, T.sp_cnt};
-        for (void *p : old) pool_free(p, c.stream);
-        T.sp_beg = nullptr;
-        T.sp_set = T.sp_chunk = T.sp_cnt = nullptr;
-        T.sp_cap = 0;
-        void **bufs[] = {(void **)&T.sp_beg, (void **)&T.sp_set, (void **)&T.sp_chunk, (void **)&T.sp_cnt};
-        const size_t sizes[] = {(size_t)(lbmax + 1) * 8, (size_t)lbmax * 4, (size_t)(lbmax + 1) * 4, 4 * 4};
-        for (size_t i = 0; i < 4; ++i)
-            if ((e = pool_alloc(bufs[i], sizes[i], c.stream, c.device)) != cudaSuccess) {
-                for (size_t j = 0; j < i; ++j) {
-                    pool_free(*bufs[j], c.stream);
-                    *bufs[j] = nullptr;
-                }
-                return e;
-            }
-        T.sp_cap = lbmax;
-    }
-    const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
-    SetsGArgs a{};
-    a.idx = idx;
-    a.Vq2 = T.Vq2;
-    a.Sx = T.Sx;
-    a.beg = T.sp_beg;
-    a.set = T.sp_set;
-    a.chunk = T.sp_chunk;
-    a.cnt = T.sp_cnt;
-    a.partial = c.set_part;
-    a.err = &c.st->err;
-    a.n = c.n;
-    a.n_pad = (int)T.n_pad;
-    a.DP = T.DP;
-    a.npu = npu;
-    a.nstages = ns;
-    a.na = na;
-    a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, BN);
-    a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
-    a.wait_ns = wait_limit_ns();
-    for (int64_t j0 = 0; j0 < l; j0 += lbmax) {
-        const int64_t lb = std::min(lbmax, l - j0);
-        k_sets_plan<<<1, SP_T, 0, c.stream>>>(idx, off + j0, lb, j0 == 0 ? 0 : -1, T.sp_beg, T.sp_set, T.sp_chunk,
-                                              T.sp_cnt, &c.st->err);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        // sets that no warp finishes (empty sets) keep a zero partial
-        if ((e = cudaMemsetAsync(c.set_part, 0, sizeof(double) * rows * lb, c.stream)) != cudaSuccess) return e;
-        a.off = off + j0;
-        a.lb = lb;
-        k_sets_tc_g<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = launch_sets_finalize(c, rows, lb, j0, l, out_f)) != cudaSuccess) return e;
-        *nlaunch += 3;
-    }
-    return cudaSuccess;
-}
-
 // Bulk upper bounds of a candidate list whose length is on the device (the
 // lazy Greedy round): rows gathered for at most m_cap entries, the plan
 // (chunks) derived inside the kernel, the chunk count left in
@@ -2613,104 +2173,101 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
 // units are (256 points, chunk); set partials [point unit][warp][set] are
 // reduced in a fixed order by k_sets_finalize.  Sets are processed in batches whose
 // partials fit the scratch.
-cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_dev, const int64_t *off_host,
-                                int64_t l, double *out_f, int64_t *nlaunch) {
+// Buffers of the multi-set evaluation for up to `sets` sets with `members`
+// members in all (padded columns <= members + 15 sets).
+cudaError_t tc_sets_reserve(Ctx &c, int64_t sets, int64_t members) {
     Ctx::Tc &T = c.tc;
-    *nlaunch = 0;
-    std::vector<int64_t> aux((size_t)l + 1);
-    aux[0] = 0;
-    for (int64_t j = 0; j < l; ++j) {
-        const int64_t sz = off_host[j + 1] - off_host[j];
-        aux[j + 1] = aux[j] + (sz + SET_GROUP - 1) / SET_GROUP * SET_GROUP;
-    }
-    const int64_t ncols = aux[l];
-    if (ncols > ((int64_t)1 << 30)) return cudaErrorInvalidValue;
-    const size_t chunk0 = aux.size();
-    int64_t sb = 0, cb = 0;
-    for (int64_t j = 0; j < l; ++j) {
-        const int64_t ps = aux[j + 1] - aux[j];
-        if (j > sb && (j - sb == SETS_PER_CHUNK || aux[j] - cb + ps > CHUNK_COLS)) {
-            aux.insert(aux.end(), {sb, j, cb, aux[j]});
-            sb = j;
-            cb = aux[j];
-        }
-    }
-    aux.insert(aux.end(), {sb, l, cb, ncols});
-    const int64_t nch = (int64_t)(aux.size() - chunk0) / 4;
-    std::vector<int> gset((size_t)(ncols / SET_GROUP));
-    for (int64_t k = 0; k < nch; ++k) {
-        const int64_t *rec = aux.data() + chunk0 + 4 * k;
-        for (int64_t j = rec[0]; j < rec[1]; ++j) {
-            const int64_t g0 = aux[j] / SET_GROUP, g1 = aux[j + 1] / SET_GROUP;
-            for (int64_t g = g0; g < g1; ++g) gset[g] = (int)(2 * (j - rec[0]) + (g == g1 - 1 ? 1 : 0));
-        }
-    }
-    // scratch
-    const int64_t rows_need = std::max<int64_t>((ncols + BN - 1) / BN * BN, BN);
     cudaError_t e;
-    if (T.mcap < rows_need) {
+    const int64_t cols = std::max<int64_t>((members + 15 * sets + BN - 1) / BN * BN, BN);
+    if (T.mcap < cols) {
         pool_free(T.Mq, c.stream);
         pool_free(T.Mx, c.stream);
         pool_free(T.gset, c.stream);
         T.Mq = T.Mx = nullptr;
         T.gset = nullptr;
         T.mcap = 0;
-        const int64_t cap = std::max<int64_t>(rows_need, T.n_pad);
-        if ((e = pool_alloc((void **)&T.Mq, (size_t)cap * T.DP * 2, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.Mx, (size_t)cap * KEXT * 2, c.stream, c.device)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&T.gset, (size_t)cap / SET_GROUP * 4, c.stream, c.device)) != cudaSuccess) return e;
-        T.mcap = cap;
+        if ((e = pool_alloc((void **)&T.Mq, (size_t)cols * T.DP * 2, c.stream, c.device)) != cudaSuccess ||
+            (e = pool_alloc((void **)&T.Mx, (size_t)cols * KEXT * 2, c.stream, c.device)) != cudaSuccess ||
+            (e = pool_alloc((void **)&T.gset, (size_t)cols / SET_GROUP * 4, c.stream, c.device)) != cudaSuccess) {
+            pool_free(T.Mq, c.stream);
+            pool_free(T.Mx, c.stream);
+            T.Mq = T.Mx = nullptr;
+            T.gset = nullptr;
+            return e;
+        }
+        T.mcap = cols;
     }
-    if (T.aux_cap < (int64_t)aux.size()) {
-        pool_free(T.sets_aux, c.stream);
-        T.sets_aux = nullptr;
-        T.aux_cap = 0;
-        const int64_t cap = std::max<int64_t>((int64_t)aux.size(), 4096);
-        if ((e = pool_alloc((void **)&T.sets_aux, (size_t)cap * 8, c.stream, c.device)) != cudaSuccess) return e;
-        T.aux_cap = cap;
+    if (T.sp_sets < sets) {
+        void *old[] = {T.sp_aux, T.sp_rec, T.sp_cj};
+        for (void *p : old) pool_free(p, c.stream);
+        T.sp_aux = T.sp_rec = nullptr;
+        T.sp_cj = nullptr;
+        T.sp_sets = 0;
+        if ((e = pool_alloc((void **)&T.sp_aux, (size_t)(sets + 1) * 8, c.stream, c.device)) != cudaSuccess ||
+            (e = pool_alloc((void **)&T.sp_rec, (size_t)(sets + 1) * 32, c.stream, c.device)) != cudaSuccess ||
+            (e = pool_alloc((void **)&T.sp_cj, (size_t)sets * 4, c.stream, c.device)) != cudaSuccess) {
+            pool_free(T.sp_aux, c.stream);
+            pool_free(T.sp_rec, c.stream);
+            T.sp_aux = T.sp_rec = nullptr;
+            T.sp_cj = nullptr;
+            return e;
+        }
+        T.sp_sets = sets;
     }
-    // pageable sources: the copies return once the data is staged
-    if ((e = cudaMemcpyAsync(T.sets_aux, aux.data(), aux.size() * 8, cudaMemcpyHostToDevice, c.stream)) != cudaSuccess)
-        return e;
-    if (!gset.empty() &&
-        (e = cudaMemcpyAsync(T.gset, gset.data(), gset.size() * 4, cudaMemcpyHostToDevice, c.stream)) != cudaSuccess)
-        return e;
-    const bool bf = T.prec == EBC_BF16;
-    CUtensorMap tmM, tmMx;
-    if ((e = make_map(&tmM, T.Mq, T.mcap, T.DP, bf, KATOM, BN, CU_TENSOR_MAP_SWIZZLE_128B)) != cudaSuccess) return e;
-    if ((e = make_map(&tmMx, T.Mx, T.mcap, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess) return e;
-    if (ncols > 0) {
-        const int64_t tot = ncols * (T.DP / 8 + 2);
-        k_gather_members<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(
-            T.Vq2, T.qn64, c.n, T.DP, idx, off_dev, T.sets_aux, l, ncols, T.Mq, T.Mx, &c.st->err);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        *nlaunch += 1;
-    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off, int64_t l, int64_t members,
+                                double *out_f, int64_t *nlaunch) {
+    Ctx::Tc &T = c.tc;
+    *nlaunch = 0;
+    if (l <= 0) return cudaSuccess;
     const bool kb = use_kb(c, 2 * T.DP);
     int na = 1, ns = KB_STAGES;
     if (!kb) pick_pipeline(2 * T.DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
     const SmemLayout L = kb ? smem_layout_kb(ns) : smem_layout(2 * T.DP, ns, na);
     const void *kfn = kb ? (const void *)k_sets_tc_kb : (const void *)k_sets_tc;
-    if ((e = allow_smem(kfn, L.total)) != cudaSuccess) return e;
+    cudaError_t e = allow_smem(kfn, L.total);
+    if (e != cudaSuccess) return e;
     const int npu = (int)(T.n_pad / BM);
     const int64_t rows = (int64_t)npu * 8;  // partial rows: (point unit, epilogue warp)
-    const int64_t max_sets = c.set_part_cap / rows;
-    int64_t chunk_sets = 0;  // every chunk's partials must fit one launch
-    for (int64_t k = 0; k < nch; ++k) chunk_sets = std::max(chunk_sets, aux[chunk0 + 4 * k + 1] - aux[chunk0 + 4 * k]);
-    if (max_sets < chunk_sets) return cudaErrorMemoryAllocation;
+    const int64_t lbmax = std::min<int64_t>(l, c.set_part_cap / rows);
+    if (lbmax < 1) return cudaErrorMemoryAllocation;
+    const int64_t nbatch = (l + lbmax - 1) / lbmax;
+    if ((e = tc_sets_reserve(c, l, members)) != cudaSuccess) return e;
+    if (T.sp_batches < nbatch + 1) {
+        pool_free(T.sp_bf, c.stream);
+        T.sp_bf = nullptr;
+        T.sp_batches = 0;
+        if ((e = pool_alloc((void **)&T.sp_bf, (size_t)(nbatch + 1) * 4, c.stream, c.device)) != cudaSuccess) return e;
+        T.sp_batches = nbatch + 1;
+    }
+    const bool bf = T.prec == EBC_BF16;
+    CUtensorMap tmM, tmMx;
+    if ((e = make_map(&tmM, T.Mq, T.mcap, T.DP, bf, KATOM, BN, CU_TENSOR_MAP_SWIZZLE_128B)) != cudaSuccess) return e;
+    if ((e = make_map(&tmMx, T.Mx, T.mcap, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess) return e;
+    // the plan, the group table and the member rows, all on the device
+    k_sets_plan<<<1, SP_T, 0, c.stream>>>(idx, off, l, lbmax, T.mcap, T.sp_aux, T.sp_rec, T.sp_cj, T.sp_bf, nbatch,
+                                          &c.st->err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const unsigned gs = (unsigned)std::max(1, c.num_sms * 4);
+    k_sets_gset<<<gs, 256, 0, c.stream>>>(T.sp_aux, l, T.sp_rec, T.sp_cj, T.mcap / SET_GROUP, T.gset);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_gather_members<<<gs * 2, 256, 0, c.stream>>>(T.Vq2, T.qn64, c.n, T.DP, idx, off, T.sp_aux, l, T.mcap, T.Mq,
+                                                   T.Mx, &c.st->err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *nlaunch += 3;
     const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
-    for (int64_t k0 = 0; k0 < nch;) {
-        const int64_t j0 = aux[chunk0 + 4 * k0];
-        int64_t k1 = k0 + 1;
-        while (k1 < nch && aux[chunk0 + 4 * k1 + 1] - j0 <= max_sets) ++k1;
-        const int64_t lb = aux[chunk0 + 4 * (k1 - 1) + 1] - j0;
+    for (int64_t b = 0; b < nbatch; ++b) {
+        const int64_t j0 = b * lbmax;
+        const int64_t lb = std::min(lbmax, l - j0);
         TcArgs a{};
         a.wait_ns = wait_limit_ns();
         a.m = 0;
         a.n_vtiles = 0;
         a.n_ctiles = npu;
-        a.nchunks = (int)(k1 - k0);
+        a.nchunks = 0;  // from the device plan (sets_bf)
         a.vt_per_chunk = 0;
         a.RB = 2 * T.DP;
         a.xatom = KATOM;
@@ -2721,23 +2278,21 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off_d
         a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
         a.partial = c.set_part;
         a.err = &c.st->err;
-        a.chunks = T.sets_aux + chunk0 + 4 * k0;
+        a.chunks = T.sp_rec;
         a.gset = T.gset;
         a.lb = lb;
         a.j0 = j0;
-        const int64_t units = (int64_t)npu * a.nchunks;
-        if (units > INT32_MAX) return cudaErrorInvalidValue;
-        const int grid = (int)std::min<int64_t>(units, G);
+        a.sets_bf = T.sp_bf;
+        a.sets_batch = (int)b;
         // empty sets get no partial from any warp
         if ((e = cudaMemsetAsync(c.set_part, 0, sizeof(double) * rows * lb, c.stream)) != cudaSuccess) return e;
         if (kb)
-            k_sets_tc_kb<<<grid, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
+            k_sets_tc_kb<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
         else
-            k_sets_tc<<<grid, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
+            k_sets_tc<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = launch_sets_finalize(c, rows, lb, j0, l, out_f)) != cudaSuccess) return e;
         *nlaunch += 2;
-        k0 = k1;
     }
     return cudaSuccess;
 }

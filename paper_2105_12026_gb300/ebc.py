@@ -107,6 +107,7 @@ _SIGS = {
     "ebc_sync": [_P],
     "ebc_get_stats": [_P, ctypes.POINTER(ebc_stats)],
     "ebc_current_f": [_P, ctypes.POINTER(ctypes.c_double)],
+    "ebc_reserve_sets": [_P, _I64, _I64],
     "ebc_last_round_candidates": [_P, _P, _I64, ctypes.POINTER(_I64)],
     "ebc_last_error": [_P],
     "ebc_eval_sets_noalloc": [_P, _I64, _I32, _P, _P, _I64, _P, _P],
@@ -518,6 +519,11 @@ class Instance:
 
     def last_round_candidates(self) -> np.ndarray:
         return ebc_last_round_candidates(self.h)
+
+    def reserve_sets(self, max_sets: int, max_members: int):
+        """Buffers of ebc_eval_sets for up to max_sets sets / max_members members
+        (tensor-core precisions): such calls read nothing back to the host."""
+        _raise(self.h, load().ebc_reserve_sets(_P(self.h), int(max_sets), int(max_members)))
 
     def gain_bounds_host(self, cand=None) -> np.ndarray:
         """Rigorous upper bounds of the gains of ``cand`` (all points if None)

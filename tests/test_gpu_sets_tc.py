@@ -178,11 +178,12 @@ def test_sets_tc_multiset_workload_sampled(torch):
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_sets_tc_device_plan_async_and_capturable(torch, prec):
-    """At d <= 128 the set plan is made on the device: the call reads nothing
-    back to the host, so it can be captured in a CUDA graph; the replay gives
-    the same values as the direct call, which equal the K-blocked kernel's
-    (planned on the host) bitwise, and cover empty sets, sets spanning many
-    tiles and several chunks."""
+    """The set plan is made on the device; with a reservation the call reads
+    nothing back to the host, so it can be captured in a CUDA graph.  The
+    replay gives the same values as the direct call, which equal the
+    K-blocked kernel's bitwise (the same MMA sequence), across empty sets,
+    sets spanning many tiles and several chunks; a call with more members
+    than the reservation holds is rejected on the device."""
     rng = np.random.default_rng(21)
     n, d = 20_000, 48
     V = synth.zscore_to_f32(rng.standard_normal((n, d)))
@@ -196,6 +197,7 @@ def test_sets_tc_device_plan_async_and_capturable(torch, prec):
     l = sizes.size
     s = torch.cuda.Stream()
     with ebc.Instance(V, precision=prec, stream=s) as inst:
+        inst.reserve_sets(l, int(off[-1]))
         idx_d, off_d = torch.from_numpy(idx).cuda(), torch.from_numpy(off).cuda()
         out = torch.zeros(l, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
@@ -213,6 +215,15 @@ def test_sets_tc_device_plan_async_and_capturable(torch, prec):
         replay = out.cpu().numpy().copy()
         inst.set_kblocked(True)
         kb = inst.eval_sets_host(idx, off)
+        inst.set_kblocked(False)
+        # more members than the buffers hold: EINVAL from the device plan
+        inst.reserve_sets(2, 16)
+        big = torch.from_numpy(np.array([0, 20000, 40000], np.int64)).cuda()
+        many = torch.zeros(40000, dtype=torch.int32, device="cuda")
+        ebc.ebc_eval_sets(inst.h, many.data_ptr(), big.data_ptr(), 2, out.data_ptr())
+        with pytest.raises(ebc.EbcError) as ei:
+            inst.sync()
+        assert ei.value.status == ebc.EBC_EINVAL
     np.testing.assert_array_equal(replay, direct)
     np.testing.assert_array_equal(direct, kb)
     assert np.all(direct[sizes == 0] == 0.0)
