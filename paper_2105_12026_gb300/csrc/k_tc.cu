@@ -657,10 +657,20 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
             const int64_t set_b = rec[0], col_e = rec[3];
             double *prow = args.partial + ((int64_t)at * 8 + ew) * args.lb + (set_b - args.j0);
             float run = -INFINITY;
+            // group table entries of the next tile are loaded one tile ahead
+            int ge_next = lane < (int)(min((int64_t)BN, col_e - b_row0) / SET_GROUP)
+                              ? __ldg(args.gset + b_row0 / SET_GROUP + lane)
+                              : 0;
             for (int i = 0; i < nb; ++i, ++t) {
                 const int64_t c0 = (int64_t)b_row0 + (int64_t)i * BN;
                 const int ngr = (int)(min((int64_t)BN, col_e - c0) / SET_GROUP);
-                const int ge = lane < ngr ? __ldg(args.gset + c0 / SET_GROUP + lane) : 0;
+                const int ge = ge_next;
+                if (i + 1 < nb) {
+                    const int64_t c1 = c0 + BN;
+                    ge_next = lane < (int)(min((int64_t)BN, col_e - c1) / SET_GROUP)
+                                  ? __ldg(args.gset + c1 / SET_GROUP + lane)
+                                  : 0;
+                }
                 const unsigned lastmask = __ballot_sync(0xffffffffu, lane < ngr && (ge & 1));  // groups ending a set
                 if (alive) {
                     const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag, wait_ns));
