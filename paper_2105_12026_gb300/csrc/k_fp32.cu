@@ -24,111 +24,180 @@ constexpr int TV = 128;  // points per block tile
 constexpr int KC = 16;   // dimensions per smem stage
 }  // namespace
 
-// 256 threads: tx = tid % 16 covers 8 points (two runs of 4), ty = tid / 16
-// covers 4 candidates.
-__global__ void __launch_bounds__(256) k_gains_fp32(const float *__restrict__ V, int64_t n, int d,
-                                                    const double *__restrict__ m64, const int *__restrict__ cand,
-                                                    int64_t m, int upper, float k1, int64_t chunk,
-                                                    double *__restrict__ partial) {
-    __shared__ __align__(16) float Cs[KC][TC];
-    __shared__ __align__(16) float Vs[KC][TV];
-    __shared__ float Ms[TV];
-    __shared__ int Ci[TC];
+// 256 threads, a tile of 128 candidates x 128 points: tx = tid % 16 covers 8
+// points (two runs of 4), ty = tid / 16 covers 8 candidates (two runs of 4),
+// 64 FP32 accumulators per thread.  Dimensions are staged 16 at a time in
+// shared memory (dimension-major), double-buffered through registers: the
+// next stage's global loads are issued before the current stage's
+// arithmetic and stored to the other buffer after it, one barrier per
+// stage.  Per (candidate, point) the arithmetic is the FMA chain over the
+// dimensions in index order, and per candidate and point tile the 8 terms
+// of a thread are summed in FP32, then the 16 lanes, then tiles in FP64.
+namespace {
+constexpr int FC = 128;  // candidates per block
+constexpr int FV = 128;  // points per block tile
+constexpr int FK = 16;   // dimensions per stage
+
+template <bool VEC>
+__device__ __forceinline__ void fp32_stage_load(const float *__restrict__ V, int d, const int *Ci, int64_t v0,
+                                                int64_t ve, int k0, int tid, float4 (&cr)[2], float4 (&vr)[2]) {
+    // 128 rows x 16 dimensions of each operand = 512 float4 pieces: two per thread
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int e = tid + 256 * s;
+        const int r = e >> 2, kq = (e & 3) * 4;
+        const int ci = Ci[r];
+        const int64_t v = v0 + r;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (VEC) {  // d % 4 == 0: a piece is inside the row or wholly past it
+            if (k0 + kq < d) {
+                if (ci >= 0) x = *reinterpret_cast<const float4 *>(V + (int64_t)ci * d + k0 + kq);
+                if (v < ve) y = *reinterpret_cast<const float4 *>(V + v * d + k0 + kq);
+            }
+        } else {
+            float xs[4] = {0.f, 0.f, 0.f, 0.f}, ys[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (k0 + kq + i < d) {
+                    if (ci >= 0) xs[i] = V[(int64_t)ci * d + k0 + kq + i];
+                    if (v < ve) ys[i] = V[v * d + k0 + kq + i];
+                }
+            x = make_float4(xs[0], xs[1], xs[2], xs[3]);
+            y = make_float4(ys[0], ys[1], ys[2], ys[3]);
+        }
+        cr[s] = x;
+        vr[s] = y;
+    }
+}
+
+__device__ __forceinline__ void fp32_stage_store(float (*Cs)[FC], float (*Vs)[FV], int tid, const float4 (&cr)[2],
+                                                 const float4 (&vr)[2]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int e = tid + 256 * s;
+        const int r = e >> 2, kq = (e & 3) * 4;
+        Cs[kq][r] = cr[s].x;
+        Cs[kq + 1][r] = cr[s].y;
+        Cs[kq + 2][r] = cr[s].z;
+        Cs[kq + 3][r] = cr[s].w;
+        Vs[kq][r] = vr[s].x;
+        Vs[kq + 1][r] = vr[s].y;
+        Vs[kq + 2][r] = vr[s].z;
+        Vs[kq + 3][r] = vr[s].w;
+    }
+}
+}  // namespace
+
+template <bool VEC>
+__global__ void __launch_bounds__(256, 1) k_gains_fp32(const float *__restrict__ V, int64_t n, int d,
+                                                       const double *__restrict__ m64, const int *__restrict__ cand,
+                                                       int64_t m, int upper, float k1, int64_t chunk,
+                                                       double *__restrict__ partial) {
+    __shared__ __align__(16) float Cs[2][FK][FC];
+    __shared__ __align__(16) float Vs[2][FK][FV];
+    __shared__ float Ms[2][FV];
+    __shared__ int Ci[FC];
+    __shared__ double Accd[8][256];  // per thread: the FP64 sums over point tiles (kept out of registers)
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int64_t c0 = (int64_t)blockIdx.x * TC;
+    const int64_t c0 = (int64_t)blockIdx.x * FC;
     const int q = blockIdx.y;
     const int64_t vb = (int64_t)q * chunk;
     const int64_t ve = lmin(vb + chunk, n);
+    const int nks = (d + FK - 1) / FK;                        // stages per point tile
+    const int nvt = (int)((ve - vb + FV - 1) / FV);           // point tiles of the chunk
+    const int nst = nvt * nks;                                // stages in all
 
-    if (tid < TC) {
-        int64_t j = c0 + tid;
+    if (tid < FC) {
+        const int64_t j = c0 + tid;
         Ci[tid] = j < m ? (cand ? cand[j] : (int)j) : -1;
     }
-    double accd[4] = {0.0, 0.0, 0.0, 0.0};
-
-    for (int64_t v0 = vb; v0 < ve; v0 += TV) {
-        __syncthreads();
-        if (tid < TV) {
-            int64_t v = v0 + tid;
+    __syncthreads();
+    auto load_m = [&](int vt, int buf) {
+        if (tid < FV) {
+            const int64_t v = vb + (int64_t)vt * FV + tid;
             float mv = -INFINITY;
             if (v < ve) {
-                double md = m64[v];
+                const double md = m64[v];
                 mv = upper ? __double2float_ru(md) : __double2float_rn(md);
             }
-            Ms[tid] = mv;
+            Ms[buf][tid] = mv;
         }
-        float acc[4][8];
+    };
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i) Accd[i][tid] = 0.0;
+    float acc[8][8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-        for (int k0 = 0; k0 < d; k0 += KC) {
-            __syncthreads();
-            // candidates: TC x KC values, 4 per thread
-#pragma unroll
-            for (int s = 0; s < (TC * KC) / 256; ++s) {
-                int e = tid + 256 * s;
-                int r = e / KC, kk = e % KC;
-                int ci = Ci[r];
-                float x = 0.f;
-                if (ci >= 0 && k0 + kk < d) x = V[(int64_t)ci * d + k0 + kk];
-                Cs[kk][r] = x;
-            }
-            // points: TV x KC values, 8 per thread
-#pragma unroll
-            for (int s = 0; s < (TV * KC) / 256; ++s) {
-                int e = tid + 256 * s;
-                int r = e / KC, kk = e % KC;
-                int64_t v = v0 + r;
-                float x = 0.f;
-                if (v < ve && k0 + kk < d) x = V[v * d + k0 + kk];
-                Vs[kk][r] = x;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < KC; ++kk) {
-                float4 c4 = *reinterpret_cast<const float4 *>(&Cs[kk][ty * 4]);
-                float4 va = *reinterpret_cast<const float4 *>(&Vs[kk][tx * 4]);
-                float4 vb4 = *reinterpret_cast<const float4 *>(&Vs[kk][64 + tx * 4]);
-                float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-                float vv[8] = {va.x, va.y, va.z, va.w, vb4.x, vb4.y, vb4.z, vb4.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float df = vv[j] - cv[i];
-                        acc[i][j] = fmaf(df, df, acc[i][j]);
-                    }
-            }
-        }
-        // epilogue for this V tile
-        float mv[8];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            mv[j] = Ms[tx * 4 + j];
-            mv[4 + j] = Ms[64 + tx * 4 + j];
+    float4 cr[2], vr[2];
+    if (nst > 0) {
+        fp32_stage_load<VEC>(V, d, Ci, vb, ve, 0, tid, cr, vr);
+        fp32_stage_store(Cs[0], Vs[0], tid, cr, vr);
+        load_m(0, 0);
+    }
+    __syncthreads();
+    for (int st = 0; st < nst; ++st) {
+        const int vt = st / nks, ks = st % nks;
+        const int buf = st & 1;
+        const bool more = st + 1 < nst;
+        if (more) {
+            const int vt1 = (st + 1) / nks, ks1 = (st + 1) % nks;
+            fp32_stage_load<VEC>(V, d, Ci, vb + (int64_t)vt1 * FV, ve, ks1 * FK, tid, cr, vr);
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float s = 0.f;
+        for (int kk = 0; kk < FK; ++kk) {
+            const float4 ca = *reinterpret_cast<const float4 *>(&Cs[buf][kk][ty * 4]);
+            const float4 cb = *reinterpret_cast<const float4 *>(&Cs[buf][kk][64 + ty * 4]);
+            const float4 va = *reinterpret_cast<const float4 *>(&Vs[buf][kk][tx * 4]);
+            const float4 vb4 = *reinterpret_cast<const float4 *>(&Vs[buf][kk][64 + tx * 4]);
+            const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+            const float vv[8] = {va.x, va.y, va.z, va.w, vb4.x, vb4.y, vb4.z, vb4.w};
 #pragma unroll
-            for (int j = 0; j < 8; ++j) s += fmaxf(0.f, fmaf(-k1, acc[i][j], mv[j]));
-            // the 16 lanes with the same ty hold the other points of this tile
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            s += __shfl_xor_sync(0xffffffffu, s, 4);
-            s += __shfl_xor_sync(0xffffffffu, s, 8);
-            accd[i] += (double)s;
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float df = vv[j] - cv[i];
+                    acc[i][j] = fmaf(df, df, acc[i][j]);
+                }
         }
+        if (ks == nks - 1) {
+            // the point tile is complete: relu terms, summed as described above
+            const int mb = vt & 1;
+            float mv[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                mv[j] = Ms[mb][tx * 4 + j];
+                mv[4 + j] = Ms[mb][64 + tx * 4 + j];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float s = 0.f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) s += fmaxf(0.f, fmaf(-k1, acc[i][j], mv[j]));
+                s += __shfl_xor_sync(0xffffffffu, s, 1);
+                s += __shfl_xor_sync(0xffffffffu, s, 2);
+                s += __shfl_xor_sync(0xffffffffu, s, 4);
+                s += __shfl_xor_sync(0xffffffffu, s, 8);
+                Accd[i][tid] += (double)s;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            }
+        }
+        if (more) {
+            fp32_stage_store(Cs[buf ^ 1], Vs[buf ^ 1], tid, cr, vr);
+            if ((st + 1) % nks == 0) load_m((st + 1) / nks, ((st + 1) / nks) & 1);
+        }
+        __syncthreads();
     }
     if (tx == 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int64_t j = c0 + ty * 4 + i;
-            if (j < m) partial[(int64_t)q * m + j] = accd[i];
+        for (int i = 0; i < 8; ++i) {
+            const int64_t j = c0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+            if (j < m) partial[(int64_t)q * m + j] = Accd[i][tid];
         }
     }
 }
@@ -141,8 +210,13 @@ cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, in
         k1 = (float)want;
         if ((double)k1 > want) k1 = nextafterf(k1, 0.f);  // round down
     }
-    dim3 grid((unsigned)((m + TC - 1) / TC), (unsigned)nchunks);
-    k_gains_fp32<<<grid, 256, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, cand, m, upper ? 1 : 0, k1, chunk, c.partial);
+    dim3 grid((unsigned)((m + FC - 1) / FC), (unsigned)nchunks);
+    if (c.d % 4 == 0)
+        k_gains_fp32<true><<<grid, 256, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, cand, m, upper ? 1 : 0, k1, chunk,
+                                                       c.partial);
+    else
+        k_gains_fp32<false><<<grid, 256, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, cand, m, upper ? 1 : 0, k1, chunk,
+                                                        c.partial);
     return cudaGetLastError();
 }
 
