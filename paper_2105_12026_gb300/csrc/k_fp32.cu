@@ -70,6 +70,28 @@ __device__ __forceinline__ void fp32_stage_load(const float *__restrict__ V, int
     }
 }
 
+// Packed FP32 pairs (sm_100+ f32x2 instructions): each element is computed
+// and rounded exactly as the scalar instruction would.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long x, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 __device__ __forceinline__ void fp32_stage_store(float (*Cs)[FC], float (*Vs)[FV], int tid, const float4 (&cr)[2],
                                                  const float4 (&vr)[2]) {
 #pragma unroll
@@ -127,11 +149,12 @@ __global__ void __launch_bounds__(256, 1) k_gains_fp32(const float *__restrict__
     };
 #pragma unroll
     for (int i = 0; i < 8; ++i) Accd[i][tid] = 0.0;
-    float acc[8][8];
+    // acc[i][p]: candidate i against the point pair p (points 2p, 2p + 1 of the thread's 8)
+    unsigned long long acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int p = 0; p < 4; ++p) acc[i][p] = 0ull;
 
     float4 cr[2], vr[2];
     if (nst > 0) {
@@ -152,17 +175,19 @@ __global__ void __launch_bounds__(256, 1) k_gains_fp32(const float *__restrict__
         for (int kk = 0; kk < FK; ++kk) {
             const float4 ca = *reinterpret_cast<const float4 *>(&Cs[buf][kk][ty * 4]);
             const float4 cb = *reinterpret_cast<const float4 *>(&Cs[buf][kk][64 + ty * 4]);
-            const float4 va = *reinterpret_cast<const float4 *>(&Vs[buf][kk][tx * 4]);
-            const float4 vb4 = *reinterpret_cast<const float4 *>(&Vs[buf][kk][64 + tx * 4]);
+            const ulonglong2 va = *reinterpret_cast<const ulonglong2 *>(&Vs[buf][kk][tx * 4]);
+            const ulonglong2 vb2 = *reinterpret_cast<const ulonglong2 *>(&Vs[buf][kk][64 + tx * 4]);
             const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-            const float vv[8] = {va.x, va.y, va.z, va.w, vb4.x, vb4.y, vb4.z, vb4.w};
+            const unsigned long long vv[4] = {va.x, va.y, vb2.x, vb2.y};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                const unsigned long long c2 = f2_pack(cv[i], cv[i]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float df = vv[j] - cv[i];
-                    acc[i][j] = fmaf(df, df, acc[i][j]);
+                for (int p = 0; p < 4; ++p) {
+                    const unsigned long long df = f2_sub(vv[p], c2);
+                    acc[i][p] = f2_fma(df, df, acc[i][p]);
                 }
+            }
         }
         if (ks == nks - 1) {
             // the point tile is complete: relu terms, summed as described above
@@ -175,16 +200,19 @@ __global__ void __launch_bounds__(256, 1) k_gains_fp32(const float *__restrict__
             }
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
+                float a[8];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) f2_unpack(acc[i][p], a[2 * p], a[2 * p + 1]);
                 float s = 0.f;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) s += fmaxf(0.f, fmaf(-k1, acc[i][j], mv[j]));
+                for (int j = 0; j < 8; ++j) s += fmaxf(0.f, fmaf(-k1, a[j], mv[j]));
                 s += __shfl_xor_sync(0xffffffffu, s, 1);
                 s += __shfl_xor_sync(0xffffffffu, s, 2);
                 s += __shfl_xor_sync(0xffffffffu, s, 4);
                 s += __shfl_xor_sync(0xffffffffu, s, 8);
                 Accd[i][tid] += (double)s;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+                for (int p = 0; p < 4; ++p) acc[i][p] = 0ull;
             }
         }
         if (more) {
