@@ -332,6 +332,9 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off, 
 // grow the multi-set buffers for `sets` sets of `members` members in all
 cudaError_t tc_sets_reserve(Ctx &c, int64_t sets, int64_t members);
 void tc_free(Ctx &c);
+// allow a kernel the per-CTA maximum of dynamic shared memory on the current
+// device (once per device and kernel); bytes is the launch's own size
+cudaError_t allow_smem(const void *kernel, uint32_t bytes);
 
 // ---- one persistent bulk launch over several handles (k_tc.cu, group.cu) ----
 // A handle's part of a shared Greedy round: its tensor maps (read by TMA from

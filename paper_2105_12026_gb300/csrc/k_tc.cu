@@ -1759,23 +1759,6 @@ void pick_pipeline(int RB, int *na, int *ns) {
             }
 }
 
-// Allow a kernel the largest dynamic shared memory any of its launches uses
-// (the per-CTA limit), once per (device, kernel): every launch then only
-// states its own size, whatever the order of launches with different sizes.
-cudaError_t allow_smem(const void *kernel, uint32_t bytes) {
-    if (bytes > (uint32_t)SMEM_LIMIT) return cudaErrorInvalidValue;
-    static std::mutex mu;
-    static std::vector<std::pair<int, const void *>> done;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lock(mu);
-    for (const auto &p : done)
-        if (p.first == dev && p.second == kernel) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
-    if (e == cudaSuccess) done.emplace_back(dev, kernel);
-    return e;
-}
 
 // Pipeline shape and chunk policy for a bulk launch: the largest shape that
 // fits shared memory, unless the tuning table (or the autotuner) says otherwise.
@@ -1809,6 +1792,24 @@ double gamma_for(int DP) { return ((double)(DP + KEXT) / 4.0 + 4.0) * ldexp(1.0,
 double gamma8_for(int DP) { return ldexp(1.0, -8) + gamma_for(DP); }
 
 }  // namespace
+
+// Allow a kernel the largest dynamic shared memory any of its launches uses
+// (the per-CTA limit), once per (device, kernel): every launch then only
+// states its own size, whatever the order of launches with different sizes.
+cudaError_t allow_smem(const void *kernel, uint32_t bytes) {
+    if (bytes > (uint32_t)SMEM_LIMIT) return cudaErrorInvalidValue;
+    static std::mutex mu;
+    static std::vector<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &p : done)
+        if (p.first == dev && p.second == kernel) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    if (e == cudaSuccess) done.emplace_back(dev, kernel);
+    return e;
+}
 
 // 16-bit tensor-core bulk bounds and multi-set evaluation: any d (K-blocked
 // above 128); the FP8 kernel keeps whole rows resident: d <= 128.
