@@ -121,8 +121,8 @@ __global__ void __launch_bounds__(256, 1) k_gains_fp32(const float *__restrict__
     auto Cs = reinterpret_cast<unsigned long long (*)[FK][FC]>(fsm);                     // [2][FK][FC]
     auto Vs = reinterpret_cast<float (*)[FK][FV]>(fsm + 2 * FK * FC * 8);                // [2][FK][FV]
     auto Accd = reinterpret_cast<double (*)[256]>(fsm + 2 * FK * FC * 8 + 2 * FK * FV * 4);  // [8][256]
-    __shared__ float Ms[2][FV];
-    __shared__ int Ci[FC];
+    auto Ms = reinterpret_cast<float (*)[FV]>(fsm + 2 * FK * FC * 8 + 2 * FK * FV * 4 + 8 * 256 * 8);  // [2][FV]
+    int *Ci = reinterpret_cast<int *>(fsm + 2 * FK * FC * 8 + 2 * FK * FV * 4 + 8 * 256 * 8 + 2 * FV * 4);  // [FC]
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -244,7 +244,7 @@ cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, in
         if ((double)k1 > want) k1 = nextafterf(k1, 0.f);  // round down
     }
     dim3 grid((unsigned)((m + FC - 1) / FC), (unsigned)nchunks);
-    const size_t smem = (size_t)2 * FK * FC * 8 + (size_t)2 * FK * FV * 4 + (size_t)8 * 256 * 8;
+    const size_t smem = (size_t)2 * FK * FC * 8 + (size_t)2 * FK * FV * 4 + (size_t)8 * 256 * 8 + 2 * FV * 4 + FC * 4;
     const void *kfn = c.d % 4 == 0 ? (const void *)k_gains_fp32<true> : (const void *)k_gains_fp32<false>;
     if (cudaError_t e = allow_smem(kfn, (uint32_t)smem); e != cudaSuccess) return e;
     if (c.d % 4 == 0)
