@@ -92,18 +92,16 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
     return r;
 }
 
-// Candidates are stored duplicated, (c, c) per 64-bit word, ready for the
-// packed arithmetic; points plainly.
-__device__ __forceinline__ void fp32_stage_store(unsigned long long (*Cs)[FC], float (*Vs)[FV], int tid,
-                                                 const float4 (&cr)[2], const float4 (&vr)[2]) {
+__device__ __forceinline__ void fp32_stage_store(float (*Cs)[FC], float (*Vs)[FV], int tid, const float4 (&cr)[2],
+                                                 const float4 (&vr)[2]) {
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const int e = tid + 256 * s;
         const int r = e >> 2, kq = (e & 3) * 4;
-        Cs[kq][r] = f2_pack(cr[s].x, cr[s].x);
-        Cs[kq + 1][r] = f2_pack(cr[s].y, cr[s].y);
-        Cs[kq + 2][r] = f2_pack(cr[s].z, cr[s].z);
-        Cs[kq + 3][r] = f2_pack(cr[s].w, cr[s].w);
+        Cs[kq][r] = cr[s].x;
+        Cs[kq + 1][r] = cr[s].y;
+        Cs[kq + 2][r] = cr[s].z;
+        Cs[kq + 3][r] = cr[s].w;
         Vs[kq][r] = vr[s].x;
         Vs[kq + 1][r] = vr[s].y;
         Vs[kq + 2][r] = vr[s].z;
@@ -118,11 +116,12 @@ __global__ void __launch_bounds__(256, 1) k_gains_fp32(const float *__restrict__
                                                        int64_t m, int upper, float k1, int64_t chunk,
                                                        double *__restrict__ partial) {
     extern __shared__ __align__(16) uint8_t fsm[];
-    auto Cs = reinterpret_cast<unsigned long long (*)[FK][FC]>(fsm);                     // [2][FK][FC]
-    auto Vs = reinterpret_cast<float (*)[FK][FV]>(fsm + 2 * FK * FC * 8);                // [2][FK][FV]
-    auto Accd = reinterpret_cast<double (*)[256]>(fsm + 2 * FK * FC * 8 + 2 * FK * FV * 4);  // [8][256]
-    auto Ms = reinterpret_cast<float (*)[FV]>(fsm + 2 * FK * FC * 8 + 2 * FK * FV * 4 + 8 * 256 * 8);  // [2][FV]
-    int *Ci = reinterpret_cast<int *>(fsm + 2 * FK * FC * 8 + 2 * FK * FV * 4 + 8 * 256 * 8 + 2 * FV * 4);  // [FC]
+    constexpr int OV = 2 * FK * FC * 4, OA = OV + 2 * FK * FV * 4, OM = OA + 8 * 256 * 8, OC = OM + 2 * FV * 4;
+    auto Cs = reinterpret_cast<float (*)[FK][FC]>(fsm);       // [2][FK][FC]
+    auto Vs = reinterpret_cast<float (*)[FK][FV]>(fsm + OV);  // [2][FK][FV]
+    auto Accd = reinterpret_cast<double (*)[256]>(fsm + OA);  // [8][256]
+    auto Ms = reinterpret_cast<float (*)[FV]>(fsm + OM);      // [2][FV]
+    int *Ci = reinterpret_cast<int *>(fsm + OC);              // [FC]
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -176,17 +175,15 @@ __global__ void __launch_bounds__(256, 1) k_gains_fp32(const float *__restrict__
         }
 #pragma unroll
         for (int kk = 0; kk < FK; ++kk) {
-            const ulonglong2 c01 = *reinterpret_cast<const ulonglong2 *>(&Cs[buf][kk][ty * 4]);
-            const ulonglong2 c23 = *reinterpret_cast<const ulonglong2 *>(&Cs[buf][kk][ty * 4 + 2]);
-            const ulonglong2 c45 = *reinterpret_cast<const ulonglong2 *>(&Cs[buf][kk][64 + ty * 4]);
-            const ulonglong2 c67 = *reinterpret_cast<const ulonglong2 *>(&Cs[buf][kk][64 + ty * 4 + 2]);
+            const float4 ca = *reinterpret_cast<const float4 *>(&Cs[buf][kk][ty * 4]);
+            const float4 cb = *reinterpret_cast<const float4 *>(&Cs[buf][kk][64 + ty * 4]);
             const ulonglong2 va = *reinterpret_cast<const ulonglong2 *>(&Vs[buf][kk][tx * 4]);
             const ulonglong2 vb2 = *reinterpret_cast<const ulonglong2 *>(&Vs[buf][kk][64 + tx * 4]);
-            const unsigned long long cv[8] = {c01.x, c01.y, c23.x, c23.y, c45.x, c45.y, c67.x, c67.y};
+            const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
             const unsigned long long vv[4] = {va.x, va.y, vb2.x, vb2.y};
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const unsigned long long c2 = cv[i];
+                const unsigned long long c2 = f2_pack(cv[i], cv[i]);
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     const unsigned long long df = f2_sub(vv[p], c2);
@@ -244,7 +241,7 @@ cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, in
         if ((double)k1 > want) k1 = nextafterf(k1, 0.f);  // round down
     }
     dim3 grid((unsigned)((m + FC - 1) / FC), (unsigned)nchunks);
-    const size_t smem = (size_t)2 * FK * FC * 8 + (size_t)2 * FK * FV * 4 + (size_t)8 * 256 * 8 + 2 * FV * 4 + FC * 4;
+    const size_t smem = (size_t)2 * FK * FC * 4 + (size_t)2 * FK * FV * 4 + (size_t)8 * 256 * 8 + 2 * FV * 4 + FC * 4;
     const void *kfn = c.d % 4 == 0 ? (const void *)k_gains_fp32<true> : (const void *)k_gains_fp32<false>;
     if (cudaError_t e = allow_smem(kfn, (uint32_t)smem); e != cudaSuccess) return e;
     if (c.d % 4 == 0)
