@@ -553,6 +553,10 @@ typedef struct {
     int64_t submitted, completed, active, queued;
     int64_t bytes_in_use, bytes_peak; /* estimated device bytes of admitted instances */
     int64_t rounds_issued;
+    int64_t evals_full;      /* completed instances: (candidate, point) pairs of full rounds,
+                                sum over rounds t of (n - t) n, whether or not the rounds were lazy */
+    int64_t evals_performed; /* completed instances: pairs the bulk kernels evaluated (lazy rounds
+                                bound only the candidates whose stale bound can still win) */
 } ebc_batch_info;
 
 /* max_slots concurrent instances, device_budget_bytes for their handles, K

@@ -21,7 +21,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "ebc_internal.cuh"
+#include "handle.cuh"
 
 struct ebc_batch_ctx {
     struct Req {
@@ -62,6 +62,7 @@ struct ebc_batch_ctx {
     int32_t max_large = 0;    // at most this many large instances at once (0 = no limit)
     int64_t budget = 0, used = 0, peak = 0;
     int64_t next_ticket = 1, submitted = 0, completed = 0, rounds = 0;
+    int64_t evals_full = 0, evals_performed = 0;
     std::deque<Req> queue;
     std::vector<Slot> slots;
     std::unordered_map<int64_t, Result> results;
@@ -126,6 +127,15 @@ void reap(ebc_batch_t b) {
         ebc_batch_ctx::Result r;
         r.status = q == cudaSuccess ? ebc_sync(s.h) : EBC_ECUDA;
         cudaGetLastError();
+        if (r.status == EBC_OK) {
+            ebc_stats hs;
+            if (ebc_get_stats(s.h, &hs) == EBC_OK) {
+                const int64_t n = s.h->c.n, k = s.k;
+                const int64_t full = (n * k - k * (k - 1) / 2) * n;  // sum over t < k of (n - t) n
+                b->evals_full += full;
+                b->evals_performed += hs.lazy ? hs.bulk_candidates * n : full;
+            }
+        }
         r.idx.assign(s.h_idx, s.h_idx + s.k);
         r.f.assign(s.h_f, s.h_f + s.k);
         b->results[s.ticket] = std::move(r);
@@ -354,6 +364,8 @@ ebc_status ebc_batch_stats(ebc_batch_t b, ebc_batch_info *out) {
     out->bytes_in_use = b->used;
     out->bytes_peak = b->peak;
     out->rounds_issued = b->rounds;
+    out->evals_full = b->evals_full;
+    out->evals_performed = b->evals_performed;
     return EBC_OK;
 }
 

@@ -50,7 +50,8 @@ class ebc_profile(ctypes.Structure):
 class ebc_batch_info(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("active", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64), ("bytes_peak", ctypes.c_int64),
-                ("rounds_issued", ctypes.c_int64)]
+                ("rounds_issued", ctypes.c_int64), ("evals_full", ctypes.c_int64),
+                ("evals_performed", ctypes.c_int64)]
 
 
 class ebc_sieve_state(ctypes.Structure):
