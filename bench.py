@@ -494,8 +494,9 @@ def run_serve(args):
                            "wall_s": wall,
                            "note": "full-round equivalent counts sum_t (n - t) n per served request; lazy rounds "
                                    "(large requests) evaluate far fewer pairs, counted in performed_evals_per_s"},
-            "saturation": {"saturated": len(done) < len(trace),
-                           "served_requests_per_s_under_load": len(done) / wall},
+            "saturation": {"saturated": len(done) < len(trace) or wall > 1.1 * args.horizon,
+                           "drain_s": wall - args.horizon,
+                           "served_requests_per_s": len(done) / wall},
             "batch_stats": st, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0

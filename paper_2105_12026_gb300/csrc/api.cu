@@ -373,6 +373,7 @@ ebc_status ebc_destroy(ebc_t h) {
     if (!h) return EBC_OK;
     cudaStreamSynchronize(h->c.stream);
     if (h->round_exec) cudaGraphExecDestroy(h->round_exec);
+    if (h->tail_exec) cudaGraphExecDestroy(h->tail_exec);
     ebc::pool_free(h->g_idx, h->c.stream);
     ebc::pool_free(h->g_f, h->c.stream);
     for (auto &r : h->prof.pending) {

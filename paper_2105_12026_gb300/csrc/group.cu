@@ -129,6 +129,60 @@ ebc_status ensure_tables(ebc_group_t g, GroupLane *l, int64_t ni, int64_t nu) {
     return EBC_OK;
 }
 
+// The tail of a handle's round after the shared launch: reduce the bulk
+// partials (nch V chunks), certify the pick into the handle's by-round
+// buffers, update m_v, and prepare the next round's point extension.
+ebc_status round_tail(ebc_t h, int nch) {
+    ebc::Ctx &c = h->c;
+    CK(h, launch(h, -1, 1, [&] { return ebc::launch_reduce_select(c, c.n, nch, nullptr, true, nullptr, h->nblk); }));
+    ebc_status s = ebc::round_certify(h, h->g_idx, h->g_f, false);
+    if (s != EBC_OK) return s;
+    CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, true); }));
+    return EBC_OK;
+}
+
+// Capture round_tail as a graph for later rounds (a capture failure keeps
+// direct launches).
+void capture_tail(ebc_t h, int nch) {
+    ebc::Ctx &c = h->c;
+    if (h->tail_exec) {
+        cudaGraphExecDestroy(h->tail_exec);
+        h->tail_exec = nullptr;
+    }
+    const ebc_profile saved = h->prof.p;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const ebc_status s = round_tail(h, nch);
+    const cudaError_t e = cudaStreamEndCapture(c.stream, &graph);
+    h->tail_launches = h->prof.p.launches - saved.launches;
+    h->prof.p = saved;
+    if (s != EBC_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->tail_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        h->tail_exec = nullptr;
+        return;
+    }
+    h->tail_key[0] = nch;
+    h->tail_key[1] = (int64_t)c.prec;
+    h->tail_key[2] = c.refine_k;
+    h->tail_key[3] = (int64_t)ebc::wait_limit_ns();
+}
+
+bool tail_graph_ok(ebc_t h, int nch) {
+    const ebc::Ctx &c = h->c;
+    return h->tail_exec && h->tail_key[0] == nch && h->tail_key[1] == (int64_t)c.prec &&
+           h->tail_key[2] == c.refine_k && h->tail_key[3] == (int64_t)ebc::wait_limit_ns();
+}
+
 }  // namespace
 
 extern "C" {
@@ -267,13 +321,25 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
         lane.staged_pending = true;
     }
 
-    // output bases: the commit kernel writes out[round since reset]
-    std::vector<int32_t *> ib(ni);
-    std::vector<double *> fb(ni);
+    // picks and f go to each handle's by-round buffers (written by round since
+    // reset), copied to the caller's outputs at the end
+    std::vector<int64_t> first(ni);
     for (int e = 0; e < ni; ++e) {
         ebc_t h = hs[shared[e]];
-        ib[e] = out_idx[shared[e]] - h->nsel;
-        fb[e] = out_f[shared[e]] - h->nsel;
+        ebc::Ctx &c = h->c;
+        first[e] = h->nsel;
+        if (!h->g_idx) {
+            cudaError_t ea = dalloc(&h->g_idx, c.n, c);
+            if (ea == cudaSuccess) ea = dalloc(&h->g_f, c.n, c);
+            if (ea != cudaSuccess) {
+                ebc::pool_free(h->g_idx, c.stream);
+                h->g_idx = nullptr;
+                h->g_f = nullptr;
+                return gcuda(g, ea, "ebc_group_greedy: by-round buffers");
+            }
+        }
+        // the first round's point extension (later rounds: the previous tail)
+        CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(c, true); }));
     }
     const int kmax = k[shared[0]];
     std::vector<int> active(L);
@@ -291,7 +357,6 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
             for (int x = 0; x < na; ++x) {
                 const int e = P.members[x];
                 ebc_t h = hs[shared[e]];
-                CK(h, launch(h, -1, 1, [&] { return ebc::launch_prep_tc(h->c, true); }));
                 GK(g, cudaEventRecord(g->ev_inst[e], h->c.stream));
                 GK(g, cudaStreamWaitEvent(lane.stream, g->ev_inst[e], 0));
             }
@@ -329,16 +394,30 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
                 h->prof.p.bulk_launches += 1;
                 h->prof.p.bulk_evals += (c.n - h->nsel) * c.n;
                 const int nchunks = P.nch[x];
-                CK(h, launch(h, -1, 1, [&] {
-                       return ebc::launch_reduce_select(c, c.n, nchunks, nullptr, true, nullptr, h->nblk);
-                   }));
-                ebc_status s = ebc::round_certify(h, ib[e], fb[e], false);
-                if (s != EBC_OK) return gfail(g, s, std::string("ebc_group_greedy: ") + ebc_last_error(h));
+                const bool graphs = h->graphs && !h->prof.on && c.stream != nullptr;
+                if (graphs && tail_graph_ok(h, nchunks)) {
+                    GK(g, cudaGraphLaunch(h->tail_exec, c.stream));
+                    h->prof.p.launches += h->tail_launches;
+                } else {
+                    ebc_status s = round_tail(h, nchunks);
+                    if (s != EBC_OK) return gfail(g, s, std::string("ebc_group_greedy: ") + ebc_last_error(h));
+                    // after one direct tail (kernel attributes set), capture for the next rounds
+                    if (graphs && k[shared[e]] - r > 1) capture_tail(h, nchunks);
+                }
                 h->nsel += 1;
                 h->attrs_ready = true;
             }
         }
         g->rounds += 1;
+    }
+    for (int e = 0; e < ni; ++e) {
+        ebc_t h = hs[shared[e]];
+        ebc::Ctx &c = h->c;
+        const int64_t cnt = k[shared[e]];
+        GK(g, cudaMemcpyAsync(out_idx[shared[e]], h->g_idx + first[e], sizeof(int32_t) * cnt,
+                              cudaMemcpyDeviceToDevice, c.stream));
+        GK(g, cudaMemcpyAsync(out_f[shared[e]], h->g_f + first[e], sizeof(double) * cnt, cudaMemcpyDeviceToDevice,
+                              c.stream));
     }
     return EBC_OK;
 }

@@ -44,6 +44,12 @@ struct ebc_ctx {
     int ctas_at_capture = -1;
     int lazy_at_capture = -1;
     uint64_t wait_at_capture = 0;  // pipeline wait limit baked into the captured round
+    // the tail of a round in a shared group launch (reduction of the bulk
+    // partials, certified pick, m_v update, next round's point extension),
+    // captured once per (V chunks, precision, K, wait limit)
+    cudaGraphExec_t tail_exec = nullptr;
+    int64_t tail_key[4] = {-1, -1, -1, -1};
+    int64_t tail_launches = 0;
     bool graphs = true;          // replay rounds from a graph when possible
     bool attrs_ready = false;    // one direct round has run (kernel attributes are set)
     // threshold sieve: upper bounds of every point's gain, valid while S only
