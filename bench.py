@@ -936,6 +936,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp8-peak", action="store_true", help="fp8: skip measuring the FP8 GEMM peak")
     ap.add_argument("--no-lazy", action="store_true", help="regime: skip the lazy comparison; serve: full rounds")
     ap.add_argument("--lazy-min-n", type=int, default=100_000, help="serve: lazy rounds from this n")
     ap.add_argument("--greedy", default="full", choices=["full", "lazy"], help="regime/small: round kind timed")
@@ -1061,7 +1062,7 @@ def main():
         peak = pk["bf16_sustained"]
         roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": f"{pk['source']} bf16 sustained"}
         if args.prec == "fp8":
-            fp8 = measure_fp8_peak()
+            fp8 = measure_fp8_peak() if not args.no_fp8_peak else {"sustained": None, "how": "not measured"}
             if fp8["sustained"]:
                 peak = fp8["sustained"]
                 roof["peak_source"] = "measured fp8 sustained in this run (" + fp8["how"] + ")"
