@@ -32,9 +32,9 @@ METRIC = "EBC distance-evals/s, BF16-TC vs FP32 plain at matched picks; serve p9
 UNIT = "distance-evals/s"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the bulk kernel from one ncu capture
-# of the current kernel (profiles/k_gains_tc_bf16_regime_n200k_d128.md), keyed
-# by (precision, n, d); None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("bf16", 200_000, 128): 298.912e6 + 11.72736e6}
+# of the current kernel at the full size (profiles/k_gains_tc_bf16_regime_d128.md),
+# keyed by (precision, n, d); None where no capture of the current kernel exists.
+NCU_TRAFFIC = {("bf16", 200_000, 128): 305.729792e6 + 11.341312e6}
 
 
 def peaks():
