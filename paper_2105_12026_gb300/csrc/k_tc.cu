@@ -845,7 +845,7 @@ __device__ __forceinline__ float reduce_scatter8(const float (&v)[8], int lane) 
 }
 }  // namespace
 
-__global__ void __launch_bounds__(S4_THREADS, 1)
+__global__ void __maxnreg__(112)
     k_sets_tc4(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
     extern __shared__ uint8_t smem_raw[];
