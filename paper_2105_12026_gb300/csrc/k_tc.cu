@@ -112,7 +112,9 @@ struct TcArgs {
 
 constexpr int MODE_GAINS = 0;
 constexpr int MODE_SETS = 1;
+constexpr int SETS_PER_CHUNK = 128;  // sets per chunk (a chunk of 2048 columns holds at most 128 non-empty sets)
 constexpr int SET_GROUP = 16;       // members per group: sets are padded to multiples of 16
+constexpr int64_t CHUNK_COLS = 2048;  // target member columns per chunk
 
 // The launch's work plan as plain values: from the arguments, or, for a
 // list whose length is on the device, derived from that length (every CTA
@@ -786,316 +788,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     k_sets_tc_kb(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                  const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
     tc_pipeline<MODE_SETS, false, true>(&tmA, &tmAx, &tmB, &tmBx, args);
-}
-
-// ---------------------------------------------------------------------------
-// Multi-set evaluation with 512-point units and 128-column member tiles
-// (whole rows resident, d <= 128).  The accumulator of a tile is four
-// 128 x 128 regions (one per 128-point sub-tile) filling the 512 TMEM
-// columns; sixteen epilogue warps drain them, four per region, each thread
-// one point and the tile's 128 member columns (8 groups of 16).  The MMA of
-// the next tile waits for each region's drain at that region's first MMA,
-// so the four regions form a ring: a region is drained while the other
-// three are computed.  Per (point, member) the accumulator is formed by the
-// same MMA sequence as in tc_pipeline's set mode (K atoms, then the
-// extension), and the per-set arithmetic is the same, so values equal the
-// 256 x 256 kernel's bitwise.
-// ---------------------------------------------------------------------------
-namespace {
-constexpr int S4_SUB = 4;                     // point sub-tiles per unit
-constexpr int S4_M = S4_SUB * BMS;            // points per unit
-constexpr int S4_N = 128;                     // member columns per tile
-constexpr int S4_EPI = 16;                    // epilogue warps
-constexpr int S4_THREADS = (2 + S4_EPI) * 32;
-
-struct S4Layout {
-    uint32_t a_main, a_sub, a_bytes, b_main, b_bytes, off_b, off_bar, off_misc, total;
-};
-__host__ __device__ inline S4Layout s4_layout(int RB, int ns, int na) {
-    S4Layout L;
-    L.a_main = (uint32_t)BMS * RB;
-    L.a_sub = L.a_main + BMS * KEXT * 2;
-    L.a_bytes = S4_SUB * L.a_sub;
-    L.b_main = (uint32_t)S4_N * RB;
-    L.b_bytes = L.b_main + S4_N * KEXT * 2;
-    L.off_b = na * L.a_bytes;
-    L.off_bar = L.off_b + ns * L.b_bytes;
-    L.off_misc = L.off_bar + (2 * ns + 4 + 2 * S4_SUB + 1) * 8;
-    L.total = L.off_misc + 64 + 1024;
-    return L;
-}
-
-// Sums over the 32 lanes of 8 per-group values as a reduce-scatter: lane l
-// ends with the total of group group_of_lane8(l) (4 lanes per group).
-__device__ __forceinline__ int group_of_lane8(int lane) {
-    return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-}
-__device__ __forceinline__ float reduce_scatter8(const float (&v)[8], int lane) {
-    float u[4], w[2];
-    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        u[j] = (b16 ? v[j + 4] : v[j]) + __shfl_xor_sync(0xffffffffu, b16 ? v[j] : v[j + 4], 16);
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-        w[j] = (b8 ? u[j + 2] : u[j]) + __shfl_xor_sync(0xffffffffu, b8 ? u[j] : u[j + 2], 8);
-    float x = (b4 ? w[1] : w[0]) + __shfl_xor_sync(0xffffffffu, b4 ? w[0] : w[1], 4);
-    x += __shfl_xor_sync(0xffffffffu, x, 2);
-    return x + __shfl_xor_sync(0xffffffffu, x, 1);
-}
-}  // namespace
-
-__global__ void __maxnreg__(112)
-    k_sets_tc4(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
-               const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int ns = args.nstages, na = args.na, RB = args.RB;
-    const uint64_t wait_ns = args.wait_ns;
-    const S4Layout L = s4_layout(RB, ns, na);
-    uint8_t *sA = base;
-    uint8_t *sB = base + L.off_b;
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + L.off_bar);
-    uint64_t *empty = full + ns;
-    uint64_t *a_full = empty + ns;
-    uint64_t *a_empty = a_full + 2;
-    uint64_t *t_full = a_empty + 2;     // [S4_SUB]
-    uint64_t *t_empty = t_full + S4_SUB;  // [S4_SUB]
-    uint64_t *fin = t_empty + S4_SUB;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + L.off_misc);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(base + L.off_misc + 4);
-    int *last_full = reinterpret_cast<int *>(base + L.off_misc + 8);  // [ns] (ns <= 8)
-    int *last_afull = last_full + 8;                                    // [2]
-    int *last_tfull = last_afull + 2;                                   // [S4_SUB]
-
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    const Plan P = make_plan(args);
-    const int total_units = P.n_ctiles * P.nchunks;
-    const int katoms = RB / 128;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < ns; ++s) {
-            tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
-            last_full[s] = -1;
-        }
-        for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&a_full[b], 1);
-            tc::mbar_init(&a_empty[b], 1);
-            last_afull[b] = -1;
-        }
-        for (int h = 0; h < S4_SUB; ++h) {
-            tc::mbar_init(&t_full[h], 1);
-            tc::mbar_init(&t_empty[h], S4_EPI / S4_SUB);
-            last_tfull[h] = -1;
-        }
-        tc::mbar_init(fin, 1);
-        *abort_flag = 0;
-        tc::fence_mbar_init();
-    }
-    if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, TMEM_COLS);
-        tc::tmem_relinquish();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-    const uint32_t tmem_base = *tmem_slot;
-
-    if (warp == 0) {
-        // ------------------------------------------------------------ producer
-        if (lane == 0) {
-            tc::tma_prefetch_desc(&tmA);
-            tc::tma_prefetch_desc(&tmAx);
-            tc::tma_prefetch_desc(&tmB);
-            tc::tma_prefetch_desc(&tmBx);
-            int g = 0, ua = 0;
-            for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
-                const int at = u / P.nchunks, ch = u % P.nchunks;
-                const int64_t *rec = args.chunks + 4 * ((int64_t)P.chunk0 + ch);
-                const int b_row0 = (int)rec[2];
-                const int nb = (int)((rec[3] - rec[2] + S4_N - 1) / S4_N);
-                const int ab = ua % na;
-                const int aph = (ua / na) & 1;
-                if (!tc::mbar_wait(&a_empty[ab], aph ^ 1, abort_flag, wait_ns)) {
-                    record_timeout(args.err, abort_flag);
-                    break;
-                }
-                uint8_t *abuf = sA + ab * L.a_bytes;
-                tc::mbar_arrive_expect_tx(&a_full[ab], L.a_bytes);
-                for (int h = 0; h < S4_SUB; ++h) {
-                    uint8_t *sub = abuf + h * L.a_sub;
-                    const int row0 = at * S4_M + h * BMS;
-                    for (int j = 0; j < katoms; ++j)
-                        tc::tma_load_2d(sub + j * (BMS * 128), &tmA, &a_full[ab], j * KATOM, row0);
-                    tc::tma_load_2d(sub + L.a_main, &tmAx, &a_full[ab], 0, row0);
-                }
-                last_afull[ab] = aph;
-                bool ok = true;
-                for (int i = 0; i < nb; ++i, ++g) {
-                    const int s = g % ns;
-                    const int ph = (g / ns) & 1;
-                    const int brow = b_row0 + i * S4_N;
-                    if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, wait_ns)) {
-                        record_timeout(args.err, abort_flag);
-                        ok = false;
-                        break;
-                    }
-                    uint8_t *bbuf = sB + s * L.b_bytes;
-                    tc::mbar_arrive_expect_tx(&full[s], L.b_bytes);
-                    for (int j = 0; j < katoms; ++j)
-                        tc::tma_load_2d(bbuf + j * (S4_N * 128), &tmB, &full[s], j * KATOM, brow);
-                    tc::tma_load_2d(bbuf + L.b_main, &tmBx, &full[s], 0, brow);
-                    last_full[s] = ph;
-                }
-                if (!ok) break;
-            }
-        }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            int g = 0, t = 0, ua = 0;
-            for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
-                const int ch = u % P.nchunks;
-                const int64_t *rec = args.chunks + 4 * ((int64_t)P.chunk0 + ch);
-                const int nb = (int)((rec[3] - rec[2] + S4_N - 1) / S4_N);
-                const int ab = ua % na;
-                if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag, wait_ns)) {
-                    record_timeout(args.err, abort_flag);
-                    break;
-                }
-                const uint32_t a0 = tc::smem_u32(sA + ab * L.a_bytes);
-                bool ok = true;
-                for (int i = 0; i < nb && ok; ++i, ++g, ++t) {
-                    const int s = g % ns;
-                    if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag, wait_ns)) {
-                        record_timeout(args.err, abort_flag);
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t b0 = tc::smem_u32(sB + s * L.b_bytes);
-                    for (int h = 0; h < S4_SUB; ++h) {
-                        if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag, wait_ns)) {
-                            record_timeout(args.err, abort_flag);
-                            ok = false;
-                            break;
-                        }
-                        tc::tc_fence_after();
-                        const uint32_t d_tmem = tmem_base + (uint32_t)(h * S4_N);
-                        const uint32_t ah = a0 + h * L.a_sub;
-                        for (int kk = 0; kk < RB / 32; ++kk) {
-                            const uint32_t j = kk >> 2, w4 = kk & 3;
-                            const uint64_t ad = tc::sdesc_sw128(ah + j * (BMS * 128) + w4 * 32);
-                            const uint64_t bd = tc::sdesc_sw128(b0 + j * (S4_N * 128) + w4 * 32);
-                            tc::mma_f16(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
-                        }
-                        tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main),
-                                    args.idesc_ext, 1u);
-                        tc::mma_commit(&t_full[h]);
-                        last_tfull[h] = t & 1;
-                    }
-                    if (!ok) break;
-                    tc::mma_commit(&empty[s]);
-                }
-                if (!ok) break;
-                tc::mma_commit(&a_empty[ab]);
-            }
-        }
-    } else {
-        // ------------------------------------------------------------ epilogue
-        const int ew = warp - 2;       // 0..15
-        const int q = warp & 3;        // TMEM lane quarter this warp may access
-        const int h = ew >> 2;         // region = point sub-tile
-        int t = 0;
-        bool alive = true;
-        for (int u = blockIdx.x; u < total_units && alive; u += gridDim.x) {
-            const int at = u / P.nchunks, ch = u % P.nchunks;
-            const int64_t *rec = args.chunks + 4 * ((int64_t)P.chunk0 + ch);
-            const int64_t set_b = rec[0], b_row0 = rec[2], col_e = rec[3];
-            const int nb = (int)((col_e - b_row0 + S4_N - 1) / S4_N);
-            double *prow = args.partial + ((int64_t)at * S4_EPI + ew) * args.lb + (set_b - args.j0);
-            float run = -INFINITY;
-            int ge_next = lane < (int)(min((int64_t)S4_N, col_e - b_row0) / SET_GROUP)
-                              ? __ldg(args.gset + b_row0 / SET_GROUP + lane)
-                              : 0;
-            for (int i = 0; i < nb; ++i, ++t) {
-                const int64_t c0 = b_row0 + (int64_t)i * S4_N;
-                const int ngr = (int)(min((int64_t)S4_N, col_e - c0) / SET_GROUP);
-                const int ge = ge_next;
-                if (i + 1 < nb) {
-                    const int64_t c1 = c0 + S4_N;
-                    ge_next = lane < (int)(min((int64_t)S4_N, col_e - c1) / SET_GROUP)
-                                  ? __ldg(args.gset + c1 / SET_GROUP + lane)
-                                  : 0;
-                }
-                const unsigned lastmask = __ballot_sync(0xffffffffu, lane < ngr && (ge & 1));  // groups ending a set
-                if (!__all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag, wait_ns))) {
-                    if (lane == 0) record_timeout(args.err, abort_flag);
-                    alive = false;
-                    break;
-                }
-                tc::tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * S4_N);
-                uint32_t r[2][32];
-                float gm[8];
-                tc::tmem_ld32(taddr, r[0]);
-                tc::tmem_ld32(taddr + 32, r[1]);
-                tc::tmem_ld_wait();
-#pragma unroll
-                for (int gg = 0; gg < 4; ++gg) gm[gg] = max16(&r[gg >> 1][(gg & 1) * 16]);
-                tc::tmem_ld32(taddr + 64, r[0]);
-                tc::tmem_ld32(taddr + 96, r[1]);
-                tc::tmem_ld_wait();
-                tc::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&t_empty[h]);
-#pragma unroll
-                for (int gg = 0; gg < 4; ++gg) gm[4 + gg] = max16(&r[gg >> 1][(gg & 1) * 16]);
-                // running maximum over the groups (reset after a set's last
-                // group); val[g] = the set's term where group g ends it
-                float val[8];
-#pragma unroll
-                for (int gg = 0; gg < 8; ++gg) {
-                    val[gg] = 0.f;
-                    if (gg < ngr) {
-                        run = fmaxf(run, gm[gg]);
-                        const bool last = (lastmask >> gg) & 1u;
-                        val[gg] = last ? fmaxf(run, 0.f) : 0.f;
-                        run = last ? -INFINITY : run;
-                    }
-                }
-                if (lastmask) {  // one batched lane reduction for all sets ending in this tile
-                    const float tot = reduce_scatter8(val, lane);
-                    const int gv = group_of_lane8(lane);
-                    const int gev = __shfl_sync(0xffffffffu, ge, gv);
-                    if ((lane & 3) == 0 && ((lastmask >> gv) & 1u)) prow[gev >> 1] = (double)tot;
-                }
-            }
-        }
-    }
-
-    // ---------------------------------------------------------------- teardown
-    __syncthreads();
-    if (warp == 1 && lane == 0) {
-        volatile int never = 0;
-        tc::mma_commit(fin);
-        tc::mbar_wait(fin, 0u, &never);
-    }
-    if (threadIdx.x == 0) {
-        volatile int never = 0;
-        for (int s = 0; s < ns; ++s)
-            if (last_full[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)last_full[s], &never);
-        for (int b = 0; b < 2; ++b)
-            if (last_afull[b] >= 0) tc::mbar_wait(&a_full[b], (uint32_t)last_afull[b], &never);
-        for (int hh = 0; hh < S4_SUB; ++hh)
-            if (last_tfull[hh] >= 0) tc::mbar_wait(&t_full[hh], (uint32_t)last_tfull[hh], &never);
-    }
-    __syncthreads();
-    if (warp == 1) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc(tmem_base, TMEM_COLS);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -2542,30 +2234,15 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off, 
     *nlaunch = 0;
     if (l <= 0) return cudaSuccess;
     const bool kb = use_kb(c, 2 * T.DP);
-    const int RB = 2 * T.DP;
-    // whole rows resident: 512-point units and 128-column member tiles
-    // (k_sets_tc4); K-blocked rows: 256 x 256 tiles (k_sets_tc_kb)
     int na = 1, ns = KB_STAGES;
-    uint32_t smem = 0;
-    cudaError_t e;
-    if (!kb) {
-        ns = 0;
-        for (int a = 2; a >= 1 && ns == 0; --a)
-            for (int st = 6; st >= 2; --st)
-                if (s4_layout(RB, st, a).total <= (uint32_t)SMEM_LIMIT) {
-                    na = a;
-                    ns = st;
-                    break;
-                }
-        if (ns == 0) return cudaErrorInvalidConfiguration;
-        smem = s4_layout(RB, ns, na).total;
-        if ((e = allow_smem((const void *)k_sets_tc4, smem)) != cudaSuccess) return e;
-    } else {
-        smem = smem_layout_kb(ns).total;
-        if ((e = allow_smem((const void *)k_sets_tc_kb, smem)) != cudaSuccess) return e;
-    }
-    const int npu = kb ? (int)(T.n_pad / BM) : (int)((T.n_pad + S4_M - 1) / S4_M);
-    const int64_t rows = (int64_t)npu * (kb ? 8 : S4_EPI);  // partial rows: (point unit, epilogue warp)
+    if (!kb) pick_pipeline(2 * T.DP, &na, &ns);
+    if (ns == 0) return cudaErrorInvalidConfiguration;
+    const SmemLayout L = kb ? smem_layout_kb(ns) : smem_layout(2 * T.DP, ns, na);
+    const void *kfn = kb ? (const void *)k_sets_tc_kb : (const void *)k_sets_tc;
+    cudaError_t e = allow_smem(kfn, L.total);
+    if (e != cudaSuccess) return e;
+    const int npu = (int)(T.n_pad / BM);
+    const int64_t rows = (int64_t)npu * 8;  // partial rows: (point unit, epilogue warp)
     const int64_t lbmax = std::min<int64_t>(l, c.set_part_cap / rows);
     if (lbmax < 1) return cudaErrorMemoryAllocation;
     const int64_t nbatch = (l + lbmax - 1) / lbmax;
@@ -2578,10 +2255,9 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off, 
         T.sp_batches = nbatch + 1;
     }
     const bool bf = T.prec == EBC_BF16;
-    const int bn = kb ? BN : S4_N;  // member rows per tile
     CUtensorMap tmM, tmMx;
-    if ((e = make_map(&tmM, T.Mq, T.mcap, T.DP, bf, KATOM, bn, CU_TENSOR_MAP_SWIZZLE_128B)) != cudaSuccess) return e;
-    if ((e = make_map(&tmMx, T.Mx, T.mcap, KEXT, true, KEXT, bn, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess) return e;
+    if ((e = make_map(&tmM, T.Mq, T.mcap, T.DP, bf, KATOM, BN, CU_TENSOR_MAP_SWIZZLE_128B)) != cudaSuccess) return e;
+    if ((e = make_map(&tmMx, T.Mx, T.mcap, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess) return e;
     // the plan, the group table and the member rows, all on the device
     k_sets_plan<<<1, SP_T, 0, c.stream>>>(idx, off, l, lbmax, T.mcap, T.sp_aux, T.sp_rec, T.sp_cj, T.sp_bf, nbatch,
                                           &c.st->err);
@@ -2604,13 +2280,13 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off, 
         a.n_ctiles = npu;
         a.nchunks = 0;  // from the device plan (sets_bf)
         a.vt_per_chunk = 0;
-        a.RB = RB;
+        a.RB = 2 * T.DP;
         a.xatom = KATOM;
         a.row_scale = nullptr;
         a.nstages = ns;
         a.na = na;
-        a.idesc = tc::idesc_f16(bf ? 1u : 0u, BMS, bn);
-        a.idesc_ext = tc::idesc_f16(1u, BMS, bn);
+        a.idesc = tc::idesc_f16(bf ? 1u : 0u, BMS, BN);
+        a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
         a.partial = c.set_part;
         a.err = &c.st->err;
         a.chunks = T.sp_rec;
@@ -2622,9 +2298,9 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off, 
         // empty sets get no partial from any warp
         if ((e = cudaMemsetAsync(c.set_part, 0, sizeof(double) * rows * lb, c.stream)) != cudaSuccess) return e;
         if (kb)
-            k_sets_tc_kb<<<G, NTHREADS, smem, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
+            k_sets_tc_kb<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
         else
-            k_sets_tc4<<<G, S4_THREADS, smem, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
+            k_sets_tc<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = launch_sets_finalize(c, rows, lb, j0, l, out_f)) != cudaSuccess) return e;
         *nlaunch += 2;
