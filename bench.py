@@ -344,7 +344,7 @@ def run_mix_resident(args):
              for V in Vs]
     outs = [(torch.empty(k, dtype=torch.int32, device=dev), torch.empty(k, dtype=torch.float64, device=dev))
             for k in ks]
-    group = ebc.Group(lanes=args.group_lanes, by_row_width=args.group_by_width)
+    group = ebc.Group(lanes=args.group_lanes, by_row_width=args.group_by_width, max_ctas=args.group_ctas)
 
     def one_step():
         for inst, V in zip(insts, Vs):
@@ -394,7 +394,8 @@ def run_mix_resident(args):
             "scaling": "strong", "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded GMM instance mix)",
             "config": {"workload": f"batched greedy, {len(specs)} instances: n log-uniform [2000, 100000], "
                                    f"d in {{16,32,64,128}}, k in [5, 50]",
-                       "mix_mode": args.mix_mode, "group_lanes": args.group_lanes, "evals_per_step": evals,
+                       "mix_mode": args.mix_mode, "group_lanes": args.group_lanes, "group_ctas": args.group_ctas,
+                       "evals_per_step": evals,
                        "parallelism": f"instances sharded over {world} GPUs" if world > 1 else "single GPU",
                        "timing": "wall clock between device synchronisations; every step uploads each instance's "
                                  "V from pinned host memory into its resident handle (ebc_reload: prologue and "
@@ -916,6 +917,7 @@ def main():
                          "(streams) or the batch runtime (batch)")
     ap.add_argument("--group-lanes", type=int, default=1, help="mix: lanes of the shared-launch group")
     ap.add_argument("--group-by-width", action="store_true", help="mix: group lanes by row width")
+    ap.add_argument("--group-ctas", type=int, default=0, help="mix: CTA cap of the shared launch (0: all SMs)")
     ap.add_argument("--slots", type=int, default=32, help="mix/serve: concurrent instances")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="mix/serve: device-memory budget")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
@@ -937,6 +939,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp8-peak", action="store_true", help="fp8: skip measuring the FP8 GEMM peak")
+    ap.add_argument("--no-raw-error", action="store_true", help="skip the raw low-precision gain error sample")
     ap.add_argument("--no-lazy", action="store_true", help="regime: skip the lazy comparison; serve: full rounds")
     ap.add_argument("--lazy-min-n", type=int, default=100_000, help="serve: lazy rounds from this n")
     ap.add_argument("--greedy", default="full", choices=["full", "lazy"], help="regime/small: round kind timed")
@@ -1161,6 +1164,19 @@ def main():
         line["e2e"] = {"value": world * args.steps * evals_step / e2e_s, "unit": UNIT,
                        "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(k * (4 + 8))}
 
+    if rank == 0 and args.prec != "fp32" and not args.no_raw_error:
+        # raw low-precision gains (no certification) of a seeded sample of
+        # candidates at S = {}, against the FP64 oracle, per result
+        import oracle
+        inst.reset()
+        samp = np.sort(np.random.default_rng(args.seed + 7).choice(n, 64, replace=False)).astype(np.int32)
+        raw = inst.gains_host(samp)
+        ref = oracle.gains(V, oracle.norms(V), samp)
+        rel = np.abs(raw - ref) / np.maximum(np.abs(ref), 1e-300)
+        line["raw_rel_err_vs_oracle"] = {"what": "ebc_gains at S = {} (raw, uncertified) vs FP64 oracle",
+                                         "max": float(rel.max()), "median": float(np.median(rel)),
+                                         "p90": float(np.percentile(rel, 90)),
+                                         "per_candidate": {str(int(c)): float(r) for c, r in zip(samp, rel)}}
     inst.close()
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:

@@ -518,6 +518,10 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *h, int32_t count, const 
 ebc_status ebc_group_set_lanes(ebc_group_t g, int32_t lanes);
 ebc_status ebc_group_set_lanes_by_row_width(ebc_group_t g, int32_t on);
 
+/* Cap the CTAs of the shared launch (0 = one per SM), leaving SMs to the
+ * per-handle picks of other lanes.  EINVAL for a negative cap. */
+ebc_status ebc_group_set_max_ctas(ebc_group_t g, int32_t max_ctas);
+
 /* Time every shared launch with CUDA events on its lane's stream (on = 1);
  * ebc_group_profile waits for the timed launches and returns their summed
  * device time, the summed time from the end of one timed launch to the start

@@ -46,6 +46,7 @@ struct ebc_group_ctx {
     int device = 0;
     int num_sms = 152;
     int nlanes = 1;
+    int max_ctas = 0;           // CTAs of the shared launch (0: one per SM)
     bool by_row_width = false;  // lanes by row width (d <= 64 / d <= 128) instead of round-robin
     GroupLane lanes[4];
     std::vector<cudaEvent_t> ev_inst;  // per handle: its point extension is ready
@@ -372,8 +373,9 @@ ebc_status ebc_group_greedy(ebc_group_t g, const ebc_t *hs, int32_t count, const
                 }
                 GK(g, cudaEventRecord(evp.first, lane.stream));
             }
+            const int G = (g->max_ctas > 0 && g->max_ctas < g->num_sms) ? g->max_ctas : g->num_sms;
             GK(g, ebc::launch_gains_tc_group(lane.d_inst, lane.d_units, (int)P.first_unit[na], lane.d_words,
-                                             lane.d_words + 1, RBmax, g->num_sms, lane.stream));
+                                             lane.d_words + 1, RBmax, G, lane.stream));
             if (g->prof) {
                 GK(g, cudaEventRecord(evp.second, lane.stream));
                 g->pending.push_back(evp);
@@ -433,6 +435,12 @@ ebc_status ebc_group_stats(ebc_group_t g, int64_t *launches, int64_t *units, int
 ebc_status ebc_group_set_profiling(ebc_group_t g, int32_t on) {
     if (!g) return EBC_EINVAL;
     g->prof = on != 0;
+    return EBC_OK;
+}
+
+ebc_status ebc_group_set_max_ctas(ebc_group_t g, int32_t max_ctas) {
+    if (!g || max_ctas < 0) return EBC_EINVAL;
+    g->max_ctas = max_ctas;
     return EBC_OK;
 }
 

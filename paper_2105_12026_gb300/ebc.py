@@ -120,6 +120,7 @@ _SIGS = {
     "ebc_group_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "ebc_group_set_lanes": [_P, _I32],
     "ebc_group_set_lanes_by_row_width": [_P, _I32],
+    "ebc_group_set_max_ctas": [_P, _I32],
     "ebc_group_set_profiling": [_P, _I32],
     "ebc_group_profile": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(_I64)],
@@ -700,7 +701,7 @@ class Group:
     """Greedy on many instances with one persistent bulk launch per round
     (include/ebc.h, ebc_group_*)."""
 
-    def __init__(self, lanes: int = 1, by_row_width: bool = False):
+    def __init__(self, lanes: int = 1, by_row_width: bool = False, max_ctas: int = 0):
         h = _P()
         rc = load().ebc_group_create(ctypes.byref(h))
         if rc != EBC_OK:
@@ -708,6 +709,7 @@ class Group:
         self.h = h.value
         self._err(load().ebc_group_set_lanes(_P(self.h), int(lanes)))
         self._err(load().ebc_group_set_lanes_by_row_width(_P(self.h), int(bool(by_row_width))))
+        self._err(load().ebc_group_set_max_ctas(_P(self.h), int(max_ctas)))
 
     def profiling(self, on: bool = True):
         self._err(load().ebc_group_set_profiling(_P(self.h), int(bool(on))))
