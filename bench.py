@@ -996,7 +996,7 @@ def main():
     if args.autotune > 0 and args.prec != "fp32":
         t0 = time.perf_counter()
         inst.autotune(args.autotune)  # outside the timed region; results do not depend on it
-        tuned = {"reps": args.autotune, "search_s": time.perf_counter() - t0}
+        tuned = {"reps": args.autotune, "search_s": time.perf_counter() - t0, "entry": inst.tune_entry()}
         if args.tune_file:
             ebc.ebc_tune_save(args.tune_file)
     out_idx = torch.empty(k, dtype=torch.int32, device=dev)

@@ -151,8 +151,10 @@ ebc_status cuda_fail(ebc_t h, cudaError_t e, const char *where) {
 
 double bulk_eta(const ebc::Ctx &c) {
     (void)c;
-    // each bulk partial is a sum of at most 128 non-negative FP32 terms,
+    // each bulk partial is an FP64 sum of FP32 block sums; a block sum joins
+    // four chains of at most 128 non-negative FP32 terms with two additions,
     // each term one rounding from its bound: relative error <= 130 * 2^-24
+    // (the FP64 additions are covered by the last term)
     return 131.0 * ldexp(1.0, -24) + 1e-12;
 }
 
@@ -578,15 +580,20 @@ ebc_status ebc::autotune_handle(ebc_t h, int32_t reps, bool only_if_missing) {
         return fp8 ? ebc::launch_gains_tc8(c, nullptr, c.n, &nch) : ebc::launch_gains_tc(c, nullptr, c.n, true, &nch);
     };
     if (err == cudaSuccess) err = fp8 ? ebc::launch_prep_tc8(c, true) : ebc::launch_prep_tc(c, true);
-    // every shape that fits shared memory x every chunk policy; the fastest
-    // of reps timed launches (after one untimed) counts
+    // every point-tile width x shape that fits shared memory x chunk
+    // policy; the fastest of reps timed launches (after one untimed) counts
+    // (with issuer turns on or off at 256 points)
+    for (int bn = 256; bn >= 128 && err == cudaSuccess; bn /= 2)
+    for (int turns = bn == 256 ? 1 : 0; turns >= 0 && err == cudaSuccess; --turns)
     for (int na = 1; na <= 2 && err == cudaSuccess; ++na)
         for (int ns = 2; ns <= 6 && err == cudaSuccess; ++ns) {
-            if (!ebc::tc_config_fits(RB, na, ns)) continue;
+            if (!ebc::tc_config_fits(RB, na, ns, bn)) continue;
             for (int chunk = 0; chunk <= 2 && err == cudaSuccess; ++chunk) {
                 cfg.na = na;
                 cfg.ns = ns;
                 cfg.chunk = chunk;
+                cfg.bn = bn;
+                cfg.turns = turns;
                 c.tune_force = &cfg;
                 err = bulk();
                 double ms_min = INFINITY;
@@ -621,6 +628,24 @@ ebc_status ebc::autotune_handle(ebc_t h, int32_t reps, bool only_if_missing) {
 extern "C" {
 
 ebc_status ebc_autotune(ebc_t h, int32_t reps) { return ebc::autotune_handle(h, reps, false); }
+
+ebc_status ebc_tune_query(ebc_t h, int32_t cfg[5], double *ms) {
+    if (check_handle(h) || !cfg) return fail(h, EBC_EINVAL, "ebc_tune_query: NULL argument");
+    ebc::TuneCfg t;
+    double tms = 0.0;
+    cfg[0] = cfg[1] = cfg[2] = cfg[3] = cfg[4] = 0;
+    if (h->c.prec != EBC_FP32 && ebc::tune_get((int)h->c.prec, ebc::tc_row_bytes(h->c), h->c.n, &t, &tms)) {
+        cfg[0] = t.bn;
+        cfg[1] = t.na;
+        cfg[2] = t.ns;
+        cfg[3] = t.chunk;
+        cfg[4] = t.turns;
+    } else {
+        tms = 0.0;
+    }
+    if (ms) *ms = tms;
+    return EBC_OK;
+}
 
 ebc_status ebc_set_lazy(ebc_t h, int32_t on) {
     if (check_handle(h)) return EBC_EINVAL;

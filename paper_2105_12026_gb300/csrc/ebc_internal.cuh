@@ -111,6 +111,8 @@ struct TuneCfg {
     int na = 0;     // candidate-tile buffers (1, 2)
     int ns = 0;     // point-tile stages (2..6)
     int chunk = 0;  // V-chunk policy: 0 load-balance model, 1 twice the chunks, 2 half
+    int bn = 256;   // points per B tile (TMEM columns per region): 256 or 128
+    int turns = -1; // 256-point tiles: MMA issuers take turns (1), run freely (0), by row width (-1)
 };
 
 // Scratch / resident buffers of one handle.
@@ -154,6 +156,8 @@ struct Ctx {
         CUtensorMap tmAx_V;       // candidate extension over Aext (box 16 x 128)
         CUtensorMap tmAx_C;       // candidate extension over Cqx
         CUtensorMap tmBx;         // point extension over Bext (box 16 x 256)
+        CUtensorMap tmB_V128;     // 128-point tiles over Vq2 (box 64 x 128)
+        CUtensorMap tmBx128;      // point extension over Bext (box 16 x 128)
         // multi-set evaluation (ebc_eval_sets at a tensor-core precision)
         uint16_t *Px = nullptr;   // [n_pad, 16] point-side extension: ||v||^2 - ||v_hat||^2 (static)
         // device plan of a multi-set call (k_sets_plan): padded offsets [l + 1], chunk records
@@ -189,6 +193,7 @@ struct Ctx {
         float *qmax = nullptr;        // [5] max qerr_c, max qnorm_c, max qerr_p, max qnorm_p, amax(V)
         float *tscale = nullptr;      // [1] t
         CUtensorMap tmA, tmAx, tmA_C, tmAx_C, tmB, tmBx;
+        CUtensorMap tmB128, tmBx128;  // 128-point tiles
     } tc8;
     int num_sms = 152;
     int max_ctas = 0;  // cap on persistent-kernel CTAs (0 = one per SM)
@@ -258,9 +263,10 @@ cudaError_t launch_reduce_select(Ctx &c, int64_t m, int nchunks, const int *cand
 // tuning table (tune.cu)
 bool tune_lookup(const Ctx &c, int prec, int RB, int64_t n, TuneCfg *cfg);
 bool tune_has(int prec, int RB, int64_t n);
+bool tune_get(int prec, int RB, int64_t n, TuneCfg *cfg, double *ms);
 void tune_store(int prec, int RB, int64_t n, const TuneCfg &cfg, double ms);
 int apply_chunk_mode(int nchunks, int mode, int n_vtiles, int64_t cap, int *vt_per_chunk);
-bool tc_config_fits(int RB, int na, int ns);  // k_tc.cu: shared memory of a pipeline shape fits
+bool tc_config_fits(int RB, int na, int ns, int bn);  // k_tc.cu: shared memory of a pipeline shape fits
 int tc_row_bytes(const Ctx &c);              // k_tc.cu: row bytes of the current precision's bulk operand
 
 // few-candidate passes over V, one warp per point (k_few.cu); d <= 256

@@ -14,8 +14,10 @@
 //     X = [q q q | s s | al al al' al' | 1 1 1 | 0..]   q = -||c_hat||^2, s = slack_c,
 //     Y = [1 1 1 | sg sg | w w' w w'  | a a a | 0..]    al = ||c_hat - c||, a = a_v,
 // giving q + sg*s + (al + al')(w + w') + a.  The epilogue only forms
-// sum_v max(0, t) over the 128 columns a thread owns (FP32), then over tiles
-// (FP64).  Candidates sit on the lane axis, so a thread's sum over V stays in
+// sum_v max(0, t) over the 128 columns a thread owns in blocks of up to four
+// tiles (FP32, four chains of at most 128 terms each), then over blocks
+// (FP64: GB300's FP64 pipe retires about two lanes per clock per SM, so it
+// adds once per block, not once per tile).  Candidates sit on the lane axis, so a thread's sum over V stays in
 // its registers.  Scaling v_hat by 2 is exact.
 //
 // Upper-bound mode (Greedy, sg = 1).  For a pair that can contribute to the
@@ -73,6 +75,7 @@ constexpr int NPAD = 256;        // row padding of the quantised arrays
 constexpr int KATOM = 64;        // 16-bit elements per 128-byte swizzle atom
 constexpr int KEXT = 16;         // extension columns (one MMA K step)
 constexpr int NTHREADS = 320;
+constexpr int NTHREADS_G = 352;  // resident bulk gains: a second MMA issuer warp
 constexpr int NEPI = 256;        // epilogue threads
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -108,13 +111,12 @@ struct TcArgs {
     // [sets_bf[sets_batch], sets_bf[sets_batch + 1]) of `chunks`
     const int *sets_bf;
     int sets_batch;
+    int turns;  // resident bulk gains with two TMEM regions: issuers take turns (1) or run freely (0)
 };
 
 constexpr int MODE_GAINS = 0;
 constexpr int MODE_SETS = 1;
-constexpr int SETS_PER_CHUNK = 128;  // sets per chunk (a chunk of 2048 columns holds at most 128 non-empty sets)
 constexpr int SET_GROUP = 16;       // members per group: sets are padded to multiples of 16
-constexpr int64_t CHUNK_COLS = 2048;  // target member columns per chunk
 
 // The launch's work plan as plain values: from the arguments, or, for a
 // list whose length is on the device, derived from that length (every CTA
@@ -151,8 +153,9 @@ __device__ __forceinline__ Plan make_plan(const TcArgs &a) {
     return p;
 }
 
-// Work unit u -> A tile index, chunk, first B row and number of B tiles.
-template <int MODE>
+// Work unit u -> A tile index, chunk, first B row and number of B tiles
+// (of TBN points each in gains mode).
+template <int MODE, int TBN = BN>
 __device__ __forceinline__ void unit_span(const TcArgs &a, const Plan &P, int u, int &at, int &ch, int &b_row0,
                                           int &nb) {
     at = u / P.nchunks;
@@ -160,7 +163,7 @@ __device__ __forceinline__ void unit_span(const TcArgs &a, const Plan &P, int u,
     if constexpr (MODE == MODE_GAINS) {
         const int vt0 = ch * P.vt_per_chunk;
         const int vt1 = min(vt0 + P.vt_per_chunk, a.n_vtiles);
-        b_row0 = vt0 * BN;
+        b_row0 = vt0 * TBN;
         nb = vt1 - vt0;
     } else {
         const int64_t *r = a.chunks + 4 * ((int64_t)P.chunk0 + ch);
@@ -175,19 +178,22 @@ struct SmemLayout {
 };
 
 // A buffer: sub-tile 0 (main K atoms, then its extension), sub-tile 1 (same).
-// B stage: main K atoms, then the extension.
-__host__ __device__ inline SmemLayout smem_layout(int RB, int nstages, int na) {
+// B stage of bn points: main K atoms, then the extension.
+__host__ __device__ inline SmemLayout smem_layout(int RB, int nstages, int na, int bn = BN) {
     SmemLayout L;
     L.a_main = (uint32_t)BMS * RB;
     L.a_sub = L.a_main + BMS * KEXT * 2;
     L.a_bytes = 2 * L.a_sub;
-    L.b_main = (uint32_t)BN * RB;
-    L.b_bytes = L.b_main + BN * KEXT * 2;
+    L.b_main = (uint32_t)bn * RB;
+    L.b_bytes = L.b_main + bn * KEXT * 2;
     L.off_b = na * L.a_bytes;
     L.off_comb = L.off_b + nstages * L.b_bytes;
     L.off_bar = L.off_comb + 2 * BMS * 8;
     L.off_misc = L.off_bar + (2 * nstages + 8) * 8;
-    L.total = L.off_misc + 64 + 1024;  // + alignment slack for the 1024-byte base
+    // misc words, the four-region barriers of 128-point tiles and the
+    // issuers' hand-over barriers, then the alignment slack for the
+    // 1024-byte base
+    L.total = L.off_misc + 160 + 1024;
     L.off_ext = 0;
     return L;
 }
@@ -257,38 +263,44 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[16], int lane
     return x + __shfl_xor_sync(0xffffffffu, x, 1);
 }
 
-// Sum of max(0, x) over 4 x 32 accumulator words with packed FP32x2 adds
-// (two FP32 lanes per instruction, each an ordinary FP32 sum of at most 64
-// non-negative terms), then one add across the lanes and the two chains.
+// Running sums of max(0, x) over accumulator words with packed FP32x2 adds:
+// two 64-bit accumulators hold four FP32 chains, word i of every 32-word
+// group going to chain i % 4 (8 terms per group and chain).  relu_fold joins
+// the chains (one packed add, one scalar add).  A caller that folds after
+// at most 16 groups (4 tiles of 128 columns, or 8 of 64) keeps every chain
+// an ordinary FP32 sum of at most 128 non-negative terms.
 __device__ __forceinline__ unsigned long long pack2(float a, float b) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
     return r;
 }
 
-__device__ __forceinline__ float relu_sum128(const uint32_t (&r0)[32], const uint32_t (&r1)[32],
-                                             const uint32_t (&r2)[32], const uint32_t (&r3)[32]) {
-    unsigned long long a = pack2(0.f, 0.f), b = pack2(0.f, 0.f);
-    auto step = [&](const uint32_t (&r)[32]) {
+struct ReluAcc {
+    unsigned long long a, b;
+};
+
+__device__ __forceinline__ void relu_zero(ReluAcc &s) {
+    s.a = pack2(0.f, 0.f);
+    s.b = pack2(0.f, 0.f);
+}
+
+__device__ __forceinline__ void relu_acc32(ReluAcc &s, const uint32_t (&r)[32]) {
 #pragma unroll
-        for (int i = 0; i < 32; i += 4) {
-            const unsigned long long x = pack2(fmaxf(__uint_as_float(r[i]), 0.f), fmaxf(__uint_as_float(r[i + 1]), 0.f));
-            const unsigned long long y =
-                pack2(fmaxf(__uint_as_float(r[i + 2]), 0.f), fmaxf(__uint_as_float(r[i + 3]), 0.f));
-            asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(x));
-            asm("add.rn.f32x2 %0, %0, %1;" : "+l"(b) : "l"(y));
-        }
-    };
-    step(r0);
-    step(r1);
-    step(r2);
-    step(r3);
-    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(b));
+    for (int i = 0; i < 32; i += 4) {
+        const unsigned long long x = pack2(fmaxf(__uint_as_float(r[i]), 0.f), fmaxf(__uint_as_float(r[i + 1]), 0.f));
+        const unsigned long long y = pack2(fmaxf(__uint_as_float(r[i + 2]), 0.f), fmaxf(__uint_as_float(r[i + 3]), 0.f));
+        asm("add.rn.f32x2 %0, %0, %1;" : "+l"(s.a) : "l"(x));
+        asm("add.rn.f32x2 %0, %0, %1;" : "+l"(s.b) : "l"(y));
+    }
+}
+
+__device__ __forceinline__ float relu_fold(const ReluAcc &s) {
+    unsigned long long a = s.a;
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(s.b));
     float lo, hi;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
     return lo + hi;
 }
-
 
 }  // namespace
 
@@ -302,16 +314,35 @@ __device__ __forceinline__ float relu_sum128(const uint32_t (&r0)[32], const uin
 // over all K atoms (the same MMA sequence, hence the same FP32
 // accumulation, as the resident layout) and the extension step follows the
 // last atom.
-template <int MODE, bool F8, bool KB = false>
+//
+// TBN: points per B tile (TMEM columns per region) of the resident gains
+// pipeline, 256 or 128.  At 128 a B stage takes half the shared memory (so
+// deeper rings fit), each epilogue thread sums 64 columns per tile, and the
+// 512 TMEM columns hold two sets of the two sub-tile regions: tile t
+// accumulates into set t % 2, so the MMAs of a tile never wait for the
+// epilogue of the previous one.  The MMA sequence over K is the same.
+template <int MODE, bool F8, bool KB = false, int TBN = BN>
 __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUtensorMap *tmAx_p,
                                             const CUtensorMap *tmB_p, const CUtensorMap *tmBx_p, const TcArgs &args) {
     static_assert(!KB || !F8, "K-blocked layout: 16-bit operands only");
+    static_assert(TBN == BN || (TBN == 128 && MODE == MODE_GAINS && !KB), "128-point tiles: resident gains only");
+    // resident bulk gains: one MMA issuer per candidate sub-tile (warp 1 and
+    // the last warp), each waiting and committing while the other issues
+    constexpr bool DUAL = MODE == MODE_GAINS && !KB;
+    constexpr int NREG = TBN == 128 ? 4 : 2;  // TMEM regions
+    // with two regions the issuers may take turns (sub-tile 0 of a tile, then
+    // sub-tile 1, then sub-tile 0 of the next), so region 0 completes half a
+    // tile before region 1 and its epilogue overlaps region 1's MMAs (pays
+    // off for long rows); otherwise their MMAs interleave freely
+    const bool turns = DUAL && NREG == 2 && args.turns != 0;
+    constexpr int RH = NREG / 2;               // point tiles in flight in TMEM
+    constexpr uint32_t kTmemCols = NREG * TBN;
     const CUtensorMap &tmA = *tmA_p, &tmAx = *tmAx_p, &tmB = *tmB_p, &tmBx = *tmBx_p;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ns = args.nstages;
     const int na = args.na;
-    const SmemLayout L = KB ? smem_layout_kb(ns) : smem_layout(args.RB, ns, na);
+    const SmemLayout L = KB ? smem_layout_kb(ns) : smem_layout(args.RB, ns, na, TBN);
     uint8_t *sA = base;
     uint8_t *sB = base + L.off_b;
     double *comb = reinterpret_cast<double *>(base + L.off_comb);  // [2][BMS]
@@ -319,16 +350,19 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
     uint64_t *empty = full + ns;
     uint64_t *a_full = empty + ns;
     uint64_t *a_empty = a_full + 2;
-    uint64_t *t_full = a_empty + 2;   // per TMEM region (candidate sub-tile)
-    uint64_t *t_empty = t_full + 2;
+    // per TMEM region: region (t % RH) * 2 + h holds sub-tile h of point tile t
+    uint64_t *t_full = NREG == 2 ? a_empty + 2 : reinterpret_cast<uint64_t *>(base + L.off_misc + 64);
+    uint64_t *t_empty = t_full + NREG;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + L.off_misc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(base + L.off_misc + 4);
     // drain bookkeeping: parity of the last issued phase, -1 if none
     int *last_full = reinterpret_cast<int *>(base + L.off_misc + 8);  // [ns] (ns <= 8)
     int *last_afull = last_full + 8;                                    // [2]
-    int *last_tfull = last_afull + 2;                                   // [2]
+    int *last_tfull = NREG == 2 ? last_afull + 2 : reinterpret_cast<int *>(base + L.off_misc + 128);  // [NREG]
     // teardown: one commit after every MMA this CTA issued (misc + 56 .. 64)
     uint64_t *fin = reinterpret_cast<uint64_t *>(base + L.off_misc + 56);
+    // issuer turns: tok[0] "sub-tile 0 of tile t issued", tok[1] "sub-tile 1 of tile t issued"
+    uint64_t *tok = reinterpret_cast<uint64_t *>(base + L.off_misc + 144);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -341,24 +375,28 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
     if (threadIdx.x == 0) {
         for (int s = 0; s < ns; ++s) {
             tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
+            tc::mbar_init(&empty[s], DUAL ? 2 : 1);
             last_full[s] = -1;
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&a_full[b], 1);
-            tc::mbar_init(&a_empty[b], 1);
-            tc::mbar_init(&t_full[b], 1);
-            // every epilogue warp drains both regions in gains mode, half of them each in sets mode
-            tc::mbar_init(&t_empty[b], MODE == MODE_GAINS ? NEPI / 32 : NEPI / 64);
+            tc::mbar_init(&a_empty[b], DUAL ? 2 : 1);
             last_afull[b] = -1;
-            last_tfull[b] = -1;
         }
-        tc::mbar_init(fin, 1);
+        for (int r = 0; r < NREG; ++r) {
+            tc::mbar_init(&t_full[r], 1);
+            // every epilogue warp drains every region in gains mode, half of them each in sets mode
+            tc::mbar_init(&t_empty[r], MODE == MODE_GAINS ? NEPI / 32 : NEPI / 64);
+            last_tfull[r] = -1;
+        }
+        tc::mbar_init(fin, DUAL ? 2 : 1);
+        tc::mbar_init(&tok[0], 1);
+        tc::mbar_init(&tok[1], 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
     if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, TMEM_COLS);
+        tc::tmem_alloc(tmem_slot, kTmemCols);
         tc::tmem_relinquish();
     }
     tc::tc_fence_before();
@@ -420,7 +458,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
             } else
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
                 int ct, ch, b_row0, nb;
-                unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
+                unit_span<MODE, TBN>(args, P, u, ct, ch, b_row0, nb);
                 const int ab = ua % na;
                 const int aph = (ua / na) & 1;
                 if (!tc::mbar_wait(&a_empty[ab], aph ^ 1, abort_flag, wait_ns)) {
@@ -441,7 +479,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 for (int i = 0; i < nb; ++i, ++g) {
                     const int s = g % ns;
                     const int ph = (g / ns) & 1;
-                    const int brow = b_row0 + i * BN;
+                    const int brow = b_row0 + i * TBN;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1, abort_flag, wait_ns)) {
                         record_timeout(args.err, abort_flag);
                         ok = false;
@@ -450,20 +488,79 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                     uint8_t *bbuf = sB + s * L.b_bytes;
                     tc::mbar_arrive_expect_tx(&full[s], L.b_bytes);
                     for (int j = 0; j < katoms; ++j)
-                        tc::tma_load_2d(bbuf + j * (BN * 128), &tmB, &full[s], j * args.xatom, brow);
+                        tc::tma_load_2d(bbuf + j * (TBN * 128), &tmB, &full[s], j * args.xatom, brow);
                     tc::tma_load_2d(bbuf + L.b_main, &tmBx, &full[s], 0, brow);
                     last_full[s] = ph;
                 }
                 if (!ok) break;
             }
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 || (DUAL && warp == NTHREADS_G / 32 - 1)) {
         // ------------------------------------------------------------ MMA issuer
         // For every point tile: sub-tile 0 into TMEM region 0, then sub-tile 1
         // into region 1.  The epilogue drains one region while the other fills.
         if (lane == 0) {
             int g = 0, t = 0, ua = 0;
-            if constexpr (KB) {
+            if constexpr (DUAL) {
+                // sub-tile h of every point tile; both issuers wait for the same
+                // A and B stages and both commit their release (count 2)
+                const int h = warp == 1 ? 0 : 1;
+                for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
+                    int ct, ch, b_row0, nb;
+                    unit_span<MODE, TBN>(args, P, u, ct, ch, b_row0, nb);
+                    const int ab = ua % na;
+                    if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag, wait_ns)) {
+                        record_timeout(args.err, abort_flag);
+                        break;
+                    }
+                    const uint32_t ah = tc::smem_u32(sA + ab * L.a_bytes) + h * L.a_sub;
+                    bool ok = true;
+                    for (int i = 0; i < nb; ++i, ++g, ++t) {
+                        const int s = g % ns;
+                        if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag, wait_ns)) {
+                            record_timeout(args.err, abort_flag);
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t b0 = tc::smem_u32(sB + s * L.b_bytes);
+                        const uint32_t tpar = (uint32_t)(t / RH) & 1u;
+                        const int rg = (t % RH) * 2 + h;
+                        if (!tc::mbar_wait(&t_empty[rg], tpar ^ 1u, abort_flag, wait_ns)) {
+                            record_timeout(args.err, abort_flag);
+                            ok = false;
+                            break;
+                        }
+                        // this issuer's turn: sub-tile 1 of tile t follows sub-tile 0
+                        // of tile t, sub-tile 0 of tile t follows sub-tile 1 of t - 1
+                        if (turns && (h == 1 || t > 0) &&
+                            !tc::mbar_wait(&tok[1 - h], (uint32_t)(h == 1 ? t : t - 1) & 1u, abort_flag, wait_ns)) {
+                            record_timeout(args.err, abort_flag);
+                            ok = false;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        const uint32_t d_tmem = tmem_base + (uint32_t)(rg * TBN);
+                        // one MMA per 32 bytes of K (16 16-bit or 32 8-bit elements)
+                        for (int kk = 0; kk < args.RB / 32; ++kk) {
+                            const uint32_t j = kk >> 2, w = kk & 3;
+                            const uint64_t ad = tc::sdesc_sw128(ah + j * (BMS * 128) + w * 32);
+                            const uint64_t bd = tc::sdesc_sw128(b0 + j * (TBN * 128) + w * 32);
+                            if constexpr (F8)
+                                tc::mma_f8(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
+                            else
+                                tc::mma_f16(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
+                        }
+                        tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main),
+                                    args.idesc_ext, 1u);
+                        if (turns) tc::mbar_arrive(&tok[h]);
+                        tc::mma_commit(&t_full[rg]);
+                        last_tfull[rg] = (int)tpar;
+                        tc::mma_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    tc::mma_commit(&a_empty[ab]);
+                }
+            } else if constexpr (KB) {
                 // both TMEM regions accumulate one point tile over all K atoms
                 for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
                     int ct, ch, b_row0, nb;
@@ -525,7 +622,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
             } else
             for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x, ++ua) {
                 int ct, ch, b_row0, nb;
-                unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
+                unit_span<MODE, TBN>(args, P, u, ct, ch, b_row0, nb);
                 const int ab = ua % na;
                 if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag, wait_ns)) {
                     record_timeout(args.err, abort_flag);
@@ -541,20 +638,22 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                         break;
                     }
                     const uint32_t b0 = tc::smem_u32(sB + s * L.b_bytes);
+                    const uint32_t tpar = (uint32_t)(t / RH) & 1u;
                     for (int h = 0; h < 2; ++h) {
-                        if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag, wait_ns)) {
+                        const int rg = (t % RH) * 2 + h;
+                        if (!tc::mbar_wait(&t_empty[rg], tpar ^ 1u, abort_flag, wait_ns)) {
                             record_timeout(args.err, abort_flag);
                             ok = false;
                             break;
                         }
                         tc::tc_fence_after();
-                        const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
+                        const uint32_t d_tmem = tmem_base + (uint32_t)(rg * TBN);
                         const uint32_t ah = a0 + h * L.a_sub;
                         // one MMA per 32 bytes of K (16 16-bit or 32 8-bit elements)
                         for (int kk = 0; kk < args.RB / 32; ++kk) {
                             const uint32_t j = kk >> 2, w = kk & 3;
                             const uint64_t ad = tc::sdesc_sw128(ah + j * (BMS * 128) + w * 32);
-                            const uint64_t bd = tc::sdesc_sw128(b0 + j * (BN * 128) + w * 32);
+                            const uint64_t bd = tc::sdesc_sw128(b0 + j * (TBN * 128) + w * 32);
                             if constexpr (F8)
                                 tc::mma_f8(d_tmem, ad, bd, args.idesc, kk > 0 ? 1u : 0u);
                             else
@@ -562,8 +661,8 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                         }
                         tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main),
                                     args.idesc_ext, 1u);
-                        tc::mma_commit(&t_full[h]);
-                        last_tfull[h] = t & 1;
+                        tc::mma_commit(&t_full[rg]);
+                        last_tfull[rg] = (int)tpar;
                     }
                     if (!ok) break;
                     tc::mma_commit(&empty[s]);
@@ -580,16 +679,25 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         const int row = q * 32 + lane;  // candidate row within a sub-tile
         int t = 0;
         bool alive = true;
+        // FP32 blocks of kBlk tiles (chains of at most 128 terms), then FP64
+        // over the blocks: the FP64 pipe does one add per block, not per tile
+        constexpr int kBlk = 512 / TBN;
         for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
             int ct, ch, b_row0, nb;
-            unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
+            unit_span<MODE, TBN>(args, P, u, ct, ch, b_row0, nb);
             double acc[2] = {0.0, 0.0};
+            ReluAcc ra[2];
+            relu_zero(ra[0]);
+            relu_zero(ra[1]);
+            int inblk = 0;
             for (int i = 0; i < nb; ++i, ++t) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
+                    const int rg = (t % RH) * 2 + h;
                     if (alive) {
                         // the TMEM loads below are warp-collective: decide per warp
-                        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag, wait_ns));
+                        const bool ok =
+                            __all_sync(0xffffffffu, tc::mbar_wait(&t_full[rg], (t / RH) & 1, abort_flag, wait_ns));
                         if (!ok) {
                             if (lane == 0) record_timeout(args.err, abort_flag);
                             alive = false;
@@ -597,20 +705,43 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                     }
                     if (!alive) continue;
                     tc::tc_fence_after();
-                    const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN + half * 128);
-                    // all 128 columns into registers, then hand the region back
-                    // to the MMA issuer before doing any arithmetic
-                    uint32_t r0[32], r1[32], r2[32], r3[32];
-                    tc::tmem_ld32(taddr, r0);
-                    tc::tmem_ld32(taddr + 32, r1);
-                    tc::tmem_ld32(taddr + 64, r2);
-                    tc::tmem_ld32(taddr + 96, r3);
-                    tc::tmem_ld_wait();
-                    tc::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&t_empty[h]);
-                    const float s = relu_sum128(r0, r1, r2, r3);
-                    acc[h] += (double)s;
+                    const uint32_t taddr =
+                        tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(rg * TBN + half * (TBN / 2));
+                    // all TBN / 2 columns into registers, then hand the region
+                    // back to the MMA issuer before doing any arithmetic
+                    if constexpr (TBN == 256) {
+                        uint32_t r0[32], r1[32], r2[32], r3[32];
+                        tc::tmem_ld32(taddr, r0);
+                        tc::tmem_ld32(taddr + 32, r1);
+                        tc::tmem_ld32(taddr + 64, r2);
+                        tc::tmem_ld32(taddr + 96, r3);
+                        tc::tmem_ld_wait();
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&t_empty[rg]);
+                        relu_acc32(ra[h], r0);
+                        relu_acc32(ra[h], r1);
+                        relu_acc32(ra[h], r2);
+                        relu_acc32(ra[h], r3);
+                    } else {
+                        uint32_t r0[32], r1[32];
+                        tc::tmem_ld32(taddr, r0);
+                        tc::tmem_ld32(taddr + 32, r1);
+                        tc::tmem_ld_wait();
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&t_empty[rg]);
+                        relu_acc32(ra[h], r0);
+                        relu_acc32(ra[h], r1);
+                    }
+                }
+                if (++inblk == kBlk || i == nb - 1) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        acc[h] += (double)relu_fold(ra[h]);
+                        relu_zero(ra[h]);
+                    }
+                    inblk = 0;
                 }
             }
             // combine the two column halves in a fixed order
@@ -730,7 +861,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
 
     // ---------------------------------------------------------------- teardown
     __syncthreads();
-    if (warp == 1 && lane == 0) {
+    if ((warp == 1 || (DUAL && warp == NTHREADS_G / 32 - 1)) && lane == 0) {
         // every MMA this thread issued, committed or not (a timeout can stop
         // the issuer between a region's MMAs and their commit), completes
         // before the tensor memory is released
@@ -744,22 +875,30 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         volatile int never = 0;
         for (int s = 0; s < ns; ++s)
             if (last_full[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)last_full[s], &never);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 2; ++b)
             if (last_afull[b] >= 0) tc::mbar_wait(&a_full[b], (uint32_t)last_afull[b], &never);
-            if (last_tfull[b] >= 0) tc::mbar_wait(&t_full[b], (uint32_t)last_tfull[b], &never);
-        }
+        for (int r = 0; r < NREG; ++r)
+            if (last_tfull[r] >= 0) tc::mbar_wait(&t_full[r], (uint32_t)last_tfull[r], &never);
     }
     __syncthreads();
     if (warp == 1) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem_base, TMEM_COLS);
+        tc::tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS_G, 1)
     k_gains_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
     tc_pipeline<MODE_GAINS, false>(&tmA, &tmAx, &tmB, &tmBx, args);
+}
+
+// 128-point B tiles (a tile shape the autotuner may choose).
+__global__ void __launch_bounds__(NTHREADS_G, 1)
+    k_gains_tc_n128(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+                    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx,
+                    const TcArgs args) {
+    tc_pipeline<MODE_GAINS, false, false, 128>(&tmA, &tmAx, &tmB, &tmBx, args);
 }
 
 // Candidate rows too long for the resident layout (d > 128 at 16 bits).
@@ -771,10 +910,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 // FP8 e4m3 operands (kind::f8f6f4), BF16 extension step; full candidate
 // ranges or host-sized lists only.
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS_G, 1)
     k_gains_tc8(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                 const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
     tc_pipeline<MODE_GAINS, true>(&tmA, &tmAx, &tmB, &tmBx, args);
+}
+
+__global__ void __launch_bounds__(NTHREADS_G, 1)
+    k_gains_tc8_n128(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+                     const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx,
+                     const TcArgs args) {
+    tc_pipeline<MODE_GAINS, true, false, 128>(&tmA, &tmAx, &tmB, &tmBx, args);
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -1041,6 +1187,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs 
             const GroupUnit w = args.units[u];
             const GroupInst *I = args.inst + w.inst;
             double acc[2] = {0.0, 0.0};
+            ReluAcc ra[2];
+            relu_zero(ra[0]);
+            relu_zero(ra[1]);
             for (int tt = 0; tt < w.ntiles && ok; ++tt, ++t) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -1061,7 +1210,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs 
                     tc::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&t_empty[h]);
-                    acc[h] += (double)relu_sum128(r0, r1, r2, r3);
+                    relu_acc32(ra[h], r0);
+                    relu_acc32(ra[h], r1);
+                    relu_acc32(ra[h], r2);
+                    relu_acc32(ra[h], r3);
+                }
+                // FP32 blocks of four tiles (chains of at most 128 terms), then FP64
+                if (ok && ((tt & 3) == 3 || tt == w.ntiles - 1)) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        acc[h] += (double)relu_fold(ra[h]);
+                        relu_zero(ra[h]);
+                    }
                 }
             }
             if (!ok) break;
@@ -1760,18 +1920,25 @@ void pick_pipeline(int RB, int *na, int *ns) {
 }
 
 
-// Pipeline shape and chunk policy for a bulk launch: the largest shape that
-// fits shared memory, unless the tuning table (or the autotuner) says otherwise.
-void choose_config(const Ctx &c, int prec, int RB, int *na, int *ns, int *chunk_mode) {
+// Pipeline shape, point-tile width and chunk policy for a bulk launch: 256-
+// point tiles in the largest shape that fits shared memory, unless the
+// tuning table (or the autotuner) says otherwise.
+void choose_config(const Ctx &c, int prec, int RB, int *na, int *ns, int *chunk_mode, int *bn, int *turns) {
     pick_pipeline(RB, na, ns);
     *chunk_mode = 0;
+    *bn = BN;
+    *turns = RB >= 256 ? 1 : 0;  // measured: turns pay off from 256-byte rows
     TuneCfg t;
     if (tune_lookup(c, prec, RB, c.n, &t)) {
-        if (t.ns >= 2 && t.na >= 1 && (int)smem_layout(RB, t.ns, t.na).total <= SMEM_LIMIT) {
+        const int tbn = t.bn == 128 ? 128 : BN;
+        if (t.ns >= 2 && t.ns <= 6 && t.na >= 1 && t.na <= 2 &&
+            (int)smem_layout(RB, t.ns, t.na, tbn).total <= SMEM_LIMIT) {
             *na = t.na;
             *ns = t.ns;
+            *bn = tbn;
         }
         *chunk_mode = t.chunk;
+        if (t.turns == 0 || t.turns == 1) *turns = t.turns;
     }
 }
 
@@ -1816,8 +1983,9 @@ cudaError_t allow_smem(const void *kernel, uint32_t bytes) {
 bool tc_supported(const Ctx &c) { return c.d <= 4096; }
 bool tc_resident_supported(const Ctx &c) { return c.d <= 128; }
 
-bool tc_config_fits(int RB, int na, int ns) {
-    return na >= 1 && na <= 2 && ns >= 2 && ns <= 6 && (int)smem_layout(RB, ns, na).total <= SMEM_LIMIT;
+bool tc_config_fits(int RB, int na, int ns, int bn) {
+    return na >= 1 && na <= 2 && ns >= 2 && ns <= 6 && (bn == 128 || bn == BN) &&
+           (int)smem_layout(RB, ns, na, bn).total <= SMEM_LIMIT;
 }
 
 int tc_row_bytes(const Ctx &c) {
@@ -1884,6 +2052,10 @@ cudaError_t tc8_setup(Ctx &c) {
             return e;
         if ((e = make_map(&T.tmBx, T.Bext, T.n_pad, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess)
             return e;
+        if ((e = make_map_u8(&T.tmB128, T.Qp, T.n_pad, T.DP, 128, 128)) != cudaSuccess) return e;
+        if ((e = make_map(&T.tmBx128, T.Bext, T.n_pad, KEXT, true, KEXT, 128, CU_TENSOR_MAP_SWIZZLE_32B)) !=
+            cudaSuccess)
+            return e;
     }
     T.ready = true;
     return tc8_quantize(c);
@@ -1899,11 +2071,12 @@ cudaError_t launch_prep_tc8(Ctx &c, bool upper) {
 
 cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks_out) {
     Ctx::Tc8 &T = c.tc8;
-    int na = 0, ns = 0, chunk_mode = 0;
-    choose_config(c, EBC_FP8E4M3, T.DP, &na, &ns, &chunk_mode);
+    int na = 0, ns = 0, chunk_mode = 0, bn = BN, turns = 0;
+    choose_config(c, EBC_FP8E4M3, T.DP, &na, &ns, &chunk_mode, &bn, &turns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = smem_layout(T.DP, ns, na);
-    if (cudaError_t e = allow_smem((const void *)k_gains_tc8, L.total); e != cudaSuccess) return e;
+    const SmemLayout L = smem_layout(T.DP, ns, na, bn);
+    const void *kfn = bn == BN ? (const void *)k_gains_tc8 : (const void *)k_gains_tc8_n128;
+    if (cudaError_t e = allow_smem(kfn, L.total); e != cudaSuccess) return e;
     if (cand) {
         const int64_t tot = m * (T.DP / 16 + 2);
         k_gather_rows8<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Qc, T.Aext, T.fc, cand, m, T.DP, T.Cq,
@@ -1913,7 +2086,7 @@ cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks_ou
     TcArgs a{};
     a.wait_ns = wait_limit_ns();
     a.m = m;
-    a.n_vtiles = (int)(T.n_pad / BN);
+    a.n_vtiles = (int)(T.n_pad / bn);
     a.n_ctiles = (int)((m + BM - 1) / BM);
     const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
     a.nchunks = pick_chunks(m, a.n_vtiles, G, c.partial_cap, &a.vt_per_chunk);
@@ -1924,16 +2097,21 @@ cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks_ou
     a.xatom = 128;
     a.nstages = ns;
     a.na = na;
-    a.idesc = tc::idesc_f16(0u, BMS, BN);  // kind::f8f6f4 with format 0: e4m3 x e4m3
-    a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
+    a.turns = turns;
+    a.idesc = tc::idesc_f16(0u, BMS, (uint32_t)bn);  // kind::f8f6f4 with format 0: e4m3 x e4m3
+    a.idesc_ext = tc::idesc_f16(1u, BMS, (uint32_t)bn);
     a.partial = c.partial;
     a.err = &c.st->err;
     a.row_scale = cand ? T.Cfc : T.fc;
     a.partial_cap = c.partial_cap;
     a.G = G;
     const int units = a.n_ctiles * a.nchunks;
-    k_gains_tc8<<<std::min(units, G), NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA, cand ? T.tmAx_C : T.tmAx,
-                                                                     T.tmB, T.tmBx, a);
+    if (bn == BN)
+        k_gains_tc8<<<std::min(units, G), NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA,
+                                                                         cand ? T.tmAx_C : T.tmAx, T.tmB, T.tmBx, a);
+    else
+        k_gains_tc8_n128<<<std::min(units, G), NTHREADS_G, L.total, c.stream>>>(
+            cand ? T.tmA_C : T.tmA, cand ? T.tmAx_C : T.tmAx, T.tmB128, T.tmBx128, a);
     *nchunks_out = a.nchunks;
     return cudaGetLastError();
 }
@@ -1996,6 +2174,8 @@ cudaError_t tc_setup(Ctx &c, int prec) {
     if (e == cudaSuccess) e = make_map(&T.tmAx_C, T.Cqx, T.n_pad, KEXT, true, KEXT, BMS, CU_TENSOR_MAP_SWIZZLE_32B);
     if (e == cudaSuccess) e = make_map(&T.tmBx, T.Bext, T.n_pad, KEXT, true, KEXT, BN, CU_TENSOR_MAP_SWIZZLE_32B);
     if (e == cudaSuccess) e = make_map(&T.tmPx, T.Px, T.n_pad, KEXT, true, KEXT, BMS, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (e == cudaSuccess) e = make_map(&T.tmB_V128, T.Vq2, T.n_pad, T.DP, bf, KATOM, 128, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e == cudaSuccess) e = make_map(&T.tmBx128, T.Bext, T.n_pad, KEXT, true, KEXT, 128, CU_TENSOR_MAP_SWIZZLE_32B);
     if (e != cudaSuccess) return e;
     return tc_quantize(c);
 }
@@ -2012,11 +2192,12 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     Ctx::Tc &T = c.tc;
     const int DP = T.DP;
     const bool kb = use_kb(c, 2 * DP);
-    int na = 1, ns = KB_STAGES, chunk_mode = 0;
-    if (!kb) choose_config(c, T.prec, 2 * DP, &na, &ns, &chunk_mode);
+    int na = 1, ns = KB_STAGES, chunk_mode = 0, bn = BN, turns = 0;
+    if (!kb) choose_config(c, T.prec, 2 * DP, &na, &ns, &chunk_mode, &bn, &turns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
-    const SmemLayout L = kb ? smem_layout_kb(ns) : smem_layout(2 * DP, ns, na);
-    const void *kfn = kb ? (const void *)k_gains_tc_kb : (const void *)k_gains_tc;
+    const SmemLayout L = kb ? smem_layout_kb(ns) : smem_layout(2 * DP, ns, na, bn);
+    const void *kfn = kb ? (const void *)k_gains_tc_kb
+                         : (bn == BN ? (const void *)k_gains_tc : (const void *)k_gains_tc_n128);
     if (cudaError_t e = allow_smem(kfn, L.total); e != cudaSuccess) return e;
     if (cand) {
         int64_t tot = m * (DP / 8 + 2);
@@ -2028,7 +2209,7 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     TcArgs a{};
     a.wait_ns = wait_limit_ns();
     a.m = m;
-    a.n_vtiles = (int)(T.n_pad / BN);
+    a.n_vtiles = (int)(T.n_pad / bn);
     a.n_ctiles = (int)((m + BM - 1) / BM);
     // V chunks: balance the persistent grid (units = candidate tiles x chunks)
     const int G = (c.max_ctas > 0 && c.max_ctas < c.num_sms) ? c.max_ctas : c.num_sms;
@@ -2049,8 +2230,9 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     a.row_scale = nullptr;
     a.nstages = ns;
     a.na = na;
-    a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, BN);
-    a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
+    a.turns = turns;
+    a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, (uint32_t)bn);
+    a.idesc_ext = tc::idesc_f16(1u, BMS, (uint32_t)bn);
     a.partial = c.partial;
     a.err = &c.st->err;
     const int units = a.n_ctiles * a.nchunks;
@@ -2058,9 +2240,12 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     if (kb)
         k_gains_tc_kb<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V,
                                                              T.tmB_V, T.tmBx, a);
-    else
-        k_gains_tc<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V, T.tmB_V,
+    else if (bn == BN)
+        k_gains_tc<<<grid, NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V, T.tmB_V,
                                                           T.tmBx, a);
+    else
+        k_gains_tc_n128<<<grid, NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V,
+                                                               T.tmB_V128, T.tmBx128, a);
     *nchunks_out = a.nchunks;
     return cudaGetLastError();
 }
@@ -2163,6 +2348,7 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     a.row_scale = nullptr;
     a.nstages = ns;
     a.na = na;
+    a.turns = 2 * DP >= 256 ? 1 : 0;
     a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, BN);
     a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
     a.partial = c.partial;
@@ -2174,7 +2360,7 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     if (kb)
         k_gains_tc_kb<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
     else
-        k_gains_tc<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
+        k_gains_tc<<<G, NTHREADS_G, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,8 @@
 // Tuning table of the tensor-core bulk kernel: for a (precision, row bytes,
-// n bucket) key, the pipeline shape (candidate-tile buffers, point-tile
-// stages) and the V-chunk policy found fastest by ebc_autotune (api.cu).
+// n bucket) key, the point-tile width (256 or 128 points), whether the two
+// MMA issuers take turns, the pipeline shape (candidate-tile buffers,
+// point-tile stages) and the V-chunk policy found fastest by ebc_autotune
+// (api.cu).
 // Process-wide, guarded by a mutex; saved to and loaded from a small JSON
 // file.  Entries only change how the bulk bounds are scheduled and summed
 // (chunk grouping); picks and f do not depend on them.
@@ -45,6 +47,15 @@ bool tune_lookup(const Ctx &c, int prec, int RB, int64_t n, TuneCfg *cfg) {
     auto it = g_table.find(Key(prec, RB, n_bucket(n)));
     if (it == g_table.end()) return false;
     *cfg = it->second.cfg;
+    return true;
+}
+
+bool tune_get(int prec, int RB, int64_t n, TuneCfg *cfg, double *ms) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_table.find(Key(prec, RB, n_bucket(n)));
+    if (it == g_table.end()) return false;
+    *cfg = it->second.cfg;
+    *ms = it->second.ms;
     return true;
 }
 
@@ -96,8 +107,11 @@ ebc_status ebc_tune_save(const char *path) {
     for (const auto &kv : ebc::g_table) {
         const auto &k = kv.first;
         const auto &e = kv.second;
-        fprintf(f, "%s\n  {\"prec\": %d, \"rb\": %d, \"nbucket\": %d, \"na\": %d, \"ns\": %d, \"chunk\": %d, \"ms\": %.6f}",
-                first ? "" : ",", std::get<0>(k), std::get<1>(k), std::get<2>(k), e.cfg.na, e.cfg.ns, e.cfg.chunk, e.ms);
+        fprintf(f,
+                "%s\n  {\"prec\": %d, \"rb\": %d, \"nbucket\": %d, \"na\": %d, \"ns\": %d, \"chunk\": %d, "
+                "\"bn\": %d, \"turns\": %d, \"ms\": %.6f}",
+                first ? "" : ",", std::get<0>(k), std::get<1>(k), std::get<2>(k), e.cfg.na, e.cfg.ns, e.cfg.chunk,
+                e.cfg.bn, e.cfg.turns, e.ms);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -135,18 +149,22 @@ ebc_status ebc_tune_load(const char *path) {
             const size_t colon = obj.find(':', p + key.size());
             return colon != std::string::npos && sscanf(obj.c_str() + colon + 1, "%lf", out) == 1;
         };
-        double prec, rb, nb, na, ns, chunk, ms = 0.0;
+        double prec, rb, nb, na, ns, chunk, bn = 256, turns = -1, ms = 0.0;
         if (!field("prec", &prec) || !field("rb", &rb) || !field("nbucket", &nb) || !field("na", &na) ||
             !field("ns", &ns) || !field("chunk", &chunk))
             return EBC_EINVAL;
         field("ms", &ms);
+        field("bn", &bn);        // absent: 256-point tiles
+        field("turns", &turns);  // absent: by row width
         if (prec < 1 || prec > 3 || rb < 128 || rb > 512 || nb < 0 || nb > 62 || na < 1 || na > 2 || ns < 2 ||
-            ns > 6 || chunk < 0 || chunk > 2)
+            ns > 6 || chunk < 0 || chunk > 2 || (bn != 256 && bn != 128) || turns < -1 || turns > 1)
             return EBC_EINVAL;
         ebc::Entry e;
         e.cfg.na = (int)na;
         e.cfg.ns = (int)ns;
         e.cfg.chunk = (int)chunk;
+        e.cfg.bn = (int)bn;
+        e.cfg.turns = (int)turns;
         e.ms = ms;
         add[ebc::Key((int)prec, (int)rb, (int)nb)] = e;
         pos = b + 1;

@@ -96,6 +96,7 @@ _SIGS = {
     "ebc_state_save": [_P, _P, _I64],
     "ebc_state_load": [_P, _P, _I64],
     "ebc_autotune": [_P, _I32],
+    "ebc_tune_query": [_P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)],
     "ebc_tune_save": [ctypes.c_char_p],
     "ebc_tune_load": [ctypes.c_char_p],
     "ebc_tune_count": [],
@@ -430,6 +431,17 @@ class Instance:
 
     def autotune(self, reps: int = 3):
         ebc_autotune(self.h, reps)
+
+    def tune_entry(self):
+        """The tuning-table entry bulk launches of this instance use at its
+        current precision: dict(bn, na, ns, chunk, turns, ms), or None when
+        its bucket has none (the default 256-point shape)."""
+        cfg = (_I32 * 5)()
+        ms = ctypes.c_double()
+        _raise(self.h, load().ebc_tune_query(_P(self.h), cfg, ctypes.byref(ms)))
+        if cfg[0] == 0:
+            return None
+        return {"bn": cfg[0], "na": cfg[1], "ns": cfg[2], "chunk": cfg[3], "turns": cfg[4], "ms": ms.value}
 
     def save_state(self) -> bytes:
         """Snapshot of the Greedy state (m_v, S, f, counters) as bytes."""

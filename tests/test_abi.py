@@ -103,7 +103,7 @@ def test_tune_table_json_roundtrip(lib, tmp_path):
     good = tmp_path / "tune.json"
     good.write_text('{"version": 1, "entries": [\n'
                     ' {"prec": 1, "rb": 256, "nbucket": 17, "na": 1, "ns": 2, "chunk": 0, "ms": 7.2},\n'
-                    ' {"ns": 3, "na": 2, "prec": 3, "rb": 128, "nbucket": 12, "chunk": 1}\n]}\n')
+                    ' {"ns": 3, "na": 2, "prec": 3, "rb": 128, "nbucket": 12, "chunk": 1, "bn": 128}\n]}\n')
     ebc.ebc_tune_load(str(good))
     assert ebc.ebc_tune_count() == 2
     out = tmp_path / "out.json"
@@ -113,8 +113,12 @@ def test_tune_table_json_roundtrip(lib, tmp_path):
     assert ebc.ebc_tune_count() == 2
     text = out.read_text()
     assert '"rb": 256' in text and '"chunk": 1' in text
+    assert text.count('"bn": 128') == 1 and text.count('"bn": 256') == 1  # absent width: 256
+    assert text.count('"turns": -1') == 2  # absent: by row width
     for bad in ['{"entries": [{"prec": 1, "rb": 256}]}',
                 '{"entries": [{"prec": 9, "rb": 256, "nbucket": 3, "na": 1, "ns": 2, "chunk": 0}]}',
+                '{"entries": [{"prec": 1, "rb": 256, "nbucket": 3, "na": 1, "ns": 2, "chunk": 0, "bn": 64}]}',
+                '{"entries": [{"prec": 1, "rb": 256, "nbucket": 3, "na": 1, "ns": 2, "chunk": 0, "turns": 2}]}',
                 'not json']:
         p = tmp_path / "bad.json"
         p.write_text(bad)
