@@ -34,7 +34,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the bulk kernel from one ncu capture
 # of the current kernel at the full size (profiles/k_gains_tc_bf16_regime_d128.md),
 # keyed by (precision, n, d); None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("bf16", 200_000, 128): 305.729792e6 + 11.341312e6}
+NCU_TRAFFIC = {("bf16", 200_000, 128): 304.929280e6 + 11.217920e6}
 
 
 def peaks():
@@ -591,8 +591,8 @@ def run_sets(args):
             "roofline": {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
                          "frac": achieved / peak if achieved else None, "traffic": None,
                          "peak_source": f"{pk['source']} bf16 burst",
-                         "kernel": "multi-set evaluation (device plan + tcgen05 sets kernel with in-kernel member "
-                                   "gather + finalize)",
+                         "kernel": "multi-set evaluation (device plan + member gather + tcgen05 sets kernel "
+                                   "+ finalize)",
                          "avg_ms": kern_ms, "algorithmic_flops_per_launch": flops},
             "gpu_launches": prof_tc["launches"], "clocks": clk,
             "fp32_plain": {"value": evals / (ms_32 / 1e3), "unit": UNIT, "ms_per_step": ms_32,

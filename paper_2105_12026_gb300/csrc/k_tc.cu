@@ -328,6 +328,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
     static_assert(TBN == BN || (TBN == 128 && MODE == MODE_GAINS && !KB), "128-point tiles: resident gains only");
     // resident bulk gains: one MMA issuer per candidate sub-tile (warp 1 and
     // the last warp), each waiting and committing while the other issues
+    // (measured: no gain for the multi-set kernel, whose set epilogue bounds it)
     constexpr bool DUAL = MODE == MODE_GAINS && !KB;
     constexpr int NREG = TBN == 128 ? 4 : 2;  // TMEM regions
     // with two regions the issuers may take turns (sub-tile 0 of a tile, then
@@ -335,6 +336,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
     // tile before region 1 and its epilogue overlaps region 1's MMAs (pays
     // off for long rows); otherwise their MMAs interleave freely
     const bool turns = DUAL && NREG == 2 && args.turns != 0;
+    static_assert(!DUAL || NTHREADS_G / 32 - 1 >= 10, "the second issuer follows the epilogue warps");
     constexpr int RH = NREG / 2;               // point tiles in flight in TMEM
     constexpr uint32_t kTmemCols = NREG * TBN;
     const CUtensorMap &tmA = *tmA_p, &tmAx = *tmAx_p, &tmB = *tmB_p, &tmBx = *tmBx_p;
@@ -969,10 +971,11 @@ struct GroupArgs {
     int *err;
     int RBmax, nstages, na;
     uint64_t wait_ns;
+    int turns;  // the two MMA issuers take turns (rows of 256 bytes or more)
 };
 }  // namespace
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs args) {
+__global__ void __launch_bounds__(NTHREADS_G, 1) k_gains_tc_group(const GroupArgs args) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ns = args.nstages;
@@ -999,18 +1002,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs 
     uint64_t *c_full = u_empty + UR;   // column half 1 -> half 0: comb written
     uint64_t *c_empty = c_full + 1;    // half 0 -> half 1: comb read
     volatile int *u_id = reinterpret_cast<volatile int *>(c_empty + 1);  // [UR]
+    uint64_t *tok = reinterpret_cast<uint64_t *>(base + L.off_misc + 160);  // [2] issuer turns
+    const bool turns = args.turns != 0;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < ns; ++s) {
             tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
+            tc::mbar_init(&empty[s], 2);  // both MMA issuers
             last_full[s] = -1;
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&a_full[b], 1);
-            tc::mbar_init(&a_empty[b], 1);
+            tc::mbar_init(&a_empty[b], 2);
             tc::mbar_init(&t_full[b], 1);
             tc::mbar_init(&t_empty[b], NEPI / 32);
             last_afull[b] = -1;
@@ -1018,11 +1023,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs 
         }
         for (int r = 0; r < UR; ++r) {
             tc::mbar_init(&u_full[r], 1);
-            tc::mbar_init(&u_empty[r], 1 + NEPI / 32);  // the MMA issuer and every epilogue warp
+            tc::mbar_init(&u_empty[r], 2 + NEPI / 32);  // both MMA issuers and every epilogue warp
         }
         tc::mbar_init(c_full, NEPI / 2);  // every thread of the column-half-1 warps
         tc::mbar_init(c_empty, NEPI / 2);
-        tc::mbar_init(fin, 1);
+        tc::mbar_init(fin, 2);
+        tc::mbar_init(&tok[0], 1);
+        tc::mbar_init(&tok[1], 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -1101,9 +1108,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs 
                 ++ua;
             }
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
+    } else if (warp == 1 || warp == NTHREADS_G / 32 - 1) {
+        // ------------------------------------------------------------ MMA issuers
+        // warp 1 issues sub-tile 0 of every point tile, the last warp sub-tile
+        // 1 (each waits and commits while the other issues); with turns they
+        // alternate, so region 0 completes half a tile before region 1
         if (lane == 0) {
+            const int h = warp == 1 ? 0 : 1;
             int g = 0, t = 0, ua = 0;
             for (int i = 0;; ++i) {
                 const int r = i % UR;
@@ -1133,27 +1144,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs 
                         break;
                     }
                     const uint32_t b0 = tc::smem_u32(sB + s * L.b_bytes);
-                    for (int h = 0; h < 2; ++h) {
-                        if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag, wait_ns)) {
-                            record_timeout(args.err, abort_flag);
-                            ok = false;
-                            break;
-                        }
-                        tc::tc_fence_after();
-                        const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
-                        const uint32_t ah = a0 + h * L.a_sub;
-                        for (int kk = 0; kk < nmma; ++kk) {
-                            const uint32_t j = kk >> 2, w4 = kk & 3;
-                            const uint64_t ad = tc::sdesc_sw128(ah + j * (BMS * 128) + w4 * 32);
-                            const uint64_t bd = tc::sdesc_sw128(b0 + j * (BN * 128) + w4 * 32);
-                            tc::mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
-                        }
-                        tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main), idesc_ext,
-                                    1u);
-                        tc::mma_commit(&t_full[h]);
-                        last_tfull[h] = t & 1;
+                    if (!tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag, wait_ns)) {
+                        record_timeout(args.err, abort_flag);
+                        ok = false;
+                        break;
                     }
-                    if (!ok) break;
+                    if (turns && (h == 1 || t > 0) &&
+                        !tc::mbar_wait(&tok[1 - h], (uint32_t)(h == 1 ? t : t - 1) & 1u, abort_flag, wait_ns)) {
+                        record_timeout(args.err, abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
+                    const uint32_t ah = a0 + h * L.a_sub;
+                    for (int kk = 0; kk < nmma; ++kk) {
+                        const uint32_t j = kk >> 2, w4 = kk & 3;
+                        const uint64_t ad = tc::sdesc_sw128(ah + j * (BMS * 128) + w4 * 32);
+                        const uint64_t bd = tc::sdesc_sw128(b0 + j * (BN * 128) + w4 * 32);
+                        tc::mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    }
+                    tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main), idesc_ext,
+                                1u);
+                    if (turns) tc::mbar_arrive(&tok[h]);
+                    tc::mma_commit(&t_full[h]);
+                    last_tfull[h] = t & 1;
                     tc::mma_commit(&empty[s]);
                 }
                 if (!ok) break;
@@ -1253,7 +1268,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_gains_tc_group(const GroupArgs 
 
     // ---------------------------------------------------------------- teardown
     __syncthreads();
-    if (warp == 1 && lane == 0) {
+    if ((warp == 1 || warp == NTHREADS_G / 32 - 1) && lane == 0) {
         volatile int never = 0;
         tc::mma_commit(fin);
         tc::mbar_wait(fin, 0u, &never);
@@ -2312,7 +2327,8 @@ cudaError_t launch_gains_tc_group(const GroupInst *d_inst, const GroupUnit *d_un
     a.nstages = ns;
     a.na = na;
     a.wait_ns = wait_limit_ns();
-    k_gains_tc_group<<<std::min(total_units, G), NTHREADS, bytes, s>>>(a);
+    a.turns = RBmax >= 256 ? 1 : 0;
+    k_gains_tc_group<<<std::min(total_units, G), NTHREADS_G, bytes, s>>>(a);
     return cudaGetLastError();
 }
 
