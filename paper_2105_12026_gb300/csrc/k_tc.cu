@@ -265,10 +265,13 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[16], int lane
 
 // Running sums of max(0, x) over accumulator words with packed FP32x2 adds:
 // two 64-bit accumulators hold four FP32 chains, word i of every 32-word
-// group going to chain i % 4 (8 terms per group and chain).  relu_fold joins
-// the chains (one packed add, one scalar add).  A caller that folds after
-// at most 16 groups (4 tiles of 128 columns, or 8 of 64) keeps every chain
-// an ordinary FP32 sum of at most 128 non-negative terms.
+// group going to chain i % 4 (8 terms per group and chain).  Words 0, 1 of
+// every four take max(x, 0) (ALU pipe); words 2, 3 take x + |x| = 2 max(x, 0)
+// exactly (one FMA-pipe add with an absolute-value operand), so the ALU pipe
+// does half of that work; relu_fold halves those chains (exact) when it
+// joins them.  A caller that folds after at most 16 groups (4 tiles of 128
+// columns, or 8 of 64) keeps every chain an ordinary FP32 sum of at most 128
+// non-negative terms.
 __device__ __forceinline__ unsigned long long pack2(float a, float b) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
@@ -284,22 +287,26 @@ __device__ __forceinline__ void relu_zero(ReluAcc &s) {
     s.b = pack2(0.f, 0.f);
 }
 
+__device__ __forceinline__ float twice_relu(uint32_t w) {
+    const float x = __uint_as_float(w);
+    return x + fabsf(x);
+}
+
 __device__ __forceinline__ void relu_acc32(ReluAcc &s, const uint32_t (&r)[32]) {
 #pragma unroll
     for (int i = 0; i < 32; i += 4) {
         const unsigned long long x = pack2(fmaxf(__uint_as_float(r[i]), 0.f), fmaxf(__uint_as_float(r[i + 1]), 0.f));
-        const unsigned long long y = pack2(fmaxf(__uint_as_float(r[i + 2]), 0.f), fmaxf(__uint_as_float(r[i + 3]), 0.f));
+        const unsigned long long y = pack2(twice_relu(r[i + 2]), twice_relu(r[i + 3]));
         asm("add.rn.f32x2 %0, %0, %1;" : "+l"(s.a) : "l"(x));
         asm("add.rn.f32x2 %0, %0, %1;" : "+l"(s.b) : "l"(y));
     }
 }
 
 __device__ __forceinline__ float relu_fold(const ReluAcc &s) {
-    unsigned long long a = s.a;
-    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(s.b));
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
-    return lo + hi;
+    float alo, ahi, blo, bhi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(alo), "=f"(ahi) : "l"(s.a));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(blo), "=f"(bhi) : "l"(s.b));
+    return (alo + ahi) + 0.5f * (blo + bhi);
 }
 
 }  // namespace
