@@ -75,7 +75,7 @@ constexpr int NPAD = 256;        // row padding of the quantised arrays
 constexpr int KATOM = 64;        // 16-bit elements per 128-byte swizzle atom
 constexpr int KEXT = 16;         // extension columns (one MMA K step)
 constexpr int NTHREADS = 320;
-constexpr int NTHREADS_G = 352;  // resident bulk gains: a second MMA issuer warp
+constexpr int NTHREADS_G = 352;  // bulk gains: a second MMA issuer warp
 constexpr int NEPI = 256;        // epilogue threads
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -333,10 +333,10 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                                             const CUtensorMap *tmB_p, const CUtensorMap *tmBx_p, const TcArgs &args) {
     static_assert(!KB || !F8, "K-blocked layout: 16-bit operands only");
     static_assert(TBN == BN || (TBN == 128 && MODE == MODE_GAINS && !KB), "128-point tiles: resident gains only");
-    // resident bulk gains: one MMA issuer per candidate sub-tile (warp 1 and
-    // the last warp), each waiting and committing while the other issues
-    // (measured: no gain for the multi-set kernel, whose set epilogue bounds it)
-    constexpr bool DUAL = MODE == MODE_GAINS && !KB;
+    // bulk gains: one MMA issuer per candidate sub-tile (warp 1 and the last
+    // warp), each waiting and committing while the other issues (measured:
+    // no gain for the multi-set kernel, whose set epilogue bounds it)
+    constexpr bool DUAL = MODE == MODE_GAINS;
     constexpr int NREG = TBN == 128 ? 4 : 2;  // TMEM regions
     // with two regions the issuers may take turns (sub-tile 0 of a tile, then
     // sub-tile 1, then sub-tile 0 of the next), so region 0 completes half a
@@ -510,7 +510,59 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         // into region 1.  The epilogue drains one region while the other fills.
         if (lane == 0) {
             int g = 0, t = 0, ua = 0;
-            if constexpr (DUAL) {
+            if constexpr (DUAL && KB) {
+                // sub-tile h of every point tile, accumulated over all K atoms;
+                // both issuers wait for the same stages and extension buffer and
+                // both commit their release (count 2)
+                const int h = warp == 1 ? 0 : 1;
+                const uint32_t sx = tc::smem_u32(base + L.off_ext);
+                for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
+                    int ct, ch, b_row0, nb;
+                    unit_span<MODE>(args, P, u, ct, ch, b_row0, nb);
+                    bool ok = true;
+                    for (int i = 0; i < nb && ok; ++i, ++t) {
+                        const uint32_t d_tmem = tmem_base + (uint32_t)(h * BN);
+                        for (int j = 0; j < katoms; ++j, ++g) {
+                            const int s = g % ns;
+                            if (!tc::mbar_wait(&full[s], (g / ns) & 1, abort_flag, wait_ns)) {
+                                record_timeout(args.err, abort_flag);
+                                ok = false;
+                                break;
+                            }
+                            const bool last = j == katoms - 1;
+                            if (last && !tc::mbar_wait(&a_full[0], t & 1, abort_flag, wait_ns)) {
+                                record_timeout(args.err, abort_flag);
+                                ok = false;
+                                break;
+                            }
+                            if (j == 0 && !tc::mbar_wait(&t_empty[h], (t & 1) ^ 1, abort_flag, wait_ns)) {
+                                record_timeout(args.err, abort_flag);
+                                ok = false;
+                                break;
+                            }
+                            tc::tc_fence_after();
+                            const uint32_t st = tc::smem_u32(sB + s * L.b_bytes);
+                            const uint32_t b0 = st + 2 * BMS * 128;
+                            const uint32_t ah = st + h * (BMS * 128);
+                            for (int w = 0; w < 4; ++w) {
+                                const uint64_t ad = tc::sdesc_sw128(ah + w * 32);
+                                const uint64_t bd = tc::sdesc_sw128(b0 + w * 32);
+                                tc::mma_f16(d_tmem, ad, bd, args.idesc, (j > 0 || w > 0) ? 1u : 0u);
+                            }
+                            if (last) {
+                                tc::mma_f16(d_tmem, tc::sdesc_sw32(sx + h * (BMS * KEXT * 2)),
+                                            tc::sdesc_sw32(sx + 2 * (BMS * KEXT * 2)), args.idesc_ext, 1u);
+                                tc::mma_commit(&a_empty[0]);
+                            }
+                            tc::mma_commit(&empty[s]);
+                        }
+                        if (!ok) break;
+                        tc::mma_commit(&t_full[h]);
+                        last_tfull[h] = t & 1;
+                    }
+                    if (!ok) break;
+                }
+            } else if constexpr (DUAL) {
                 // sub-tile h of every point tile; both issuers wait for the same
                 // A and B stages and both commit their release (count 2)
                 const int h = warp == 1 ? 0 : 1;
@@ -911,7 +963,7 @@ __global__ void __launch_bounds__(NTHREADS_G, 1)
 }
 
 // Candidate rows too long for the resident layout (d > 128 at 16 bits).
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS_G, 1)
     k_gains_tc_kb(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                   const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
     tc_pipeline<MODE_GAINS, false, true>(&tmA, &tmAx, &tmB, &tmBx, args);
@@ -2260,7 +2312,7 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     const int units = a.n_ctiles * a.nchunks;
     const int grid = std::min(units, G);
     if (kb)
-        k_gains_tc_kb<<<grid, NTHREADS, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V,
+        k_gains_tc_kb<<<grid, NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V,
                                                              T.tmB_V, T.tmBx, a);
     else if (bn == BN)
         k_gains_tc<<<grid, NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V, T.tmB_V,
@@ -2381,7 +2433,7 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     a.G = G;
     a.nch_out = &c.st->list_nch;
     if (kb)
-        k_gains_tc_kb<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
+        k_gains_tc_kb<<<G, NTHREADS_G, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
     else
         k_gains_tc<<<G, NTHREADS_G, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
     return cudaGetLastError();
