@@ -1030,7 +1030,6 @@ struct GroupArgs {
     int *err;
     int RBmax, nstages, na;
     uint64_t wait_ns;
-    int turns;  // the two MMA issuers take turns (rows of 256 bytes or more)
 };
 }  // namespace
 
@@ -1062,7 +1061,6 @@ __global__ void __launch_bounds__(NTHREADS_G, 1) k_gains_tc_group(const GroupArg
     uint64_t *c_empty = c_full + 1;    // half 0 -> half 1: comb read
     volatile int *u_id = reinterpret_cast<volatile int *>(c_empty + 1);  // [UR]
     uint64_t *tok = reinterpret_cast<uint64_t *>(base + L.off_misc + 160);  // [2] issuer turns
-    const bool turns = args.turns != 0;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -1170,11 +1168,13 @@ __global__ void __launch_bounds__(NTHREADS_G, 1) k_gains_tc_group(const GroupArg
     } else if (warp == 1 || warp == NTHREADS_G / 32 - 1) {
         // ------------------------------------------------------------ MMA issuers
         // warp 1 issues sub-tile 0 of every point tile, the last warp sub-tile
-        // 1 (each waits and commits while the other issues); with turns they
-        // alternate, so region 0 completes half a tile before region 1
+        // 1 (each waits and commits while the other issues); in units of
+        // 256-byte rows they take turns, so region 0 completes half a tile
+        // before region 1
         if (lane == 0) {
             const int h = warp == 1 ? 0 : 1;
             int g = 0, t = 0, ua = 0;
+            int tk = 0;  // tiles of units that take turns (both issuers count the same ones)
             for (int i = 0;; ++i) {
                 const int r = i % UR;
                 if (!tc::mbar_wait(&u_full[r], (i / UR) & 1, abort_flag, wait_ns)) {
@@ -1188,6 +1188,7 @@ __global__ void __launch_bounds__(NTHREADS_G, 1) k_gains_tc_group(const GroupArg
                 const GroupInst *I = args.inst + w.inst;
                 const int nmma = I->RB / 32;  // one MMA per 32 bytes of K
                 const uint32_t idesc = I->idesc, idesc_ext = I->idesc_ext;
+                const bool turns = I->RB >= 256;  // rows of 256 bytes: turns; shorter rows: free issue
                 const int ab = ua % na;
                 if (!tc::mbar_wait(&a_full[ab], (ua / na) & 1, abort_flag, wait_ns)) {
                     record_timeout(args.err, abort_flag);
@@ -1208,8 +1209,8 @@ __global__ void __launch_bounds__(NTHREADS_G, 1) k_gains_tc_group(const GroupArg
                         ok = false;
                         break;
                     }
-                    if (turns && (h == 1 || t > 0) &&
-                        !tc::mbar_wait(&tok[1 - h], (uint32_t)(h == 1 ? t : t - 1) & 1u, abort_flag, wait_ns)) {
+                    if (turns && (h == 1 || tk > 0) &&
+                        !tc::mbar_wait(&tok[1 - h], (uint32_t)(h == 1 ? tk : tk - 1) & 1u, abort_flag, wait_ns)) {
                         record_timeout(args.err, abort_flag);
                         ok = false;
                         break;
@@ -1225,7 +1226,10 @@ __global__ void __launch_bounds__(NTHREADS_G, 1) k_gains_tc_group(const GroupArg
                     }
                     tc::mma_f16(d_tmem, tc::sdesc_sw32(ah + L.a_main), tc::sdesc_sw32(b0 + L.b_main), idesc_ext,
                                 1u);
-                    if (turns) tc::mbar_arrive(&tok[h]);
+                    if (turns) {
+                        tc::mbar_arrive(&tok[h]);
+                        ++tk;
+                    }
                     tc::mma_commit(&t_full[h]);
                     last_tfull[h] = t & 1;
                     tc::mma_commit(&empty[s]);
@@ -2386,7 +2390,6 @@ cudaError_t launch_gains_tc_group(const GroupInst *d_inst, const GroupUnit *d_un
     a.nstages = ns;
     a.na = na;
     a.wait_ns = wait_limit_ns();
-    a.turns = RBmax >= 256 ? 1 : 0;
     k_gains_tc_group<<<std::min(total_units, G), NTHREADS_G, bytes, s>>>(a);
     return cudaGetLastError();
 }
