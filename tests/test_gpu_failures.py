@@ -4,7 +4,8 @@
   pipeline's waits is set to 1 ns, so waits on TMA copies, MMAs and the
   epilogue give up; each CTA records EBC_ETIMEOUT, waits (with the default
   limit) for the work it already issued, frees its tensor memory and
-  returns.  The host reads the status; with the default limit restored the
+  returns.  Covered for the resident, K-blocked, 128-point-tile, FP8,
+  multi-set and shared group kernels.  The host reads the status; with the default limit restored the
   same handle gives the same results as before, bitwise.
 * A device allocation that fails (injected on the host, in the library's
   pool allocator): ebc_create and ebc_set_precision return EBC_ENOMEM and
@@ -70,6 +71,50 @@ def test_wait_timeout_reported_and_handle_recovers(torch, prec):
         if idx[t] != ref_i[t]:
             break
     np.testing.assert_allclose(f, ref_f, rtol=1e-5)
+
+
+@pytest.mark.parametrize("case", ["kblocked", "tile128", "group"])
+def test_wait_timeout_other_kernels(torch, case, tmp_path):
+    """The same for the K-blocked kernel (d > 128), the 128-point tile shape
+    (forced through a tuning-table entry) and the shared group launch: every
+    variant's waits give up, report EBC_ETIMEOUT and leave the handles
+    usable."""
+    import json
+    import math
+    d = 256 if case == "kblocked" else 64
+    V = gmm(12_000, d, 7)
+    ebc.ebc_tune_clear()
+    if case == "tile128":
+        ent = {"prec": ebc.PRECISIONS["bf16"], "rb": 128, "nbucket": int(math.floor(math.log2(V.shape[0]))),
+               "na": 2, "ns": 3, "chunk": 0, "bn": 128}
+        path = tmp_path / "t.json"
+        path.write_text(json.dumps({"version": 1, "entries": [ent]}))
+        ebc.ebc_tune_load(str(path))
+    try:
+        with ebc.Instance(V, precision="bf16") as inst:
+            if case == "tile128":
+                assert inst.tune_entry()["bn"] == 128
+            ref_g = inst.gains_host()
+            ref_i, ref_f = inst.greedy_host(4)
+            inst.reset()
+            ebc.ebc_set_wait_limit_ns(1)
+            if case == "group":
+                with ebc.Group() as g:
+                    g.greedy([inst], [2])
+                with pytest.raises(ebc.EbcError) as ei:
+                    inst.sync()
+            else:
+                with pytest.raises(ebc.EbcError) as ei:
+                    inst.gains_host()
+            assert ei.value.status == ebc.EBC_ETIMEOUT
+            ebc.ebc_set_wait_limit_ns(0)
+            inst.reset()
+            np.testing.assert_array_equal(inst.gains_host(), ref_g)
+            idx, f = inst.greedy_host(4)
+        np.testing.assert_array_equal(idx, ref_i)
+        np.testing.assert_array_equal(f, ref_f)
+    finally:
+        ebc.ebc_tune_clear()
 
 
 def test_wait_limit_arguments(torch):
