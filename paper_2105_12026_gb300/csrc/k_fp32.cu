@@ -32,7 +32,10 @@ constexpr int KC = 16;   // dimensions per smem stage
 // arithmetic and stored to the other buffer after it, one barrier per
 // stage.  Per (candidate, point) the arithmetic is the FMA chain over the
 // dimensions in index order, and per candidate and point tile the 8 terms
-// of a thread are summed in FP32, then the 16 lanes, then tiles in FP64.
+// of a thread are summed in FP32, then the 16 lanes; the tile sums are
+// added in FP32 over blocks of up to 16 point tiles (a sum of depth at most
+// 28, within the bulk partials' error bound), and the blocks in FP64: the
+// FP64 pipe, a few lanes per clock on GB300, then adds once per block.
 namespace {
 constexpr int FC = 128;  // candidates per block
 constexpr int FV = 128;  // points per block tile
@@ -159,6 +162,10 @@ __global__ void __launch_bounds__(256, 1) k_gains_fp32(const float *__restrict__
 #pragma unroll
         for (int p = 0; p < 4; ++p) acc[i][p] = 0ull;
 
+    float tacc[8];  // FP32 sums of the current block of point tiles
+#pragma unroll
+    for (int i = 0; i < 8; ++i) tacc[i] = 0.f;
+    int tb = 0;     // point tiles in the block
     float4 cr[FPT], vr[FPT];
     if (nst > 0) {
         fp32_stage_load<VEC>(V, d, Ci, vb, ve, 0, tid, cr, vr);
@@ -213,9 +220,17 @@ __global__ void __launch_bounds__(256, 1) k_gains_fp32(const float *__restrict__
                 s += __shfl_xor_sync(0xffffffffu, s, 2);
                 s += __shfl_xor_sync(0xffffffffu, s, 4);
                 s += __shfl_xor_sync(0xffffffffu, s, 8);
-                Accd[i][tid] += (double)s;
+                tacc[i] += s;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) acc[i][p] = 0ull;
+            }
+            if (++tb == 16 || !more) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    Accd[i][tid] += (double)tacc[i];
+                    tacc[i] = 0.f;
+                }
+                tb = 0;
             }
         }
         if (more) {
