@@ -306,6 +306,10 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
             Ci[tid] = e < cnt ? list[e] : -1;
         }
         double lod[4] = {0.0, 0.0, 0.0, 0.0}, hid[4] = {0.0, 0.0, 0.0, 0.0};
+        // FP32 sums of blocks of up to 16 point tiles (depth <= 28, inside the
+        // 131 * 2^-24 widening), then FP64: one FP64 add per block, not per tile
+        float lob[4] = {0.f, 0.f, 0.f, 0.f}, hib[4] = {0.f, 0.f, 0.f, 0.f};
+        int tb = 0;
         for (int64_t v0 = vb; v0 < ve; v0 += TV) {
             __syncthreads();
             if (tid < TV) {
@@ -381,8 +385,17 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
                 sl += __shfl_xor_sync(0xffffffffu, sl, 2);
                 sl += __shfl_xor_sync(0xffffffffu, sl, 4);
                 sl += __shfl_xor_sync(0xffffffffu, sl, 8);
-                hid[i] += (double)sh;
-                lod[i] += (double)sl;
+                hib[i] += sh;
+                lob[i] += sl;
+            }
+            if (++tb == 16 || v0 + TV >= ve) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    hid[i] += (double)hib[i];
+                    lod[i] += (double)lob[i];
+                    hib[i] = lob[i] = 0.f;
+                }
+                tb = 0;
             }
         }
         if (tx == 0) {

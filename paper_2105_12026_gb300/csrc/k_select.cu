@@ -24,10 +24,11 @@ namespace ebc {
 
 namespace {
 // Relative widening of the folded bounds.  Each bound term is one FP32
-// rounding from its exact value; the bound kernel adds at most 128 terms of
-// one sign in FP32 (8 per thread, then 16 lanes) before the FP64 sums over
-// tiles and chunks, so the relative error is at most 130 * 2^-24 plus the
-// FP64 part.
+// rounding from its exact value; the bound kernels add terms of one sign in
+// FP32 along chains of at most 128 additions (k_bounds_fp32: 8 per thread,
+// 16 lanes, then up to 16 point tiles, depth 28; the few-candidate kernels:
+// 64 terms) before the FP64 sums, so the relative error is at most
+// 130 * 2^-24 plus the FP64 part.
 double fold_eta(int64_t chunk) {
     (void)chunk;
     return 131.0 * ldexp(1.0, -24) + 1e-12;
