@@ -292,7 +292,7 @@ __device__ __forceinline__ float twice_relu(uint32_t w) {
     return x + fabsf(x);
 }
 
-__device__ __forceinline__ void relu_acc32(ReluAcc &s, const uint32_t (&r)[32]) {
+__device__ __forceinline__ void relu_acc32(ReluAcc &s, const uint32_t *r) {
 #pragma unroll
     for (int i = 0; i < 32; i += 4) {
         const unsigned long long x = pack2(fmaxf(__uint_as_float(r[i]), 0.f), fmaxf(__uint_as_float(r[i + 1]), 0.f));
@@ -771,19 +771,14 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                     // all TBN / 2 columns into registers, then hand the region
                     // back to the MMA issuer before doing any arithmetic
                     if constexpr (TBN == 256) {
-                        uint32_t r0[32], r1[32], r2[32], r3[32];
-                        tc::tmem_ld32(taddr, r0);
-                        tc::tmem_ld32(taddr + 32, r1);
-                        tc::tmem_ld32(taddr + 64, r2);
-                        tc::tmem_ld32(taddr + 96, r3);
+                        uint32_t r[128];
+                        tc::tmem_ld128(taddr, r);
                         tc::tmem_ld_wait();
                         tc::tc_fence_before();
                         __syncwarp();
                         if (lane == 0) tc::mbar_arrive(&t_empty[rg]);
-                        relu_acc32(ra[h], r0);
-                        relu_acc32(ra[h], r1);
-                        relu_acc32(ra[h], r2);
-                        relu_acc32(ra[h], r3);
+#pragma unroll
+                        for (int l = 0; l < 4; ++l) relu_acc32(ra[h], r + 32 * l);
                     } else {
                         uint32_t r0[32], r1[32];
                         tc::tmem_ld32(taddr, r0);
@@ -1279,19 +1274,14 @@ __global__ void __launch_bounds__(NTHREADS_G, 1) k_gains_tc_group(const GroupArg
                     }
                     tc::tc_fence_after();
                     const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN + half * 128);
-                    uint32_t r0[32], r1[32], r2[32], r3[32];
-                    tc::tmem_ld32(taddr, r0);
-                    tc::tmem_ld32(taddr + 32, r1);
-                    tc::tmem_ld32(taddr + 64, r2);
-                    tc::tmem_ld32(taddr + 96, r3);
+                    uint32_t r[128];
+                    tc::tmem_ld128(taddr, r);
                     tc::tmem_ld_wait();
                     tc::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&t_empty[h]);
-                    relu_acc32(ra[h], r0);
-                    relu_acc32(ra[h], r1);
-                    relu_acc32(ra[h], r2);
-                    relu_acc32(ra[h], r3);
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) relu_acc32(ra[h], r + 32 * l);
                 }
                 // FP32 blocks of four tiles (chains of at most 128 terms), then FP64
                 if (ok && ((tt & 3) == 3 || tt == w.ntiles - 1)) {
