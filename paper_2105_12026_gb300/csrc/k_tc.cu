@@ -869,20 +869,14 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 if (!alive) continue;
                 tc::tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN);
-                uint32_t r[4][32];
+                uint32_t r[128];
                 float gm[16];
-                tc::tmem_ld32(taddr, r[0]);
-                tc::tmem_ld32(taddr + 32, r[1]);
-                tc::tmem_ld32(taddr + 64, r[2]);
-                tc::tmem_ld32(taddr + 96, r[3]);
+                tc::tmem_ld128(taddr, r);
                 tc::tmem_ld_wait();
 #pragma unroll
-                for (int gg = 0; gg < 8; ++gg) gm[gg] = max16(&r[gg >> 1][(gg & 1) * 16]);
+                for (int gg = 0; gg < 8; ++gg) gm[gg] = max16(&r[gg * 16]);
                 if (ngr > 8) {
-                    tc::tmem_ld32(taddr + 128, r[0]);
-                    tc::tmem_ld32(taddr + 160, r[1]);
-                    tc::tmem_ld32(taddr + 192, r[2]);
-                    tc::tmem_ld32(taddr + 224, r[3]);
+                    tc::tmem_ld128(taddr + 128, r);
                     tc::tmem_ld_wait();
                 }
                 tc::tc_fence_before();
@@ -890,7 +884,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 if (lane == 0) tc::mbar_arrive(&t_empty[h]);
                 if (ngr > 8) {
 #pragma unroll
-                    for (int gg = 0; gg < 8; ++gg) gm[8 + gg] = max16(&r[gg >> 1][(gg & 1) * 16]);
+                    for (int gg = 0; gg < 8; ++gg) gm[8 + gg] = max16(&r[gg * 16]);
                 }
                 // running maximum over the groups (reset after a set's last
                 // group); val[g] = the set's term where group g ends it
