@@ -36,16 +36,23 @@
 // caller accounts for.  Plain mode (sg = 0, w = 0, a rounded to nearest)
 // gives the raw low-precision gain.
 //
-// Warp roles (320 threads, one CTA per SM, persistent over work units):
+// Warp roles (352 threads, one CTA per SM, persistent over work units):
 //   warp 0      TMA producer: the 256-candidate tile (A, one or two buffers)
 //               and a ring of point tiles (B stages), each with its extension
-//   warp 1      TMEM allocator and single-thread MMA issuer: for every point
-//               tile, sub-tile 0 into region 0, then sub-tile 1 into region 1
+//   warp 1      TMEM allocator and MMA issuer of candidate sub-tile 0 (one
+//               thread): for every point tile, its MMAs into region 0
+//   warp 10     MMA issuer of sub-tile 1 (one thread), into region 1.  A
+//               tcgen05.mma holds its issuing thread for about its own
+//               execution time, so each issuer waits and commits while the
+//               other issues; with 256-byte rows they take turns (sub-tile 0
+//               of a tile, then sub-tile 1), so region 0 completes first
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, warps
-//               2-5 the first 128 columns of a region, 6-9 the rest; they
-//               drain region 0 while region 1 fills and vice versa
-// The two regions use all 512 TMEM columns; the tensor pipe never waits for
-// the epilogue as long as draining a region is faster than filling the other.
+//               2-5 the first 128 columns of a region, 6-9 the rest (one
+//               128-column load each); they drain region 0 while region 1
+//               fills and vice versa
+// The two regions use all 512 TMEM columns.  The multi-set kernel and the
+// K-blocked kernels use the same roles (the K-blocked multi-set kernel with
+// one issuer, 320 threads).
 //
 // Every wait is bounded (tc_ptx.cuh); on a timeout the CTA records
 // EBC_ETIMEOUT, stops issuing, waits (bounded) for its own TMA copies and
