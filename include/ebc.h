@@ -226,7 +226,8 @@ ebc_status ebc_set_lazy(ebc_t h, int32_t on);
 /*
  * Autotuner of the tensor-core bulk kernel.  The kernel's point-tile width
  * (256 or 128 points per MMA, i.e. the N of the 128 x N tile), at 256
- * points whether its two MMA-issuing threads take turns or issue freely,
+ * points whether its two MMA-issuing threads take turns or issue freely and
+ * whether its drain warps split the TMEM regions by columns or by region,
  * its pipeline shape (candidate-tile buffers x point-tile stages that fit
  * shared memory at that width) and its V-chunk policy (load-balance model,
  * twice or half as many chunks) are timed with CUDA events on this handle (reps timed
@@ -245,15 +246,17 @@ ebc_status ebc_autotune(ebc_t h, int32_t reps);
  * current precision: cfg[0] = points per tile (256 or 128), cfg[1] =
  * candidate-tile buffers, cfg[2] = point-tile stages, cfg[3] = chunk policy
  * (0, 1, 2), cfg[4] = issuer turns (1 on, 0 off, -1 by row width: on from
- * 256 bytes per row), and *ms (may be NULL) the time the autotuner measured
- * for it.  All zero when the bucket has no entry (the default shape is
- * used).  Host only; EINVAL for a NULL handle or cfg.
+ * 256 bytes per row), cfg[5] = drain split (0 by column halves, 1 by
+ * region), and *ms (may be NULL) the time the autotuner measured for it.
+ * All zero when the bucket has no entry (the default shape is used).  Host
+ * only; EINVAL for a NULL handle or cfg.
  */
-ebc_status ebc_tune_query(ebc_t h, int32_t cfg[5], double *ms);
+ebc_status ebc_tune_query(ebc_t h, int32_t cfg[6], double *ms);
 
 /* The tuning table: save as JSON, merge a saved file (EINVAL for an
  * unreadable or malformed file; the table is then unchanged; an entry
- * without "bn" means 256-point tiles, without "turns" turns by row width),
+ * without "bn" means 256-point tiles, without "turns" turns by row width, without "es" the drain split by
+ * column halves),
  * count and clear its entries. */
 ebc_status ebc_tune_save(const char *path);
 ebc_status ebc_tune_load(const char *path);

@@ -582,8 +582,10 @@ ebc_status ebc::autotune_handle(ebc_t h, int32_t reps, bool only_if_missing) {
     if (err == cudaSuccess) err = fp8 ? ebc::launch_prep_tc8(c, true) : ebc::launch_prep_tc(c, true);
     // every point-tile width x shape that fits shared memory x chunk
     // policy; the fastest of reps timed launches (after one untimed) counts
-    // (with issuer turns on or off at 256 points)
+    // (at 256 points also: issuer turns on or off, drain split by column
+    // halves or by region)
     for (int bn = 256; bn >= 128 && err == cudaSuccess; bn /= 2)
+    for (int es = 0; es <= (bn == 256 ? 1 : 0) && err == cudaSuccess; ++es)
     for (int turns = bn == 256 ? 1 : 0; turns >= 0 && err == cudaSuccess; --turns)
     for (int na = 1; na <= 2 && err == cudaSuccess; ++na)
         for (int ns = 2; ns <= 6 && err == cudaSuccess; ++ns) {
@@ -594,6 +596,7 @@ ebc_status ebc::autotune_handle(ebc_t h, int32_t reps, bool only_if_missing) {
                 cfg.chunk = chunk;
                 cfg.bn = bn;
                 cfg.turns = turns;
+                cfg.es = es;
                 c.tune_force = &cfg;
                 err = bulk();
                 double ms_min = INFINITY;
@@ -629,17 +632,18 @@ extern "C" {
 
 ebc_status ebc_autotune(ebc_t h, int32_t reps) { return ebc::autotune_handle(h, reps, false); }
 
-ebc_status ebc_tune_query(ebc_t h, int32_t cfg[5], double *ms) {
+ebc_status ebc_tune_query(ebc_t h, int32_t cfg[6], double *ms) {
     if (check_handle(h) || !cfg) return fail(h, EBC_EINVAL, "ebc_tune_query: NULL argument");
     ebc::TuneCfg t;
     double tms = 0.0;
-    cfg[0] = cfg[1] = cfg[2] = cfg[3] = cfg[4] = 0;
+    cfg[0] = cfg[1] = cfg[2] = cfg[3] = cfg[4] = cfg[5] = 0;
     if (h->c.prec != EBC_FP32 && ebc::tune_get((int)h->c.prec, ebc::tc_row_bytes(h->c), h->c.n, &t, &tms)) {
         cfg[0] = t.bn;
         cfg[1] = t.na;
         cfg[2] = t.ns;
         cfg[3] = t.chunk;
         cfg[4] = t.turns;
+        cfg[5] = t.es;
     } else {
         tms = 0.0;
     }

@@ -113,6 +113,7 @@ struct TuneCfg {
     int chunk = 0;  // V-chunk policy: 0 load-balance model, 1 twice the chunks, 2 half
     int bn = 256;   // points per B tile (TMEM columns per region): 256 or 128
     int turns = -1; // 256-point tiles: MMA issuers take turns (1), run freely (0), by row width (-1)
+    int es = 0;     // 256-point tiles: drain split by column halves (0) or by region (1)
 };
 
 // Scratch / resident buffers of one handle.

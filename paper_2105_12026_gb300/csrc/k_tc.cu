@@ -335,11 +335,12 @@ __device__ __forceinline__ float relu_fold(const ReluAcc &s) {
 // 512 TMEM columns hold two sets of the two sub-tile regions: tile t
 // accumulates into set t % 2, so the MMAs of a tile never wait for the
 // epilogue of the previous one.  The MMA sequence over K is the same.
-template <int MODE, bool F8, bool KB = false, int TBN = BN>
+template <int MODE, bool F8, bool KB = false, int TBN = BN, bool ES = false>
 __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUtensorMap *tmAx_p,
                                             const CUtensorMap *tmB_p, const CUtensorMap *tmBx_p, const TcArgs &args) {
     static_assert(!KB || !F8, "K-blocked layout: 16-bit operands only");
     static_assert(TBN == BN || (TBN == 128 && MODE == MODE_GAINS && !KB), "128-point tiles: resident gains only");
+    static_assert(!ES || (MODE == MODE_GAINS && TBN == BN), "region-split drain: 256-point gains only");
     // one MMA issuer per A sub-tile (warp 1 and the last warp), each waiting
     // and committing while the other issues: bulk gains (resident and
     // K-blocked) and the resident multi-set kernel (with turns)
@@ -402,7 +403,7 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
         for (int r = 0; r < NREG; ++r) {
             tc::mbar_init(&t_full[r], 1);
             // every epilogue warp drains every region in gains mode, half of them each in sets mode
-            tc::mbar_init(&t_empty[r], MODE == MODE_GAINS ? NEPI / 32 : NEPI / 64);
+            tc::mbar_init(&t_empty[r], (MODE == MODE_GAINS && !ES) ? NEPI / 32 : NEPI / 64);
             last_tfull[r] = -1;
         }
         tc::mbar_init(fin, DUAL ? 2 : 1);
@@ -739,6 +740,67 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
                 tc::mma_commit(&a_empty[ab]);
             }
         }
+    } else if constexpr (MODE == MODE_GAINS && ES) {
+        // ------------------------------------------------ region-split epilogue
+        // Warps 2-5 drain region 0 (sub-tile 0), warps 6-9 region 1; a thread
+        // owns one candidate row and all 256 columns of its region, read as
+        // two 128-column loads (the first half summed while the second
+        // loads), and hands the region back after the second load.  The two
+        // regions drain at the same time, which suits issuers that run freely
+        // (both regions complete together); no join of column halves.
+        const int ew = warp - 2;        // 0..7
+        const int q = warp & 3;         // TMEM lane quarter this warp may access
+        const int h = ew >> 2;          // region (candidate sub-tile)
+        const int row = q * 32 + lane;  // candidate row within the sub-tile
+        int t = 0;
+        bool alive = true;
+        constexpr int kBlk = 2;  // 64 terms per chain and tile: chains of at most 128 terms
+        for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+            int ct, ch, b_row0, nb;
+            unit_span<MODE, TBN>(args, P, u, ct, ch, b_row0, nb);
+            double acc = 0.0;
+            ReluAcc ra;
+            relu_zero(ra);
+            int inblk = 0;
+            for (int i = 0; i < nb; ++i, ++t) {
+                if (alive) {
+                    // the TMEM loads below are warp-collective: decide per warp
+                    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[h], t & 1, abort_flag, wait_ns));
+                    if (!ok) {
+                        if (lane == 0) record_timeout(args.err, abort_flag);
+                        alive = false;
+                    }
+                }
+                if (!alive) continue;
+                tc::tc_fence_after();
+                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * TBN);
+                uint32_t r[128];
+                tc::tmem_ld128(taddr, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int l = 0; l < 4; ++l) relu_acc32(ra, r + 32 * l);
+                tc::tmem_ld128(taddr + 128, r);
+                tc::tmem_ld_wait();
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&t_empty[h]);
+#pragma unroll
+                for (int l = 0; l < 4; ++l) relu_acc32(ra, r + 32 * l);
+                if (++inblk == kBlk || i == nb - 1) {
+                    acc += (double)relu_fold(ra);
+                    relu_zero(ra);
+                    inblk = 0;
+                }
+            }
+            if (alive) {
+                const int64_t j = (int64_t)ct * BM + h * BMS + row;
+                if (j < P.m) {
+                    double v = acc;
+                    if (F8) v *= (double)args.row_scale[j];  // a power of two: exact
+                    args.partial[(int64_t)ch * P.m + j] = v;
+                }
+            }
+        }
     } else if constexpr (MODE == MODE_GAINS) {
         // ------------------------------------------------------------ epilogue
         const int ew = warp - 2;        // 0..7
@@ -950,12 +1012,36 @@ __global__ void __launch_bounds__(NTHREADS_G, 1)
     tc_pipeline<MODE_GAINS, false>(&tmA, &tmAx, &tmB, &tmBx, args);
 }
 
+// Region-split drain (a variant the autotuner may choose).
+__global__ void __launch_bounds__(NTHREADS_G, 1)
+    k_gains_tc_es(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+                  const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
+    tc_pipeline<MODE_GAINS, false, false, BN, true>(&tmA, &tmAx, &tmB, &tmBx, args);
+}
+
+__global__ void __launch_bounds__(NTHREADS_G, 1)
+    k_gains_tc8_es(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+                   const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx,
+                   const TcArgs args) {
+    tc_pipeline<MODE_GAINS, true, false, BN, true>(&tmA, &tmAx, &tmB, &tmBx, args);
+}
+
 // 128-point B tiles (a tile shape the autotuner may choose).
 __global__ void __launch_bounds__(NTHREADS_G, 1)
     k_gains_tc_n128(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                     const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx,
                     const TcArgs args) {
     tc_pipeline<MODE_GAINS, false, false, 128>(&tmA, &tmAx, &tmB, &tmBx, args);
+}
+
+// The K-blocked kernel with the region-split drain: the resident kernel's
+// default for 128-byte rows, so a forced K-blocked launch there gives the
+// same sums.
+__global__ void __launch_bounds__(NTHREADS_G, 1)
+    k_gains_tc_kb_es(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
+                     const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx,
+                     const TcArgs args) {
+    tc_pipeline<MODE_GAINS, false, true, BN, true>(&tmA, &tmAx, &tmB, &tmBx, args);
 }
 
 // Candidate rows too long for the resident layout (d > 128 at 16 bits).
@@ -1989,14 +2075,24 @@ void pick_pipeline(int RB, int *na, int *ns) {
 }
 
 
+// Default issue and drain of the 256-point kernels by row width, as measured
+// (n = 20k to 400k, BF16 and FP8): 128-byte rows drain fastest split by
+// region with the issuers taking turns (7 % over column halves), longer rows
+// split by column halves with turns.
+void default_issue(int RB, int *turns, int *es) {
+    *turns = 1;
+    *es = RB <= 128 ? 1 : 0;
+}
+
 // Pipeline shape, point-tile width and chunk policy for a bulk launch: 256-
 // point tiles in the largest shape that fits shared memory, unless the
 // tuning table (or the autotuner) says otherwise.
-void choose_config(const Ctx &c, int prec, int RB, int *na, int *ns, int *chunk_mode, int *bn, int *turns) {
+void choose_config(const Ctx &c, int prec, int RB, int *na, int *ns, int *chunk_mode, int *bn, int *turns,
+                   int *es) {
     pick_pipeline(RB, na, ns);
     *chunk_mode = 0;
     *bn = BN;
-    *turns = RB >= 256 ? 1 : 0;  // measured: turns pay off from 256-byte rows
+    default_issue(RB, turns, es);
     TuneCfg t;
     if (tune_lookup(c, prec, RB, c.n, &t)) {
         const int tbn = t.bn == 128 ? 128 : BN;
@@ -2008,6 +2104,7 @@ void choose_config(const Ctx &c, int prec, int RB, int *na, int *ns, int *chunk_
         }
         *chunk_mode = t.chunk;
         if (t.turns == 0 || t.turns == 1) *turns = t.turns;
+        *es = (t.es == 1 && *bn == BN) ? 1 : 0;
     }
 }
 
@@ -2140,11 +2237,12 @@ cudaError_t launch_prep_tc8(Ctx &c, bool upper) {
 
 cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks_out) {
     Ctx::Tc8 &T = c.tc8;
-    int na = 0, ns = 0, chunk_mode = 0, bn = BN, turns = 0;
-    choose_config(c, EBC_FP8E4M3, T.DP, &na, &ns, &chunk_mode, &bn, &turns);
+    int na = 0, ns = 0, chunk_mode = 0, bn = BN, turns = 0, es = 0;
+    choose_config(c, EBC_FP8E4M3, T.DP, &na, &ns, &chunk_mode, &bn, &turns, &es);
     if (ns == 0) return cudaErrorInvalidConfiguration;
     const SmemLayout L = smem_layout(T.DP, ns, na, bn);
-    const void *kfn = bn == BN ? (const void *)k_gains_tc8 : (const void *)k_gains_tc8_n128;
+    const void *kfn = bn != BN ? (const void *)k_gains_tc8_n128
+                               : (es ? (const void *)k_gains_tc8_es : (const void *)k_gains_tc8);
     if (cudaError_t e = allow_smem(kfn, L.total); e != cudaSuccess) return e;
     if (cand) {
         const int64_t tot = m * (T.DP / 16 + 2);
@@ -2175,7 +2273,10 @@ cudaError_t launch_gains_tc8(Ctx &c, const int *cand, int64_t m, int *nchunks_ou
     a.partial_cap = c.partial_cap;
     a.G = G;
     const int units = a.n_ctiles * a.nchunks;
-    if (bn == BN)
+    if (bn == BN && es)
+        k_gains_tc8_es<<<std::min(units, G), NTHREADS_G, L.total, c.stream>>>(
+            cand ? T.tmA_C : T.tmA, cand ? T.tmAx_C : T.tmAx, T.tmB, T.tmBx, a);
+    else if (bn == BN)
         k_gains_tc8<<<std::min(units, G), NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA,
                                                                          cand ? T.tmAx_C : T.tmAx, T.tmB, T.tmBx, a);
     else
@@ -2261,12 +2362,16 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     Ctx::Tc &T = c.tc;
     const int DP = T.DP;
     const bool kb = use_kb(c, 2 * DP);
-    int na = 1, ns = KB_STAGES, chunk_mode = 0, bn = BN, turns = 0;
-    if (!kb) choose_config(c, T.prec, 2 * DP, &na, &ns, &chunk_mode, &bn, &turns);
+    int na = 1, ns = KB_STAGES, chunk_mode = 0, bn = BN, turns = 0, es = 0;
+    if (kb)
+        default_issue(2 * DP, &turns, &es);
+    else
+        choose_config(c, T.prec, 2 * DP, &na, &ns, &chunk_mode, &bn, &turns, &es);
     if (ns == 0) return cudaErrorInvalidConfiguration;
     const SmemLayout L = kb ? smem_layout_kb(ns) : smem_layout(2 * DP, ns, na, bn);
-    const void *kfn = kb ? (const void *)k_gains_tc_kb
-                         : (bn == BN ? (const void *)k_gains_tc : (const void *)k_gains_tc_n128);
+    const void *kfn = kb ? (es ? (const void *)k_gains_tc_kb_es : (const void *)k_gains_tc_kb)
+                         : (bn != BN ? (const void *)k_gains_tc_n128
+                                     : (es ? (const void *)k_gains_tc_es : (const void *)k_gains_tc));
     if (cudaError_t e = allow_smem(kfn, L.total); e != cudaSuccess) return e;
     if (cand) {
         int64_t tot = m * (DP / 8 + 2);
@@ -2306,8 +2411,14 @@ cudaError_t launch_gains_tc(Ctx &c, const int *cand, int64_t m, bool upper, int 
     a.err = &c.st->err;
     const int units = a.n_ctiles * a.nchunks;
     const int grid = std::min(units, G);
-    if (kb)
+    if (kb && es)
+        k_gains_tc_kb_es<<<grid, NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V,
+                                                                T.tmB_V, T.tmBx, a);
+    else if (kb)
         k_gains_tc_kb<<<grid, NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V,
+                                                             T.tmB_V, T.tmBx, a);
+    else if (bn == BN && es)
+        k_gains_tc_es<<<grid, NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V,
                                                              T.tmB_V, T.tmBx, a);
     else if (bn == BN)
         k_gains_tc<<<grid, NTHREADS_G, L.total, c.stream>>>(cand ? T.tmA_C : T.tmA_V, cand ? T.tmAx_C : T.tmAx_V, T.tmB_V,
@@ -2397,7 +2508,10 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     if (!kb) pick_pipeline(2 * DP, &na, &ns);
     if (ns == 0) return cudaErrorInvalidConfiguration;
     const SmemLayout L = kb ? smem_layout_kb(ns) : smem_layout(2 * DP, ns, na);
-    const void *kfn = kb ? (const void *)k_gains_tc_kb : (const void *)k_gains_tc;
+    int turns = 1, es = 0;
+    default_issue(2 * DP, &turns, &es);
+    const void *kfn = kb ? (es ? (const void *)k_gains_tc_kb_es : (const void *)k_gains_tc_kb)
+                         : (es ? (const void *)k_gains_tc_es : (const void *)k_gains_tc);
     if (cudaError_t e = allow_smem(kfn, L.total); e != cudaSuccess) return e;
     const int64_t tot = m_cap * (DP / 8 + 2);
     k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, c.stream>>>(T.Vq, T.Aext, cand, m_cap, m_dev, DP, T.Cq,
@@ -2417,7 +2531,7 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     a.row_scale = nullptr;
     a.nstages = ns;
     a.na = na;
-    a.turns = 2 * DP >= 256 ? 1 : 0;
+    a.turns = turns;
     a.idesc = tc::idesc_f16(T.prec == EBC_BF16 ? 1u : 0u, BMS, BN);
     a.idesc_ext = tc::idesc_f16(1u, BMS, BN);
     a.partial = c.partial;
@@ -2426,8 +2540,12 @@ cudaError_t launch_gains_tc_list(Ctx &c, const int *cand, const int *m_dev, int6
     a.partial_cap = c.partial_cap;
     a.G = G;
     a.nch_out = &c.st->list_nch;
-    if (kb)
+    if (kb && es)
+        k_gains_tc_kb_es<<<G, NTHREADS_G, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
+    else if (kb)
         k_gains_tc_kb<<<G, NTHREADS_G, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
+    else if (es)
+        k_gains_tc_es<<<G, NTHREADS_G, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
     else
         k_gains_tc<<<G, NTHREADS_G, L.total, c.stream>>>(T.tmA_C, T.tmAx_C, T.tmB_V, T.tmBx, a);
     return cudaGetLastError();

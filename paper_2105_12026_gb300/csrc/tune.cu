@@ -1,6 +1,6 @@
 // Tuning table of the tensor-core bulk kernel: for a (precision, row bytes,
 // n bucket) key, the point-tile width (256 or 128 points), whether the two
-// MMA issuers take turns, the pipeline shape (candidate-tile buffers,
+// MMA issuers take turns, how the drain is split, the pipeline shape (candidate-tile buffers,
 // point-tile stages) and the V-chunk policy found fastest by ebc_autotune
 // (api.cu).
 // Process-wide, guarded by a mutex; saved to and loaded from a small JSON
@@ -109,9 +109,9 @@ ebc_status ebc_tune_save(const char *path) {
         const auto &e = kv.second;
         fprintf(f,
                 "%s\n  {\"prec\": %d, \"rb\": %d, \"nbucket\": %d, \"na\": %d, \"ns\": %d, \"chunk\": %d, "
-                "\"bn\": %d, \"turns\": %d, \"ms\": %.6f}",
+                "\"bn\": %d, \"turns\": %d, \"es\": %d, \"ms\": %.6f}",
                 first ? "" : ",", std::get<0>(k), std::get<1>(k), std::get<2>(k), e.cfg.na, e.cfg.ns, e.cfg.chunk,
-                e.cfg.bn, e.cfg.turns, e.ms);
+                e.cfg.bn, e.cfg.turns, e.cfg.es, e.ms);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -149,15 +149,17 @@ ebc_status ebc_tune_load(const char *path) {
             const size_t colon = obj.find(':', p + key.size());
             return colon != std::string::npos && sscanf(obj.c_str() + colon + 1, "%lf", out) == 1;
         };
-        double prec, rb, nb, na, ns, chunk, bn = 256, turns = -1, ms = 0.0;
+        double prec, rb, nb, na, ns, chunk, bn = 256, turns = -1, es = 0, ms = 0.0;
         if (!field("prec", &prec) || !field("rb", &rb) || !field("nbucket", &nb) || !field("na", &na) ||
             !field("ns", &ns) || !field("chunk", &chunk))
             return EBC_EINVAL;
         field("ms", &ms);
         field("bn", &bn);        // absent: 256-point tiles
         field("turns", &turns);  // absent: by row width
+        field("es", &es);        // absent: drain split by column halves
         if (prec < 1 || prec > 3 || rb < 128 || rb > 512 || nb < 0 || nb > 62 || na < 1 || na > 2 || ns < 2 ||
-            ns > 6 || chunk < 0 || chunk > 2 || (bn != 256 && bn != 128) || turns < -1 || turns > 1)
+            ns > 6 || chunk < 0 || chunk > 2 || (bn != 256 && bn != 128) || turns < -1 || turns > 1 ||
+            (es != 0 && es != 1) || (es == 1 && bn != 256))
             return EBC_EINVAL;
         ebc::Entry e;
         e.cfg.na = (int)na;
@@ -165,6 +167,7 @@ ebc_status ebc_tune_load(const char *path) {
         e.cfg.chunk = (int)chunk;
         e.cfg.bn = (int)bn;
         e.cfg.turns = (int)turns;
+        e.cfg.es = (int)es;
         e.ms = ms;
         add[ebc::Key((int)prec, (int)rb, (int)nb)] = e;
         pos = b + 1;

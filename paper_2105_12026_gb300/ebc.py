@@ -434,14 +434,15 @@ class Instance:
 
     def tune_entry(self):
         """The tuning-table entry bulk launches of this instance use at its
-        current precision: dict(bn, na, ns, chunk, turns, ms), or None when
+        current precision: dict(bn, na, ns, chunk, turns, es, ms), or None when
         its bucket has none (the default 256-point shape)."""
-        cfg = (_I32 * 5)()
+        cfg = (_I32 * 6)()
         ms = ctypes.c_double()
         _raise(self.h, load().ebc_tune_query(_P(self.h), cfg, ctypes.byref(ms)))
         if cfg[0] == 0:
             return None
-        return {"bn": cfg[0], "na": cfg[1], "ns": cfg[2], "chunk": cfg[3], "turns": cfg[4], "ms": ms.value}
+        return {"bn": cfg[0], "na": cfg[1], "ns": cfg[2], "chunk": cfg[3], "turns": cfg[4], "es": cfg[5],
+                "ms": ms.value}
 
     def save_state(self) -> bytes:
         """Snapshot of the Greedy state (m_v, S, f, counters) as bytes."""

@@ -115,10 +115,12 @@ def test_tune_table_json_roundtrip(lib, tmp_path):
     assert '"rb": 256' in text and '"chunk": 1' in text
     assert text.count('"bn": 128') == 1 and text.count('"bn": 256') == 1  # absent width: 256
     assert text.count('"turns": -1') == 2  # absent: by row width
+    assert text.count('"es": 0') == 2  # absent: column halves
     for bad in ['{"entries": [{"prec": 1, "rb": 256}]}',
                 '{"entries": [{"prec": 9, "rb": 256, "nbucket": 3, "na": 1, "ns": 2, "chunk": 0}]}',
                 '{"entries": [{"prec": 1, "rb": 256, "nbucket": 3, "na": 1, "ns": 2, "chunk": 0, "bn": 64}]}',
                 '{"entries": [{"prec": 1, "rb": 256, "nbucket": 3, "na": 1, "ns": 2, "chunk": 0, "turns": 2}]}',
+                '{"entries": [{"prec": 1, "rb": 256, "nbucket": 3, "na": 1, "ns": 2, "chunk": 0, "bn": 128, "es": 1}]}',
                 'not json']:
         p = tmp_path / "bad.json"
         p.write_text(bad)

@@ -99,14 +99,17 @@ def _force_entry(tmp_path, prec, d, n, **cfg):
     ebc.ebc_tune_load(str(path))
 
 
-@pytest.mark.parametrize("prec,d,na,ns,chunk,bn,turns", [
-    ("bf16", 128, 1, 4, 0, 128, -1), ("bf16", 128, 2, 2, 1, 128, -1), ("fp16", 40, 2, 6, 0, 128, -1),
-    ("fp8", 128, 2, 6, 2, 128, -1), ("bf16", 64, 1, 3, 0, 128, -1),
-    ("bf16", 128, 1, 2, 0, 256, 0), ("bf16", 64, 2, 3, 0, 256, 1), ("fp8", 128, 2, 2, 1, 256, 1)])
-def test_tile_shapes_match_default(torch, prec, d, na, ns, chunk, bn, turns, tmp_path):
-    """A forced table entry: 128-point tiles give the default's raw gains up
-    to FP32 summation order; issuer turns on or off give them bitwise (each
-    region's MMA sequence is the same); picks and f are always bitwise."""
+@pytest.mark.parametrize("prec,d,na,ns,chunk,bn,turns,es", [
+    ("bf16", 128, 1, 4, 0, 128, -1, 0), ("bf16", 128, 2, 2, 1, 128, -1, 0), ("fp16", 40, 2, 6, 0, 128, -1, 0),
+    ("fp8", 128, 2, 6, 2, 128, -1, 0), ("bf16", 64, 1, 3, 0, 128, -1, 0),
+    ("bf16", 128, 1, 2, 0, 256, 0, 0), ("bf16", 64, 2, 3, 0, 256, 1, 0), ("fp8", 128, 2, 2, 1, 256, 1, 0),
+    ("bf16", 128, 1, 2, 0, 256, 1, 1), ("bf16", 64, 2, 3, 0, 256, 0, 1), ("fp8", 128, 2, 3, 0, 256, -1, 1),
+    ("fp16", 40, 1, 4, 2, 256, 0, 1)])
+def test_tile_shapes_match_default(torch, prec, d, na, ns, chunk, bn, turns, es, tmp_path):
+    """A forced table entry: 128-point tiles and the other drain split give
+    the default's raw gains up to FP32 summation order; issuer turns on or
+    off give them bitwise (each region's MMA sequence is the same); picks
+    and f are always bitwise."""
     n = 5037  # 20 tiles of 256 / 40 of 128 after padding, ragged tail
     V = gmm(n, d, 21)
     cand = np.random.default_rng(5).choice(n, 700, replace=False).astype(np.int32)
@@ -117,16 +120,18 @@ def test_tile_shapes_match_default(torch, prec, d, na, ns, chunk, bn, turns, tmp
             g0 = a.gains_host()
             l0 = a.gains_host(cand)
             i0, f0 = a.greedy_host(8)
-        _force_entry(tmp_path, prec, d, n, bn=bn, na=na, ns=ns, chunk=chunk, turns=turns)
+        _force_entry(tmp_path, prec, d, n, bn=bn, na=na, ns=ns, chunk=chunk, turns=turns, es=es)
         with ebc.Instance(V, precision=prec) as b:
-            assert b.tune_entry() == {"bn": bn, "na": na, "ns": ns, "chunk": chunk, "turns": turns, "ms": 0.0}
+            assert b.tune_entry() == {"bn": bn, "na": na, "ns": ns, "chunk": chunk, "turns": turns, "es": es,
+                                      "ms": 0.0}
             g1 = b.gains_host()
             l1 = b.gains_host(cand)
             i1, f1 = b.greedy_host(8)
             st = b.stats()
     finally:
         ebc.ebc_tune_clear()
-    if bn == 256 and chunk == 0:
+    default_es = 1 if _row_bytes(prec, d) <= 128 else 0  # the library's default drain split
+    if bn == 256 and chunk == 0 and es == default_es:
         np.testing.assert_array_equal(g1, g0)
         np.testing.assert_array_equal(l1, l0)
     else:
