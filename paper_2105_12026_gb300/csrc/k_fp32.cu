@@ -280,12 +280,21 @@ cudaError_t launch_gains_fp32(Ctx &c, const int *cand, int64_t m, bool upper, in
 // the 16 lanes of a candidate in FP32, then tiles in FP64: at most
 // 128 terms per FP32 sum.
 // ---------------------------------------------------------------------------
+// RES: rows of at most 128 dimensions; the candidate tile stays in shared
+// memory for a whole (tile, chunk) item instead of being staged again for
+// every point tile.  The pair arithmetic uses packed FP32x2 subtract and
+// FMA (each element rounded as the scalar instruction would), so the FMA
+// chain per pair over the dimensions in index order, and hence every bound,
+// is the same in both forms.
+constexpr int BF_DMAX = 128;
+
+template <bool RES>
 __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V, int64_t n, int d,
                                                      const double *__restrict__ m64, const int *__restrict__ list,
                                                      const int *__restrict__ count, int cap, int64_t chunk,
                                                      int nchunks, float kh, float kl, double *__restrict__ out_lo,
                                                      double *__restrict__ out_hi, int min_cnt) {
-    __shared__ __align__(16) float Cs[KC][TC];
+    __shared__ __align__(16) float Cs[RES ? BF_DMAX : KC][TC];
     __shared__ __align__(16) float Vs[KC][TV];
     __shared__ float MsU[TV], MsD[TV];
     __shared__ int Ci[TC];
@@ -305,6 +314,15 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
             const int e = ct * TC + tid;
             Ci[tid] = e < cnt ? list[e] : -1;
         }
+        if constexpr (RES) {
+            __syncthreads();
+            // the whole candidate tile, dimension-major, zero past d
+            for (int e = tid; e < TC * BF_DMAX; e += 256) {
+                const int r = e / BF_DMAX, k = e % BF_DMAX;
+                const int ci = Ci[r];
+                Cs[k][r] = (ci >= 0 && k < d) ? V[(int64_t)ci * d + k] : 0.f;
+            }
+        }
         double lod[4] = {0.0, 0.0, 0.0, 0.0}, hid[4] = {0.0, 0.0, 0.0, 0.0};
         // FP32 sums of blocks of up to 16 point tiles (depth <= 28, inside the
         // 131 * 2^-24 widening), then FP64: one FP64 add per block, not per tile
@@ -323,19 +341,22 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
                 MsU[tid] = mu;
                 MsD[tid] = md;
             }
-            float acc[4][8];
+            // acc[i][p]: candidate i against the point pair p (points 2p, 2p + 1 of the thread's 8)
+            unsigned long long acc[4][4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+                for (int p2 = 0; p2 < 4; ++p2) acc[i][p2] = 0ull;
             for (int k0 = 0; k0 < d; k0 += KC) {
                 __syncthreads();
+                if constexpr (!RES) {
 #pragma unroll
-                for (int s = 0; s < (TC * KC) / 256; ++s) {
-                    int e = tid + 256 * s;
-                    int r = e / KC, kk = e % KC;
-                    int ci = Ci[r];
-                    Cs[kk][r] = (ci >= 0 && k0 + kk < d) ? V[(int64_t)ci * d + k0 + kk] : 0.f;
+                    for (int s = 0; s < (TC * KC) / 256; ++s) {
+                        int e = tid + 256 * s;
+                        int r = e / KC, kk = e % KC;
+                        int ci = Ci[r];
+                        Cs[kk][r] = (ci >= 0 && k0 + kk < d) ? V[(int64_t)ci * d + k0 + kk] : 0.f;
+                    }
                 }
 #pragma unroll
                 for (int s = 0; s < (TV * KC) / 256; ++s) {
@@ -345,20 +366,23 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
                     Vs[kk][r] = (v < ve && k0 + kk < d) ? V[v * d + k0 + kk] : 0.f;
                 }
                 __syncthreads();
+                const int kc0 = RES ? k0 : 0;
 #pragma unroll
                 for (int kk = 0; kk < KC; ++kk) {
-                    float4 c4 = *reinterpret_cast<const float4 *>(&Cs[kk][ty * 4]);
-                    float4 va = *reinterpret_cast<const float4 *>(&Vs[kk][tx * 4]);
-                    float4 vb4 = *reinterpret_cast<const float4 *>(&Vs[kk][64 + tx * 4]);
-                    float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-                    float vv[8] = {va.x, va.y, va.z, va.w, vb4.x, vb4.y, vb4.z, vb4.w};
+                    const float4 c4 = *reinterpret_cast<const float4 *>(&Cs[kc0 + kk][ty * 4]);
+                    const ulonglong2 va = *reinterpret_cast<const ulonglong2 *>(&Vs[kk][tx * 4]);
+                    const ulonglong2 vb2 = *reinterpret_cast<const ulonglong2 *>(&Vs[kk][64 + tx * 4]);
+                    const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                    const unsigned long long vv[4] = {va.x, va.y, vb2.x, vb2.y};
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 4; ++i) {
+                        const unsigned long long c2 = f2_pack(cv[i], cv[i]);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            float df = vv[j] - cv[i];
-                            acc[i][j] = fmaf(df, df, acc[i][j]);
+                        for (int p2 = 0; p2 < 4; ++p2) {
+                            const unsigned long long df = f2_sub(vv[p2], c2);
+                            acc[i][p2] = f2_fma(df, df, acc[i][p2]);
                         }
+                    }
                 }
             }
             float mu[8], md[8];
@@ -371,11 +395,14 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
+                float a[8];
+#pragma unroll
+                for (int p2 = 0; p2 < 4; ++p2) f2_unpack(acc[i][p2], a[2 * p2], a[2 * p2 + 1]);
                 float sl = 0.f, sh = 0.f;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    sh += fmaxf(fmaf(-kh, acc[i][j], mu[j]), 0.f);
-                    sl += fmaxf(fmaf(-kl, acc[i][j], md[j]), 0.f);
+                    sh += fmaxf(fmaf(-kh, a[j], mu[j]), 0.f);
+                    sl += fmaxf(fmaf(-kl, a[j], md[j]), 0.f);
                 }
                 sh += __shfl_xor_sync(0xffffffffu, sh, 1);
                 sh += __shfl_xor_sync(0xffffffffu, sh, 2);
@@ -413,8 +440,12 @@ __global__ void __launch_bounds__(256) k_bounds_fp32(const float *__restrict__ V
 
 cudaError_t launch_bounds_fp32(Ctx &c, const int *list, const int *count, int cap, double *out_lo, double *out_hi,
                                int64_t chunk, int nchunks, float kh, float kl, int min_cnt) {
-    k_bounds_fp32<<<c.num_sms * 4, 256, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk, nchunks, kh,
-                                                       kl, out_lo, out_hi, min_cnt);
+    if (c.d <= BF_DMAX)
+        k_bounds_fp32<true><<<c.num_sms * 4, 256, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk,
+                                                                 nchunks, kh, kl, out_lo, out_hi, min_cnt);
+    else
+        k_bounds_fp32<false><<<c.num_sms * 4, 256, 0, c.stream>>>(c.V32, c.n, c.d, c.m64, list, count, cap, chunk,
+                                                                  nchunks, kh, kl, out_lo, out_hi, min_cnt);
     return cudaGetLastError();
 }
 
