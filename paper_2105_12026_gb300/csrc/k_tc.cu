@@ -51,8 +51,7 @@
 //               128-column load each); they drain region 0 while region 1
 //               fills and vice versa
 // The two regions use all 512 TMEM columns.  The multi-set kernel and the
-// K-blocked kernels use the same roles (the K-blocked multi-set kernel with
-// one issuer, 320 threads).
+// K-blocked kernels use the same roles.
 //
 // Every wait is bounded (tc_ptx.cuh); on a timeout the CTA records
 // EBC_ETIMEOUT, stops issuing, waits (bounded) for its own TMA copies and
@@ -81,8 +80,7 @@ constexpr int BN = 256;          // points per tile (TMEM columns per region)
 constexpr int NPAD = 256;        // row padding of the quantised arrays
 constexpr int KATOM = 64;        // 16-bit elements per 128-byte swizzle atom
 constexpr int KEXT = 16;         // extension columns (one MMA K step)
-constexpr int NTHREADS = 320;
-constexpr int NTHREADS_G = 352;  // bulk gains and resident multi-set: a second MMA issuer warp
+constexpr int NTHREADS_G = 352;  // producer, two MMA issuers, eight epilogue warps
 constexpr int NEPI = 256;        // epilogue threads
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -342,9 +340,8 @@ __device__ __forceinline__ void tc_pipeline(const CUtensorMap *tmA_p, const CUte
     static_assert(TBN == BN || (TBN == 128 && MODE == MODE_GAINS && !KB), "128-point tiles: resident gains only");
     static_assert(!ES || (MODE == MODE_GAINS && TBN == BN), "region-split drain: 256-point gains only");
     // one MMA issuer per A sub-tile (warp 1 and the last warp), each waiting
-    // and committing while the other issues: bulk gains (resident and
-    // K-blocked) and the resident multi-set kernel (with turns)
-    constexpr bool DUAL = MODE == MODE_GAINS || !KB;
+    // and committing while the other issues (every variant)
+    constexpr bool DUAL = true;
     constexpr int NREG = TBN == 128 ? 4 : 2;  // TMEM regions
     // with two regions the issuers may take turns (sub-tile 0 of a tile, then
     // sub-tile 1, then sub-tile 0 of the next), so region 0 completes half a
@@ -1073,7 +1070,7 @@ __global__ void __launch_bounds__(NTHREADS_G, 1)
 }
 
 // Multi-set evaluation with point and member rows streamed in K blocks (d > 128).
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS_G, 1)
     k_sets_tc_kb(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAx,
                  const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBx, const TcArgs args) {
     tc_pipeline<MODE_SETS, false, true>(&tmA, &tmAx, &tmB, &tmBx, args);
@@ -2672,7 +2669,7 @@ cudaError_t launch_eval_sets_tc(Ctx &c, const int32_t *idx, const int64_t *off, 
         // empty sets get no partial from any warp
         if ((e = cudaMemsetAsync(c.set_part, 0, sizeof(double) * rows * lb, c.stream)) != cudaSuccess) return e;
         if (kb)
-            k_sets_tc_kb<<<G, NTHREADS, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
+            k_sets_tc_kb<<<G, NTHREADS_G, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
         else
             k_sets_tc<<<G, NTHREADS_G, L.total, c.stream>>>(T.tmA_V, T.tmPx, tmM, tmMx, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
